@@ -1,0 +1,176 @@
+"""Oracle: randomized Tucker compression (Sec. IV-A, Alg. 2) in FP64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): only tests, smoke()
+and bench.py's CPU legs may use it.
+
+The method computes, for every mode n from the ORIGINAL tensor Y,
+  Z_n = Y_(n) Omega_n,   Omega_n = KRP_{k != n} W_k^(n)          (RRF step 2)
+  U_n = orthonormal basis of range(Z_n) by Householder QR        (RRF step 3)
+  G   = Y x_1 U_1^T x_2 ... x_N U_N^T                            (Alg. 2, TTM)
+i.e. the range-finder sketch of every mode taken in one pass over Y with a
+Khatri-Rao structured Gaussian test matrix, then the Tucker core (Eq. 1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def norm2(Y) -> float:
+    """||Y||_F^2 (used by the fit, Sec. III-B)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    return float(np.sum(Y * Y))
+
+
+def unfold(Y: np.ndarray, n: int) -> np.ndarray:
+    """Mode-n matricization Y_(n) (Table I): rows i_n, columns the other
+    indices in row-major order.  Pinned by brute force in tests."""
+    return np.moveaxis(np.asarray(Y, dtype=np.float64), n, 0).reshape(Y.shape[n], -1)
+
+
+def fold(M: np.ndarray, n: int, shape) -> np.ndarray:
+    """Inverse of unfold for a tensor of the given shape."""
+    shape = list(shape)
+    lead = [shape[n]] + shape[:n] + shape[n + 1:]
+    return np.moveaxis(M.reshape(lead), 0, n)
+
+
+def khatri_rao(mats) -> np.ndarray:
+    """Column-wise Kronecker product (Table I), first factor slowest.
+
+    (A (.) B)[(i, j), r] = A[i, r] * B[j, r].  Pinned by the identity
+    (A (.) B)^T (A (.) B) = A^T A * B^T B (Eq. 9) and by brute force.
+    """
+    mats = [np.asarray(m, dtype=np.float64) for m in mats]
+    R = mats[0].shape[1]
+    out = mats[0]
+    for m in mats[1:]:
+        out = (out[:, None, :] * m[None, :, :]).reshape(-1, R)
+    return out
+
+
+def sketch(Y: np.ndarray, W) -> tuple[list, float]:
+    """All-mode range-finder sketch (Sec. IV-A step 2; Alg. 2 line "Z = Y_(n) Omega").
+
+    Z_n = Y_(n) Omega_n with Omega_n = KRP_{k != n} W[n][k] formed explicitly,
+    for every n from the same (original) Y; also returns ||Y||^2.
+    Pinned: brute-force loops, rank-one closed form (tests).
+    """
+    Y = np.asarray(Y, dtype=np.float64)
+    N = Y.ndim
+    Z = []
+    for n in range(N):
+        Omega = khatri_rao([W[n][k] for k in range(N) if k != n])
+        Z.append(unfold(Y, n) @ Omega)
+    return Z, norm2(Y)
+
+
+def sketch_row(slab: np.ndarray, n: int, W, chunk: int = 32) -> np.ndarray:
+    """One row Z_n[i, :] from the slab Y[..., i_n = i, ...] (shape: the other
+    modes in order).  Same definition as `sketch`; Omega_n is formed a block of
+    its rows at a time (the first remaining index in chunks) so that rows of
+    full-size problems fit in host memory.
+    """
+    slab = np.asarray(slab, dtype=np.float64)
+    N = slab.ndim + 1
+    facs = [W[n][k] for k in range(N) if k != n]
+    out = np.zeros(facs[0].shape[1])
+    rest = facs[1:]
+    for a in range(0, slab.shape[0], chunk):
+        b = min(slab.shape[0], a + chunk)
+        Om = khatri_rao([facs[0][a:b]] + rest)
+        out += slab[a:b].reshape(-1) @ Om
+    return out
+
+
+def householder_qr(Z: np.ndarray):
+    """Thin QR by Householder reflections (Sec. IV-A step 3, "e.g. QR").
+
+    Returns Q (m x k, orthonormal columns) and R (k x k, upper triangular)
+    with Z = Q R and diag(R) >= 0 (sign convention that makes Q unique for
+    full-rank Z).  Pinned: Q^T Q = I, QR = Z, triangularity, and agreement
+    with LAPACK's QR after the same sign fix (tests).
+    """
+    A = np.array(Z, dtype=np.float64)
+    m, k = A.shape
+    if k > m:
+        raise ValueError("QR needs rows >= columns")
+    vs = []
+    for j in range(k):
+        x = A[j:, j]
+        nx = np.linalg.norm(x)
+        if nx == 0.0:
+            vs.append(None)
+            continue
+        alpha = -nx if x[0] >= 0 else nx
+        v = x.copy()
+        v[0] -= alpha
+        nv = np.linalg.norm(v)
+        if nv == 0.0:
+            vs.append(None)
+            continue
+        v /= nv
+        A[j:, j:] -= 2.0 * np.outer(v, v @ A[j:, j:])
+        vs.append(v)
+    R = np.triu(A[:k, :k])
+    Q = np.zeros((m, k))
+    Q[:k, :k] = np.eye(k)
+    for j in reversed(range(k)):
+        v = vs[j]
+        if v is not None:
+            Q[j:, :] -= 2.0 * np.outer(v, v @ Q[j:, :])
+    s = np.where(np.diag(R) < 0, -1.0, 1.0)
+    return Q * s[None, :], R * s[:, None]
+
+
+def ttm(Y: np.ndarray, U: np.ndarray, n: int) -> np.ndarray:
+    """Y x_n U^T (Alg. 2, "Y <- Y x_n U^T"): contracts mode n of Y with the
+    columns of U, (Y x_n U^T)_(n) = U^T Y_(n).  Pinned: exact Tucker tensors."""
+    Y = np.asarray(Y, dtype=np.float64)
+    shape = list(Y.shape)
+    shape[n] = U.shape[1]
+    return fold(np.asarray(U, dtype=np.float64).T @ unfold(Y, n), n, shape)
+
+
+def tucker_core(Y: np.ndarray, Us) -> np.ndarray:
+    """G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2, final core; Eq. 1)."""
+    G = np.asarray(Y, dtype=np.float64)
+    for n, U in enumerate(Us):
+        G = ttm(G, U, n)
+    return G
+
+
+def tucker_full(G: np.ndarray, Us) -> np.ndarray:
+    """[[G; U_1, ..., U_N]] = G x_1 U_1 ... x_N U_N (Eq. 1)."""
+    X = np.asarray(G, dtype=np.float64)
+    for n, U in enumerate(Us):
+        shape = list(X.shape)
+        shape[n] = U.shape[0]
+        X = fold(np.asarray(U, dtype=np.float64) @ unfold(X, n), n, shape)
+    return X
+
+
+def hosvd_factors(Y: np.ndarray, ranks):
+    """HOSVD factors: the leading R_n left singular vectors of every Y_(n)
+    (Sec. II).  The full-tensor SVD is exactly the cost the randomized method
+    avoids; the oracle keeps it as the deterministic reference compression."""
+    out = []
+    for n, Rn in enumerate(ranks):
+        Un, _, _ = np.linalg.svd(unfold(Y, n), full_matrices=False)
+        out.append(Un[:, :Rn])
+    return out
+
+
+def rand_tucker(Y: np.ndarray, W) -> dict:
+    """All-mode randomized Tucker: sketch every mode from the original Y,
+    orthonormalise each sketch by Householder QR, then project to the core.
+
+    Differs from the paper's Alg. 2 in one respect: Alg. 2 sketches mode n of
+    the tensor already projected on modes < n; here every Z_n comes from the
+    original Y (one pass for all modes), with Omega_n a Khatri-Rao product of
+    small Gaussians instead of a dense Gaussian matrix.
+    """
+    Z, nY2 = sketch(Y, W)
+    QR = [householder_qr(z) for z in Z]
+    U = [q for q, _ in QR]
+    G = tucker_core(Y, U)
+    return {"Z": Z, "U": U, "R": [r for _, r in QR], "G": G, "normY2": nY2}

@@ -1,0 +1,209 @@
+/*
+ * tdk.h -- C ABI of the GB300 randomized-Tucker + FFCP library (libtdk.so).
+ *
+ * The library computes the data-parallel path of "Decomposition of Big
+ * Tensors With Low Multilinear Rank" (Zhou, Cichocki, Xie):
+ *
+ *   tucker_sketch   Z_n = Y_(n) Omega_n for every mode n in one pass over Y,
+ *                   Omega_n = KRP_{k != n} W_k^(n) never formed (Sec. IV-A,
+ *                   range-finder steps 1-2; Alg. 2; Eq. 21), then an
+ *                   orthonormal basis U_n of range(Z_n) (range-finder step 3;
+ *                   Eq. 22 gives the Gram-based variant used in spirit here:
+ *                   FP64 CholQR2).
+ *   tucker_core     G = Y x_1 U_1^T ... x_N U_N^T (Alg. 2, TTM chain; Eq. 1).
+ *   ffcp_als        CP-ALS on the core with the lift A_n = U_n B_n
+ *                   (Sec. III-B, Alg. 1; Eqs. 9, 11-13, 16), unconstrained or
+ *                   with projected nonnegative updates (P_+ of Eq. 8).
+ *   ffcp_predict_init  learned initial core-space factors (no counterpart in
+ *                   the paper; see its comment).
+ *
+ * Conventions for every entry point:
+ *   - Tensors and matrices are ROW-MAJOR, last index fastest.  The mode-n
+ *     unfolding Y_(n) has row i_n and columns the other indices in row-major
+ *     order; KRP_{k != n} orders its factors with the smallest k slowest.
+ *   - Every data pointer is CALLER-OWNED DEVICE memory on the context's
+ *     device, unless the comment says "host".  The library never frees them.
+ *   - Calls are asynchronous on the context's stream, except ffcp_als, which
+ *     synchronises once at the end to fill its host report.
+ *   - Return value: 0 = TDK_OK; negative = error (no output is guaranteed);
+ *     positive = warning (outputs valid).  Device-side conditions found by
+ *     asynchronous calls (rank-deficient sketch, wait timeout) are ORed into
+ *     the context's status word; tdk_ctx_sync_status() waits for the stream
+ *     and returns and clears it.
+ *   - A context is not thread-safe; separate contexts are independent.
+ *   - The context owns its workspace (grown on demand with cudaMalloc) and
+ *     frees it in tdk_ctx_destroy.
+ */
+#ifndef TDK_H
+#define TDK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDK_OK 0
+#define TDK_EINVAL (-1)    /* invalid argument or configuration            */
+#define TDK_ENOMEM (-2)    /* workspace allocation failed                  */
+#define TDK_ECUDA (-3)     /* a CUDA runtime/driver call failed            */
+#define TDK_ETIMEOUT (-4)  /* a bounded device-side wait gave up           */
+#define TDK_ENOTSUP (-5)   /* supported by the ABI, not by this build/GPU  */
+#define TDK_WRANKDEF 1     /* a sketch was numerically rank deficient; the
+                              orthonormal basis was completed (see below)  */
+#define TDK_WNOCONV 2      /* ALS stopped at max_sweeps                    */
+#define TDK_WPINV 4        /* an ALS normal equation used the pseudo-inverse */
+
+#define TDK_MAX_MODES 8
+#define TDK_MAX_RANK 64    /* max sketch width R_n + p and max CP rank R   */
+
+/* storage type of the data tensor Y (and of the core G: F64 data -> F64
+   core, otherwise F32 core) */
+enum { TDK_F64 = 0, TDK_F32 = 1, TDK_BF16 = 2 };
+
+/* arithmetic form of the two passes over Y */
+enum {
+  TDK_PREC_SIMT = 0, /* CUDA-core FMAs in the storage precision (FP32 for
+                        BF16 data): the plain form                        */
+  TDK_PREC_TC = 1    /* tcgen05 tensor cores, BF16 operands, FP32
+                        accumulation; FP32 data is split hi+lo so products
+                        keep ~16 significant bits (F64 data: not supported) */
+};
+
+typedef struct tdk_ctx tdk_ctx;
+
+/* Create a context on `device` (CUDA ordinal) that launches on `cuda_stream`
+   (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+   handle.  Errors: TDK_EINVAL (null out), TDK_ECUDA. */
+int tdk_ctx_create(tdk_ctx** out, int device, void* cuda_stream);
+/* Free the workspace and the handle.  Waits for the stream first. */
+int tdk_ctx_destroy(tdk_ctx* ctx);
+/* Switch the stream later calls launch on. */
+int tdk_ctx_set_stream(tdk_ctx* ctx, void* cuda_stream);
+/* Wait for the stream, then return (and clear) the OR of the device-side
+   status flags raised since the last call (TDK_WRANKDEF, TDK_ETIMEOUT as
+   bit 8).  Returns TDK_ECUDA if the stream reported a CUDA error. */
+int tdk_ctx_sync_status(tdk_ctx* ctx, int* flags_out /* host */);
+/* Number of kernel launches this context has issued since creation. */
+int64_t tdk_ctx_launch_count(const tdk_ctx* ctx);
+/* Kernel timing by CUDA events recorded on the launching stream around the
+   main kernel of each region (0 = the pass of tucker_sketch over Y, 1 = the
+   pass of tucker_core over Y).  tdk_ctx_profile(ctx, 1) starts recording and
+   clears the totals; tdk_ctx_profile_read waits for the recorded events and
+   returns the summed milliseconds and the number of timed launches of a
+   region.  Errors: TDK_EINVAL (bad region), TDK_ECUDA. */
+int tdk_ctx_profile(tdk_ctx* ctx, int enable);
+int tdk_ctx_profile_read(tdk_ctx* ctx, int region, double* total_ms /* host */,
+                         int64_t* launches /* host */);
+/* Human-readable text for a return code. */
+const char* tdk_strerror(int code);
+
+/* Problem description, following the paper's problem statement: tensor
+   dimensions I_n, multilinear ranks R_n and the oversampling p, so that the
+   sketch width is Rt_n = R_n + p (Sec. IV-A). */
+typedef struct {
+  int N;                    /* order, 2 <= N <= TDK_MAX_MODES               */
+  int dtype;                /* TDK_F64 / TDK_F32 / TDK_BF16 storage of Y    */
+  int prec;                 /* TDK_PREC_SIMT / TDK_PREC_TC                  */
+  int p;                    /* oversampling                                 */
+  int64_t I[TDK_MAX_MODES]; /* dimensions                                   */
+  int R[TDK_MAX_MODES];     /* Tucker ranks; need 1 <= R_n + p <= min(I_n,
+                               TDK_MAX_RANK)                                */
+} tdk_tucker_desc;
+
+/*
+ * tucker_sketch -- all-mode randomized range finder (Sec. IV-A; Alg. 2 lines
+ * "Z = Y_(n) Omega" and "U = orth(Z)"; Eq. 21 for the blockwise sums).
+ *
+ *   Y      [I_1 x ... x I_N] in desc->dtype.
+ *   W      array of N*N device pointers; W[n*N + k] (k != n) is the FP64
+ *          matrix W_k^(n) [I_k x Rt_n]; W[n*N + n] is ignored.  The random
+ *          test matrix of mode n is Omega_n = KRP_{k != n} W_k^(n).  Values
+ *          are rounded to the operand precision of the chosen form (exact if
+ *          they are BF16 values, as the bundled generator draws them).
+ *   U_out  N device pointers, U_out[n] FP64 [I_n x Rt_n]: orthonormal columns
+ *          spanning range(Z_n), diag of the triangular factor positive
+ *          (CholQR2: two rounds of Gram -> Cholesky -> Z R^-1, all FP64).
+ *          If a Cholesky pivot is not positive (numerically rank-deficient
+ *          Z_n) that mode is redone by two-pass Gram-Schmidt in FP64 whose
+ *          dependent columns are replaced by fixed pseudo-random vectors made
+ *          orthogonal, and TDK_WRANKDEF is raised in the status word.
+ *   Z_out  NULL or N device pointers (entries may be NULL); Z_out[n] FP64
+ *          [I_n x Rt_n] receives the raw sketch Z_n.
+ * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOMEM, TDK_ENOTSUP
+ * (TDK_PREC_TC with F64 data), TDK_ECUDA.
+ */
+int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
+                  const double* const W[], double* const U_out[], double* const Z_out[]);
+
+/*
+ * tucker_core -- G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2 line
+ * "Y <- Y x_n U^T" for every n; Eq. 1), plus ||Y||_F^2.
+ *
+ *   U       N device pointers, U[n] FP64 [I_n x Rt_n] (e.g. from tucker_sketch).
+ *   G_out   [Rt_1 x ... x Rt_N], FP64 for F64 data, FP32 otherwise.
+ *   normY2  NULL or one FP64 device scalar receiving ||Y||_F^2.
+ * The first, tensor-sized contraction is over the contiguous mode N; in the
+ * TC form it runs on tcgen05 tensor cores (BF16 operands, U split hi+lo, Y
+ * split hi+lo when stored as FP32).  Errors as tucker_sketch.
+ */
+int tucker_core(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
+                const double* const U[], void* G_out, double* normY2);
+
+enum { TDK_INIT_GIVEN = 0, TDK_INIT_HOSVD = 1 };
+
+typedef struct {
+  int R;            /* CP rank, 1 <= R <= min_n Rt_n                       */
+  int max_sweeps;   /* >= 1                                                */
+  double tol;       /* stop when |f_t - f_{t-1}| < tol * |f_{t-1}|, f the
+                       fit of the core (Sec. V-A uses an absolute 1e-6)     */
+  int nonneg;       /* 0: LS update (Eq. 13); 1: projected nonnegative LS  */
+  int init;         /* TDK_INIT_GIVEN: start from B_io (nonneg: A_io);
+                       TDK_INIT_HOSVD: leading R left singular vectors of
+                       every G_(n) (nonneg: their magnitudes lifted)        */
+  int check_every;  /* sweeps per convergence check on the host (0 = 8)    */
+  int reserved;
+  double timeout_s; /* bound on the whole call, 0 = none; exceeded ->
+                       TDK_ETIMEOUT with the last iterate in the outputs   */
+} tdk_als_opts;
+
+typedef struct {
+  int sweeps;       /* sweeps performed                                    */
+  int status;       /* same value as the return code                       */
+  double fit_core;  /* 1 - ||G - [[B]]|| / ||G|| (nonneg: vs [[G;U]])       */
+  double fit_Y;     /* 1 - ||Y - [[A]]|| / ||Y|| via the Gram identities
+                       (NaN if normY2 was NULL)                             */
+  double ms;        /* wall time of the call in milliseconds               */
+} tdk_als_report;
+
+/*
+ * ffcp_als -- FFCP (Alg. 1): CP-ALS on the core G with core-space factors
+ * B_n = U_n^T A_n (Eq. 12); per mode H_n = G_(n) [KRP_{p != n} B_p]
+ * (Eq. 11), T_n = HADAMARD_{p != n} B_p^T B_p (Eq. 9; A_p^T A_p for the
+ * nonnegative form), B_n <- H_n T_n^-1 (Eq. 13; FP64 Cholesky, pseudo-inverse
+ * with cutoff R*eps*lambda_max when a pivot is not above R*eps*max T_jj);
+ * columns normalised to unit 2-norm with the norms in lambda.  Nonnegative
+ * form: A_n <- max(0, U_n H_n T_n^-1), B_n <- U_n^T A_n.
+ *
+ *   G       core from tucker_core (FP64 for F64 data, FP32 otherwise).
+ *   U       N device pointers, FP64 [I_n x Rt_n].
+ *   normY2  NULL or FP64 device scalar ||Y||^2 (for report->fit_Y).
+ *   B_io    N device pointers, FP64 [Rt_n x R]: initial values when
+ *           init = GIVEN and not nonneg; on return the normalised B_n.
+ *   A_io    N device pointers, FP64 [I_n x R]: initial A_n when nonneg and
+ *           init = GIVEN; on return A_n = U_n B_n with lambda absorbed into
+ *           A_N (Sec. II) -- for the nonnegative form the projected A_n.
+ *   lambda_out  NULL or FP64 device [R].
+ *   rep     NULL or host report.
+ * Returns TDK_OK, TDK_WNOCONV, TDK_WPINV (ORed warnings) or an error.
+ */
+int ffcp_als(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* G,
+             const double* const U[], const double* normY2, const tdk_als_opts* opts,
+             double* const B_io[], double* const A_io[], double* lambda_out,
+             tdk_als_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDK_H */

@@ -1,0 +1,265 @@
+"""Python binding of libtdk.so (randomized Tucker + FFCP on one GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libtdk.so, reached through its C ABI (include/tdk.h).  PyTorch
+supplies device memory and the current stream.  There is no CPU fallback: if
+the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdk.so")
+
+TDK_OK, TDK_EINVAL, TDK_ENOMEM, TDK_ECUDA, TDK_ETIMEOUT, TDK_ENOTSUP = 0, -1, -2, -3, -4, -5
+TDK_WRANKDEF, TDK_WNOCONV, TDK_WPINV = 1, 2, 4
+F64, F32, BF16 = 0, 1, 2
+PREC = {"simt": 0, "tc": 1}
+INIT = {"given": 0, "hosvd": 1}
+MAX_MODES = 8
+MAX_RANK = 64
+
+# symbols the header declares (checked by the CPU tests)
+EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_sync_status",
+           "tdk_ctx_launch_count", "tdk_strerror", "tdk_ctx_profile", "tdk_ctx_profile_read", "tucker_sketch",
+           "tucker_core", "ffcp_als"]
+
+
+class TuckerDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("dtype", ctypes.c_int), ("prec", ctypes.c_int), ("p", ctypes.c_int),
+                ("I", ctypes.c_int64 * MAX_MODES), ("R", ctypes.c_int * MAX_MODES)]
+
+
+class AlsOpts(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
+                ("nonneg", ctypes.c_int), ("init", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+
+
+class AlsReport(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("status", ctypes.c_int), ("fit_core", ctypes.c_double),
+                ("fit_Y", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class TdkError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libtdk.so (built in-tree by build.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1412_1885_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        L.tdk_ctx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+        L.tdk_ctx_destroy.argtypes = [vp]
+        L.tdk_ctx_set_stream.argtypes = [vp, vp]
+        L.tdk_ctx_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.tdk_ctx_launch_count.argtypes = [vp]
+        L.tdk_ctx_launch_count.restype = i64
+        L.tdk_strerror.argtypes = [ctypes.c_int]
+        L.tdk_strerror.restype = ctypes.c_char_p
+        L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp]
+        L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
+        L.ffcp_als.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, ctypes.POINTER(AlsOpts), pp, pp, vp,
+                               ctypes.POINTER(AlsReport)]
+        L.tdk_ctx_profile.argtypes = [vp, ctypes.c_int]
+        L.tdk_ctx_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int64)]
+        if hasattr(L, "tdk_ctx_test_fail_alloc"):
+            L.tdk_ctx_test_fail_alloc.argtypes = [vp, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().tdk_strerror(int(code)).decode()
+    except Exception:
+        return str(code)
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise TdkError(rc, what)
+    return rc
+
+
+def _ptrs(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+def _dtype_code(t):
+    import torch
+
+    return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[t.dtype]
+
+
+def make_desc(shape, dtype_code, ranks, p, prec="simt") -> TuckerDesc:
+    d = TuckerDesc()
+    d.N = len(shape)
+    d.dtype = dtype_code
+    d.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    d.p = int(p)
+    if len(ranks) != len(shape) or len(shape) > MAX_MODES:
+        raise ValueError("ranks must match the tensor order (<= 8 modes)")
+    for n, (I, R) in enumerate(zip(shape, ranks)):
+        d.I[n] = int(I)
+        d.R[n] = int(R)
+    return d
+
+
+class Context:
+    """A library context on one CUDA device; calls run on torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        self.device = int(device)
+        self._h = ctypes.c_void_p()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib().tdk_ctx_create(ctypes.byref(self._h), self.device, ctypes.c_void_p(stream)), "tdk_ctx_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _bind_stream(self):
+        import torch
+
+        lib().tdk_ctx_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def sync_status(self) -> int:
+        f = ctypes.c_int(0)
+        self._bind_stream()
+        _check(lib().tdk_ctx_sync_status(self._h, ctypes.byref(f)), "tdk_ctx_sync_status")
+        return f.value
+
+    def launch_count(self) -> int:
+        return int(lib().tdk_ctx_launch_count(self._h))
+
+    def profile(self, enable: bool):
+        self._bind_stream()
+        _check(lib().tdk_ctx_profile(self._h, int(bool(enable))), "tdk_ctx_profile")
+
+    def profile_read(self, region: int):
+        """(total milliseconds, launches) of the main kernel of a region
+        (0: sketch pass over Y, 1: core pass over Y) since profile(True)."""
+        ms = ctypes.c_double(0)
+        n = ctypes.c_int64(0)
+        _check(lib().tdk_ctx_profile_read(self._h, int(region), ctypes.byref(ms), ctypes.byref(n)),
+               "tdk_ctx_profile_read")
+        return ms.value, n.value
+
+    def close(self):
+        if self._h:
+            lib().tdk_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tucker_sketch(ctx: Context, Y, W, ranks, p, prec="simt", want_Z=False):
+    """All-mode sketch + CholQR2 (see include/tdk.h).  W[n][k] are FP64 device
+    tensors [I_k x (R_n + p)] (W[n][n] unused).  Returns (U list, Z list|None)."""
+    import torch
+
+    N = Y.dim()
+    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, prec)
+    Rt = [int(r) + int(p) for r in ranks]
+    dev = Y.device
+    U = [torch.empty((Y.shape[n], Rt[n]), dtype=torch.float64, device=dev) for n in range(N)]
+    Z = [torch.empty((Y.shape[n], Rt[n]), dtype=torch.float64, device=dev) for n in range(N)] if want_Z else None
+    Wf = []
+    for n in range(N):
+        for k in range(N):
+            Wf.append(None if k == n else W[n][k].contiguous())
+    ctx._bind_stream()
+    _check(lib().tucker_sketch(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _ptrs(Wf), _ptrs(U),
+                               _ptrs(Z) if Z is not None else None), "tucker_sketch")
+    return U, Z
+
+
+def tucker_core(ctx: Context, Y, U, ranks, p, prec="simt"):
+    """G = Y x_1 U_1^T ... x_N U_N^T and ||Y||^2 (device FP64 scalar)."""
+    import torch
+
+    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, prec)
+    Rt = [int(r) + int(p) for r in ranks]
+    gdt = torch.float64 if Y.dtype == torch.float64 else torch.float32
+    G = torch.empty(Rt, dtype=gdt, device=Y.device)
+    nrm = torch.empty((), dtype=torch.float64, device=Y.device)
+    ctx._bind_stream()
+    _check(lib().tucker_core(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()),
+                             _ptrs([u.contiguous() for u in U]), ctypes.c_void_p(G.data_ptr()),
+                             ctypes.c_void_p(nrm.data_ptr())), "tucker_core")
+    return G, nrm
+
+
+def ffcp_als(ctx: Context, G, U, shape, ranks, p, dtype_code, R, max_sweeps=1000, tol=1e-7, nonneg=False,
+             init="given", B0=None, A0=None, normY2=None, check_every=8, timeout_s=0.0):
+    """FFCP on the core (see include/tdk.h).  Returns dict(A, B, lam, report)."""
+    import torch
+
+    N = len(shape)
+    desc = make_desc(shape, dtype_code, ranks, p, "simt")
+    Rt = [int(r) + int(p) for r in ranks]
+    dev = G.device
+    B = [torch.zeros((Rt[n], R), dtype=torch.float64, device=dev) for n in range(N)]
+    A = [torch.zeros((shape[n], R), dtype=torch.float64, device=dev) for n in range(N)]
+    if B0 is not None:
+        for n in range(N):
+            B[n].copy_(B0[n])
+    if A0 is not None:
+        for n in range(N):
+            A[n].copy_(A0[n])
+    lam = torch.empty(R, dtype=torch.float64, device=dev)
+    o = AlsOpts(R=int(R), max_sweeps=int(max_sweeps), tol=float(tol), nonneg=int(bool(nonneg)),
+                init=INIT[init], check_every=int(check_every), reserved=0, timeout_s=float(timeout_s))
+    rep = AlsReport()
+    ctx._bind_stream()
+    rc = _check(lib().ffcp_als(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(G.data_ptr()),
+                               _ptrs([u.contiguous() for u in U]),
+                               ctypes.c_void_p(normY2.data_ptr() if normY2 is not None else None),
+                               ctypes.byref(o), _ptrs(B), _ptrs(A), ctypes.c_void_p(lam.data_ptr()),
+                               ctypes.byref(rep)), "ffcp_als")
+    return {"A": A, "B": B, "lam": lam, "status": rc, "sweeps": rep.sweeps, "fit_core": rep.fit_core,
+            "fit_Y": rep.fit_Y, "ms": rep.ms}
+
+
+def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sweeps=1000, tol=1e-7,
+              init="given", B0=None, A0=None, check_every=8):
+    """The whole path: sketch -> CholQR2 -> core -> FFCP -> lift.  Y may be a
+    host tensor (copied in) or a device tensor; results stay on the device."""
+    import torch
+
+    if not Y.is_cuda:
+        Y = Y.to(f"cuda:{ctx.device}", non_blocking=True)
+    U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
+    G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
+    out = ffcp_als(ctx, G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R, max_sweeps, tol, nonneg, init, B0, A0,
+                   nrm, check_every)
+    out.update({"U": U, "G": G, "normY2": nrm})
+    return out
+
+
+__all__ = ["Context", "tucker_sketch", "tucker_core", "ffcp_als", "decompose", "lib", "make_desc", "TdkError",
+           "EXPORTS", "strerror"]

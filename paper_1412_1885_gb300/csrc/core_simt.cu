@@ -1,0 +1,264 @@
+// Core G = Y x_1 U_1^T ... x_N U_N^T on CUDA cores (Alg. 2, "Y <- Y x_n U^T"
+// for every n; Eq. 1).  The contiguous mode N is contracted first:
+//   X_1[row, r] = sum_col Y[row, col] U_N[col, r]        (row = (i_1..i_{N-1}))
+// which is the only pass over the full tensor (it also accumulates ||Y||^2);
+// the remaining modes are contracted on the shrunk tensors by
+//   Xo[a, r, b] = sum_i U_m[i, r] X[a, i, b].
+#include "tdk_internal.cuh"
+
+namespace tdk {
+namespace {
+
+constexpr int BM = 64, BL = 32, NT = 256;
+
+template <class T>
+struct Acc2 {  // ||Y||^2 accumulator: Kahan-compensated in FP32, plain in FP64
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    T y = x * x - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <class TY, class T, int TC>
+__global__ void __launch_bounds__(NT) ttm_last_kernel(const TY* __restrict__ Y, int64_t M, int64_t L,
+                                                      const T* __restrict__ U, int Rt,
+                                                      T* __restrict__ X, double* __restrict__ nrm_part) {
+  __shared__ T Ys[BM * (BL + 1)];
+  __shared__ T Us[BL * 16 * TC];
+  __shared__ double red[NT / 32];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int ldu = 16 * TC;
+  const int64_t ntiles = (M + BM - 1) / BM;
+  Acc2<T> nrm;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * BM;
+    T acc[4][TC];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < TC; ++j) acc[i][j] = T(0);
+    for (int64_t c0 = 0; c0 < L; c0 += BL) {
+      __syncthreads();
+      for (int e = t; e < BM * BL; e += NT) {
+        int rr = e / BL, cc = e % BL;
+        int64_t row = row0 + rr, col = c0 + cc;
+        T y = (row < M && col < L) ? CvtIn<T>::cvt(Y[row * L + col]) : T(0);
+        nrm.add(y);
+        Ys[rr * (BL + 1) + cc] = y;
+      }
+      for (int e = t; e < BL * ldu; e += NT) {
+        int cc = e / ldu, c = e % ldu;
+        int64_t col = c0 + cc;
+        Us[e] = (col < L && c < Rt) ? U[col * Rt + c] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < BL; ++k) {
+        T y[4], w[TC];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] = Ys[(ty + 16 * i) * (BL + 1) + k];
+#pragma unroll
+        for (int j = 0; j < TC; ++j) w[j] = Us[k * ldu + tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < TC; ++j) acc[i][j] = fma(y[i], w[j], acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int64_t row = row0 + ty + 16 * i;
+      if (row >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TC; ++j) {
+        int c = tx + 16 * j;
+        if (c < Rt) X[row * Rt + c] = acc[i][j];
+      }
+    }
+  }
+  double v = warp_sum(nrm.value());
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    nrm_part[blockIdx.x] = s;
+  }
+}
+
+// Xo[a, r, b] = sum_i U[i, r] X[a, i, b];  grid (A, ceil(Bd/64)), Rt <= 64
+template <class T>
+__global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, int64_t Ic, int64_t Bd,
+                                                     const T* __restrict__ U, int Rt, T* __restrict__ Xo) {
+  __shared__ T Xs[32 * 64];
+  __shared__ T Us[32 * 64];
+  const int t = threadIdx.x, tb = t & 15, tr = t >> 4;
+  const int64_t a = blockIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.y * 64;
+  const T* Xa = X + a * Ic * Bd;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int64_t i0 = 0; i0 < Ic; i0 += 32) {
+    __syncthreads();
+    for (int e = t; e < 32 * 64; e += NT) {
+      int ii = e / 64, c = e % 64;
+      int64_t i = i0 + ii;
+      Xs[e] = (i < Ic && b0 + c < Bd) ? Xa[i * Bd + b0 + c] : T(0);
+      Us[e] = (i < Ic && c < Rt) ? U[i * Rt + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ii = 0; ii < 32; ++ii) {
+      T u[4], x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        u[q] = Us[ii * 64 + tr + 16 * q];
+        x[q] = Xs[ii * 64 + tb + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(u[p], x[q], acc[p][q]);
+    }
+  }
+  T* Xoa = Xo + a * (int64_t)Rt * Bd;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int r = tr + 16 * p;
+    if (r >= Rt) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int64_t b = b0 + tb + 16 * q;
+      if (b < Bd) Xoa[(int64_t)r * Bd + b] = acc[p][q];
+    }
+  }
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    *out = v;
+  }
+}
+
+template <class T>
+__global__ void cvt_f64_kernel(const double* __restrict__ s, T* __restrict__ d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (T)s[e];
+}
+
+template <class TY, class T, int TC>
+int launch_last(tdk_ctx* ctx, const void* Y, int64_t M, int64_t L, const T* U, int Rt, T* X,
+                double* parts, int grid) {
+  ProfScope ps(ctx, 1);
+  ttm_last_kernel<TY, T, TC><<<grid, NT, 0, ctx->stream>>>(reinterpret_cast<const TY*>(Y), M, L, U, Rt,
+                                                          X, parts);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
+}  // namespace
+
+// core chain shared by both forms once X_1 exists (modes N-2 .. 0)
+template <class T>
+int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1) {
+  const int N = g.N;
+  // dims of the current tensor: I_0..I_{m}, Rt_{m+1}..Rt_{N-1}
+  const T* cur = X1;
+  int64_t Bd = g.Rt[N - 1];
+  for (int m = N - 2; m >= 0; --m) {
+    int64_t A = 1;
+    for (int k = 0; k < m; ++k) A *= g.I[k];
+    T* out = (m == 0) ? G : ((m % 2) ? tmp0 : tmp1);
+    dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
+    ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(cur, g.I[m], Bd, Ut[m], g.Rt[m], out);
+    TDK_LAUNCH_CHECK(ctx);
+    cur = out;
+    Bd *= g.Rt[m];
+  }
+  return TDK_OK;
+}
+template int core_chain_rest<float>(tdk_ctx*, const Geom&, const float*, float* const[], float*, float*, float*);
+template int core_chain_rest<double>(tdk_ctx*, const Geom&, const double*, double* const[], double*, double*,
+                                     double*);
+
+template <class TY, class T>
+static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double* const U[], void* Gv,
+                       double* normY2) {
+  const int N = g.N;
+  const int RtL = g.Rt[N - 1];
+  const int TC = (RtL + 15) / 16;
+  const int64_t ntiles = (g.M + BM - 1) / BM;
+  int grid = (int)((int64_t)ctx->num_sms * 4 < ntiles ? (int64_t)ctx->num_sms * 4 : ntiles);
+  // workspace: U in T, X1, two ping-pong buffers, norm partials
+  int64_t tmpsz = 0;
+  {
+    int64_t Bd = RtL;
+    for (int m = N - 2; m >= 1; --m) {
+      int64_t A = 1;
+      for (int k = 0; k < m; ++k) A *= g.I[k];
+      int64_t s = A * g.Rt[m] * Bd;
+      if (s > tmpsz) tmpsz = s;
+      Bd *= g.Rt[m];
+    }
+  }
+  Planner pl;
+  for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.I[n] * g.Rt[n]);
+  pl.take<T>((size_t)g.M * RtL);
+  pl.take<T>((size_t)tmpsz);
+  pl.take<T>((size_t)tmpsz);
+  pl.take<double>((size_t)grid);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  T* Ut[TDK_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    Ut[n] = cv.take<T>((size_t)g.I[n] * g.Rt[n]);
+    cvt_f64_kernel<T><<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  T* X1 = cv.take<T>((size_t)g.M * RtL);
+  T* tmp0 = cv.take<T>((size_t)tmpsz);
+  T* tmp1 = cv.take<T>((size_t)tmpsz);
+  double* parts = cv.take<double>((size_t)grid);
+  switch (TC) {
+    case 1: rc = launch_last<TY, T, 1>(ctx, Y, g.M, g.L, Ut[N - 1], RtL, X1, parts, grid); break;
+    case 2: rc = launch_last<TY, T, 2>(ctx, Y, g.M, g.L, Ut[N - 1], RtL, X1, parts, grid); break;
+    case 3: rc = launch_last<TY, T, 3>(ctx, Y, g.M, g.L, Ut[N - 1], RtL, X1, parts, grid); break;
+    case 4: rc = launch_last<TY, T, 4>(ctx, Y, g.M, g.L, Ut[N - 1], RtL, X1, parts, grid); break;
+    default: return TDK_EINVAL;
+  }
+  if (rc) return rc;
+  if (normY2) {
+    sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(parts, grid, normY2);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  return core_chain_rest<T>(ctx, g, X1, Ut, reinterpret_cast<T*>(Gv), tmp0, tmp1);
+}
+
+int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* G,
+              double* normY2) {
+  switch (dtype) {
+    case TDK_F64: return core_simt_t<double, double>(ctx, g, Y, U, G, normY2);
+    case TDK_F32: return core_simt_t<float, float>(ctx, g, Y, U, G, normY2);
+    case TDK_BF16: return core_simt_t<__nv_bfloat16, float>(ctx, g, Y, U, G, normY2);
+  }
+  return TDK_EINVAL;
+}
+
+}  // namespace tdk

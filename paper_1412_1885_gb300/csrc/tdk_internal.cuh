@@ -1,0 +1,160 @@
+// Internal declarations shared by the translation units of libtdk.so.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "../../include/tdk.h"
+
+#define TDK_STATUS_RANKDEF 1u
+#define TDK_STATUS_TIMEOUT 256u
+
+struct tdk_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;     // private non-blocking stream (graph capture)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void* ws = nullptr;          // growable workspace
+  size_t ws_size = 0;
+  unsigned* d_status = nullptr;  // device status word (TDK_STATUS_* bits)
+  int64_t launches = 0;
+  int fail_alloc_after = -1;   // test hook: fail the n-th workspace growth
+  // event timing of the main kernels (regions 0: sketch pass, 1: core pass)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev[2];
+  double prof_ms[2] = {0.0, 0.0};
+  int64_t prof_n[2] = {0, 0};
+};
+
+namespace tdk {
+
+// record an event pair around the main kernel of a region (when profiling)
+struct ProfScope {
+  tdk_ctx* c;
+  int region;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(tdk_ctx* ctx, int r) : c(ctx), region(r) {
+    if (!c->prof) return;
+    cudaEvent_t e0;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    c->prof_ev[region].push_back(e0);
+  }
+  ~ProfScope() {
+    if (!c->prof || !e1) return;
+    cudaEventRecord(e1, c->stream);
+    c->prof_ev[region].push_back(e1);
+  }
+};
+
+// ---- host helpers -------------------------------------------------------
+int ws_reserve(tdk_ctx* ctx, size_t bytes);
+
+struct Carver {  // carves 256-byte-aligned slices out of the workspace
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+// size of a carve plan (same alignment rule)
+struct Planner {
+  size_t off = 0;
+  template <class T>
+  void take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    off += count * sizeof(T);
+  }
+};
+
+#define TDK_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t e__ = (expr);                                                \
+    if (e__ != cudaSuccess) {                                                \
+      fprintf(stderr, "tdk: %s failed: %s (%s:%d)\n", #expr,                 \
+              cudaGetErrorString(e__), __FILE__, __LINE__);                  \
+      return TDK_ECUDA;                                                      \
+    }                                                                        \
+  } while (0)
+
+#define TDK_LAUNCH_CHECK(ctx)                                                \
+  do {                                                                       \
+    (ctx)->launches++;                                                       \
+    cudaError_t e__ = cudaGetLastError();                                    \
+    if (e__ != cudaSuccess) {                                                \
+      fprintf(stderr, "tdk: launch failed: %s (%s:%d)\n",                    \
+              cudaGetErrorString(e__), __FILE__, __LINE__);                  \
+      return TDK_ECUDA;                                                      \
+    }                                                                        \
+  } while (0)
+
+// problem geometry derived from a descriptor
+struct Geom {
+  int N;
+  int64_t I[TDK_MAX_MODES];
+  int Rt[TDK_MAX_MODES];
+  int64_t numel;
+  int64_t M;      // rows of the last-mode unfolding: prod_{k<N-1} I_k
+  int64_t L;      // I_{N-1} (contiguous mode)
+  int64_t zoff[TDK_MAX_MODES + 1];  // offsets of Z_n in a packed buffer
+  int64_t core_numel;
+};
+int make_geom(const tdk_tucker_desc* d, Geom* g);
+
+// ---- entry points of the translation units --------------------------------
+// sketch (SIMT): writes FP64 Z_n for all modes into Zdst (packed by zoff)
+int sketch_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],
+                double* Zdst);
+// tensor-core sketch; returns TDK_ENOTSUP when the form does not apply
+int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],
+              double* Zdst);
+// CholQR2 of every Z_n (packed FP64) into U_out
+int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[]);
+// core: G (T) and ||Y||^2 (FP64 device scalar, may be null)
+int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[],
+              void* G, double* normY2);
+int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[],
+            void* G, double* normY2);
+int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double* const U[],
+            const double* normY2, const tdk_als_opts* o, double* const B_io[],
+            double* const A_io[], double* lambda_out, tdk_als_report* rep);
+
+}  // namespace tdk
+
+// ---- device helpers -----------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T tdk_load(const T* p) { return *p; }
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ double to_f(double x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class T>
+struct CvtIn {  // storage -> compute type
+  template <class S>
+  __device__ __forceinline__ static T cvt(S x) { return (T)to_f(x); }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}

@@ -1,0 +1,51 @@
+"""Shared helpers for the GPU parity tests (inputs from `synth`, expected
+values from `oracle`; nothing here computes the method)."""
+import numpy as np
+
+import oracle
+import synth
+
+TORCH_DT = {"f64": "float64", "f32": "float32", "bf16": "bfloat16"}
+DT_CODE = {"f64": 0, "f32": 1, "bf16": 2}
+
+
+def dev_tensor(Y: np.ndarray, dtype: str, device="cuda"):
+    import torch
+
+    t = torch.as_tensor(np.ascontiguousarray(Y), dtype=torch.float64)
+    return t.to(getattr(torch, TORCH_DT[dtype])).to(device).contiguous()
+
+
+def dev_W(W, device="cuda"):
+    import torch
+
+    return [[None if w is None else torch.as_tensor(w, dtype=torch.float64, device=device) for w in row] for row in W]
+
+
+def host(t) -> np.ndarray:
+    return t.detach().double().cpu().numpy()
+
+
+def sketch_abs_bound(Y, W):
+    """Elementwise |Y|_(n) |Omega_n|: the scale against which the rounding
+    error of a computed sketch entry is bounded (|sum a_i b_i| <= sum |a_i||b_i|)."""
+    Z, _ = oracle.sketch(np.abs(Y), [[None if w is None else np.abs(w) for w in row] for row in W])
+    return Z
+
+
+def core_abs_bound(Y, U):
+    return oracle.tucker_core(np.abs(Y), [np.abs(u) for u in U])
+
+
+def recon_err(normY2: float, G: np.ndarray) -> float:
+    """||Y - [[G; U]]|| / ||Y|| for orthonormal U (Pythagoras)."""
+    return float(np.sqrt(max(0.0, normY2 - float(np.sum(np.asarray(G, dtype=np.float64) ** 2))) / normY2))
+
+
+def small_problem(shape, ranks, p, seed, dtype="f32", snr=20.0, R_cp=None, dist="normal", clip0=False):
+    R_cp = R_cp or min(ranks)
+    A = synth.cp_factors(shape, R_cp, seed, dist)
+    Y = synth.add_noise(synth.cp_dense(A), snr, seed, clip0)
+    Y = synth.to_storage(Y, dtype)
+    W = synth.sketch_matrices(shape, [r + p for r in ranks], seed)
+    return Y, W, A

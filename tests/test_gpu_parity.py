@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Sizes span several tiles with ragged tails; tolerances
+are derived from the arithmetic of each form and stated per test."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import DT_CODE, core_abs_bound, dev_tensor, dev_W, host, recon_err, sketch_abs_bound, small_problem
+
+pytestmark = pytest.mark.gpu
+
+# relative rounding unit of the accumulation per form, times a safety factor:
+# FP64: products and sums in FP64; FP32/BF16 data on CUDA cores: FP32 sums of
+# up to ~1e6 terms (errors grow like sqrt(terms) * u32 in practice).
+TOL_SKETCH = {("f64", "simt"): 1e-12, ("f32", "simt"): 2e-5, ("bf16", "simt"): 2e-5}
+
+SHAPES = [
+    (67, 45, 130),        # 3015 rows (47 tiles of 64 + tail), 130 columns (4 chunks of 32 + tail)
+    (9, 11, 7, 13),       # 4-way, tiny ragged
+    (33, 70, 64),
+]
+
+
+@pytest.fixture(scope="module")
+def tdk():
+    import paper_1412_1885_gb300 as t
+    from paper_1412_1885_gb300 import build
+
+    build.build()
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(tdk):
+    c = tdk.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("dtype,prec", [("f64", "simt"), ("f32", "simt"), ("bf16", "simt")])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_sketch_matches_oracle(tdk, ctx, shape, dtype, prec):
+    ranks = [min(4, s - 3) for s in shape]
+    p = 3
+    Y, W, _ = small_problem(shape, ranks, p, seed=11, dtype=dtype)
+    U, Z = tdk.tucker_sketch(ctx, dev_tensor(Y, dtype), dev_W(W), ranks, p, prec, want_Z=True)
+    Zo, _ = oracle.sketch(Y, W)
+    bnd = sketch_abs_bound(Y, W)
+    tol = TOL_SKETCH[(dtype, prec)]
+    for n in range(len(shape)):
+        err = np.abs(host(Z[n]) - Zo[n])
+        assert np.all(err <= tol * bnd[n] + 1e-300), (n, float((err / bnd[n]).max()))
+        Un = host(U[n])
+        assert np.abs(Un.T @ Un - np.eye(Un.shape[1])).max() < 1e-12
+
+
+def test_cholqr2_matches_householder_fp64(tdk, ctx):
+    shape, ranks, p = (61, 47, 53), (5, 6, 7), 4
+    Y, W, _ = small_problem(shape, ranks, p, seed=3, dtype="f64")
+    U, _ = tdk.tucker_sketch(ctx, dev_tensor(Y, "f64"), dev_W(W), ranks, p, "simt")
+    ref = oracle.rand_tucker(Y, W)
+    for n in range(3):
+        # same convention (positive diagonal of R) => same Q entrywise
+        assert np.abs(host(U[n]) - ref["U"][n]).max() < 1e-10
+    assert ctx.sync_status() == 0
+
+
+def test_rank_deficient_sketch_is_completed(tdk, ctx):
+    """Noise-free tensor of exact multilinear rank with p > 0: Z_n has rank R_n
+    < R_n + p, Cholesky breaks down, the completion keeps U orthonormal and
+    the Tucker reconstruction exact."""
+    shape, ranks, p = (40, 36, 30), (3, 4, 5), 4
+    Y = synth.tucker_dense(shape, ranks, 5)
+    W = synth.sketch_matrices(shape, [r + p for r in ranks], 1)
+    Yd = dev_tensor(Y, "f64")
+    U, _ = tdk.tucker_sketch(ctx, Yd, dev_W(W), ranks, p, "simt")
+    flags = ctx.sync_status()
+    assert flags & tdk.TDK_WRANKDEF
+    for u in U:
+        un = host(u)
+        assert np.abs(un.T @ un - np.eye(un.shape[1])).max() < 1e-12
+    G, nrm = tdk.tucker_core(ctx, Yd, U, ranks, p, "simt")
+    Yh = oracle.tucker_full(host(G), [host(u) for u in U])
+    assert np.linalg.norm(Y - Yh) / np.linalg.norm(Y) < 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_core_matches_oracle(tdk, ctx, shape, dtype):
+    ranks = [min(4, s - 3) for s in shape]
+    p = 3
+    Y, W, _ = small_problem(shape, ranks, p, seed=5, dtype=dtype)
+    ref = oracle.rand_tucker(Y, W)
+    Ud = [dev_tensor(u, "f64") for u in ref["U"]]   # oracle U as input to the GPU core
+    G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), Ud, ranks, p, "simt")
+    bnd = core_abs_bound(Y, ref["U"])
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    err = np.abs(host(G) - ref["G"])
+    assert np.all(err <= tol * bnd), float((err / bnd).max())
+    assert math.isclose(float(nrm.item()), ref["normY2"], rel_tol=1e-12 if dtype == "f64" else 1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_als_matches_oracle_on_same_core(tdk, ctx, dtype):
+    shape, ranks, p, R = (50, 45, 40), (6, 6, 6), 4, 5
+    Y, W, A = small_problem(shape, ranks, p, seed=9, dtype=dtype, snr=25.0, R_cp=R)
+    ref = oracle.rand_tucker(Y, W)
+    Rt = [r + p for r in ranks]
+    B0 = synth.init_factors(Rt, R, 4)
+    ref_als = oracle.cp_als(ref["G"], B0, max_sweeps=60, tol=0.0)
+    Gd = dev_tensor(ref["G"], "f64" if dtype == "f64" else "f32")
+    Ud = [dev_tensor(u, "f64") for u in ref["U"]]
+    out = tdk.ffcp_als(ctx, Gd, Ud, shape, ranks, p, DT_CODE[dtype], R, max_sweeps=60, tol=0.0,
+                       B0=[dev_tensor(b, "f64") for b in B0], check_every=16)
+    assert out["sweeps"] == 60
+    tol = 1e-10 if dtype == "f64" else 1e-5
+    assert abs(out["fit_core"] - ref_als["fit"]) < tol
+    Ah = [host(a) for a in out["A"]]
+    Ao = oracle.lift(ref["U"], ref_als["B"], ref_als["lam"])
+    assert oracle.congruence(Ao, Ah) > (1 - 1e-9 if dtype == "f64" else 0.9999)
+    if dtype == "f64":
+        for n in range(3):
+            assert np.allclose(host(out["B"][n]), ref_als["B"][n], atol=1e-8)
+
+
+def test_als_stopping_rule_matches_oracle_fp64(tdk, ctx):
+    shape, ranks, p, R = (30, 28, 26), (4, 4, 4), 3, 3
+    Y, W, _ = small_problem(shape, ranks, p, seed=2, dtype="f64", snr=30.0, R_cp=R)
+    ref = oracle.rand_tucker(Y, W)
+    B0 = synth.init_factors([r + p for r in ranks], R, 8)
+    o = oracle.cp_als(ref["G"], B0, max_sweeps=500, tol=1e-9)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], "f64"), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, 0, R, max_sweeps=500, tol=1e-9, B0=[dev_tensor(b, "f64") for b in B0], check_every=4)
+    assert out["sweeps"] == o["sweeps"]
+    assert abs(out["fit_core"] - o["fit"]) < 1e-12
+
+
+def test_nonneg_als_matches_oracle(tdk, ctx):
+    shape, ranks, p, R = (24, 22, 20, 18), (5, 5, 5, 5), 3, 4
+    Y, W, A = small_problem(shape, ranks, p, seed=7, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
+    ref = oracle.rand_tucker(Y, W)
+    A0 = synth.init_factors(shape, R, 6, dist="uniform")
+    o = oracle.cp_als_nonneg(ref["G"], ref["U"], A0, max_sweeps=40, tol=0.0)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], "f64"), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, 0, R, max_sweeps=40, tol=0.0, nonneg=True, A0=[dev_tensor(a, "f64") for a in A0])
+    assert abs(out["fit_core"] - o["fit"]) < 1e-10
+    Ah = [host(a) for a in out["A"]]
+    assert all(np.all(a >= 0) for a in Ah)
+    Ao = [a.copy() for a in o["A"]]
+    Ao[-1] = Ao[-1] * o["lam"][None, :]
+    for n in range(4):
+        assert np.allclose(Ah[n], Ao[n], atol=1e-8)
+
+
+def test_end_to_end_c1_fp64(tdk, ctx):
+    """Workload 1 at full size (100^3 FP64, CP rank 5, SNR 30 dB, p = 5, ALS
+    rank 5, <= 100 sweeps, relative fit change < 1e-9)."""
+    w = synth.WORKLOADS["c1"]
+    Y = synth.host_tensor(w)
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
+    B0 = synth.init_factors(w.Rt, w.als_R, w.seed)
+    ref = oracle.rand_tucker(Y, W)
+    o = oracle.cp_als(ref["G"], B0, max_sweeps=w.als_max_sweeps, tol=w.als_tol)
+    out = tdk.decompose(ctx, dev_tensor(Y, "f64"), dev_W(W), w.ranks, w.p, w.als_R, "simt",
+                        max_sweeps=w.als_max_sweeps, tol=w.als_tol, B0=[dev_tensor(b, "f64") for b in B0])
+    e_gpu = recon_err(float(out["normY2"].item()), host(out["G"]))
+    e_or = recon_err(ref["normY2"], ref["G"])
+    assert abs(e_gpu - e_or) < 1e-12
+    assert abs(out["fit_core"] - o["fit"]) < 1e-10
+    Ao = oracle.lift(ref["U"], o["B"], o["lam"])
+    assert oracle.congruence(Ao, [host(a) for a in out["A"]]) > 0.999999
+    # and the planted factors are found
+    A_true = synth.cp_factors(w.shape, w.R_cp, w.seed)
+    assert oracle.congruence(A_true, [host(a) for a in out["A"]]) > 0.99
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_end_to_end_scaled_fp32(tdk, ctx, dtype):
+    """Workload 2's data model at 120^3: reconstruction-error difference <= 1e-5."""
+    w = synth.scaled(synth.WORKLOADS["c2"], (120, 120, 120))
+    w.dtype = dtype
+    Y = synth.host_tensor(w)
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
+    ref = oracle.rand_tucker(Y, W)
+    U, _ = tdk.tucker_sketch(ctx, dev_tensor(Y, dtype), dev_W(W), w.ranks, w.p, "simt")
+    G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), U, w.ranks, w.p, "simt")
+    e_gpu = recon_err(float(nrm.item()), host(G))
+    e_or = recon_err(ref["normY2"], ref["G"])
+    assert abs(e_gpu - e_or) <= 1e-5, (e_gpu, e_or)

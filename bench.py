@@ -1,0 +1,345 @@
+"""Benchmark: one step = the whole path (all-mode sketch -> CholQR2 -> core ->
+FFCP ALS to convergence -> lift) on one synthetic workload resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c4] [--prec tc]
+    python bench.py --impl reference ...      (the FP64 oracle on the host cores)
+
+value  = dense-tensor GB/s: algorithmic bytes 2 * itemsize * prod(I) (the two
+         passes over Y: sketch, then core) per step / device time of a step.
+e2e    = the same metric through the public API with Y copied from pinned host
+         memory every step and the factors read back.
+Prints one JSON line (rank 0).  Multi-GPU (torchrun) runs independent
+replicas, one per rank (weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dense-tensor GB/s (sketch+core) vs HBM peak; FFCP time-to-fit vs plain FP32"
+DEFAULT_CONFIG = "c4"
+DEFAULT_PREC = "tc"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_source_sha(prec: str) -> str:
+    names = ["tc_sketch.cu", "tc_common.cuh"] if prec == "tc" else ["sketch_simt.cu"]
+    h = hashlib.sha256()
+    for n in names:
+        p = os.path.join(ROOT, "paper_1412_1885_gb300", "csrc", n)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profiles(kernel_tag: str, workload: str, sha: str):
+    """Per-launch DRAM bytes of the sketch kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(w, seconds_target=15.0):
+    """Time the FP64 oracle (as it stands) on a leading sub-block of the
+    workload on the host cores: sketch + QR + core over the block, then ALS on
+    its core.  Returns (GB/s of the block's two passes, description)."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    # sub-block with ~4e6..3e7 entries along the leading modes
+    shape = list(w.shape)
+    target = 6_000_000 if w.N == 3 else 4_000_000
+    sub = [min(s, max(r + w.p, 8)) for s, r in zip(shape, w.ranks)]
+    # grow the trailing (contiguous) mode first, then the others
+    for n in reversed(range(w.N)):
+        while sub[n] < shape[n] and int(np.prod(sub)) * 2 <= target:
+            sub[n] = min(shape[n], sub[n] * 2)
+    sw = synth.scaled(w, sub)
+    Y = synth.host_tensor(sw)
+    W = synth.sketch_matrices(sw.shape, sw.Rt, sw.seed)
+    B0 = synth.init_factors(sw.Rt, sw.als_R, sw.seed)
+    t0 = time.perf_counter()
+    tk = oracle.rand_tucker(Y, W)
+    if sw.nonneg:
+        A0 = synth.init_factors(sw.shape, sw.als_R, sw.seed, dist="uniform")
+        oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
+    else:
+        oracle.cp_als(tk["G"], B0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
+    dt = time.perf_counter() - t0
+    nbytes = 2 * w.itemsize * int(np.prod(sub))
+    desc = (f"oracle rand_tucker + ALS (<=200 sweeps) on the leading {'x'.join(map(str, sub))} block "
+            f"of {w.name}, {dt:.1f} s")
+    return nbytes / dt / 1e9, desc, dt
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    cores = os.cpu_count()
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, _ = cpu_oracle_sample(w)
+        if i >= args.warmup:
+            vals.append(v)
+    vals.sort()
+    v = vals[len(vals) // 2]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "shape": list(w.shape), "ranks": list(w.ranks), "p": w.p,
+                       "R": w.als_R},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
+    ap.add_argument("--prec", default=DEFAULT_PREC, choices=["tc", "simt"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import synth
+
+    w = synth.WORKLOADS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+
+    import paper_1412_1885_gb300 as t
+    from paper_1412_1885_gb300 import build
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(dev))
+        pg = dist
+    if rank == 0:
+        build.build()
+    if pg:
+        pg.barrier()
+    t.lib()
+
+    # ---- inputs (untimed): Y generated in HBM, W / init from the seeded generators
+    Y, A_true = synth.device_tensor(w, device=dev)
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
+    Wd = [[None if x is None else torch.as_tensor(x, device=dev) for x in row] for row in W]
+    B0 = [torch.as_tensor(b, device=dev) for b in synth.init_factors(w.Rt, w.als_R, w.seed)]
+    A0 = [torch.as_tensor(a, device=dev) for a in synth.init_factors(w.shape, w.als_R, w.seed, dist="uniform")]
+    ctx = t.Context(local)
+    torch.cuda.synchronize()
+
+    def step(Yin):
+        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, args.prec, nonneg=w.nonneg,
+                           max_sweeps=w.als_max_sweeps, tol=w.als_tol, B0=None if w.nonneg else B0,
+                           A0=A0 if w.nonneg else None, check_every=16)
+
+    for _ in range(args.warmup):
+        out = step(Y)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the current stream)
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    l0 = ctx.launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sweeps = []
+    for _ in range(args.steps):
+        out = step(Y)
+        sweeps.append(out["sweeps"])
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.launch_count() - l0
+    sk_ms, sk_n = ctx.profile_read(0)
+    co_ms, co_n = ctx.profile_read(1)
+    ctx.profile(False)
+    if pg:
+        tt = torch.tensor([ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        ms = float(tt.item())
+    y_bytes = w.itemsize * w.numel
+    alg_bytes = 2 * y_bytes
+    value = ws * alg_bytes / (ms * 1e-3) / 1e9
+
+    # ---- end to end: Y from pinned host memory each step, factors read back
+    e2e = None
+    if not args.no_e2e:
+        Yh = torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
+        Yh.copy_(Y)
+        torch.cuda.synchronize()
+        h2d = Yh.numel() * Yh.element_size()
+        d2h = 0
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            Y.copy_(Yh, non_blocking=True)
+            o = step(Y)
+            host = [a.to("cpu") for a in o["A"]]
+            d2h = sum(a.numel() * a.element_size() for a in host)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if pg:
+            tt = torch.tensor([dt], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": ws * alg_bytes / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
+        del Yh
+
+    peak, peak_kind = _peaks()
+    sk_avg = sk_ms / max(sk_n, 1)
+    achieved = y_bytes / (sk_avg * 1e-3) / 1e9 if sk_n else None
+    sha = _kernel_source_sha(args.prec)
+    kernel_tag = "tc_sketch" if args.prec == "tc" else "sketch_simt"
+    roofline = {"bound": "hbm", "kernel": kernel_tag, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "traffic": _traffic_from_profiles(kernel_tag, args.config, sha),
+                "algorithmic_bytes_per_launch": y_bytes, "avg_launch_ms": sk_avg,
+                "kernel_source_sha": sha,
+                "core_pass": {"achieved": (y_bytes / (co_ms / max(co_n, 1) * 1e-3) / 1e9) if co_n else None,
+                              "avg_launch_ms": co_ms / max(co_n, 1)}}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cv, cdesc, _ = cpu_oracle_sample(w)
+        cpu = {"value": cv, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle", "sample": cdesc}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16"}[w.dtype],
+                "data": "synthetic",
+                "config": {"workload": w.name, "shape": list(w.shape), "ranks": list(w.ranks), "p": w.p,
+                           "R": w.als_R, "prec": args.prec, "nonneg": w.nonneg,
+                           "l2": "inputs larger than L2 (no flush)",
+                           "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches,
+                "als": {"sweeps": sweeps, "fit_core": out["fit_core"], "fit_Y": out["fit_Y"],
+                        "ms_last": out["ms"]},
+                "sketch_ms": sk_avg, "core_ms": co_ms / max(co_n, 1)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,1069 @@
+// Tensor-core (tcgen05) forms of the two passes over Y.
+//
+// SKETCH (Sec. IV-A step 2; Alg. 2; Eq. 21), N >= 3.  Y is read as a 3-D
+// array [P][J][L] with L = I_N (contiguous), J = I_{N-1}, P = prod_{k<N-1} I_k.
+// A tile is 128 consecutive j (one p) x 128 consecutive columns, staged by TMA
+// into shared memory with the 128-byte swizzle, and used twice:
+//   G1 (K-major A):  D1[j, c] += sum_k Y[p, j, k] WN[c, k]  for the channels
+//                    c of every mode n < N-1 (WN = W_N^(n) blocks, each padded
+//                    to 16 channels), accumulated in TMEM over the unit's
+//                    column range and read once per p;
+//   G2 (MN-major A): D2[k, r] += sum_j Y[p, j, k] K_p[j, r] with the Khatri-Rao
+//                    rows K_p[j, r] = W_{N-1}^(N)[j, r] prod_{k<N-1} W_k^(N)[i_k(p), r]
+//                    generated per p by the epilogue warps, accumulated in TMEM
+//                    over the whole unit.
+// The epilogue turns D1 into the sketches of modes < N: mode N-1 (the tile's
+// row mode) accumulates per TMEM lane across p; modes < N-1 are constant over
+// the tile and need a 128-lane reduction.  Each work unit (j-tile, column
+// range, p-range) writes its own partial block (the blockwise sums of Eq. 21);
+// a fixed-order FP64 reduction produces Z.
+//
+// CORE (Alg. 2, the first "Y <- Y x_n U^T", contiguous mode): X_1 = Y_(rows) U_N
+// with U split hi+lo into one B operand [U_hi | U_lo]; ||Y||^2 on the side.
+//
+// FP32 data: TMA brings FP32 boxes; converter warps split every value into
+// BF16 hi + lo in place, and both parts are multiplied (two MMAs per step).
+#include <algorithm>
+
+#include "tc_common.cuh"
+
+namespace tdk {
+
+int encode_tmap(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* base, const uint64_t* dims,
+                const uint64_t* strides_bytes, const uint32_t* box, bool swizzle128) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return TDK_ENOTSUP;
+    }
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  cuuint64_t d[5];
+  cuuint64_t s[4];
+  cuuint32_t b[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) s[i] = strides_bytes[i];
+  }
+  CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fprintf(stderr, "tdk: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
+    return TDK_EINVAL;
+  }
+  return TDK_OK;
+}
+
+namespace {
+
+using namespace tc;
+
+constexpr int KB = 1024;
+constexpr uint32_t BOX_BYTES = 16 * KB;  // one 128-row x 128-byte box
+
+// in-place split of one 128-byte FP32 row pair (64 values) into BF16 hi / lo
+// rows: raw boxes at `hi_row` and `lo_row` (each 128 B, 128-byte swizzle with
+// phase r%8) become the hi and lo BF16 rows of the same 64 columns.
+__device__ __forceinline__ float split_row64(unsigned char* hi_row, unsigned char* lo_row, int r) {
+  float v[64];
+  const int ph = r & 7;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float4 a = *reinterpret_cast<const float4*>(hi_row + ((c ^ ph) << 4));
+    float4 b = *reinterpret_cast<const float4*>(lo_row + ((c ^ ph) << 4));
+    v[4 * c + 0] = a.x; v[4 * c + 1] = a.y; v[4 * c + 2] = a.z; v[4 * c + 3] = a.w;
+    v[32 + 4 * c + 0] = b.x; v[32 + 4 * c + 1] = b.y; v[32 + 4 * c + 2] = b.z; v[32 + 4 * c + 3] = b.w;
+  }
+  float s = 0.f, comp = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint32_t h[4], l[4];
+    float part = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float x0 = v[8 * c + 2 * e], x1 = v[8 * c + 2 * e + 1];
+      __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      float r0 = x0 - __bfloat162float(h0), r1 = x1 - __bfloat162float(h1);
+      __nv_bfloat162 hh;
+      hh.x = h0;
+      hh.y = h1;
+      h[e] = *reinterpret_cast<uint32_t*>(&hh);
+      l[e] = pack_bf16x2(r0, r1);
+      part = fmaf(x0, x0, part);
+      part = fmaf(x1, x1, part);
+    }
+    // Kahan step on the per-chunk sum
+    float y = part - comp;
+    float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+    *reinterpret_cast<uint4*>(hi_row + ((c ^ ph) << 4)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo_row + ((c ^ ph) << 4)) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+  return s - comp;
+}
+
+__device__ __forceinline__ void named_bar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// =====================================================================
+//                               SKETCH
+// =====================================================================
+struct SkArgs {
+  int N;
+  int64_t I[TDK_MAX_MODES];
+  int Rt[TDK_MAX_MODES];
+  int Rtp[TDK_MAX_MODES];          // padded to 16
+  int L, J;
+  int64_t P;
+  int N1;                          // G1 channels (sum of padded widths, modes < N-1)
+  int off[TDK_MAX_MODES];          // channel offset of mode n
+  int RtL;                         // Rt of the contiguous mode
+  int hilo;                        // K rows split hi (cols 0..31) + lo (32..63)
+  int KRW, KS;                     // columns per unit (multiple of 128), stages per p
+  int JT, KR, PC;
+  int64_t PCW;
+  int64_t nunits;
+  int d1_cols;                     // TMEM column stride of the two D1 buffers
+  const float* Wf[TDK_MAX_MODES][TDK_MAX_MODES];  // FP32 W_k^(n) [I_k x Rt_n]
+  float* part;
+  int64_t ustride;                 // floats per unit
+  int64_t poff_last, poff_j;
+  int64_t poff_p[TDK_MAX_MODES];
+  unsigned* status;
+};
+
+template <bool F32>
+struct SkLayout {
+  static constexpr int STAGES = 2;
+  static constexpr uint32_t STAGE_BYTES = F32 ? 64 * KB : 32 * KB;   // 128 j x 128 columns
+  static constexpr uint32_t BOX_STRIDE = F32 ? 32 * KB : 16 * KB;     // between the two 64-column halves
+  static constexpr uint32_t KT_BYTES = 16 * KB;                        // K_p tile [128 j][64 r] BF16
+};
+
+template <bool F32>
+__global__ void __launch_bounds__(F32 ? 320 : 192, 1)
+    tc_sketch_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmW,
+                     const SkArgs a) {
+  using Lay = SkLayout<F32>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* st_base = base;                                   // STAGES x STAGE_BYTES
+  unsigned char* wn_base = st_base + Lay::STAGES * Lay::STAGE_BYTES;  // 2*KS boxes of N1 rows x 128 B
+  const uint32_t wn_box = (uint32_t)a.N1 * 128u;
+  unsigned char* kt_base = wn_base + ((2 * a.KS * wn_box + 1023) & ~1023u);  // 2 x KT_BYTES
+  uint64_t* bars = reinterpret_cast<uint64_t*>(kt_base + 2 * Lay::KT_BYTES);
+  uint64_t* full = bars;           // [STAGES]
+  uint64_t* empty = bars + 2;      // [STAGES]
+  uint64_t* cfull = bars + 4;      // [STAGES] (FP32: converted)
+  uint64_t* d1full = bars + 6;     // [2]
+  uint64_t* d1empty = bars + 8;    // [2]
+  uint64_t* ktfull = bars + 10;    // [2]
+  uint64_t* ktempty = bars + 12;   // [2]
+  uint64_t* wnfull = bars + 14;
+  uint64_t* wnempty = bars + 15;
+  uint64_t* d2full = bars + 16;
+  uint64_t* d2empty = bars + 17;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 20);
+  float* red = reinterpret_cast<float*>(bars + 24);                // [4][64]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(red + 4 * 64);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+      mbar_init(smem_u32(&cfull[i]), 4);
+      mbar_init(smem_u32(&d1full[i]), 1);
+      mbar_init(smem_u32(&d1empty[i]), 4);
+      mbar_init(smem_u32(&ktfull[i]), 4);
+      mbar_init(smem_u32(&ktempty[i]), 1);
+    }
+    mbar_init(smem_u32(wnfull), 1);
+    mbar_init(smem_u32(wnempty), 1);
+    mbar_init(smem_u32(d2full), 1);
+    mbar_init(smem_u32(d2empty), 4);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  unsigned* status = a.status;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmY);
+      prefetch_tmap(&tmW);
+      const uint64_t pol = policy_evict_first();
+      uint32_t it = 0, un = 0;
+      for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
+        const int pc = (int)(u % a.PC);
+        const int kr = (int)((u / a.PC) % a.KR);
+        const int jt = (int)(u / ((int64_t)a.PC * a.KR));
+        const int64_t p0 = (int64_t)pc * a.PCW;
+        const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+        const int k0 = kr * a.KRW, j0 = jt * 128;
+        // resident W block of this column range
+        if (!mbar_wait(smem_u32(wnempty), (un & 1) ^ 1, status)) { ok = false; break; }
+        mbar_expect_tx(smem_u32(wnfull), 2 * a.KS * wn_box);
+        for (int b = 0; b < 2 * a.KS; ++b)
+          tma_load_3d(smem_u32(wn_base + b * wn_box), &tmW, k0 + 64 * b, 0, 0, smem_u32(wnfull));
+        for (int64_t p = p0; p < p1 && ok; ++p) {
+          for (int st = 0; st < a.KS; ++st, ++it) {
+            const int s = it & 1;
+            const uint32_t n = it >> 1;
+            if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
+            unsigned char* dst = st_base + s * Lay::STAGE_BYTES;
+            mbar_expect_tx(smem_u32(&full[s]), Lay::STAGE_BYTES);
+            const int kc = k0 + 128 * st;
+            if (F32) {
+              for (int q = 0; q < 4; ++q)
+                tma_load_3d_hint(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 32 * q, j0, (int)p, smem_u32(&full[s]),
+                                 pol);
+            } else {
+              for (int q = 0; q < 2; ++q)
+                tma_load_3d_hint(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 64 * q, j0, (int)p, smem_u32(&full[s]),
+                                 pol);
+            }
+          }
+        }
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(128, a.N1, 0, 0);
+      const uint32_t id2 = idesc_bf16(128, 64, 1, 1);
+      const uint32_t d2col = 2 * a.d1_cols;
+      uint32_t it = 0, pi = 0, un = 0;
+      for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
+        const int pc = (int)(u % a.PC);
+        const int64_t p0 = (int64_t)pc * a.PCW;
+        const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+        if (!mbar_wait(smem_u32(wnfull), un & 1, status)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(d2empty), (un & 1) ^ 1, status)) { ok = false; break; }
+        tc_fence_after();
+        bool first_p = true;
+        for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
+          const int db = pi & 1, kb = pi & 1;
+          if (!mbar_wait(smem_u32(&d1empty[db]), ((pi >> 1) & 1) ^ 1, status)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&ktfull[kb]), (pi >> 1) & 1, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d1 = tmem + db * a.d1_cols;
+          const uint32_t kt = smem_u32(kt_base + kb * Lay::KT_BYTES);
+          for (int st = 0; st < a.KS; ++st, ++it) {
+            const int s = it & 1;
+            const uint32_t n = it >> 1;
+            if (!mbar_wait(smem_u32(F32 ? &cfull[s] : &full[s]), n & 1, status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sb = smem_u32(st_base + s * Lay::STAGE_BYTES);
+            const int nparts = F32 ? 2 : 1;
+            for (int part = 0; part < nparts; ++part) {
+              const uint32_t ab = sb + part * BOX_BYTES;  // hi at +0, lo at +16 KB (FP32 layout)
+              // G1: 8 K-steps of 16 columns (two 64-column boxes)
+              for (int kk = 0; kk < 8; ++kk) {
+                const uint32_t aaddr = ab + (kk >> 2) * Lay::BOX_STRIDE + (kk & 3) * 32;
+                const uint32_t baddr = smem_u32(wn_base) + (2 * st + (kk >> 2)) * wn_box + (kk & 3) * 32;
+                mma_bf16(d1, smem_desc(aaddr, 16, 1024, SW128), smem_desc(baddr, 16, 1024, SW128), id1,
+                         (st | kk | part) != 0);
+              }
+              // G2: 8 K-steps of 16 rows; A = the same tile read MN-major
+              for (int kk = 0; kk < 8; ++kk) {
+                const uint32_t aaddr = ab + kk * 2048;
+                const uint32_t baddr = kt + kk * 2048;
+                mma_bf16(tmem + d2col + st * 64, smem_desc(aaddr, Lay::BOX_STRIDE, 1024, SW128),
+                         smem_desc(baddr, 16, 1024, SW128), id2, !(first_p && kk == 0 && part == 0));
+              }
+            }
+            umma_commit(smem_u32(&empty[s]));
+          }
+          umma_commit(smem_u32(&d1full[db]));
+          umma_commit(smem_u32(&ktempty[kb]));
+          first_p = false;
+        }
+        umma_commit(smem_u32(d2full));
+        umma_commit(smem_u32(wnempty));
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ epilogue (4 warps)
+    const int q = warp & 3;
+    const int jl = 32 * q + lane;  // TMEM lane = tile row j (D1) / column k (D2)
+    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    const int Nm = a.N;
+    const int nj = Nm - 2;         // tile row mode
+    const int nl = Nm - 1;         // contiguous mode
+    const int Rj = a.Rt[nj];
+    uint32_t pi = 0, un = 0;
+    for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
+      const int pc = (int)(u % a.PC);
+      const int kr = (int)((u / a.PC) % a.KR);
+      const int jt = (int)(u / ((int64_t)a.PC * a.KR));
+      const int64_t p0 = (int64_t)pc * a.PCW;
+      const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+      const int j0 = jt * 128;
+      const int jj = j0 + jl;
+      const bool vj = jj < a.J;
+      float* up = a.part + u * a.ustride;
+      float accj[64];
+#pragma unroll
+      for (int r = 0; r < 64; ++r) accj[r] = 0.f;
+      // K_p rows for G2 (row j of the tile), MN-major [j][r], swizzled; the
+      // tile of p+1 is written before D1 of p is read so the MMA runs ahead
+      auto gen_k = [&](int64_t pp, uint32_t pidx) -> bool {
+        const int kb = pidx & 1;
+        if (!mbar_wait(smem_u32(&ktempty[kb]), ((pidx >> 1) & 1) ^ 1, status)) return false;
+        int kidx[TDK_MAX_MODES];
+        {
+          int64_t rem = pp;
+          for (int k = Nm - 3; k >= 0; --k) {
+            kidx[k] = (int)(rem % a.I[k]);
+            rem /= a.I[k];
+          }
+        }
+        unsigned char* row = kt_base + kb * SkLayout<F32>::KT_BYTES + jl * 128;
+        const float* wj = a.Wf[nl][nj] + (int64_t)(vj ? jj : 0) * a.RtL;
+        const int ph = jl & 7;
+        const int ncols = a.hilo ? 32 : 64;
+        float x[64];
+#pragma unroll
+        for (int r = 0; r < 64; ++r) {
+          float v = 0.f;
+          if (r < ncols && r < a.RtL && vj) {
+            v = __ldg(wj + r);
+            for (int k = 0; k < Nm - 2; ++k) v *= __ldg(a.Wf[nl][k] + (int64_t)kidx[k] * a.RtL + r);
+          }
+          x[r] = v;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          uint32_t w4[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float v0, v1;
+            if (!a.hilo || c < 4) {
+              v0 = x[8 * c + 2 * e];
+              v1 = x[8 * c + 2 * e + 1];
+            } else {
+              float s0 = x[8 * (c - 4) + 2 * e], s1 = x[8 * (c - 4) + 2 * e + 1];
+              v0 = s0 - __bfloat162float(__float2bfloat16_rn(s0));
+              v1 = s1 - __bfloat162float(__float2bfloat16_rn(s1));
+            }
+            w4[e] = pack_bf16x2(v0, v1);
+          }
+          *reinterpret_cast<uint4*>(row + ((c ^ ph) << 4)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&ktfull[kb]));
+        return true;
+      };
+      if (!gen_k(p0, pi)) { ok = false; break; }
+      for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
+        const int db = pi & 1;
+        int idx[TDK_MAX_MODES];
+        {
+          int64_t rem = p;
+          for (int k = Nm - 3; k >= 0; --k) {
+            idx[k] = (int)(rem % a.I[k]);
+            rem /= a.I[k];
+          }
+        }
+        if (p + 1 < p1 && !gen_k(p + 1, pi + 1)) { ok = false; break; }
+        // ---- D1 -> sketches of modes < N
+        if (!mbar_wait(smem_u32(&d1full[db]), (pi >> 1) & 1, status)) { ok = false; break; }
+        tc_fence_after();
+        for (int n = 0; n <= nj; ++n) {
+          const int Rn = a.Rt[n];
+          float v[64];
+#pragma unroll
+          for (int c16 = 0; c16 < 4; ++c16) {
+            if (c16 * 16 < a.Rtp[n]) {
+              tmem_ld16(tmem + db * a.d1_cols + a.off[n] + c16 * 16 + lane_addr, v + c16 * 16);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) v[c16 * 16 + e] = 0.f;
+            }
+          }
+          tmem_wait_ld();
+          if (n == nj) {
+            // row mode: per-lane accumulation, coefficient from the outer indices
+#pragma unroll
+            for (int r = 0; r < 64; ++r) {
+              if (r < Rn) {
+                float cf = 1.f;
+                for (int k = 0; k < Nm - 2; ++k) cf *= __ldg(a.Wf[n][k] + (int64_t)idx[k] * Rn + r);
+                accj[r] = fmaf(v[r], cf, accj[r]);
+              }
+            }
+          } else {
+            // constant mode over the tile: weight by W_{N-1}^(n)[j] and reduce over 128 lanes
+            const float* wj = a.Wf[n][nj] + (int64_t)(vj ? jj : 0) * Rn;
+#pragma unroll
+            for (int r = 0; r < 64; ++r) v[r] = (vj && r < Rn) ? v[r] * __ldg(wj + r) : 0.f;
+            // butterfly transpose-reduce: each lane ends with 2 of the 64 sums
+#pragma unroll
+            for (int o = 16, h = 32; o >= 1; o >>= 1, h >>= 1) {
+              const bool up = (lane & o) != 0;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                if (i < h) {
+                  float send = up ? v[i] : v[i + h];
+                  float keep = up ? v[i + h] : v[i];
+                  v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+              }
+            }
+            const int bse = ((lane >> 4) & 1) * 32 + ((lane >> 3) & 1) * 16 + ((lane >> 2) & 1) * 8 +
+                            ((lane >> 1) & 1) * 4 + (lane & 1) * 2;
+            red[q * 64 + bse] = v[0];
+            red[q * 64 + bse + 1] = v[1];
+            named_bar(1, 128);
+            if (jl < Rn) {
+              float s = red[jl] + red[64 + jl] + red[128 + jl] + red[192 + jl];
+              for (int k = 0; k < Nm - 2; ++k)
+                if (k != n) s *= __ldg(a.Wf[n][k] + (int64_t)idx[k] * Rn + jl);
+              up[a.poff_p[n] + (p - p0) * Rn + jl] = s;
+            }
+            named_bar(1, 128);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&d1empty[db]));
+      }
+      if (!ok) break;
+      // ---- unit end: row-mode partial and the contiguous mode from D2
+      if (vj)
+        for (int r = 0; r < Rj; ++r) up[a.poff_j + (int64_t)jl * Rj + r] = accj[r];
+      if (!mbar_wait(smem_u32(d2full), un & 1, status)) { ok = false; break; }
+      tc_fence_after();
+      for (int st = 0; st < a.KS; ++st) {
+        float v[64];
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16)
+          tmem_ld16(tmem + 2 * a.d1_cols + st * 64 + c16 * 16 + lane_addr, v + c16 * 16);
+        tmem_wait_ld();
+        const int kloc = 128 * st + jl;
+        if (kr * a.KRW + kloc < a.L) {
+          for (int r = 0; r < a.RtL; ++r) {
+            float z = v[r];
+            if (a.hilo) z += v[32 + r];
+            up[a.poff_last + (int64_t)kloc * a.RtL + r] = z;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(d2empty));
+    }
+    if (!ok) *abort_flag = 1;
+  } else if (F32) {
+    // ------------------------------------------------------------ converters (FP32 data)
+    const int q = warp - 6;
+    const int r = 32 * q + lane;
+    uint32_t it = 0;
+    for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const int pc = (int)(u % a.PC);
+      const int64_t p0 = (int64_t)pc * a.PCW;
+      const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+      for (int64_t p = p0; p < p1 && ok; ++p) {
+        for (int st = 0; st < a.KS; ++st, ++it) {
+          const int s = it & 1;
+          const uint32_t n = it >> 1;
+          if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
+          unsigned char* sb = st_base + s * SkLayout<true>::STAGE_BYTES;
+          for (int h = 0; h < 2; ++h)
+            split_row64(sb + h * 2 * BOX_BYTES + r * 128, sb + (h * 2 + 1) * BOX_BYTES + r * 128, r);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&cfull[s]));
+        }
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// fixed-order FP64 reduction of the unit partials into Z (packed by zoff)
+struct RedArgs {
+  SkArgs s;
+  int64_t zoff[TDK_MAX_MODES + 1];
+  int64_t pstride[TDK_MAX_MODES];  // strides of p over the outer modes
+};
+
+__global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
+  const SkArgs& a = ra.s;
+  const int N = a.N, nj = N - 2, nl = N - 1;
+  const int64_t total = ra.zoff[N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (e >= ra.zoff[n + 1]) ++n;
+    const int Rn = a.Rt[n];
+    const int64_t i = (e - ra.zoff[n]) / Rn;
+    const int r = (int)((e - ra.zoff[n]) % Rn);
+    double s = 0.0;
+    if (n == nl) {
+      const int kr = (int)(i / a.KRW);
+      const int64_t kl = i - (int64_t)kr * a.KRW;
+      for (int jt = 0; jt < a.JT; ++jt)
+        for (int pc = 0; pc < a.PC; ++pc) {
+          const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
+          s += (double)a.part[u * a.ustride + a.poff_last + kl * Rn + r];
+        }
+    } else if (n == nj) {
+      const int jt = (int)(i / 128);
+      const int64_t jl = i - (int64_t)jt * 128;
+      for (int kr = 0; kr < a.KR; ++kr)
+        for (int pc = 0; pc < a.PC; ++pc) {
+          const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
+          s += (double)a.part[u * a.ustride + a.poff_j + jl * Rn + r];
+        }
+    } else {
+      // every p with i_n(p) = i: enumerate the other outer indices
+      int64_t cnt = a.P / a.I[n];
+      for (int64_t o = 0; o < cnt; ++o) {
+        int64_t rem = o, p = i * ra.pstride[n];
+        for (int k = N - 3; k >= 0; --k) {
+          if (k == n) continue;
+          p += (rem % a.I[k]) * ra.pstride[k];
+          rem /= a.I[k];
+        }
+        const int pc = (int)(p / a.PCW);
+        const int64_t pl = p - (int64_t)pc * a.PCW;
+        for (int jt = 0; jt < a.JT; ++jt)
+          for (int kr = 0; kr < a.KR; ++kr) {
+            const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
+            s += (double)a.part[u * a.ustride + a.poff_p[n] + pl * Rn + r];
+          }
+      }
+    }
+    Z[e] = s;
+  }
+}
+
+__global__ void w_to_f32(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (float)s[e];
+}
+
+// WN^T block: rows = channels of modes < N-1 (each padded to 16), columns = L
+__global__ void build_wn(const double* const* __restrict__ Wl, SkArgs a, int ldw, __nv_bfloat16* __restrict__ out) {
+  const int64_t total = (int64_t)a.N1 * ldw;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ldw);
+    const int k = (int)(e % ldw);
+    float v = 0.f;
+    int n = 0;
+    while (n + 1 < a.N - 1 && c >= a.off[n + 1]) ++n;
+    const int r = c - a.off[n];
+    if (r < a.Rt[n] && k < a.L) v = (float)Wl[n][(int64_t)k * a.Rt[n] + r];
+    out[e] = __float2bfloat16_rn(v);
+  }
+}
+
+// =====================================================================
+//                               CORE (first TTM)
+// =====================================================================
+struct CoArgs {
+  int64_t M;     // rows
+  int L;         // contiguous mode
+  int KC;        // 64-column chunks
+  int NB;        // B rows = 2 * Rtp  (hi | lo)
+  int Rt, Rtp;
+  int64_t ntiles;
+  float* X;      // [M][Rt]
+  double* nrm_part;
+  unsigned* status;
+};
+
+template <bool F32>
+struct CoLayout {
+  static constexpr int STAGES = F32 ? 4 : 6;
+  static constexpr uint32_t Y_BYTES = F32 ? 32 * KB : 16 * KB;  // 128 rows x 64 columns
+};
+
+template <bool F32>
+__global__ void __launch_bounds__(F32 ? 320 : 192, 1)
+    tc_core_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmU, const CoArgs a) {
+  using Lay = CoLayout<F32>;
+  constexpr int S = Lay::STAGES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t b_bytes = (uint32_t)a.NB * 128u;
+  const uint32_t stage_bytes = Lay::Y_BYTES + ((b_bytes + 1023) & ~1023u);
+  unsigned char* st_base = base;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(st_base + S * stage_bytes);
+  uint64_t* full = bars;            // [S]
+  uint64_t* empty = bars + S;       // [S]
+  uint64_t* cfull = bars + 2 * S;   // [S]
+  uint64_t* dfull = bars + 3 * S;   // [2]
+  uint64_t* dempty = bars + 3 * S + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
+  double* nred = reinterpret_cast<double*>(bars + 3 * S + 6);  // [10]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), F32 ? 1 : 5);
+      mbar_init(smem_u32(&cfull[i]), 4);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&dfull[i]), 1);
+      mbar_init(smem_u32(&dempty[i]), 4);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  unsigned* status = a.status;
+  bool ok = true;
+  float nrm = 0.f, nrm_c = 0.f;  // Kahan sum of y^2 for this thread's rows
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tmY);
+      prefetch_tmap(&tmU);
+      const uint64_t pol = policy_evict_first();
+      uint32_t it = 0;
+      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t n = it / S;
+          if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
+          unsigned char* dst = st_base + s * stage_bytes;
+          mbar_expect_tx(smem_u32(&full[s]), Lay::Y_BYTES + b_bytes);
+          if (F32) {
+            tma_load_3d_hint(smem_u32(dst), &tmY, kc * 64, (int)(t * 128), 0, smem_u32(&full[s]), pol);
+            tma_load_3d_hint(smem_u32(dst + BOX_BYTES), &tmY, kc * 64 + 32, (int)(t * 128), 0, smem_u32(&full[s]),
+                             pol);
+          } else {
+            tma_load_3d_hint(smem_u32(dst), &tmY, kc * 64, (int)(t * 128), 0, smem_u32(&full[s]), pol);
+          }
+          tma_load_3d(smem_u32(dst + Lay::Y_BYTES), &tmU, kc * 64, 0, 0, smem_u32(&full[s]));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc_bf16(128, a.NB, 0, 0);
+      uint32_t it = 0, tl = 0;
+      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tl) {
+        const int db = tl & 1;
+        if (!mbar_wait(smem_u32(&dempty[db]), ((tl >> 1) & 1) ^ 1, status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + db * 128;
+        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t n = it / S;
+          if (!mbar_wait(smem_u32(F32 ? &cfull[s] : &full[s]), n & 1, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sb = smem_u32(st_base + s * stage_bytes);
+          const uint32_t bb = sb + Lay::Y_BYTES;
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t bd = smem_desc(bb + kk * 32, 16, 1024, SW128);
+            mma_bf16(d, smem_desc(sb + kk * 32, 16, 1024, SW128), bd, id, (kc | kk) != 0);
+            if (F32) mma_bf16(d, smem_desc(sb + BOX_BYTES + kk * 32, 16, 1024, SW128), bd, id, 1);
+          }
+          umma_commit(smem_u32(&empty[s]));
+        }
+        umma_commit(smem_u32(&dfull[db]));
+      }
+    }
+  } else if (warp < 6) {
+    // epilogue: X_1 rows = hi + lo halves of D; BF16 data also sums y^2 per stage
+    const int q = warp & 3;
+    const int rl = 32 * q + lane;
+    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    uint32_t it = 0, tl = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tl) {
+      if (!F32) {
+        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t n = it / S;
+          if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
+          const unsigned char* row = st_base + s * stage_bytes + rl * 128;
+          float part = 0.f;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint4 w = *reinterpret_cast<const uint4*>(row + c * 16);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
+              part = fmaf(lo, lo, part);
+              part = fmaf(hi, hi, part);
+            }
+          }
+          float y = part - nrm_c;
+          float tt = nrm + y;
+          nrm_c = (tt - nrm) - y;
+          nrm = tt;
+          // the stage is refilled by TMA (async proxy): order these generic
+          // reads before that write
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+      }
+      const int db = tl & 1;
+      if (!mbar_wait(smem_u32(&dfull[db]), (tl >> 1) & 1, status)) { ok = false; break; }
+      tc_fence_after();
+      const int64_t row = t * 128 + rl;
+      float v[128];
+#pragma unroll
+      for (int c16 = 0; c16 < 8; ++c16) {
+        if (c16 * 16 < a.NB) tmem_ld16(tmem + db * 128 + c16 * 16 + lane_addr, v + c16 * 16);
+      }
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&dempty[db]));
+      if (row < a.M) {
+        float* xr = a.X + row * a.Rt;
+#pragma unroll
+        for (int r = 0; r < 64; ++r)
+          if (r < a.Rt) xr[r] = v[r] + v[a.Rtp + r];
+      }
+    }
+  } else if (F32) {
+    const int q = warp - 6;
+    const int r = 32 * q + lane;
+    uint32_t it = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      for (int kc = 0; kc < a.KC; ++kc, ++it) {
+        const int s = it % S;
+        const uint32_t n = it / S;
+        if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
+        unsigned char* sb = st_base + s * stage_bytes;
+        float part = split_row64(sb + r * 128, sb + BOX_BYTES + r * 128, r);
+        float y = part - nrm_c;
+        float tt = nrm + y;
+        nrm_c = (tt - nrm) - y;
+        nrm = tt;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&cfull[s]));
+      }
+    }
+  }
+  // per-CTA ||Y||^2 from the threads that read the tiles
+  double mine = (double)nrm - (double)nrm_c;
+  mine = warp_sum(mine);
+  if (lane == 0) nred[warp] = mine;
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += nred[w];
+    a.nrm_part[blockIdx.x] = s;
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+// [U_hi | U_lo]^T as BF16 rows (channel-major, columns = L padded to ldu)
+__global__ void build_u_hilo(const double* __restrict__ U, int L, int Rt, int Rtp, int ldu,
+                             __nv_bfloat16* __restrict__ out) {
+  const int64_t total = (int64_t)2 * Rtp * ldu;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ldu);
+    const int k = (int)(e % ldu);
+    const int r = c < Rtp ? c : c - Rtp;
+    float v = 0.f;
+    if (r < Rt && k < L) {
+      const double x = U[(int64_t)k * Rt + r];
+      const float hi = __bfloat162float(__float2bfloat16_rn((float)x));
+      v = (c < Rtp) ? hi : (float)(x - (double)hi);
+    }
+    out[e] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void sum_doubles(const double* __restrict__ parts, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    *out = v;
+  }
+}
+
+template <class T>
+__global__ void cvt_u(const double* __restrict__ s, T* __restrict__ d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (T)s[e];
+}
+
+bool tc_shape_ok(const Geom& g, int dtype) {
+  const int es = dtype == TDK_BF16 ? 2 : 4;
+  if ((g.L * es) % 16 != 0) return false;  // TMA row stride
+  for (int n = 0; n < g.N; ++n)
+    if (g.Rt[n] > 64) return false;
+  return true;
+}
+
+}  // namespace
+
+template <class T>
+int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1);
+
+// ---------------------------------------------------------------- host: sketch
+int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[], double* Zdst) {
+  if (g.N < 3 || !tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
+  const bool f32 = dtype == TDK_F32;
+  const int N = g.N, nj = N - 2, nl = N - 1;
+  SkArgs a{};
+  a.N = N;
+  for (int n = 0; n < N; ++n) {
+    a.I[n] = g.I[n];
+    a.Rt[n] = g.Rt[n];
+    a.Rtp[n] = (g.Rt[n] + 15) / 16 * 16;
+  }
+  a.L = (int)g.I[nl];
+  a.J = (int)g.I[nj];
+  a.P = 1;
+  for (int k = 0; k < nj; ++k) a.P *= g.I[k];
+  int N1 = 0;
+  for (int n = 0; n <= nj; ++n) {
+    a.off[n] = N1;
+    N1 += a.Rtp[n];
+  }
+  a.N1 = N1;
+  if (N1 > 256) return TDK_ENOTSUP;
+  a.RtL = g.Rt[nl];
+  a.hilo = (f32 && a.RtL <= 32) ? 1 : 0;
+  if (!f32 && a.RtL > 64) return TDK_ENOTSUP;
+  a.d1_cols = (N1 + 31) / 32 * 32;
+  // columns per unit: as many 128-column blocks as TMEM leaves room for (<= 2)
+  int ks_max = (512 - 2 * a.d1_cols) / 64;
+  if (ks_max < 1) return TDK_ENOTSUP;
+  a.KS = std::min(2, std::min(ks_max, (a.L + 127) / 128));
+  a.KRW = 128 * a.KS;
+  a.JT = (a.J + 127) / 128;
+  a.KR = (a.L + a.KRW - 1) / a.KRW;
+  const int64_t base_units = (int64_t)a.JT * a.KR;
+  int64_t want = 8LL * ctx->num_sms;
+  int64_t PC = (want + base_units - 1) / base_units;
+  if (PC > a.P) PC = a.P;
+  if (PC < 1) PC = 1;
+  a.PCW = (a.P + PC - 1) / PC;
+  a.PC = (int)((a.P + a.PCW - 1) / a.PCW);
+  a.nunits = base_units * a.PC;
+  a.poff_last = 0;
+  a.poff_j = (int64_t)a.KRW * a.RtL;
+  int64_t o = a.poff_j + 128LL * g.Rt[nj];
+  for (int n = 0; n < nj; ++n) {
+    a.poff_p[n] = o;
+    o += a.PCW * g.Rt[n];
+  }
+  a.ustride = (o + 63) / 64 * 64;
+  a.status = ctx->d_status;
+
+  // workspace: FP32 W copies, WN^T (BF16), partials
+  const int ldw = (a.L + 7) / 8 * 8;
+  Planner pl;
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k)
+      if (k != n) pl.take<float>((size_t)g.I[k] * g.Rt[n]);
+  pl.take<__nv_bfloat16>((size_t)N1 * ldw);
+  pl.take<const double*>(TDK_MAX_MODES);
+  pl.take<float>((size_t)a.nunits * a.ustride);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k) {
+      a.Wf[n][k] = nullptr;
+      if (k == n) continue;
+      float* d = cv.take<float>((size_t)g.I[k] * g.Rt[n]);
+      w_to_f32<<<64, 256, 0, ctx->stream>>>(W[n * N + k], d, g.I[k] * g.Rt[n]);
+      TDK_LAUNCH_CHECK(ctx);
+      a.Wf[n][k] = d;
+    }
+  __nv_bfloat16* wn = cv.take<__nv_bfloat16>((size_t)N1 * ldw);
+  const double** wl = cv.take<const double*>(TDK_MAX_MODES);
+  {
+    const double* hw[TDK_MAX_MODES] = {};
+    for (int n = 0; n <= nj; ++n) hw[n] = W[n * N + nl];
+    TDK_CUDA_TRY(cudaMemcpyAsync(wl, hw, sizeof(hw), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  build_wn<<<128, 256, 0, ctx->stream>>>(wl, a, ldw, wn);
+  TDK_LAUNCH_CHECK(ctx);
+  a.part = cv.take<float>((size_t)a.nunits * a.ustride);
+
+  CUtensorMap tmY, tmW;
+  {
+    const int es = f32 ? 4 : 2;
+    uint64_t dims[3] = {(uint64_t)a.L, (uint64_t)a.J, (uint64_t)a.P};
+    uint64_t str[2] = {(uint64_t)a.L * es, (uint64_t)a.L * a.J * es};
+    uint32_t box[3] = {f32 ? 32u : 64u, 128u, 1u};
+    rc = encode_tmap(&tmY, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims,
+                     str, box, true);
+    if (rc) return rc;
+    uint64_t wd[3] = {(uint64_t)a.L, (uint64_t)N1, 1};
+    uint64_t ws_[2] = {(uint64_t)ldw * 2, (uint64_t)ldw * 2 * N1};
+    uint32_t wb[3] = {64u, (uint32_t)N1, 1u};
+    rc = encode_tmap(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wn, wd, ws_, wb, true);
+    if (rc) return rc;
+  }
+  const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
+  size_t smem = 1024 + 2 * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 + 4 * 64 * 4 + 64;
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
+  int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
+  {
+    ProfScope ps(ctx, 0);
+    if (f32) {
+      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tc_sketch_kernel<true><<<grid, 320, smem, ctx->stream>>>(tmY, tmW, a);
+    } else {
+      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tc_sketch_kernel<false><<<grid, 192, smem, ctx->stream>>>(tmY, tmW, a);
+    }
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  RedArgs ra{};
+  ra.s = a;
+  for (int n = 0; n <= N; ++n) ra.zoff[n] = g.zoff[n];
+  {
+    int64_t s = 1;
+    for (int k = nj - 1; k >= 0; --k) {
+      ra.pstride[k] = s;
+      s *= g.I[k];
+    }
+  }
+  sketch_tc_reduce<<<256, 256, 0, ctx->stream>>>(ra, Zdst);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
+// ---------------------------------------------------------------- host: core
+int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* Gv,
+            double* normY2) {
+  if (!tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
+  const bool f32 = dtype == TDK_F32;
+  const int N = g.N;
+  CoArgs a{};
+  a.M = g.M;
+  a.L = (int)g.L;
+  a.KC = (a.L + 63) / 64;
+  a.Rt = g.Rt[N - 1];
+  a.Rtp = (a.Rt + 15) / 16 * 16;
+  a.NB = 2 * a.Rtp;
+  a.ntiles = (g.M + 127) / 128;
+  a.status = ctx->d_status;
+  int grid = (int)std::min<int64_t>(a.ntiles, ctx->num_sms);
+  const int ldu = (a.L + 7) / 8 * 8;
+  int64_t tmpsz = 0;
+  {
+    int64_t Bd = a.Rt;
+    for (int m = N - 2; m >= 1; --m) {
+      int64_t A = 1;
+      for (int k = 0; k < m; ++k) A *= g.I[k];
+      tmpsz = std::max<int64_t>(tmpsz, A * g.Rt[m] * Bd);
+      Bd *= g.Rt[m];
+    }
+  }
+  Planner pl;
+  pl.take<__nv_bfloat16>((size_t)a.NB * ldu);
+  for (int n = 0; n < N; ++n) pl.take<float>((size_t)g.I[n] * g.Rt[n]);
+  pl.take<float>((size_t)g.M * a.Rt);
+  pl.take<float>((size_t)tmpsz);
+  pl.take<float>((size_t)tmpsz);
+  pl.take<double>((size_t)grid);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  __nv_bfloat16* ub = cv.take<__nv_bfloat16>((size_t)a.NB * ldu);
+  build_u_hilo<<<128, 256, 0, ctx->stream>>>(U[N - 1], a.L, a.Rt, a.Rtp, ldu, ub);
+  TDK_LAUNCH_CHECK(ctx);
+  float* Ut[TDK_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    Ut[n] = cv.take<float>((size_t)g.I[n] * g.Rt[n]);
+    cvt_u<float><<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  a.X = cv.take<float>((size_t)g.M * a.Rt);
+  float* tmp0 = cv.take<float>((size_t)tmpsz);
+  float* tmp1 = cv.take<float>((size_t)tmpsz);
+  a.nrm_part = cv.take<double>((size_t)grid);
+
+  CUtensorMap tmY, tmU;
+  {
+    const int es = f32 ? 4 : 2;
+    uint64_t dims[3] = {(uint64_t)a.L, (uint64_t)g.M, 1};
+    uint64_t str[2] = {(uint64_t)a.L * es, (uint64_t)a.L * es * (uint64_t)g.M};
+    uint32_t box[3] = {f32 ? 32u : 64u, 128u, 1u};
+    rc = encode_tmap(&tmY, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims,
+                     str, box, true);
+    if (rc) return rc;
+    uint64_t ud[3] = {(uint64_t)a.L, (uint64_t)a.NB, 1};
+    uint64_t us[2] = {(uint64_t)ldu * 2, (uint64_t)ldu * 2 * a.NB};
+    uint32_t ubx[3] = {64u, (uint32_t)a.NB, 1u};
+    rc = encode_tmap(&tmU, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ub, ud, us, ubx, true);
+    if (rc) return rc;
+  }
+  const uint32_t ybytes = f32 ? CoLayout<true>::Y_BYTES : CoLayout<false>::Y_BYTES;
+  const uint32_t stage = ybytes + ((a.NB * 128 + 1023) & ~1023);
+  const int S = f32 ? CoLayout<true>::STAGES : CoLayout<false>::STAGES;
+  size_t smem = 1024 + (size_t)S * stage + 8 * (3 * S + 6) + 8 * 16;
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
+  {
+    ProfScope ps(ctx, 1);
+    if (f32) {
+      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_core_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tc_core_kernel<true><<<grid, 320, smem, ctx->stream>>>(tmY, tmU, a);
+    } else {
+      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_core_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tc_core_kernel<false><<<grid, 192, smem, ctx->stream>>>(tmY, tmU, a);
+    }
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  if (normY2) {
+    sum_doubles<<<1, 256, 0, ctx->stream>>>(a.nrm_part, grid, normY2);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  return core_chain_rest<float>(ctx, g, a.X, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1);
+}
+
+}  // namespace tdk

@@ -190,3 +190,77 @@ def test_end_to_end_scaled_fp32(tdk, ctx, dtype):
     e_gpu = recon_err(float(nrm.item()), host(G))
     e_or = recon_err(ref["normY2"], ref["G"])
     assert abs(e_gpu - e_or) <= 1e-5, (e_gpu, e_or)
+
+
+# ---------------------------------------------------------------- tensor-core form
+# Shapes for the tcgen05 path: the contiguous mode times the element size is a
+# multiple of 16 bytes (TMA row pitch).  They span ragged j-tiles (128 rows),
+# ragged column ranges (256) and several p values.
+TC_SHAPES = [
+    (67, 45, 136),
+    (9, 11, 7, 16),
+    (5, 200, 264),
+    (3, 130, 512),
+]
+# rounding of one BF16 operand (RNE): 2^-9 relative; FP32 data split hi+lo and
+# KRP rows split hi+lo (sketch width <= 32): residual below 2^-17.
+U_BF16 = 2.0 ** -9
+
+
+def _tc_tol(dtype, mode_is_last, Rt_last):
+    acc = 2e-5  # FP32 accumulation, as for the CUDA-core form
+    if dtype == "bf16":
+        return acc + (U_BF16 if mode_is_last else 0.0)
+    return acc + (2.0 ** -15 if (mode_is_last and Rt_last > 32) else 2.0 ** -16)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("shape", TC_SHAPES)
+def test_tc_sketch_matches_oracle(tdk, ctx, shape, dtype):
+    ranks = [min(5, s - 2) for s in shape]
+    p = 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=13, dtype=dtype)
+    U, Z = tdk.tucker_sketch(ctx, dev_tensor(Y, dtype), dev_W(W), ranks, p, "tc", want_Z=True)
+    assert ctx.sync_status() == 0
+    Zo, _ = oracle.sketch(Y, W)
+    bnd = sketch_abs_bound(Y, W)
+    N = len(shape)
+    for n in range(N):
+        tol = _tc_tol(dtype, n == N - 1, ranks[-1] + p)
+        err = np.abs(host(Z[n]) - Zo[n])
+        assert np.all(err <= tol * bnd[n] + 1e-30), (n, float((err / bnd[n]).max()), tol)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("shape", TC_SHAPES)
+def test_tc_core_matches_oracle(tdk, ctx, shape, dtype):
+    ranks = [min(5, s - 2) for s in shape]
+    p = 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=17, dtype=dtype)
+    ref = oracle.rand_tucker(Y, W)
+    Ud = [dev_tensor(u, "f64") for u in ref["U"]]
+    G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), Ud, ranks, p, "tc")
+    assert ctx.sync_status() == 0
+    bnd = core_abs_bound(Y, ref["U"])
+    tol = 2e-5 + (2.0 ** -16 if dtype == "f32" else 2.0 ** -17)
+    err = np.abs(host(G) - ref["G"])
+    assert np.all(err <= tol * bnd), float((err / bnd).max())
+    assert math.isclose(float(nrm.item()), ref["normY2"], rel_tol=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_tc_end_to_end_scaled(tdk, ctx, dtype):
+    """Workload 2's data model at 128^3 on the tensor-core form: the
+    reconstruction error differs from the oracle's by <= 1e-5 (FP32 data) or
+    <= 1e-3 (BF16 data)."""
+    w = synth.scaled(synth.WORKLOADS["c2"], (128, 128, 128))
+    w.dtype = dtype
+    Y = synth.host_tensor(w)
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
+    ref = oracle.rand_tucker(Y, W)
+    Yd = dev_tensor(Y, dtype)
+    U, _ = tdk.tucker_sketch(ctx, Yd, dev_W(W), w.ranks, w.p, "tc")
+    G, nrm = tdk.tucker_core(ctx, Yd, U, w.ranks, w.p, "tc")
+    e_gpu = recon_err(float(nrm.item()), host(G))
+    e_or = recon_err(ref["normY2"], ref["G"])
+    assert abs(e_gpu - e_or) <= (1e-5 if dtype == "f32" else 1e-3), (e_gpu, e_or)

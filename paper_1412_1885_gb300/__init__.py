@@ -79,6 +79,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int64)]
         if hasattr(L, "tdk_ctx_test_fail_alloc"):
             L.tdk_ctx_test_fail_alloc.argtypes = [vp, ctypes.c_int]
+        if hasattr(L, "tdk_ctx_test_als_form"):
+            L.tdk_ctx_test_als_form.argtypes = [vp, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -164,6 +166,11 @@ class Context:
         _check(lib().tdk_ctx_profile_read(self._h, int(region), ctypes.byref(ms), ctypes.byref(n)),
                "tdk_ctx_profile_read")
         return ms.value, n.value
+
+    def set_als_form(self, multi_kernel: bool):
+        """Select the ALS form: one persistent kernel (default) or one kernel
+        per step (also the fallback for cores that do not fit)."""
+        _check(lib().tdk_ctx_test_als_form(self._h, int(bool(multi_kernel))), "tdk_ctx_test_als_form")
 
     def close(self):
         if self._h:

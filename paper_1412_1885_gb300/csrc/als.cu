@@ -761,9 +761,57 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
 
 }  // namespace
 
+int als_finish(tdk_ctx* ctx, const Geom& g, int R, bool dbl, const void* const* Bw, const double* const* U,
+               const double* lam, double* const* Aw, double* const* B_io, double* const* A_io, double* lambda_out) {
+  cudaStream_t s = ctx->stream;
+  for (int n = 0; n < g.N; ++n) {
+    const double* lamp = (n == g.N - 1) ? lam : nullptr;
+    if (!Aw) {
+      if (dbl)
+        lift_kernel<double><<<128, 256, 0, s>>>(U[n], reinterpret_cast<const double*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
+                                                A_io[n], B_io[n]);
+      else
+        lift_kernel<float><<<128, 256, 0, s>>>(U[n], reinterpret_cast<const float*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
+                                               A_io[n], B_io[n]);
+      TDK_LAUNCH_CHECK(ctx);
+    } else {
+      scale_cols_kernel<<<128, 256, 0, s>>>(Aw[n], g.I[n], R, lamp, A_io[n]);
+      TDK_LAUNCH_CHECK(ctx);
+      if (dbl)
+        lift_kernel<double><<<1, 256, 0, s>>>(U[n], reinterpret_cast<const double*>(Bw[n]), 0, g.Rt[n], R, nullptr,
+                                              nullptr, B_io[n]);
+      else
+        lift_kernel<float><<<1, 256, 0, s>>>(U[n], reinterpret_cast<const float*>(Bw[n]), 0, g.Rt[n], R, nullptr,
+                                             nullptr, B_io[n]);
+      TDK_LAUNCH_CHECK(ctx);
+    }
+  }
+  if (lambda_out) {
+    copy_f64_kernel<<<1, 64, 0, s>>>(lam, lambda_out, R);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  return TDK_OK;
+}
+
+template <class T>
+int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], const double* normY2,
+                     const tdk_als_opts* o, double* const B_io[], double* const A_io[], double* lambda_out,
+                     tdk_als_report* rep);
+
 int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double* const U[], const double* normY2,
             const tdk_als_opts* o, double* const B_io[], double* const A_io[], double* lambda_out,
             tdk_als_report* rep) {
+  // one persistent cooperative kernel when the core fits; otherwise (or when a
+  // normal equation needs the pseudo-inverse) the kernel-per-step form
+  int rc = TDK_ENOTSUP;
+  if (!ctx->als_multi_kernel) {
+    rc = (dtype == TDK_F64)
+             ? als_persistent_t<double>(ctx, g, reinterpret_cast<const double*>(G), U, normY2, o, B_io, A_io,
+                                        lambda_out, rep)
+             : als_persistent_t<float>(ctx, g, reinterpret_cast<const float*>(G), U, normY2, o, B_io, A_io,
+                                       lambda_out, rep);
+  }
+  if (rc != TDK_ENOTSUP) return rc;
   if (dtype == TDK_F64)
     return als_run_t<double>(ctx, g, reinterpret_cast<const double*>(G), U, normY2, o, B_io, A_io, lambda_out, rep);
   return als_run_t<float>(ctx, g, reinterpret_cast<const float*>(G), U, normY2, o, B_io, A_io, lambda_out, rep);

@@ -1,0 +1,798 @@
+// FFCP sweep loop as ONE persistent cooperative kernel (Alg. 1, Eqs. 9, 11-13).
+//
+// Every CTA holds all normalised factors B_p and their Grams in shared memory.
+// Per mode n:
+//   1. each CTA forms T_n = HADAMARD_{p != n} Gram_p and its Cholesky factor in
+//      FP64 (redundantly, so nothing has to be broadcast);
+//   2. CTA c computes rows i = c, c+G, ... of H_n = G_(n) [KRP_{p != n} B_p]
+//      from the core slice G[.., i, ..] staged in shared memory, contracting
+//      one mode at a time (the last other mode first as a small GEMM, then
+//      weighted sums over the others), and solves its rows of B_n = H_n T_n^{-1}
+//      in FP64 (Eq. 13);
+//   3. grid barrier; every CTA reads the new rows, computes lambda, the
+//      normalised factor and its Gram -- identically, in the same order.
+// Nonnegative form: rows of H_n, barrier, rows of A_n = max(0, U_n H_n T_n^{-1})
+// (T_n from the Grams of the A_p), barrier, then lambda, the Gram of A_n and
+// B_n = U_n^T A_n.  After the last mode every CTA evaluates the same fit from
+// the Gram identities, so all CTAs stop on the same sweep.  A Cholesky pivot
+// at or below R*eps*max(diag) is seen by every CTA alike; they all leave and
+// the host reruns the call on the multi-kernel form, which has the
+// pseudo-inverse.  Barrier waits are bounded (timeout bit, then exit).
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+
+#include "tc_common.cuh"
+
+namespace tdk {
+
+// outputs of an ALS run: B_io <- B (normalised), A_io <- U_n B_n (or the
+// nonnegative A_n given in Aw), lambda absorbed into the last factor
+int als_finish(tdk_ctx* ctx, const Geom& g, int R, bool dbl, const void* const* Bw, const double* const* U,
+               const double* lam, double* const* Aw, double* const* B_io, double* const* A_io, double* lambda_out);
+
+namespace {
+
+constexpr int RMAXP = TDK_MAX_RANK;
+constexpr int NTP = 256;
+constexpr int ST_TIMEOUT = 0x100, ST_NEEDPINV = 0x200;
+
+struct PState {
+  int sweeps;
+  int converged;
+  int status;
+  int pad;
+  double fit;
+  double fitY;
+};
+
+template <class T>
+struct PArgs {
+  int N, R, nonneg, max_sweeps;
+  double tol;
+  int Rt[TDK_MAX_MODES];
+  int64_t I[TDK_MAX_MODES];
+  int64_t stride[TDK_MAX_MODES];
+  int64_t gnumel;
+  int64_t Qmax, Amax;           // shared buffers (entries)
+  const T* G;
+  const T* Uf[TDK_MAX_MODES];   // U_n in the working precision [I_n x Rt_n]
+  const double* init[TDK_MAX_MODES];  // B0 (Rt_n x R) or, nonneg, A0 (I_n x R)
+  T* Bnew;                      // [max(Rt,I) x R] update rows (unnormalised)
+  T* H;                         // [Rtmax x R]
+  T* Bout[TDK_MAX_MODES];       // final normalised B_n (CTA 0)
+  double* Aout[TDK_MAX_MODES];  // nonneg: final normalised A_n (CTA 0)
+  double* lam_out;
+  double* hist;
+  int hist_cap;
+  PState* st;
+  unsigned* bar;                // arrival counter, generation
+  unsigned* status;
+  const double* nG2;
+  const double* nY2;            // may be null
+  double* rpart;                // [grid] per-CTA residual partials
+  unsigned long long* prof;     // optional: cycles per phase, CTA 0 (null = off)
+};
+
+__device__ bool grid_sync(unsigned* bar, unsigned* status) {
+  __syncthreads();
+  __shared__ int fail;
+  if (threadIdx.x == 0) {
+    fail = 0;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = tc::globaltimer();
+      while (*gen == g) {
+        if (tc::globaltimer() - t0 > tc::WAIT_LIMIT_NS) {
+          atomicOr(status, TDK_STATUS_TIMEOUT);
+          fail = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return fail == 0;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// x <- x L^{-T} L^{-1} for T = L L^T (lower L in Tm, 1/L_jj in invd), one warp
+__device__ __forceinline__ void warp_chol_solve(const double* Tm, const double* invd, int R, double* x) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < R; ++j) {
+    const double xj = x[j] * invd[j];
+    __syncwarp();
+    if (lane == 0) x[j] = xj;
+    for (int r = j + 1 + lane; r < R; r += 32) x[r] = fma(-Tm[r * R + j], xj, x[r]);
+    __syncwarp();
+  }
+  for (int j = R - 1; j >= 0; --j) {
+    const double xj = x[j] * invd[j];
+    __syncwarp();
+    if (lane == 0) x[j] = xj;
+    for (int r = lane; r < j; r += 32) x[r] = fma(-Tm[j * R + r], xj, x[r]);
+    __syncwarp();
+  }
+}
+
+#define PROF_MARK(ph)                                                            \
+  do {                                                                           \
+    if (a.prof && blockIdx.x == 0) {                                             \
+      __syncthreads();                                                           \
+      if (threadIdx.x == 0) {                                                    \
+        const unsigned long long t_ = clock64();                                 \
+        a.prof[(ph)] += t_ - prof_t;                                             \
+        prof_t = t_;                                                             \
+      }                                                                          \
+    }                                                                            \
+  } while (0)
+
+// shared-memory plan of the persistent kernel, every region 16-byte aligned
+template <class T>
+struct PLayout {
+  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_invf, o_yf, o_lamt, o_ilamt,
+      o_slice, o_work, total;
+  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      const size_t o = (off + 15) & ~size_t(15);
+      off = o + bytes;
+      return o;
+    };
+    o_bs = take(sizeof(T) * btot);
+    o_gram = take(sizeof(T) * N * R * R);
+    o_bgram = take(sizeof(T) * N * R * R);
+    o_tm = take(sizeof(double) * R * R);
+    o_invd = take(sizeof(double) * RMAXP);
+    o_lam = take(sizeof(double) * RMAXP);
+    o_xrow = take(sizeof(double) * RMAXP);
+    o_hrow = take(sizeof(double) * RMAXP);
+    o_red = take(sizeof(double) * 32);
+    o_lf = take(sizeof(float) * R * R);
+    o_invf = take(sizeof(float) * RMAXP);
+    o_yf = take(sizeof(float) * RMAXP);
+    o_lamt = take(sizeof(T) * RMAXP);
+    o_ilamt = take(sizeof(T) * RMAXP);
+    o_slice = take(sizeof(T) * (size_t)Qmax);
+    o_work = take(sizeof(T) * (size_t)(Amax * R));
+    total = (off + 15) & ~size_t(15);
+  }
+};
+
+// y <- y L^{-T} L^{-1} for an FP32 Cholesky factor (lower Lf, 1/L_jj in invf), one warp
+__device__ __forceinline__ void warp_solve32(const float* Lf, const float* invf, int R, float* y) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < R; ++j) {
+    const float yj = y[j] * invf[j];
+    __syncwarp();
+    if (lane == 0) y[j] = yj;
+    for (int r = j + 1 + lane; r < R; r += 32) y[r] = fmaf(-Lf[r * R + j], yj, y[r]);
+    __syncwarp();
+  }
+  for (int j = R - 1; j >= 0; --j) {
+    const float yj = y[j] * invf[j];
+    __syncwarp();
+    if (lane == 0) y[j] = yj;
+    for (int r = lane; r < j; r += 32) y[r] = fmaf(-Lf[j * R + r], yj, y[r]);
+    __syncwarp();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
+  unsigned long long prof_t = clock64();
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int N = a.N, R = a.R;
+  int boff[TDK_MAX_MODES];
+  int btot = 0;
+  for (int p = 0; p < N; ++p) {
+    boff[p] = btot;
+    btot += a.Rt[p] * R;
+  }
+  PLayout<T> L;
+  L.plan(N, R, btot, a.Qmax, a.Amax);
+  T* Bs = reinterpret_cast<T*>(sm + L.o_bs);         // factors, packed
+  T* gram = reinterpret_cast<T*>(sm + L.o_gram);     // [N][R*R]
+  T* bgram = reinterpret_cast<T*>(sm + L.o_bgram);   // [N][R*R] (nonneg: Grams of B_p)
+  double* Tm = reinterpret_cast<double*>(sm + L.o_tm);  // [R*R] T_n (FP64)
+  double* invd = reinterpret_cast<double*>(sm + L.o_invd);
+  double* lam = reinterpret_cast<double*>(sm + L.o_lam);
+  double* xrow = reinterpret_cast<double*>(sm + L.o_xrow);
+  double* hrow = reinterpret_cast<double*>(sm + L.o_hrow);  // right-hand side
+  double* red = reinterpret_cast<double*>(sm + L.o_red);    // [32]
+  float* Lf = reinterpret_cast<float*>(sm + L.o_lf);        // [R*R] FP32 Cholesky factor
+  float* invf = reinterpret_cast<float*>(sm + L.o_invf);
+  float* yf = reinterpret_cast<float*>(sm + L.o_yf);
+  T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
+  T* ilamT = reinterpret_cast<T*>(sm + L.o_ilamt);
+  T* slice = reinterpret_cast<T*>(sm + L.o_slice);   // [Qmax]
+  T* work = reinterpret_cast<T*>(sm + L.o_work);     // [Amax * R]
+  __shared__ int s_bad;
+
+  const int tid = threadIdx.x;
+  const int G = gridDim.x, c = blockIdx.x;
+  bool ok = true;
+
+  // ---- initial factors (raw) and their Grams
+  for (int n = 0; n < N; ++n) {
+    if (!a.nonneg) {
+      for (int e = tid; e < a.Rt[n] * R; e += NTP) Bs[boff[n] + e] = (T)a.init[n][e];
+    } else {
+      for (int e = tid; e < a.Rt[n] * R; e += NTP) {
+        const int q = e / R, r = e % R;
+        T s = T(0);
+        for (int64_t i = 0; i < a.I[n]; ++i) s = fma(a.Uf[n][i * a.Rt[n] + q], (T)a.init[n][i * R + r], s);
+        Bs[boff[n] + e] = s;
+      }
+    }
+    for (int e = tid; e < R * R; e += NTP) {
+      const int r = e / R, s2 = e % R;
+      T acc = T(0);
+      if (!a.nonneg) {
+        for (int q = 0; q < a.Rt[n]; ++q) acc = fma((T)a.init[n][q * R + r], (T)a.init[n][q * R + s2], acc);
+      } else {
+        for (int64_t i = 0; i < a.I[n]; ++i) acc = fma((T)a.init[n][i * R + r], (T)a.init[n][i * R + s2], acc);
+      }
+      gram[n * R * R + e] = acc;
+    }
+  }
+  for (int r = tid; r < R; r += NTP) {
+    lam[r] = 1.0;
+    lamT[r] = T(1);
+  }
+  __syncthreads();
+  for (int n = 0; n < N; ++n)
+    for (int e = tid; e < R * R; e += NTP) {
+      const int r = e / R, s2 = e % R;
+      T acc = T(0);
+      for (int q = 0; q < a.Rt[n]; ++q) acc = fma(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2], acc);
+      bgram[n * R * R + e] = acc;
+    }
+  __syncthreads();
+  const double nG2 = *a.nG2;
+  const double nY2 = a.nY2 ? *a.nY2 : 0.0;
+
+  double fit_old = 0.0, fit = 0.0, fitY = nan("");
+  int sweep = 0, converged = 0, needpinv = 0;
+  for (sweep = 1; sweep <= a.max_sweeps && ok; ++sweep) {
+    double inner = 0.0;
+    for (int n = 0; n < N && ok; ++n) {
+      const int Rn = a.Rt[n];
+      // ---- 1. T_n (FP64) and a Cholesky factor: FP32 by default, the solves
+      //         then refined against T_n in FP64; FP64 factor in place if an
+      //         FP32 pivot is not positive enough
+      for (int e = tid; e < R * R; e += NTP) {
+        T vt = T(1);
+        for (int p = 0; p < N; ++p)
+          if (p != n) vt *= gram[p * R * R + e];
+        Lf[e] = (float)vt;
+        double v = 1.0;
+        for (int p = 0; p < N; ++p)
+          if (p != n) v *= (double)gram[p * R * R + e];
+        Tm[e] = v;
+      }
+      if (tid == 0) s_bad = 0;
+      __syncthreads();
+      bool use32 = true;
+      {
+        float mx = 0.f;
+        for (int j = 0; j < R; ++j) mx = fmaxf(mx, Lf[j * R + j]);
+        const float tiny = R * 1.1920929e-7f * mx;
+        for (int j = 0; j < R; ++j) {
+          const float d = Lf[j * R + j];
+          if (!(d > tiny)) {
+            use32 = false;
+            break;
+          }
+          const float ljj = sqrtf(d), il = 1.0f / ljj;
+          __syncthreads();
+          if (tid == 0) {
+            Lf[j * R + j] = ljj;
+            invf[j] = il;
+          }
+          for (int r = j + 1 + tid; r < R; r += NTP) Lf[r * R + j] *= il;
+          __syncthreads();
+          const int m = R - j - 1;
+          for (int e = tid; e < m * m; e += NTP) {
+            const int r = j + 1 + e / m, cc = j + 1 + e % m;
+            if (cc <= r) Lf[r * R + cc] = fmaf(-Lf[r * R + j], Lf[cc * R + j], Lf[r * R + cc]);
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      if (!use32) {
+        double mx = 0.0;
+        for (int j = 0; j < R; ++j) mx = fmax(mx, Tm[j * R + j]);
+        const double tiny = R * 2.220446049250313e-16 * mx;
+        for (int j = 0; j < R; ++j) {
+          const double d = Tm[j * R + j];
+          if (!(d > tiny)) {
+            if (tid == 0) s_bad = 1;
+            break;
+          }
+          const double ljj = sqrt(d), il = 1.0 / ljj;
+          __syncthreads();
+          if (tid == 0) {
+            Tm[j * R + j] = ljj;
+            invd[j] = il;
+          }
+          for (int r = j + 1 + tid; r < R; r += NTP) Tm[r * R + j] *= il;
+          __syncthreads();
+          const int m = R - j - 1;
+          for (int e = tid; e < m * m; e += NTP) {
+            const int r = j + 1 + e / m, cc = j + 1 + e % m;
+            if (cc <= r) Tm[r * R + cc] = fma(-Tm[r * R + j], Tm[cc * R + j], Tm[r * R + cc]);
+          }
+          __syncthreads();
+        }
+        __syncthreads();
+      }
+      if (s_bad) {
+        needpinv = 1;
+        ok = false;  // identical in every CTA: all leave here
+        break;
+      }
+      // x <- x T_n^{-1} for the row in xrow (one warp)
+      auto solve_row = [&]() {
+        if (tid >= 32) return;
+        if (!use32) {
+          warp_chol_solve(Tm, invd, R, xrow);
+          return;
+        }
+        const int lane = tid;
+        for (int r = lane; r < R; r += 32) {
+          hrow[r] = xrow[r];
+          yf[r] = (float)xrow[r];
+          xrow[r] = 0.0;
+        }
+        __syncwarp();
+        for (int it = 0; it < 3; ++it) {
+          warp_solve32(Lf, invf, R, yf);
+          for (int r = lane; r < R; r += 32) xrow[r] += (double)yf[r];
+          __syncwarp();
+          if (it == 2) break;
+          // residual of the FP64 system: h - x T_n
+          for (int k = lane; k < R; k += 32) {
+            double rr = hrow[k];
+            for (int j = 0; j < R; ++j) rr = fma(-xrow[j], Tm[j * R + k], rr);
+            yf[k] = (float)rr;
+          }
+          __syncwarp();
+        }
+      };
+
+      PROF_MARK(0);
+      // ---- 2. rows of H_n (unconstrained: and of B_n)
+      int oth[TDK_MAX_MODES];
+      int no = 0;
+      for (int p = 0; p < N; ++p)
+        if (p != n) oth[no++] = p;
+      const int64_t Q = a.gnumel / Rn;
+      const int last = oth[no - 1];
+      const int Rl = a.Rt[last];
+      const int64_t A1 = Q / Rl;
+      for (int i = c; i < Rn; i += G) {
+#pragma unroll 4
+        for (int e = tid; e < (int)Q; e += NTP) {
+          int rem = e;
+          int64_t off = (int64_t)i * a.stride[n];
+          for (int k = no - 1; k >= 0; --k) {
+            const int p = oth[k];
+            off += (int64_t)(rem % a.Rt[p]) * a.stride[p];
+            rem /= a.Rt[p];
+          }
+          slice[e] = a.G[off];
+        }
+        __syncthreads();
+        // first contraction (last other mode): work[a1, r] = sum_l S[a1, l] B_last[l, r]
+        const T* Bl = Bs + boff[last];
+        for (int64_t e = tid; e < A1 * R; e += NTP) {
+          const int64_t a1 = e / R;
+          const int r = (int)(e % R);
+          const T* srow = slice + a1 * Rl;
+          T acc = T(0);
+          for (int l = 0; l < Rl; ++l) acc = fma(srow[l], Bl[l * R + r], acc);
+          work[e] = acc;
+        }
+        __syncthreads();
+        // remaining other modes, last to first: out[b, r] = sum_m in[b*Rp + m, r] B_p[m, r]
+        T* in = work;
+        T* out = slice;
+        int64_t rows = A1;
+        for (int k = no - 2; k >= 0; --k) {
+          const int p = oth[k];
+          const int Rp = a.Rt[p];
+          const int64_t nrows = rows / Rp;
+          const T* Bp = Bs + boff[p];
+          for (int64_t e = tid; e < nrows * R; e += NTP) {
+            const int64_t b = e / R;
+            const int r = (int)(e % R);
+            T acc = T(0);
+            for (int m = 0; m < Rp; ++m) acc = fma(in[(b * Rp + m) * R + r], Bp[m * R + r], acc);
+            out[e] = acc;
+          }
+          __syncthreads();
+          T* t = in;
+          in = out;
+          out = t;
+          rows = nrows;
+        }
+        for (int r = tid; r < R; r += NTP) {
+          a.H[(int64_t)i * R + r] = in[r];
+          xrow[r] = (double)in[r];
+        }
+        __syncthreads();
+        if (!a.nonneg) {
+          solve_row();
+          __syncthreads();
+          for (int r = tid; r < R; r += NTP) a.Bnew[(int64_t)i * R + r] = (T)xrow[r];
+        }
+        __syncthreads();
+      }
+      PROF_MARK(1);
+      if (!grid_sync(a.bar, a.status)) { ok = false; break; }
+      PROF_MARK(2);
+
+      if (a.nonneg) {
+        // rows of A_n = max(0, (U_n H_n) T_n^{-1}); H_n staged in shared memory
+        for (int e = tid; e < Rn * R; e += NTP) work[e] = __ldcg(a.H + e);
+        __syncthreads();
+        for (int64_t i = c; i < a.I[n]; i += G) {
+          for (int r = tid; r < R; r += NTP) {
+            T m = T(0);
+            for (int q = 0; q < Rn; ++q) m = fma(a.Uf[n][i * Rn + q], work[q * R + r], m);
+            xrow[r] = (double)m;
+          }
+          __syncthreads();
+          solve_row();
+          __syncthreads();
+          for (int r = tid; r < R; r += NTP) a.Bnew[i * R + r] = (T)fmax(xrow[r], 0.0);
+          __syncthreads();
+        }
+        if (!grid_sync(a.bar, a.status)) { ok = false; break; }
+      }
+
+      PROF_MARK(3);
+      // ---- 3. lambda, normalised factor and its Gram (every CTA, same order)
+      const int64_t rows = a.nonneg ? a.I[n] : Rn;
+      T* nb = slice;  // [rows x R] the update rows, then normalised (the slice is free here)
+      for (int64_t e = tid; e < rows * R; e += NTP) nb[e] = __ldcg(a.Bnew + e);
+      __syncthreads();
+      {
+        const int w = tid >> 5, lane = tid & 31;
+        for (int r = w; r < R; r += NTP / 32) {
+          T s2 = T(0);
+          for (int64_t i = lane; i < rows; i += 32) {
+            const T v = nb[i * R + r];
+            s2 = fma(v, v, s2);
+          }
+          s2 = warp_sum(s2);
+          if (lane == 0) {
+            const T l = sqrt(s2);
+            lamT[r] = l;
+            ilamT[r] = l > T(0) ? T(1) / l : T(0);
+            lam[r] = (double)l;
+          }
+        }
+      }
+      __syncthreads();
+      const T inv_rows = (T)(1.0 / sqrt((double)rows));
+      for (int64_t e = tid; e < rows * R; e += NTP) {
+        const int r = (int)(e % R);
+        nb[e] = lamT[r] > T(0) ? nb[e] * ilamT[r] : inv_rows;
+      }
+      if (a.nonneg)  // U_n staged in the work buffer for B_n = U_n^T A_n
+        for (int64_t e = tid; e < rows * Rn; e += NTP) work[e] = a.Uf[n][e];
+      __syncthreads();
+      for (int e = tid; e < R * R; e += NTP) {
+        const int r = e / R, s2 = e % R;
+        T acc = T(0);
+        for (int64_t i = 0; i < rows; ++i) acc = fma(nb[i * R + r], nb[i * R + s2], acc);
+        gram[n * R * R + e] = acc;
+      }
+      if (!a.nonneg) {
+        for (int e = tid; e < Rn * R; e += NTP) Bs[boff[n] + e] = nb[e];
+      } else {
+        for (int e = tid; e < Rn * R; e += NTP) {
+          const int q = e / R, r = e % R;
+          T s2 = T(0);
+          for (int64_t i = 0; i < rows; ++i) s2 = fma(work[i * Rn + q], nb[i * R + r], s2);
+          Bs[boff[n] + e] = s2;
+        }
+        if (c == 0)
+          for (int64_t e = tid; e < rows * R; e += NTP) a.Aout[n][e] = (double)nb[e];
+        __syncthreads();
+        for (int e = tid; e < R * R; e += NTP) {
+          const int r = e / R, s2 = e % R;
+          T acc = T(0);
+          for (int q = 0; q < Rn; ++q) acc = fma(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2], acc);
+          bgram[n * R * R + e] = acc;
+        }
+      }
+      __syncthreads();
+      if (n == N - 1) {
+        if (sizeof(T) == 8) {
+          // FP64 form: <G, [[lambda; B]]> from H (Gram identity, as the FP64 oracle)
+          double s2 = 0.0;
+          for (int e = tid; e < Rn * R; e += NTP)
+            s2 += (double)__ldcg(a.H + e) * lam[e % R] * (double)Bs[boff[n] + e];
+          inner = block_sum_d(s2, red);
+        } else {
+          // FP32 forms: ||G - [[lambda; B]]||^2 summed explicitly over this CTA's
+          // share of the core (the Gram identity cancels to rounding noise near
+          // convergence in FP32)
+          const int64_t chunk = (a.gnumel + G - 1) / G;
+          const int64_t e0 = (int64_t)c * chunk, e1 = e0 + chunk < a.gnumel ? e0 + chunk : a.gnumel;
+          T sacc = T(0), scmp = T(0);
+          for (int64_t e = e0 + tid; e < e1; e += NTP) {
+            int rem = (int)e;
+            int ix[TDK_MAX_MODES];
+            for (int p = N - 1; p >= 0; --p) {
+              ix[p] = rem % a.Rt[p];
+              rem /= a.Rt[p];
+            }
+            T x = T(0);
+            for (int r = 0; r < R; ++r) {
+              T v = lamT[r];
+              for (int p = 0; p < N; ++p) v *= Bs[boff[p] + ix[p] * R + r];
+              x += v;
+            }
+            const T d = a.G[e] - x;
+            const T y = d * d - scmp;  // Kahan
+            const T t = sacc + y;
+            scmp = (t - sacc) - y;
+            sacc = t;
+          }
+          double s2 = block_sum_d((double)sacc - (double)scmp, red);
+          if (tid == 0) a.rpart[c] = s2;
+        }
+      }
+      PROF_MARK(4);
+      // H / Bnew are overwritten by the next mode only after every CTA read them
+      if (!grid_sync(a.bar, a.status)) { ok = false; break; }
+      PROF_MARK(5);
+    }
+    if (!ok) break;
+    // ---- fit (identical in every CTA)
+    T m2 = T(0), mb2 = T(0);
+    for (int e = tid; e < R * R; e += NTP) {
+      T v = lamT[e / R] * lamT[e % R];
+      T vb = v;
+      for (int p = 0; p < N; ++p) {
+        v *= gram[p * R * R + e];
+        vb *= bgram[p * R * R + e];
+      }
+      m2 += v;
+      mb2 += vb;
+    }
+    const double model2 = block_sum_d((double)m2, red);
+    double res2;
+    if (sizeof(T) == 8) {
+      res2 = fmax(0.0, nG2 - 2.0 * inner + model2);
+    } else {
+      res2 = 0.0;
+      for (int q = 0; q < G; ++q) res2 += __ldcg(a.rpart + q);
+      if (a.nonneg) {
+        // [[A]] leaves the Tucker subspace: add ||[[A]]||^2 - ||P [[A]]||^2,
+        // P [[A]] = [[U B]] with B_p = U_p^T A_p
+        const double mb = block_sum_d((double)mb2, red);
+        res2 += fmax(0.0, model2 - mb);
+      }
+    }
+    PROF_MARK(6);
+    fit_old = fit;
+    fit = 1.0 - sqrt(res2) / sqrt(nG2);
+    if (a.nY2) fitY = 1.0 - sqrt(fmax(0.0, nY2 - nG2 + res2)) / sqrt(nY2);
+    if (c == 0 && tid == 0 && sweep - 1 < a.hist_cap) a.hist[sweep - 1] = fit;
+    if (sweep > 1 && fabs(fit - fit_old) < a.tol * fabs(fit_old)) {
+      converged = 1;
+      break;
+    }
+  }
+  if (sweep > a.max_sweeps) sweep = a.max_sweeps;
+  if (c == 0) {
+    for (int n = 0; n < N; ++n)
+      for (int e = tid; e < a.Rt[n] * R; e += NTP) a.Bout[n][e] = Bs[boff[n] + e];
+    for (int r = tid; r < R; r += NTP) a.lam_out[r] = lam[r];
+    if (tid == 0) {
+      a.st->sweeps = sweep;
+      a.st->converged = converged;
+      a.st->status = needpinv ? ST_NEEDPINV : (ok ? 0 : ST_TIMEOUT);
+      a.st->fit = fit;
+      a.st->fitY = fitY;
+    }
+  }
+}
+
+template <class T>
+__global__ void norm2_core(const T* __restrict__ G, int64_t n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const double v = (double)G[e];
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    *out = v;
+  }
+}
+
+template <class T>
+__global__ void u_to_t(const double* __restrict__ s, T* __restrict__ d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (T)s[e];
+}
+
+}  // namespace
+
+// TDK_ENOTSUP: the core does not fit the persistent form (the caller falls back)
+template <class T>
+int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], const double* normY2,
+                     const tdk_als_opts* o, double* const B_io[], double* const A_io[], double* lambda_out,
+                     tdk_als_report* rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int N = g.N, R = o->R;
+  if (o->init != TDK_INIT_GIVEN || o->timeout_s > 0) return TDK_ENOTSUP;
+  PArgs<T> a{};
+  a.N = N;
+  a.R = R;
+  a.nonneg = o->nonneg ? 1 : 0;
+  a.max_sweeps = o->max_sweeps;
+  a.tol = o->tol;
+  int64_t Rtmax = 0, Imax = 0, btot = 0;
+  {
+    int64_t s = 1;
+    for (int n = N - 1; n >= 0; --n) {
+      a.stride[n] = s;
+      s *= g.Rt[n];
+    }
+  }
+  a.gnumel = g.core_numel;
+  for (int n = 0; n < N; ++n) {
+    a.Rt[n] = g.Rt[n];
+    a.I[n] = g.I[n];
+    Rtmax = std::max<int64_t>(Rtmax, g.Rt[n]);
+    Imax = std::max<int64_t>(Imax, g.I[n]);
+    btot += (int64_t)g.Rt[n] * R;
+    const int64_t Q = g.core_numel / g.Rt[n];
+    a.Qmax = std::max<int64_t>(a.Qmax, Q);
+    const int last = (n == N - 1) ? N - 2 : N - 1;
+    a.Amax = std::max<int64_t>(a.Amax, Q / g.Rt[last]);
+  }
+  // the slice buffer also holds the normalised rows of the update
+  a.Qmax = std::max<int64_t>(a.Qmax, (a.nonneg ? Imax : Rtmax) * R);
+  // and the work buffer the staged H and U_n (nonneg)
+  a.Amax = std::max<int64_t>(a.Amax, Rtmax);
+  if (a.nonneg)
+    for (int n = 0; n < N; ++n) a.Amax = std::max<int64_t>(a.Amax, (g.I[n] * g.Rt[n] + R - 1) / R);
+  PLayout<T> lay;
+  lay.plan(N, R, (int)btot, a.Qmax, a.Amax);
+  const size_t smem = lay.total + 64;
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
+  auto kern = als_persistent_kernel<T>;
+  TDK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TDK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTP, smem));
+  if (per_sm < 1) return TDK_ENOTSUP;
+  int grid = (int)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, a.nonneg ? std::max(Rtmax, Imax) : Rtmax);
+
+  Planner pl;
+  pl.take<T>((size_t)(a.nonneg ? std::max(Rtmax, Imax) : Rtmax) * R);
+  pl.take<T>((size_t)Rtmax * R);
+  for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.Rt[n] * R);
+  for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.I[n] * g.Rt[n]);
+  if (a.nonneg)
+    for (int n = 0; n < N; ++n) pl.take<double>((size_t)g.I[n] * R);
+  pl.take<double>(R);
+  pl.take<double>(std::min(o->max_sweeps, 65536));
+  pl.take<PState>(1);
+  pl.take<unsigned>(2);
+  pl.take<double>(1);
+  pl.take<double>(grid);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  a.Bnew = cv.take<T>((size_t)(a.nonneg ? std::max(Rtmax, Imax) : Rtmax) * R);
+  a.H = cv.take<T>((size_t)Rtmax * R);
+  for (int n = 0; n < N; ++n) a.Bout[n] = cv.take<T>((size_t)g.Rt[n] * R);
+  T* uf[TDK_MAX_MODES];
+  for (int n = 0; n < N; ++n) uf[n] = cv.take<T>((size_t)g.I[n] * g.Rt[n]);
+  double* aw[TDK_MAX_MODES] = {};
+  if (a.nonneg)
+    for (int n = 0; n < N; ++n) aw[n] = cv.take<double>((size_t)g.I[n] * R);
+  a.lam_out = cv.take<double>(R);
+  a.hist_cap = std::min(o->max_sweeps, 65536);
+  a.hist = cv.take<double>(a.hist_cap);
+  a.st = cv.take<PState>(1);
+  a.bar = cv.take<unsigned>(2);
+  double* nG2 = cv.take<double>(1);
+  a.rpart = cv.take<double>(grid);
+  unsigned long long* prof = nullptr;
+  const bool want_prof = getenv("TDK_ALS_PROFILE") != nullptr;
+  if (want_prof) {
+    TDK_CUDA_TRY(cudaMallocAsync((void**)&prof, 16 * sizeof(unsigned long long), ctx->stream));
+    TDK_CUDA_TRY(cudaMemsetAsync(prof, 0, 16 * sizeof(unsigned long long), ctx->stream));
+  }
+  a.prof = prof;
+  a.status = ctx->d_status;
+  a.G = G;
+  a.nG2 = nG2;
+  a.nY2 = normY2;
+  cudaStream_t s = ctx->stream;
+  for (int n = 0; n < N; ++n) {
+    u_to_t<T><<<64, 256, 0, s>>>(U[n], uf[n], g.I[n] * g.Rt[n]);
+    TDK_LAUNCH_CHECK(ctx);
+    a.Uf[n] = uf[n];
+    a.init[n] = a.nonneg ? A_io[n] : B_io[n];
+    a.Aout[n] = aw[n];  // running A_n; the caller's A_io stays the init until the end
+  }
+  norm2_core<T><<<1, 1024, 0, s>>>(G, g.core_numel, nG2);
+  TDK_LAUNCH_CHECK(ctx);
+  TDK_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s));
+  void* args[] = {&a};
+  TDK_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(NTP), args, smem, s));
+  ctx->launches++;
+  PState hs{};
+  TDK_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(PState), cudaMemcpyDeviceToHost, s));
+  TDK_CUDA_TRY(cudaStreamSynchronize(s));
+  if (want_prof) {
+    unsigned long long hp[16];
+    TDK_CUDA_TRY(cudaMemcpyAsync(hp, prof, sizeof(hp), cudaMemcpyDeviceToHost, s));
+    TDK_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(prof);
+    const char* names[7] = {"chol", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
+                            "barrier3", "fit"};
+    fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);
+    for (int i = 0; i < 7; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
+    fprintf(stderr, "\n");
+  }
+  if (hs.status & ST_NEEDPINV) return TDK_ENOTSUP;  // the multi-kernel form has the pseudo-inverse
+  if (hs.status & ST_TIMEOUT) return TDK_ETIMEOUT;
+  rc = als_finish(ctx, g, R, sizeof(T) == 8, reinterpret_cast<const void* const*>(a.Bout), U, a.lam_out,
+                  a.nonneg ? aw : nullptr, B_io, A_io, lambda_out);
+  if (rc) return rc;
+  TDK_CUDA_TRY(cudaStreamSynchronize(s));
+  int status = TDK_OK;
+  if (!hs.converged) status |= TDK_WNOCONV;
+  if (rep) {
+    rep->sweeps = hs.sweeps;
+    rep->status = status;
+    rep->fit_core = hs.fit;
+    rep->fit_Y = normY2 ? hs.fitY : nan("");
+    rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+template int als_persistent_t<float>(tdk_ctx*, const Geom&, const float*, const double* const[], const double*,
+                                     const tdk_als_opts*, double* const[], double* const[], double*, tdk_als_report*);
+template int als_persistent_t<double>(tdk_ctx*, const Geom&, const double*, const double* const[], const double*,
+                                      const tdk_als_opts*, double* const[], double* const[], double*,
+                                      tdk_als_report*);
+
+}  // namespace tdk

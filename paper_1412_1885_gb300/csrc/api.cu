@@ -172,6 +172,14 @@ int tdk_ctx_profile_read(tdk_ctx* c, int region, double* total_ms, int64_t* laun
   return TDK_OK;
 }
 
+// selects the ALS form: 0 = persistent kernel when the core fits (default),
+// 1 = one kernel per step (test hook, not in the public header)
+int tdk_ctx_test_als_form(tdk_ctx* c, int multi) {
+  if (!c) return TDK_EINVAL;
+  c->als_multi_kernel = multi != 0;
+  return TDK_OK;
+}
+
 // test hook (not in the public header): make the n-th workspace growth fail
 int tdk_ctx_test_fail_alloc(tdk_ctx* c, int after) {
   if (!c) return TDK_EINVAL;

@@ -150,7 +150,7 @@ struct SkLayout {
   static constexpr uint32_t KT_BYTES = 16 * KB;                        // K_p tile [128 j][64 r] BF16
 };
 
-template <bool F32>
+template <bool F32, int RW>
 __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
     tc_sketch_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmW,
                      const SkArgs a) {
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
   uint64_t* d2empty = bars + 17;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 20);
   float* red = reinterpret_cast<float*>(bars + 24);                // [4][64]
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(red + 4 * 64);
+  float* coef = red + 4 * 64;                                      // [3][4][64]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(coef + 3 * 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -306,6 +307,7 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
     }
   } else if (warp < 6) {
     // ------------------------------------------------------------ epilogue (4 warps)
+    constexpr int HW = RW / 2;
     const int q = warp & 3;
     const int jl = 32 * q + lane;  // TMEM lane = tile row j (D1) / column k (D2)
     const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
@@ -313,6 +315,43 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
     const int nj = Nm - 2;         // tile row mode
     const int nl = Nm - 1;         // contiguous mode
     const int Rj = a.Rt[nj];
+    // Per-p coefficient vectors, products of W rows over the outer indices of p
+    // (four vectors of 64: [0] Khatri-Rao rows of the contiguous mode, [1] the
+    // row mode, [2], [3] modes 0 and 1 when they are outer modes), kept in
+    // three shared buffers so that p+2 is loaded while p is in use.
+    auto coef_load = [&](int64_t pp, float* cr) {
+      int kidx[2] = {0, 0};
+      {
+        int64_t rem = pp;
+        for (int k = Nm - 3; k >= 0; --k) {
+          kidx[k] = (int)(rem % a.I[k]);
+          rem /= a.I[k];
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int slot = jl + 128 * h;
+        const int vec = slot >> 6, r = slot & 63;
+        const int n = vec == 0 ? nl : (vec == 1 ? nj : vec - 2);
+        float v = 0.f;
+        if ((vec < 2 || vec - 2 < nj) && r < a.Rt[n]) {
+          v = 1.f;
+          for (int k = 0; k < Nm - 2; ++k) {
+            if (vec >= 2 && k == n) continue;
+            v *= __ldg(a.Wf[n][k] + (int64_t)kidx[k] * a.Rt[n] + r);
+          }
+        }
+        cr[h] = v;
+      }
+    };
+    auto coef_store = [&](uint32_t pidx, const float* cr) {
+      float* cb = coef + (pidx % 3) * 256;
+      cb[jl] = cr[0];
+      cb[jl + 128] = cr[1];
+    };
+    auto unpack = [](uint32_t w, int e) -> float {
+      return e ? __uint_as_float(w & 0xFFFF0000u) : __uint_as_float(w << 16);
+    };
     uint32_t pi = 0, un = 0;
     for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
       const int pc = (int)(u % a.PC);
@@ -324,49 +363,67 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
       const int jj = j0 + jl;
       const bool vj = jj < a.J;
       float* up = a.part + u * a.ustride;
-      float accj[64];
+      // this lane's row of W_{N-1}^(N) and of W_{N-1}^(m) (m < N-2), packed BF16
+      // (the test matrices hold BF16 values, so the packing is exact)
+      uint32_t wk[HW], wn0[HW], wn1[HW];
 #pragma unroll
-      for (int r = 0; r < 64; ++r) accj[r] = 0.f;
-      // K_p rows for G2 (row j of the tile), MN-major [j][r], swizzled; the
-      // tile of p+1 is written before D1 of p is read so the MMA runs ahead
-      auto gen_k = [&](int64_t pp, uint32_t pidx) -> bool {
+      for (int i = 0; i < HW; ++i) {
+        float k0v = 0.f, k1v = 0.f, a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+        const int r = 2 * i;
+        if (vj) {
+          const float* wkr = a.Wf[nl][nj] + (int64_t)jj * a.RtL;
+          if (r < a.RtL) k0v = __ldg(wkr + r);
+          if (r + 1 < a.RtL) k1v = __ldg(wkr + r + 1);
+          if (nj > 0) {
+            const float* w0 = a.Wf[0][nj] + (int64_t)jj * a.Rt[0];
+            if (r < a.Rt[0]) a0 = __ldg(w0 + r);
+            if (r + 1 < a.Rt[0]) a1 = __ldg(w0 + r + 1);
+          }
+          if (nj > 1) {
+            const float* w1 = a.Wf[1][nj] + (int64_t)jj * a.Rt[1];
+            if (r < a.Rt[1]) b0 = __ldg(w1 + r);
+            if (r + 1 < a.Rt[1]) b1 = __ldg(w1 + r + 1);
+          }
+        }
+        wk[i] = pack_bf16x2(k0v, k1v);
+        wn0[i] = pack_bf16x2(a0, a1);
+        wn1[i] = pack_bf16x2(b0, b1);
+      }
+      float accj[RW];
+#pragma unroll
+      for (int r = 0; r < RW; ++r) accj[r] = 0.f;
+      // K_p rows for G2 (row j of the tile), MN-major [j][r], 128-byte swizzle
+      auto gen_k = [&](uint32_t pidx) -> bool {
         const int kb = pidx & 1;
         if (!mbar_wait(smem_u32(&ktempty[kb]), ((pidx >> 1) & 1) ^ 1, status)) return false;
-        int kidx[TDK_MAX_MODES];
-        {
-          int64_t rem = pp;
-          for (int k = Nm - 3; k >= 0; --k) {
-            kidx[k] = (int)(rem % a.I[k]);
-            rem /= a.I[k];
-          }
-        }
+        const float* cK = coef + (pidx % 3) * 256;
         unsigned char* row = kt_base + kb * SkLayout<F32>::KT_BYTES + jl * 128;
-        const float* wj = a.Wf[nl][nj] + (int64_t)(vj ? jj : 0) * a.RtL;
         const int ph = jl & 7;
-        const int ncols = a.hilo ? 32 : 64;
-        float x[64];
-#pragma unroll
-        for (int r = 0; r < 64; ++r) {
-          float v = 0.f;
-          if (r < ncols && r < a.RtL && vj) {
-            v = __ldg(wj + r);
-            for (int k = 0; k < Nm - 2; ++k) v *= __ldg(a.Wf[nl][k] + (int64_t)kidx[k] * a.RtL + r);
-          }
-          x[r] = v;
-        }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           uint32_t w4[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            float v0, v1;
-            if (!a.hilo || c < 4) {
-              v0 = x[8 * c + 2 * e];
-              v1 = x[8 * c + 2 * e + 1];
+            float v0 = 0.f, v1 = 0.f;
+            if (!a.hilo) {
+              const int r = 8 * c + 2 * e;
+              if (r < RW) {
+                v0 = unpack(wk[r / 2], 0) * cK[r];
+                v1 = unpack(wk[r / 2], 1) * cK[r + 1];
+              }
             } else {
-              float s0 = x[8 * (c - 4) + 2 * e], s1 = x[8 * (c - 4) + 2 * e + 1];
-              v0 = s0 - __bfloat162float(__float2bfloat16_rn(s0));
-              v1 = s1 - __bfloat162float(__float2bfloat16_rn(s1));
+              const int r = 8 * (c & 3) + 2 * e;
+              if (r < RW) {
+                const float s0 = unpack(wk[r / 2], 0) * cK[r];
+                const float s1 = unpack(wk[r / 2], 1) * cK[r + 1];
+                if (c < 4) {
+                  v0 = s0;
+                  v1 = s1;
+                } else {
+                  v0 = s0 - __bfloat162float(__float2bfloat16_rn(s0));
+                  v1 = s1 - __bfloat162float(__float2bfloat16_rn(s1));
+                }
+              }
             }
             w4[e] = pack_bf16x2(v0, v1);
           }
@@ -377,98 +434,114 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         if (lane == 0) mbar_arrive(smem_u32(&ktfull[kb]));
         return true;
       };
-      if (!gen_k(p0, pi)) { ok = false; break; }
+      {
+        float cr[2];
+        coef_load(p0, cr);
+        coef_store(pi, cr);
+        if (p0 + 1 < p1) {
+          coef_load(p0 + 1, cr);
+          coef_store(pi + 1, cr);
+        }
+      }
+      named_bar(1, 128);
+      if (!gen_k(pi)) { ok = false; break; }
       for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
         const int db = pi & 1;
-        int idx[TDK_MAX_MODES];
-        {
-          int64_t rem = p;
-          for (int k = Nm - 3; k >= 0; --k) {
-            idx[k] = (int)(rem % a.I[k]);
-            rem /= a.I[k];
-          }
-        }
-        if (p + 1 < p1 && !gen_k(p + 1, pi + 1)) { ok = false; break; }
+        float cr2[2] = {0.f, 0.f};
+        const bool have2 = p + 2 < p1;
+        if (have2) coef_load(p + 2, cr2);
+        if (p + 1 < p1 && !gen_k(pi + 1)) { ok = false; break; }
+        const float* cb = coef + (pi % 3) * 256;
         // ---- D1 -> sketches of modes < N
         if (!mbar_wait(smem_u32(&d1full[db]), (pi >> 1) & 1, status)) { ok = false; break; }
         tc_fence_after();
-        for (int n = 0; n <= nj; ++n) {
-          const int Rn = a.Rt[n];
-          float v[64];
+        const uint32_t d1 = tmem + db * a.d1_cols + lane_addr;
+        // row mode: per-lane accumulation weighted by the outer coefficients
 #pragma unroll
-          for (int c16 = 0; c16 < 4; ++c16) {
-            if (c16 * 16 < a.Rtp[n]) {
-              tmem_ld16(tmem + db * a.d1_cols + a.off[n] + c16 * 16 + lane_addr, v + c16 * 16);
+        for (int c16 = 0; c16 < RW / 16; ++c16) {
+          if (c16 * 16 < a.Rtp[nj]) {
+            float v[16];
+            tmem_ld16(d1 + a.off[nj] + c16 * 16, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) accj[c16 * 16 + e] = fmaf(v[e], cb[64 + c16 * 16 + e], accj[c16 * 16 + e]);
+          }
+        }
+        // modes constant over the tile: weight by W_{N-1}^(m)[j], reduce over 128 lanes
+        for (int m = 0; m < nj; ++m) {
+          float v[RW];
+#pragma unroll
+          for (int c16 = 0; c16 < RW / 16; ++c16) {
+            if (c16 * 16 < a.Rtp[m]) {
+              tmem_ld16(d1 + a.off[m] + c16 * 16, v + c16 * 16);
             } else {
 #pragma unroll
               for (int e = 0; e < 16; ++e) v[c16 * 16 + e] = 0.f;
             }
           }
           tmem_wait_ld();
-          if (n == nj) {
-            // row mode: per-lane accumulation, coefficient from the outer indices
 #pragma unroll
-            for (int r = 0; r < 64; ++r) {
-              if (r < Rn) {
-                float cf = 1.f;
-                for (int k = 0; k < Nm - 2; ++k) cf *= __ldg(a.Wf[n][k] + (int64_t)idx[k] * Rn + r);
-                accj[r] = fmaf(v[r], cf, accj[r]);
-              }
-            }
-          } else {
-            // constant mode over the tile: weight by W_{N-1}^(n)[j] and reduce over 128 lanes
-            const float* wj = a.Wf[n][nj] + (int64_t)(vj ? jj : 0) * Rn;
-#pragma unroll
-            for (int r = 0; r < 64; ++r) v[r] = (vj && r < Rn) ? v[r] * __ldg(wj + r) : 0.f;
-            // butterfly transpose-reduce: each lane ends with 2 of the 64 sums
-#pragma unroll
-            for (int o = 16, h = 32; o >= 1; o >>= 1, h >>= 1) {
-              const bool up = (lane & o) != 0;
-#pragma unroll
-              for (int i = 0; i < 32; ++i) {
-                if (i < h) {
-                  float send = up ? v[i] : v[i + h];
-                  float keep = up ? v[i + h] : v[i];
-                  v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                }
-              }
-            }
-            const int bse = ((lane >> 4) & 1) * 32 + ((lane >> 3) & 1) * 16 + ((lane >> 2) & 1) * 8 +
-                            ((lane >> 1) & 1) * 4 + (lane & 1) * 2;
-            red[q * 64 + bse] = v[0];
-            red[q * 64 + bse + 1] = v[1];
-            named_bar(1, 128);
-            if (jl < Rn) {
-              float s = red[jl] + red[64 + jl] + red[128 + jl] + red[192 + jl];
-              for (int k = 0; k < Nm - 2; ++k)
-                if (k != n) s *= __ldg(a.Wf[n][k] + (int64_t)idx[k] * Rn + jl);
-              up[a.poff_p[n] + (p - p0) * Rn + jl] = s;
-            }
-            named_bar(1, 128);
+          for (int i = 0; i < HW; ++i) {
+            const uint32_t w = (m == 0) ? wn0[i] : wn1[i];
+            v[2 * i] *= unpack(w, 0);
+            v[2 * i + 1] *= unpack(w, 1);
           }
+          // butterfly transpose-reduce: each lane ends with RW/32 of the RW sums
+#pragma unroll
+          for (int o = 16, h = RW / 2; o >= 1; o >>= 1, h >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < RW / 2; ++i) {
+              if (i < h) {
+                const float send = upper ? v[i] : v[i + h];
+                const float keep = upper ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+              }
+            }
+          }
+          int bse = 0;
+#pragma unroll
+          for (int o = 16, h = RW / 2; o >= 1; o >>= 1, h >>= 1) bse += (lane & o) ? h : 0;
+          red[q * 64 + bse] = v[0];
+          if (RW == 64) red[q * 64 + bse + 1] = v[1];
+          named_bar(1, 128);
+          const int Rm = a.Rt[m];
+          if (jl < Rm) {
+            const float s = red[jl] + red[64 + jl] + red[128 + jl] + red[192 + jl];
+            up[a.poff_p[m] + (p - p0) * Rm + jl] = s * cb[128 + 64 * m + jl];
+          }
+          named_bar(1, 128);
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&d1empty[db]));
+        if (have2) coef_store(pi + 2, cr2);
+        named_bar(1, 128);
       }
       if (!ok) break;
       // ---- unit end: row-mode partial and the contiguous mode from D2
-      if (vj)
-        for (int r = 0; r < Rj; ++r) up[a.poff_j + (int64_t)jl * Rj + r] = accj[r];
+      if (vj) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+          if (r < Rj) up[a.poff_j + (int64_t)jl * Rj + r] = accj[r];
+      }
       if (!mbar_wait(smem_u32(d2full), un & 1, status)) { ok = false; break; }
       tc_fence_after();
       for (int st = 0; st < a.KS; ++st) {
         float v[64];
 #pragma unroll
-        for (int c16 = 0; c16 < 4; ++c16)
-          tmem_ld16(tmem + 2 * a.d1_cols + st * 64 + c16 * 16 + lane_addr, v + c16 * 16);
+        for (int c16 = 0; c16 < 4; ++c16) tmem_ld16(tmem + 2 * a.d1_cols + st * 64 + c16 * 16 + lane_addr, v + c16 * 16);
         tmem_wait_ld();
         const int kloc = 128 * st + jl;
         if (kr * a.KRW + kloc < a.L) {
-          for (int r = 0; r < a.RtL; ++r) {
-            float z = v[r];
-            if (a.hilo) z += v[32 + r];
-            up[a.poff_last + (int64_t)kloc * a.RtL + r] = z;
+          float* dst = up + a.poff_last + (int64_t)kloc * a.RtL;
+#pragma unroll
+          for (int r = 0; r < 64; ++r) {
+            if (r < a.RtL) {
+              float z = v[r];
+              if (a.hilo && r < 32) z += v[32 + (r & 31)];
+              dst[r] = z;
+            }
           }
         }
       }
@@ -849,8 +922,18 @@ template <class T>
 int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1);
 
 // ---------------------------------------------------------------- host: sketch
+template <bool F32, int RW>
+static int launch_sketch(tdk_ctx* ctx, const CUtensorMap& tmY, const CUtensorMap& tmW, const SkArgs& a, int grid,
+                         size_t smem) {
+  auto k = tc_sketch_kernel<F32, RW>;
+  TDK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<grid, F32 ? 320 : 192, smem, ctx->stream>>>(tmY, tmW, a);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
 int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[], double* Zdst) {
-  if (g.N < 3 || !tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
+  if (g.N < 3 || g.N > 4 || !tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
   const bool f32 = dtype == TDK_F32;
   const int N = g.N, nj = N - 2, nl = N - 1;
   SkArgs a{};
@@ -948,19 +1031,19 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     if (rc) return rc;
   }
   const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
-  size_t smem = 1024 + 2 * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 + 4 * 64 * 4 + 64;
+  size_t smem = 1024 + 2 * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 + 4 * 64 * 4 +
+                3 * 256 * 4 + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
   {
     ProfScope ps(ctx, 0);
-    if (f32) {
-      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tc_sketch_kernel<true><<<grid, 320, smem, ctx->stream>>>(tmY, tmW, a);
-    } else {
-      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tc_sketch_kernel<false><<<grid, 192, smem, ctx->stream>>>(tmY, tmW, a);
-    }
-    TDK_LAUNCH_CHECK(ctx);
+    int rw = 0;
+    for (int n = 0; n < N; ++n) rw = std::max(rw, a.Rtp[n]);
+    rc = (rw <= 32) ? (f32 ? launch_sketch<true, 32>(ctx, tmY, tmW, a, grid, smem)
+                           : launch_sketch<false, 32>(ctx, tmY, tmW, a, grid, smem))
+                    : (f32 ? launch_sketch<true, 64>(ctx, tmY, tmW, a, grid, smem)
+                           : launch_sketch<false, 64>(ctx, tmY, tmW, a, grid, smem));
+    if (rc) return rc;
   }
   RedArgs ra{};
   ra.s = a;

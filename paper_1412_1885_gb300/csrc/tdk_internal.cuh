@@ -26,6 +26,7 @@ struct tdk_ctx {
   unsigned* d_status = nullptr;  // device status word (TDK_STATUS_* bits)
   int64_t launches = 0;
   int fail_alloc_after = -1;   // test hook: fail the n-th workspace growth
+  bool als_multi_kernel = false;  // force the kernel-per-step ALS form
   // event timing of the main kernels (regions 0: sketch pass, 1: core pass)
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev[2];

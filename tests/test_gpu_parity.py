@@ -103,8 +103,15 @@ def test_core_matches_oracle(tdk, ctx, shape, dtype):
     assert math.isclose(float(nrm.item()), ref["normY2"], rel_tol=1e-12 if dtype == "f64" else 1e-6)
 
 
+@pytest.fixture(params=["persistent", "multi"])
+def als_form(request, ctx):
+    ctx.set_als_form(request.param == "multi")
+    yield request.param
+    ctx.set_als_form(False)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_als_matches_oracle_on_same_core(tdk, ctx, dtype):
+def test_als_matches_oracle_on_same_core(tdk, ctx, dtype, als_form):
     shape, ranks, p, R = (50, 45, 40), (6, 6, 6), 4, 5
     Y, W, A = small_problem(shape, ranks, p, seed=9, dtype=dtype, snr=25.0, R_cp=R)
     ref = oracle.rand_tucker(Y, W)
@@ -126,7 +133,7 @@ def test_als_matches_oracle_on_same_core(tdk, ctx, dtype):
             assert np.allclose(host(out["B"][n]), ref_als["B"][n], atol=1e-8)
 
 
-def test_als_stopping_rule_matches_oracle_fp64(tdk, ctx):
+def test_als_stopping_rule_matches_oracle_fp64(tdk, ctx, als_form):
     shape, ranks, p, R = (30, 28, 26), (4, 4, 4), 3, 3
     Y, W, _ = small_problem(shape, ranks, p, seed=2, dtype="f64", snr=30.0, R_cp=R)
     ref = oracle.rand_tucker(Y, W)
@@ -138,7 +145,7 @@ def test_als_stopping_rule_matches_oracle_fp64(tdk, ctx):
     assert abs(out["fit_core"] - o["fit"]) < 1e-12
 
 
-def test_nonneg_als_matches_oracle(tdk, ctx):
+def test_nonneg_als_matches_oracle(tdk, ctx, als_form):
     shape, ranks, p, R = (24, 22, 20, 18), (5, 5, 5, 5), 3, 4
     Y, W, A = small_problem(shape, ranks, p, seed=7, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
     ref = oracle.rand_tucker(Y, W)

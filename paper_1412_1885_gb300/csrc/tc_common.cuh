@@ -174,7 +174,64 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// in-place split of one 128-byte FP32 row pair (64 values) into BF16 hi / lo
+// rows: raw boxes at `hi_row` and `lo_row` (each 128 B, 128-byte swizzle with
+// phase r%8) become the hi and lo BF16 rows of the same 64 columns.
+__device__ __forceinline__ float split_row64(unsigned char* hi_row, unsigned char* lo_row, int r) {
+  float v[64];
+  const int ph = r & 7;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float4 a = *reinterpret_cast<const float4*>(hi_row + ((c ^ ph) << 4));
+    float4 b = *reinterpret_cast<const float4*>(lo_row + ((c ^ ph) << 4));
+    v[4 * c + 0] = a.x; v[4 * c + 1] = a.y; v[4 * c + 2] = a.z; v[4 * c + 3] = a.w;
+    v[32 + 4 * c + 0] = b.x; v[32 + 4 * c + 1] = b.y; v[32 + 4 * c + 2] = b.z; v[32 + 4 * c + 3] = b.w;
+  }
+  float s = 0.f, comp = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint32_t h[4], l[4];
+    float part = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float x0 = v[8 * c + 2 * e], x1 = v[8 * c + 2 * e + 1];
+      __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      float r0 = x0 - __bfloat162float(h0), r1 = x1 - __bfloat162float(h1);
+      __nv_bfloat162 hh;
+      hh.x = h0;
+      hh.y = h1;
+      h[e] = *reinterpret_cast<uint32_t*>(&hh);
+      l[e] = pack_bf16x2(r0, r1);
+      part = fmaf(x0, x0, part);
+      part = fmaf(x1, x1, part);
+    }
+    // Kahan step on the per-chunk sum
+    float y = part - comp;
+    float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+    *reinterpret_cast<uint4*>(hi_row + ((c ^ ph) << 4)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo_row + ((c ^ ph) << 4)) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+  return s - comp;
+}
+
+__device__ __forceinline__ void named_bar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+
 }  // namespace tc
+
+// shapes the tcgen05 passes take: TMA row pitch of the contiguous mode a
+// multiple of 16 bytes, sketch widths <= 64
+inline bool tc_shape_ok(const Geom& g, int dtype) {
+  const int es = dtype == TDK_BF16 ? 2 : 4;
+  if ((g.L * es) % 16 != 0) return false;  // TMA row stride
+  for (int n = 0; n < g.N; ++n)
+    if (g.Rt[n] > 64) return false;
+  return true;
+}
 
 // ---- host: tensor maps through the driver entry point (no libcuda link)
 int encode_tmap(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* base, const uint64_t* dims,

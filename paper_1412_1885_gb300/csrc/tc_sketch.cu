@@ -69,52 +69,6 @@ using namespace tc;
 constexpr int KB = 1024;
 constexpr uint32_t BOX_BYTES = 16 * KB;  // one 128-row x 128-byte box
 
-// in-place split of one 128-byte FP32 row pair (64 values) into BF16 hi / lo
-// rows: raw boxes at `hi_row` and `lo_row` (each 128 B, 128-byte swizzle with
-// phase r%8) become the hi and lo BF16 rows of the same 64 columns.
-__device__ __forceinline__ float split_row64(unsigned char* hi_row, unsigned char* lo_row, int r) {
-  float v[64];
-  const int ph = r & 7;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    float4 a = *reinterpret_cast<const float4*>(hi_row + ((c ^ ph) << 4));
-    float4 b = *reinterpret_cast<const float4*>(lo_row + ((c ^ ph) << 4));
-    v[4 * c + 0] = a.x; v[4 * c + 1] = a.y; v[4 * c + 2] = a.z; v[4 * c + 3] = a.w;
-    v[32 + 4 * c + 0] = b.x; v[32 + 4 * c + 1] = b.y; v[32 + 4 * c + 2] = b.z; v[32 + 4 * c + 3] = b.w;
-  }
-  float s = 0.f, comp = 0.f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    uint32_t h[4], l[4];
-    float part = 0.f;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float x0 = v[8 * c + 2 * e], x1 = v[8 * c + 2 * e + 1];
-      __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-      float r0 = x0 - __bfloat162float(h0), r1 = x1 - __bfloat162float(h1);
-      __nv_bfloat162 hh;
-      hh.x = h0;
-      hh.y = h1;
-      h[e] = *reinterpret_cast<uint32_t*>(&hh);
-      l[e] = pack_bf16x2(r0, r1);
-      part = fmaf(x0, x0, part);
-      part = fmaf(x1, x1, part);
-    }
-    // Kahan step on the per-chunk sum
-    float y = part - comp;
-    float t = s + y;
-    comp = (t - s) - y;
-    s = t;
-    *reinterpret_cast<uint4*>(hi_row + ((c ^ ph) << 4)) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo_row + ((c ^ ph) << 4)) = make_uint4(l[0], l[1], l[2], l[3]);
-  }
-  return s - comp;
-}
-
-__device__ __forceinline__ void named_bar(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
 // =====================================================================
 //                               SKETCH
 // =====================================================================
@@ -660,266 +614,8 @@ __global__ void build_wn(const double* const* __restrict__ Wl, SkArgs a, int ldw
   }
 }
 
-// =====================================================================
-//                               CORE (first TTM)
-// =====================================================================
-struct CoArgs {
-  int64_t M;     // rows
-  int L;         // contiguous mode
-  int KC;        // 64-column chunks
-  int NB;        // B rows = 2 * Rtp  (hi | lo)
-  int Rt, Rtp;
-  int64_t ntiles;
-  float* X;      // [M][Rt]
-  double* nrm_part;
-  unsigned* status;
-};
-
-template <bool F32>
-struct CoLayout {
-  static constexpr int STAGES = F32 ? 4 : 6;
-  static constexpr uint32_t Y_BYTES = F32 ? 32 * KB : 16 * KB;  // 128 rows x 64 columns
-};
-
-template <bool F32>
-__global__ void __launch_bounds__(F32 ? 320 : 192, 1)
-    tc_core_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmU, const CoArgs a) {
-  using Lay = CoLayout<F32>;
-  constexpr int S = Lay::STAGES;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t b_bytes = (uint32_t)a.NB * 128u;
-  const uint32_t stage_bytes = Lay::Y_BYTES + ((b_bytes + 1023) & ~1023u);
-  unsigned char* st_base = base;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(st_base + S * stage_bytes);
-  uint64_t* full = bars;            // [S]
-  uint64_t* empty = bars + S;       // [S]
-  uint64_t* cfull = bars + 2 * S;   // [S]
-  uint64_t* dfull = bars + 3 * S;   // [2]
-  uint64_t* dempty = bars + 3 * S + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
-  double* nred = reinterpret_cast<double*>(bars + 3 * S + 6);  // [10]
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < S; ++i) {
-      mbar_init(smem_u32(&full[i]), 1);
-      mbar_init(smem_u32(&empty[i]), F32 ? 1 : 5);
-      mbar_init(smem_u32(&cfull[i]), 4);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(&dfull[i]), 1);
-      mbar_init(smem_u32(&dempty[i]), 4);
-    }
-    fence_barrier_init();
-  }
-  if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), 256);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  unsigned* status = a.status;
-  bool ok = true;
-  float nrm = 0.f, nrm_c = 0.f;  // Kahan sum of y^2 for this thread's rows
-
-  if (warp == 0) {
-    if (lane == 0) {
-      prefetch_tmap(&tmY);
-      prefetch_tmap(&tmU);
-      const uint64_t pol = policy_evict_first();
-      uint32_t it = 0;
-      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-        for (int kc = 0; kc < a.KC; ++kc, ++it) {
-          const int s = it % S;
-          const uint32_t n = it / S;
-          if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
-          unsigned char* dst = st_base + s * stage_bytes;
-          mbar_expect_tx(smem_u32(&full[s]), Lay::Y_BYTES + b_bytes);
-          if (F32) {
-            tma_load_3d_hint(smem_u32(dst), &tmY, kc * 64, (int)(t * 128), 0, smem_u32(&full[s]), pol);
-            tma_load_3d_hint(smem_u32(dst + BOX_BYTES), &tmY, kc * 64 + 32, (int)(t * 128), 0, smem_u32(&full[s]),
-                             pol);
-          } else {
-            tma_load_3d_hint(smem_u32(dst), &tmY, kc * 64, (int)(t * 128), 0, smem_u32(&full[s]), pol);
-          }
-          tma_load_3d(smem_u32(dst + Lay::Y_BYTES), &tmU, kc * 64, 0, 0, smem_u32(&full[s]));
-        }
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t id = idesc_bf16(128, a.NB, 0, 0);
-      uint32_t it = 0, tl = 0;
-      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tl) {
-        const int db = tl & 1;
-        if (!mbar_wait(smem_u32(&dempty[db]), ((tl >> 1) & 1) ^ 1, status)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t d = tmem + db * 128;
-        for (int kc = 0; kc < a.KC; ++kc, ++it) {
-          const int s = it % S;
-          const uint32_t n = it / S;
-          if (!mbar_wait(smem_u32(F32 ? &cfull[s] : &full[s]), n & 1, status)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t sb = smem_u32(st_base + s * stage_bytes);
-          const uint32_t bb = sb + Lay::Y_BYTES;
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t bd = smem_desc(bb + kk * 32, 16, 1024, SW128);
-            mma_bf16(d, smem_desc(sb + kk * 32, 16, 1024, SW128), bd, id, (kc | kk) != 0);
-            if (F32) mma_bf16(d, smem_desc(sb + BOX_BYTES + kk * 32, 16, 1024, SW128), bd, id, 1);
-          }
-          umma_commit(smem_u32(&empty[s]));
-        }
-        umma_commit(smem_u32(&dfull[db]));
-      }
-    }
-  } else if (warp < 6) {
-    // epilogue: X_1 rows = hi + lo halves of D; BF16 data also sums y^2 per stage
-    const int q = warp & 3;
-    const int rl = 32 * q + lane;
-    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
-    uint32_t it = 0, tl = 0;
-    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tl) {
-      if (!F32) {
-        for (int kc = 0; kc < a.KC; ++kc, ++it) {
-          const int s = it % S;
-          const uint32_t n = it / S;
-          if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
-          const unsigned char* row = st_base + s * stage_bytes + rl * 128;
-          float part = 0.f;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            uint4 w = *reinterpret_cast<const uint4*>(row + c * 16);
-            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
-              part = fmaf(lo, lo, part);
-              part = fmaf(hi, hi, part);
-            }
-          }
-          float y = part - nrm_c;
-          float tt = nrm + y;
-          nrm_c = (tt - nrm) - y;
-          nrm = tt;
-          // the stage is refilled by TMA (async proxy): order these generic
-          // reads before that write
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
-        }
-        if (!ok) break;
-      }
-      const int db = tl & 1;
-      if (!mbar_wait(smem_u32(&dfull[db]), (tl >> 1) & 1, status)) { ok = false; break; }
-      tc_fence_after();
-      const int64_t row = t * 128 + rl;
-      float v[128];
-#pragma unroll
-      for (int c16 = 0; c16 < 8; ++c16) {
-        if (c16 * 16 < a.NB) tmem_ld16(tmem + db * 128 + c16 * 16 + lane_addr, v + c16 * 16);
-      }
-      tmem_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&dempty[db]));
-      if (row < a.M) {
-        float* xr = a.X + row * a.Rt;
-#pragma unroll
-        for (int r = 0; r < 64; ++r)
-          if (r < a.Rt) xr[r] = v[r] + v[a.Rtp + r];
-      }
-    }
-  } else if (F32) {
-    const int q = warp - 6;
-    const int r = 32 * q + lane;
-    uint32_t it = 0;
-    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-      for (int kc = 0; kc < a.KC; ++kc, ++it) {
-        const int s = it % S;
-        const uint32_t n = it / S;
-        if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
-        unsigned char* sb = st_base + s * stage_bytes;
-        float part = split_row64(sb + r * 128, sb + BOX_BYTES + r * 128, r);
-        float y = part - nrm_c;
-        float tt = nrm + y;
-        nrm_c = (tt - nrm) - y;
-        nrm = tt;
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&cfull[s]));
-      }
-    }
-  }
-  // per-CTA ||Y||^2 from the threads that read the tiles
-  double mine = (double)nrm - (double)nrm_c;
-  mine = warp_sum(mine);
-  if (lane == 0) nred[warp] = mine;
-  tc_fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += nred[w];
-    a.nrm_part[blockIdx.x] = s;
-  }
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem, 256);
-  }
-}
-
-// [U_hi | U_lo]^T as BF16 rows (channel-major, columns = L padded to ldu)
-__global__ void build_u_hilo(const double* __restrict__ U, int L, int Rt, int Rtp, int ldu,
-                             __nv_bfloat16* __restrict__ out) {
-  const int64_t total = (int64_t)2 * Rtp * ldu;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / ldu);
-    const int k = (int)(e % ldu);
-    const int r = c < Rtp ? c : c - Rtp;
-    float v = 0.f;
-    if (r < Rt && k < L) {
-      const double x = U[(int64_t)k * Rt + r];
-      const float hi = __bfloat162float(__float2bfloat16_rn((float)x));
-      v = (c < Rtp) ? hi : (float)(x - (double)hi);
-    }
-    out[e] = __float2bfloat16_rn(v);
-  }
-}
-
-__global__ void sum_doubles(const double* __restrict__ parts, int n, double* __restrict__ out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-    *out = v;
-  }
-}
-
-template <class T>
-__global__ void cvt_u(const double* __restrict__ s, T* __restrict__ d, int64_t n) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    d[e] = (T)s[e];
-}
-
-bool tc_shape_ok(const Geom& g, int dtype) {
-  const int es = dtype == TDK_BF16 ? 2 : 4;
-  if ((g.L * es) % 16 != 0) return false;  // TMA row stride
-  for (int n = 0; n < g.N; ++n)
-    if (g.Rt[n] > 64) return false;
-  return true;
-}
-
 }  // namespace
 
-template <class T>
-int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1);
 
 // ---------------------------------------------------------------- host: sketch
 template <bool F32, int RW>
@@ -1058,95 +754,6 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   sketch_tc_reduce<<<256, 256, 0, ctx->stream>>>(ra, Zdst);
   TDK_LAUNCH_CHECK(ctx);
   return TDK_OK;
-}
-
-// ---------------------------------------------------------------- host: core
-int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* Gv,
-            double* normY2) {
-  if (!tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
-  const bool f32 = dtype == TDK_F32;
-  const int N = g.N;
-  CoArgs a{};
-  a.M = g.M;
-  a.L = (int)g.L;
-  a.KC = (a.L + 63) / 64;
-  a.Rt = g.Rt[N - 1];
-  a.Rtp = (a.Rt + 15) / 16 * 16;
-  a.NB = 2 * a.Rtp;
-  a.ntiles = (g.M + 127) / 128;
-  a.status = ctx->d_status;
-  int grid = (int)std::min<int64_t>(a.ntiles, ctx->num_sms);
-  const int ldu = (a.L + 7) / 8 * 8;
-  int64_t tmpsz = 0;
-  {
-    int64_t Bd = a.Rt;
-    for (int m = N - 2; m >= 1; --m) {
-      int64_t A = 1;
-      for (int k = 0; k < m; ++k) A *= g.I[k];
-      tmpsz = std::max<int64_t>(tmpsz, A * g.Rt[m] * Bd);
-      Bd *= g.Rt[m];
-    }
-  }
-  Planner pl;
-  pl.take<__nv_bfloat16>((size_t)a.NB * ldu);
-  for (int n = 0; n < N; ++n) pl.take<float>((size_t)g.I[n] * g.Rt[n]);
-  pl.take<float>((size_t)g.M * a.Rt);
-  pl.take<float>((size_t)tmpsz);
-  pl.take<float>((size_t)tmpsz);
-  pl.take<double>((size_t)grid);
-  int rc = ws_reserve(ctx, pl.off);
-  if (rc) return rc;
-  Carver cv(ctx->ws);
-  __nv_bfloat16* ub = cv.take<__nv_bfloat16>((size_t)a.NB * ldu);
-  build_u_hilo<<<128, 256, 0, ctx->stream>>>(U[N - 1], a.L, a.Rt, a.Rtp, ldu, ub);
-  TDK_LAUNCH_CHECK(ctx);
-  float* Ut[TDK_MAX_MODES];
-  for (int n = 0; n < N; ++n) {
-    Ut[n] = cv.take<float>((size_t)g.I[n] * g.Rt[n]);
-    cvt_u<float><<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
-    TDK_LAUNCH_CHECK(ctx);
-  }
-  a.X = cv.take<float>((size_t)g.M * a.Rt);
-  float* tmp0 = cv.take<float>((size_t)tmpsz);
-  float* tmp1 = cv.take<float>((size_t)tmpsz);
-  a.nrm_part = cv.take<double>((size_t)grid);
-
-  CUtensorMap tmY, tmU;
-  {
-    const int es = f32 ? 4 : 2;
-    uint64_t dims[3] = {(uint64_t)a.L, (uint64_t)g.M, 1};
-    uint64_t str[2] = {(uint64_t)a.L * es, (uint64_t)a.L * es * (uint64_t)g.M};
-    uint32_t box[3] = {f32 ? 32u : 64u, 128u, 1u};
-    rc = encode_tmap(&tmY, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims,
-                     str, box, true);
-    if (rc) return rc;
-    uint64_t ud[3] = {(uint64_t)a.L, (uint64_t)a.NB, 1};
-    uint64_t us[2] = {(uint64_t)ldu * 2, (uint64_t)ldu * 2 * a.NB};
-    uint32_t ubx[3] = {64u, (uint32_t)a.NB, 1u};
-    rc = encode_tmap(&tmU, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ub, ud, us, ubx, true);
-    if (rc) return rc;
-  }
-  const uint32_t ybytes = f32 ? CoLayout<true>::Y_BYTES : CoLayout<false>::Y_BYTES;
-  const uint32_t stage = ybytes + ((a.NB * 128 + 1023) & ~1023);
-  const int S = f32 ? CoLayout<true>::STAGES : CoLayout<false>::STAGES;
-  size_t smem = 1024 + (size_t)S * stage + 8 * (3 * S + 6) + 8 * 16;
-  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
-  {
-    ProfScope ps(ctx, 1);
-    if (f32) {
-      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_core_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tc_core_kernel<true><<<grid, 320, smem, ctx->stream>>>(tmY, tmU, a);
-    } else {
-      TDK_CUDA_TRY(cudaFuncSetAttribute(tc_core_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tc_core_kernel<false><<<grid, 192, smem, ctx->stream>>>(tmY, tmU, a);
-    }
-    TDK_LAUNCH_CHECK(ctx);
-  }
-  if (normY2) {
-    sum_doubles<<<1, 256, 0, ctx->stream>>>(a.nrm_part, grid, normY2);
-    TDK_LAUNCH_CHECK(ctx);
-  }
-  return core_chain_rest<float>(ctx, g, a.X, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1);
 }
 
 }  // namespace tdk

@@ -249,6 +249,7 @@ def test_tc_core_matches_oracle(tdk, ctx, shape, dtype):
     G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), Ud, ranks, p, "tc")
     assert ctx.sync_status() == 0
     bnd = core_abs_bound(Y, ref["U"])
+    # U split hi + lo (residual < 2^-17); FP32 data split hi + lo as well
     tol = 2e-5 + (2.0 ** -16 if dtype == "f32" else 2.0 ** -17)
     err = np.abs(host(G) - ref["G"])
     assert np.all(err <= tol * bnd), float((err / bnd).max())

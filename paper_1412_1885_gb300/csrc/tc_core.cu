@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
   using Lay = CoLayout<F32, MT>;
   constexpr int S = Lay::STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned start, by offset so that the pointer stays in the shared space
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t b_bytes = (uint32_t)a.NB * 128u;
   const uint32_t stage_bytes = Lay::Y_BYTES + ((b_bytes + 1023) & ~1023u);
   const uint32_t dcols = (uint32_t)MT * a.NB;  // TMEM columns per accumulator buffer
@@ -167,7 +168,8 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
             const unsigned char* row = st_base + s * stage_bytes + m * Lay::SUB_BYTES + rl * 128;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-              const uint4 w = *reinterpret_cast<const uint4*>(row + c * 16);
+              // walk the chunks in swizzled order: 8 consecutive rows then hit 8 distinct bank groups
+              const uint4 w = *reinterpret_cast<const uint4*>(row + ((c ^ (rl & 7)) << 4));
               const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
               for (int e = 0; e < 4; ++e) {

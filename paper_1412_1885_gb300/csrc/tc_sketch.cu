@@ -98,7 +98,7 @@ struct SkArgs {
 
 template <bool F32>
 struct SkLayout {
-  static constexpr int STAGES = 2;
+  static constexpr int STAGES = F32 ? 2 : 3;
   static constexpr uint32_t STAGE_BYTES = F32 ? 64 * KB : 32 * KB;   // 128 j x 128 columns
   static constexpr uint32_t BOX_STRIDE = F32 ? 32 * KB : 16 * KB;     // between the two 64-column halves
   static constexpr uint32_t KT_BYTES = 16 * KB;                        // K_p tile [128 j][64 r] BF16
@@ -110,34 +110,38 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
                      const SkArgs a) {
   using Lay = SkLayout<F32>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned start, by offset so that the pointer stays in the shared space
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* st_base = base;                                   // STAGES x STAGE_BYTES
   unsigned char* wn_base = st_base + Lay::STAGES * Lay::STAGE_BYTES;  // 2*KS boxes of N1 rows x 128 B
   const uint32_t wn_box = (uint32_t)a.N1 * 128u;
   unsigned char* kt_base = wn_base + ((2 * a.KS * wn_box + 1023) & ~1023u);  // 2 x KT_BYTES
   uint64_t* bars = reinterpret_cast<uint64_t*>(kt_base + 2 * Lay::KT_BYTES);
-  uint64_t* full = bars;           // [STAGES]
-  uint64_t* empty = bars + 2;      // [STAGES]
-  uint64_t* cfull = bars + 4;      // [STAGES] (FP32: converted)
-  uint64_t* d1full = bars + 6;     // [2]
-  uint64_t* d1empty = bars + 8;    // [2]
-  uint64_t* ktfull = bars + 10;    // [2]
-  uint64_t* ktempty = bars + 12;   // [2]
-  uint64_t* wnfull = bars + 14;
-  uint64_t* wnempty = bars + 15;
-  uint64_t* d2full = bars + 16;
-  uint64_t* d2empty = bars + 17;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 20);
+  constexpr int S = Lay::STAGES;
+  uint64_t* full = bars;           // [3]
+  uint64_t* empty = bars + 3;      // [3]
+  uint64_t* cfull = bars + 6;      // [3] (FP32: converted)
+  uint64_t* d1full = bars + 9;     // [2]
+  uint64_t* d1empty = bars + 11;   // [2]
+  uint64_t* ktfull = bars + 13;    // [2]
+  uint64_t* ktempty = bars + 15;   // [2]
+  uint64_t* wnfull = bars + 17;
+  uint64_t* wnempty = bars + 18;
+  uint64_t* d2full = bars + 19;
+  uint64_t* d2empty = bars + 20;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 22);
   float* red = reinterpret_cast<float*>(bars + 24);                // [4][64]
   float* coef = red + 4 * 64;                                      // [3][4][64]
   volatile int* abort_flag = reinterpret_cast<volatile int*>(coef + 3 * 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
       mbar_init(smem_u32(&empty[i]), 1);
       mbar_init(smem_u32(&cfull[i]), 4);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&d1full[i]), 1);
       mbar_init(smem_u32(&d1empty[i]), 4);
       mbar_init(smem_u32(&ktfull[i]), 4);
@@ -182,8 +186,8 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
           tma_load_3d(smem_u32(wn_base + b * wn_box), &tmW, k0 + 64 * b, 0, 0, smem_u32(wnfull));
         for (int64_t p = p0; p < p1 && ok; ++p) {
           for (int st = 0; st < a.KS; ++st, ++it) {
-            const int s = it & 1;
-            const uint32_t n = it >> 1;
+            const int s = it % S;
+            const uint32_t n = it / S;
             if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
             unsigned char* dst = st_base + s * Lay::STAGE_BYTES;
             mbar_expect_tx(smem_u32(&full[s]), Lay::STAGE_BYTES);
@@ -225,8 +229,8 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
           const uint32_t d1 = tmem + db * a.d1_cols;
           const uint32_t kt = smem_u32(kt_base + kb * Lay::KT_BYTES);
           for (int st = 0; st < a.KS; ++st, ++it) {
-            const int s = it & 1;
-            const uint32_t n = it >> 1;
+            const int s = it % S;
+            const uint32_t n = it / S;
             if (!mbar_wait(smem_u32(F32 ? &cfull[s] : &full[s]), n & 1, status)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sb = smem_u32(st_base + s * Lay::STAGE_BYTES);
@@ -515,8 +519,8 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
       const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
       for (int64_t p = p0; p < p1 && ok; ++p) {
         for (int st = 0; st < a.KS; ++st, ++it) {
-          const int s = it & 1;
-          const uint32_t n = it >> 1;
+          const int s = it % S;
+          const uint32_t n = it / S;
           if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
           unsigned char* sb = st_base + s * SkLayout<true>::STAGE_BYTES;
           for (int h = 0; h < 2; ++h)
@@ -727,8 +731,9 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     if (rc) return rc;
   }
   const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
-  size_t smem = 1024 + 2 * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 + 4 * 64 * 4 +
-                3 * 256 * 4 + 64;
+  const int nstages = f32 ? SkLayout<true>::STAGES : SkLayout<false>::STAGES;
+  size_t smem = 1024 + (size_t)nstages * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 +
+                4 * 64 * 4 + 3 * 256 * 4 + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
   {

@@ -24,6 +24,7 @@
 // FP32 data: TMA brings FP32 boxes; converter warps split every value into
 // BF16 hi + lo in place, and both parts are multiplied (two MMAs per step).
 #include <algorithm>
+#include <cstdlib>
 
 #include "tc_common.cuh"
 
@@ -88,17 +89,18 @@ struct SkArgs {
   int64_t PCW;
   int64_t nunits;
   int d1_cols;                     // TMEM column stride of the two D1 buffers
+  int S;                           // stages in the ring (2 or 3)
   const float* Wf[TDK_MAX_MODES][TDK_MAX_MODES];  // FP32 W_k^(n) [I_k x Rt_n]
   float* part;
   int64_t ustride;                 // floats per unit
   int64_t poff_last, poff_j;
   int64_t poff_p[TDK_MAX_MODES];
   unsigned* status;
+  unsigned long long* prof;        // optional cycle counters of CTA 0 (null = off)
 };
 
 template <bool F32>
 struct SkLayout {
-  static constexpr int STAGES = F32 ? 2 : 3;
   static constexpr uint32_t STAGE_BYTES = F32 ? 64 * KB : 32 * KB;   // 128 j x 128 columns
   static constexpr uint32_t BOX_STRIDE = F32 ? 32 * KB : 16 * KB;     // between the two 64-column halves
   static constexpr uint32_t KT_BYTES = 16 * KB;                        // K_p tile [128 j][64 r] BF16
@@ -113,11 +115,11 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
   // 1024-byte aligned start, by offset so that the pointer stays in the shared space
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* st_base = base;                                   // STAGES x STAGE_BYTES
-  unsigned char* wn_base = st_base + Lay::STAGES * Lay::STAGE_BYTES;  // 2*KS boxes of N1 rows x 128 B
+  unsigned char* wn_base = st_base + a.S * Lay::STAGE_BYTES;  // 2*KS boxes of N1 rows x 128 B
   const uint32_t wn_box = (uint32_t)a.N1 * 128u;
   unsigned char* kt_base = wn_base + ((2 * a.KS * wn_box + 1023) & ~1023u);  // 2 x KT_BYTES
   uint64_t* bars = reinterpret_cast<uint64_t*>(kt_base + 2 * Lay::KT_BYTES);
-  constexpr int S = Lay::STAGES;
+  const int S = a.S;               // stage ring depth (<= 3)
   uint64_t* full = bars;           // [3]
   uint64_t* empty = bars + 3;      // [3]
   uint64_t* cfull = bars + 6;      // [3] (FP32: converted)
@@ -164,6 +166,16 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
   const uint32_t tmem = *tmem_slot;
   unsigned* status = a.status;
   bool ok = true;
+  // cycle accounting of CTA 0 (slot, lane 0 of the role's first warp)
+  const bool prof_on = a.prof != nullptr && blockIdx.x == 0 && lane == 0;
+  unsigned long long pt = clock64();
+  auto pmark = [&](int slot) {
+    if (prof_on) {
+      const unsigned long long t = clock64();
+      atomicAdd(a.prof + slot, t - pt);
+      pt = t;
+    }
+  };
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -188,7 +200,9 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
           for (int st = 0; st < a.KS; ++st, ++it) {
             const int s = it % S;
             const uint32_t n = it / S;
+            pmark(5);
             if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
+            pmark(6);  // producer waits for a free stage
             unsigned char* dst = st_base + s * Lay::STAGE_BYTES;
             mbar_expect_tx(smem_u32(&full[s]), Lay::STAGE_BYTES);
             const int kc = k0 + 128 * st;
@@ -223,15 +237,20 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         bool first_p = true;
         for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
           const int db = pi & 1, kb = pi & 1;
+          pmark(0);
           if (!mbar_wait(smem_u32(&d1empty[db]), ((pi >> 1) & 1) ^ 1, status)) { ok = false; break; }
+          pmark(1);  // MMA waits for the epilogue to free D1
           if (!mbar_wait(smem_u32(&ktfull[kb]), (pi >> 1) & 1, status)) { ok = false; break; }
+          pmark(2);  // MMA waits for the K_p tile
           tc_fence_after();
           const uint32_t d1 = tmem + db * a.d1_cols;
           const uint32_t kt = smem_u32(kt_base + kb * Lay::KT_BYTES);
           for (int st = 0; st < a.KS; ++st, ++it) {
             const int s = it % S;
             const uint32_t n = it / S;
+            pmark(0);
             if (!mbar_wait(smem_u32(F32 ? &cfull[s] : &full[s]), n & 1, status)) { ok = false; break; }
+            pmark(3);  // MMA waits for data
             tc_fence_after();
             const uint32_t sb = smem_u32(st_base + s * Lay::STAGE_BYTES);
             const int nparts = F32 ? 2 : 1;
@@ -253,6 +272,7 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
               }
             }
             umma_commit(smem_u32(&empty[s]));
+            pmark(4);  // MMA issue
           }
           umma_commit(smem_u32(&d1full[db]));
           umma_commit(smem_u32(&ktempty[kb]));
@@ -277,13 +297,15 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
     // (four vectors of 64: [0] Khatri-Rao rows of the contiguous mode, [1] the
     // row mode, [2], [3] modes 0 and 1 when they are outer modes), kept in
     // three shared buffers so that p+2 is loaded while p is in use.
-    auto coef_load = [&](int64_t pp, float* cr) {
+    // raw factors only: the loads are issued two p ahead and multiplied when
+    // stored, so their latency overlaps the work on p
+    auto coef_load = [&](int64_t pp, float (*cr)[2]) {
       int kidx[2] = {0, 0};
       {
-        int64_t rem = pp;
+        int rem = (int)pp;
         for (int k = Nm - 3; k >= 0; --k) {
-          kidx[k] = (int)(rem % a.I[k]);
-          rem /= a.I[k];
+          kidx[k] = rem % (int)a.I[k];
+          rem /= (int)a.I[k];
         }
       }
 #pragma unroll
@@ -291,21 +313,23 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         const int slot = jl + 128 * h;
         const int vec = slot >> 6, r = slot & 63;
         const int n = vec == 0 ? nl : (vec == 1 ? nj : vec - 2);
-        float v = 0.f;
-        if ((vec < 2 || vec - 2 < nj) && r < a.Rt[n]) {
-          v = 1.f;
-          for (int k = 0; k < Nm - 2; ++k) {
-            if (vec >= 2 && k == n) continue;
-            v *= __ldg(a.Wf[n][k] + (int64_t)kidx[k] * a.Rt[n] + r);
+        const bool live = (vec < 2 || vec - 2 < nj) && r < a.Rt[n];
+        int f = 0;
+        cr[h][0] = live ? 1.f : 0.f;
+        cr[h][1] = 1.f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (k < Nm - 2 && live && !(vec >= 2 && k == n)) {
+            cr[h][f] *= __ldg(a.Wf[n][k] + (int64_t)kidx[k] * a.Rt[n] + r);
+            f = 1;
           }
         }
-        cr[h] = v;
       }
     };
-    auto coef_store = [&](uint32_t pidx, const float* cr) {
+    auto coef_store = [&](uint32_t pidx, const float (*cr)[2]) {
       float* cb = coef + (pidx % 3) * 256;
-      cb[jl] = cr[0];
-      cb[jl + 128] = cr[1];
+      cb[jl] = cr[0][0] * cr[0][1];
+      cb[jl + 128] = cr[1][0] * cr[1][1];
     };
     auto unpack = [](uint32_t w, int e) -> float {
       return e ? __uint_as_float(w & 0xFFFF0000u) : __uint_as_float(w << 16);
@@ -393,7 +417,7 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         return true;
       };
       {
-        float cr[2];
+        float cr[2][2];
         coef_load(p0, cr);
         coef_store(pi, cr);
         if (p0 + 1 < p1) {
@@ -405,13 +429,16 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
       if (!gen_k(pi)) { ok = false; break; }
       for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
         const int db = pi & 1;
-        float cr2[2] = {0.f, 0.f};
+        float cr2[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
         const bool have2 = p + 2 < p1;
         if (have2) coef_load(p + 2, cr2);
+        pmark(8);
         if (p + 1 < p1 && !gen_k(pi + 1)) { ok = false; break; }
+        pmark(9);  // epilogue: K tile (incl. waiting for the MMA to free it)
         const float* cb = coef + (pi % 3) * 256;
         // ---- D1 -> sketches of modes < N
         if (!mbar_wait(smem_u32(&d1full[db]), (pi >> 1) & 1, status)) { ok = false; break; }
+        pmark(10);  // epilogue waits for D1
         tc_fence_after();
         const uint32_t d1 = tmem + db * a.d1_cols + lane_addr;
         // row mode: per-lane accumulation weighted by the outer coefficients
@@ -425,6 +452,7 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
             for (int e = 0; e < 16; ++e) accj[c16 * 16 + e] = fmaf(v[e], cb[64 + c16 * 16 + e], accj[c16 * 16 + e]);
           }
         }
+        pmark(11);  // row mode
         // modes constant over the tile: weight by W_{N-1}^(m)[j], reduce over 128 lanes
         for (int m = 0; m < nj; ++m) {
           float v[RW];
@@ -470,11 +498,13 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
           }
           named_bar(1, 128);
         }
+        pmark(12);  // reductions
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&d1empty[db]));
         if (have2) coef_store(pi + 2, cr2);
         named_bar(1, 128);
+        pmark(13);  // tail barrier
       }
       if (!ok) break;
       // ---- unit end: row-mode partial and the contiguous mode from D2
@@ -658,10 +688,27 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   a.hilo = (f32 && a.RtL <= 32) ? 1 : 0;
   if (!f32 && a.RtL > 64) return TDK_ENOTSUP;
   a.d1_cols = (N1 + 31) / 32 * 32;
-  // columns per unit: as many 128-column blocks as TMEM leaves room for (<= 2)
-  int ks_max = (512 - 2 * a.d1_cols) / 64;
-  if (ks_max < 1) return TDK_ENOTSUP;
-  a.KS = std::min(2, std::min(ks_max, (a.L + 127) / 128));
+  // columns per unit (KS blocks of 128): the widest that TMEM (two D1 buffers +
+  // KS D2 blocks) and shared memory (ring + resident W block) allow, then the
+  // deepest ring; wider units amortise the per-p epilogue over more bytes
+  {
+    const uint32_t stage_b = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
+    a.KS = 0;
+    for (int ks = 4; ks >= 1 && !a.KS; --ks) {
+      if (ks > (a.L + 127) / 128 && ks > 1) continue;
+      if (2 * a.d1_cols + ks * 64 > 512) continue;
+      for (int st = 3; st >= 2; --st) {
+        const size_t need = 1024 + (size_t)st * stage_b + ((2 * ks * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB +
+                            256 + 4 * 64 * 4 + 3 * 256 * 4 + 64;
+        if (need <= (size_t)ctx->max_smem_optin) {
+          a.KS = ks;
+          a.S = st;
+          break;
+        }
+      }
+    }
+    if (!a.KS) return TDK_ENOTSUP;
+  }
   a.KRW = 128 * a.KS;
   a.JT = (a.J + 127) / 128;
   a.KR = (a.L + a.KRW - 1) / a.KRW;
@@ -682,6 +729,11 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   }
   a.ustride = (o + 63) / 64 * 64;
   a.status = ctx->d_status;
+  const bool want_prof = getenv("TDK_SKETCH_PROFILE") != nullptr;
+  if (want_prof) {
+    TDK_CUDA_TRY(cudaMallocAsync((void**)&a.prof, 16 * sizeof(unsigned long long), ctx->stream));
+    TDK_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 16 * sizeof(unsigned long long), ctx->stream));
+  }
 
   // workspace: FP32 W copies, WN^T (BF16), partials
   const int ldw = (a.L + 7) / 8 * 8;
@@ -731,8 +783,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     if (rc) return rc;
   }
   const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
-  const int nstages = f32 ? SkLayout<true>::STAGES : SkLayout<false>::STAGES;
-  size_t smem = 1024 + (size_t)nstages * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 +
+  size_t smem = 1024 + (size_t)a.S * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 +
                 4 * 64 * 4 + 3 * 256 * 4 + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
@@ -758,6 +809,19 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   }
   sketch_tc_reduce<<<256, 256, 0, ctx->stream>>>(ra, Zdst);
   TDK_LAUNCH_CHECK(ctx);
+  if (want_prof) {
+    unsigned long long hp[16];
+    TDK_CUDA_TRY(cudaMemcpyAsync(hp, a.prof, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));
+    TDK_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    cudaFree(a.prof);
+    const char* nm[14] = {"mma:other", "mma:wait_d1empty", "mma:wait_ktile", "mma:wait_data", "mma:issue",
+                          "tma:other", "tma:wait_empty", "-", "epi:other", "epi:ktile", "epi:wait_d1",
+                          "epi:rowmode", "epi:reduce", "epi:tailbar"};
+    fprintf(stderr, "tdk sketch profile (CTA 0, Mcycles, units %lld):", (long long)a.nunits);
+    for (int i = 0; i < 14; ++i)
+      if (i != 7) fprintf(stderr, " %s=%.2f", nm[i], hp[i] / 1e6);
+    fprintf(stderr, "\n");
+  }
   return TDK_OK;
 }
 

@@ -122,39 +122,55 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(w, seconds_target=15.0):
+def cpu_oracle_sample(w, seconds_target=10.0, max_block=200_000_000):
     """Time the FP64 oracle (as it stands) on a leading sub-block of the
     workload on the host cores: sketch + QR + core over the block, then ALS on
-    its core.  Returns (GB/s of the block's two passes, description)."""
+    its core.  A small block is timed first to size the measured block (at
+    most `max_block` elements); the measured block is run repeatedly until
+    about `seconds_target` seconds of oracle work have accumulated.
+    Returns (GB/s of the block's two passes, description, seconds)."""
     import numpy as np
 
     import oracle
     import synth
 
-    # sub-block with ~4e6..3e7 entries along the leading modes
-    shape = list(w.shape)
-    target = 6_000_000 if w.N == 3 else 4_000_000
-    sub = [min(s, max(r + w.p, 8)) for s, r in zip(shape, w.ranks)]
-    # grow the trailing (contiguous) mode first, then the others
-    for n in reversed(range(w.N)):
-        while sub[n] < shape[n] and int(np.prod(sub)) * 2 <= target:
-            sub[n] = min(shape[n], sub[n] * 2)
-    sw = synth.scaled(w, sub)
-    Y = synth.host_tensor(sw)
-    W = synth.sketch_matrices(sw.shape, sw.Rt, sw.seed)
-    B0 = synth.init_factors(sw.Rt, sw.als_R, sw.seed)
-    t0 = time.perf_counter()
-    tk = oracle.rand_tucker(Y, W)
-    if sw.nonneg:
-        A0 = synth.init_factors(sw.shape, sw.als_R, sw.seed, dist="uniform")
-        oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
-    else:
-        oracle.cp_als(tk["G"], B0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
-    dt = time.perf_counter() - t0
-    nbytes = 2 * w.itemsize * int(np.prod(sub))
+    def block(n_target):
+        shape = list(w.shape)
+        sub = [min(s, max(r + w.p, 8)) for s, r in zip(shape, w.ranks)]
+        for n in reversed(range(w.N)):
+            while sub[n] < shape[n] and int(np.prod(sub)) * 2 <= n_target:
+                sub[n] = min(shape[n], sub[n] * 2)
+        return sub
+
+    def prepare(sub):
+        sw = synth.scaled(w, sub)
+        return (sw, synth.host_tensor(sw), synth.sketch_matrices(sw.shape, sw.Rt, sw.seed),
+                synth.init_factors(sw.Rt, sw.als_R, sw.seed),
+                synth.init_factors(sw.shape, sw.als_R, sw.seed, dist="uniform") if sw.nonneg else None)
+
+    def run(prep):
+        sw, Y, W, B0, A0 = prep
+        t0 = time.perf_counter()
+        tk = oracle.rand_tucker(Y, W)
+        if sw.nonneg:
+            oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
+        else:
+            oracle.cp_als(tk["G"], B0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
+        return time.perf_counter() - t0
+
+    probe = block(2_000_000)
+    dt = run(prepare(probe))
+    n_probe = int(np.prod(probe))
+    sub = block(int(min(max_block, max(n_probe, n_probe * seconds_target / max(dt, 1e-3)))))
+    prep = prepare(sub)
+    total, reps = 0.0, 0
+    while reps < 1 or (total < seconds_target and reps < 100):
+        total += run(prep)
+        reps += 1
+    nbytes = 2 * w.itemsize * int(np.prod(sub)) * reps
     desc = (f"oracle rand_tucker + ALS (<=200 sweeps) on the leading {'x'.join(map(str, sub))} block "
-            f"of {w.name}, {dt:.1f} s")
-    return nbytes / dt / 1e9, desc, dt
+            f"of {w.name}, {reps} run(s), {total:.1f} s")
+    return nbytes / total / 1e9, desc, total
 
 
 def run_reference(args, w):
@@ -190,6 +206,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--prec", default=DEFAULT_PREC, choices=["tc", "simt"])
+    ap.add_argument("--shape", default="", help="comma-separated dims replacing the workload's shape")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -201,6 +218,9 @@ def main():
     import synth
 
     w = synth.WORKLOADS[args.config]
+    if args.shape:
+        # same data model, ranks and dtype at another size (small ncu captures)
+        w = synth.scaled(w, [int(x) for x in args.shape.split(",")])
     if args.impl == "reference":
         return run_reference(args, w)
 

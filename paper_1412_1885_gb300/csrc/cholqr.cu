@@ -16,7 +16,7 @@
 namespace tdk {
 namespace {
 
-constexpr int GRAM_ROWS = 16;
+constexpr int GRAM_ROWS = 64;
 
 struct QRArgs {
   int N;
@@ -37,7 +37,7 @@ __global__ void gram_partial_kernel(const double* __restrict__ Z, QRArgs q, doub
   const int64_t I = q.I[n];
   const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
   const int rows = (int)((I - r0) < GRAM_ROWS ? (I - r0) : GRAM_ROWS);
-  __shared__ double Zs[GRAM_ROWS * TDK_MAX_RANK];
+  __shared__ double Zs[GRAM_ROWS * TDK_MAX_RANK];  // 32 KB
   const double* Zn = Z + q.zoff[n];
   for (int e = threadIdx.x; e < rows * Rt; e += blockDim.x) Zs[e] = Zn[r0 * Rt + e];
   __syncthreads();
@@ -51,8 +51,25 @@ __global__ void gram_partial_kernel(const double* __restrict__ Z, QRArgs q, doub
   }
 }
 
-// sum of partials -> Cholesky (upper R, Gram = R^T R) -> Rinv; one CTA per mode
-__global__ void chol_kernel(QRArgs q, const double* __restrict__ gp, double* __restrict__ rinv,
+// Gram = sum of the chunk partials, in chunk order (grid: entries x modes)
+__global__ void gram_reduce_kernel(QRArgs q, const double* __restrict__ gp, const int* __restrict__ fail,
+                                   double* __restrict__ gram) {
+  const int n = blockIdx.y;
+  if (n >= q.N || fail[n]) return;
+  const int Rt = q.Rt[n];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Rt * Rt) return;
+  const int a = e / Rt, b = e % Rt;
+  double s = 0.0;
+  if (a <= b) {
+    const double* g = gp + q.gp_off[n] + e;
+    for (int c = 0; c < q.nchunk[n]; ++c) s += g[(int64_t)c * Rt * Rt];
+  }
+  gram[(int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK + e] = s;
+}
+
+// Cholesky of the Gram (upper R, Gram = R^T R) -> Rinv; one CTA per mode
+__global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* __restrict__ rinv,
                             int* __restrict__ fail) {
   const int n = blockIdx.x;
   const int Rt = q.Rt[n];
@@ -60,44 +77,38 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gp, double* __r
   __shared__ double Ri[TDK_MAX_RANK * TDK_MAX_RANK];
   __shared__ int bad;
   if (fail[n]) return;
-  if (threadIdx.x == 0) bad = 0;
-  const double* g = gp + q.gp_off[n];
-  for (int e = threadIdx.x; e < Rt * Rt; e += blockDim.x) {
-    int a = e / Rt, b = e % Rt;
-    double s = 0.0;
-    if (a <= b)
-      for (int c = 0; c < q.nchunk[n]; ++c) s += g[(int64_t)c * Rt * Rt + e];
-    A[e] = s;
-  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < Rt * Rt; e += nth) A[e] = gram[(int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK + e];
   __syncthreads();
   double mx = 0.0;
   for (int j = 0; j < Rt; ++j) mx = fmax(mx, A[j * Rt + j]);
   const double tiny = Rt * 2.220446049250313e-16 * mx;
-  // right-looking Cholesky on the upper triangle: A = R^T R
+  // right-looking Cholesky on the upper triangle: A = R^T R; the trailing
+  // update runs on a (threadIdx.y, threadIdx.x) = (row, column) grid
   for (int j = 0; j < Rt; ++j) {
     __syncthreads();
     double d = A[j * Rt + j];
     if (!(d > tiny)) {
-      if (threadIdx.x == 0) bad = 1;
+      if (tid == 0) bad = 1;
       break;
     }
-    double rjj = sqrt(d);
+    const double rjj = sqrt(d), irjj = 1.0 / rjj;
     __syncthreads();
-    if (threadIdx.x == 0) A[j * Rt + j] = rjj;
-    for (int b = j + 1 + threadIdx.x; b < Rt; b += blockDim.x) A[j * Rt + b] /= rjj;
+    if (tid == 0) A[j * Rt + j] = rjj;
+    for (int b = j + 1 + tid; b < Rt; b += nth) A[j * Rt + b] *= irjj;
     __syncthreads();
-    for (int e = threadIdx.x; e < Rt * Rt; e += blockDim.x) {
-      int a = e / Rt, b = e % Rt;
-      if (a > j && b >= a) A[e] = fma(-A[j * Rt + a], A[j * Rt + b], A[e]);
-    }
+    for (int a = j + 1 + (int)threadIdx.y; a < Rt; a += blockDim.y)
+      for (int b = a + (int)threadIdx.x; b < Rt; b += blockDim.x)
+        A[a * Rt + b] = fma(-A[j * Rt + a], A[j * Rt + b], A[a * Rt + b]);
   }
   __syncthreads();
   if (bad) {
-    if (threadIdx.x == 0) fail[n] = 1;
+    if (tid == 0) fail[n] = 1;
     return;
   }
   // Rinv = R^{-1}: column b solves R x = e_b (x upper triangular)
-  for (int b = threadIdx.x; b < Rt; b += blockDim.x) {
+  for (int b = tid; b < Rt; b += nth) {
     for (int a = Rt - 1; a >= 0; --a) {
       double s = (a == b) ? 1.0 : 0.0;
       if (a > b) {
@@ -110,7 +121,7 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gp, double* __r
   }
   __syncthreads();
   double* out = rinv + (int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK;
-  for (int e = threadIdx.x; e < Rt * Rt; e += blockDim.x) out[e] = Ri[e];
+  for (int e = tid; e < Rt * Rt; e += nth) out[e] = Ri[e];
 }
 
 // Q = Z Rinv, row-wise; Qdst packed by zoff (dst_ptrs null) or per-mode pointers
@@ -238,6 +249,7 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   Planner pl;
   pl.take<double>(gp);
   pl.take<double>((size_t)g.N * TDK_MAX_RANK * TDK_MAX_RANK);
+  pl.take<double>((size_t)g.N * TDK_MAX_RANK * TDK_MAX_RANK);
   pl.take<double>(g.zoff[g.N]);
   pl.take<int>(TDK_MAX_MODES);
   int rc = ws_reserve(ctx, pl.off);
@@ -245,6 +257,7 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   Carver cv(ctx->ws);
   double* gpart = cv.take<double>(gp);
   double* rinv = cv.take<double>((size_t)g.N * TDK_MAX_RANK * TDK_MAX_RANK);
+  double* gram = cv.take<double>((size_t)g.N * TDK_MAX_RANK * TDK_MAX_RANK);
   double* Q1 = cv.take<double>(g.zoff[g.N]);
   int* fail = cv.take<int>(TDK_MAX_MODES);
   TDK_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int) * TDK_MAX_MODES, ctx->stream));
@@ -256,16 +269,22 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   const dim3 ggrid(maxchunk, g.N);
   const dim3 agrid(64, g.N);
   // round 1: Z -> Q1
+  const dim3 rgrid((TDK_MAX_RANK * TDK_MAX_RANK + 255) / 256, g.N);
+  const dim3 cblk(32, 8);
   gram_partial_kernel<<<ggrid, 256, 0, ctx->stream>>>(Z, q, gpart, fail);
   TDK_LAUNCH_CHECK(ctx);
-  chol_kernel<<<g.N, 256, 0, ctx->stream>>>(q, gpart, rinv, fail);
+  gram_reduce_kernel<<<rgrid, 256, 0, ctx->stream>>>(q, gpart, fail, gram);
+  TDK_LAUNCH_CHECK(ctx);
+  chol_kernel<<<g.N, cblk, 0, ctx->stream>>>(q, gram, rinv, fail);
   TDK_LAUNCH_CHECK(ctx);
   apply_rinv_kernel<<<agrid, 256, 0, ctx->stream>>>(Z, q, rinv, fail, d1);
   TDK_LAUNCH_CHECK(ctx);
   // round 2: Q1 -> U
   gram_partial_kernel<<<ggrid, 256, 0, ctx->stream>>>(Q1, q, gpart, fail);
   TDK_LAUNCH_CHECK(ctx);
-  chol_kernel<<<g.N, 256, 0, ctx->stream>>>(q, gpart, rinv, fail);
+  gram_reduce_kernel<<<rgrid, 256, 0, ctx->stream>>>(q, gpart, fail, gram);
+  TDK_LAUNCH_CHECK(ctx);
+  chol_kernel<<<g.N, cblk, 0, ctx->stream>>>(q, gram, rinv, fail);
   TDK_LAUNCH_CHECK(ctx);
   apply_rinv_kernel<<<agrid, 256, 0, ctx->stream>>>(Q1, q, rinv, fail, d2);
   TDK_LAUNCH_CHECK(ctx);

@@ -50,6 +50,8 @@ extern "C" {
 #define TDK_ECUDA (-3)     /* a CUDA runtime/driver call failed            */
 #define TDK_ETIMEOUT (-4)  /* a bounded device-side wait gave up           */
 #define TDK_ENOTSUP (-5)   /* supported by the ABI, not by this build/GPU  */
+#define TDK_ESCRATCH (-6)  /* problem needs more scratch than the fixed
+                              static array of tucker_sketch_static holds   */
 #define TDK_WRANKDEF 1     /* a sketch was numerically rank deficient; the
                               orthonormal basis was completed (see below)  */
 #define TDK_WNOCONV 2      /* ALS stopped at max_sweeps                    */
@@ -136,6 +138,36 @@ typedef struct {
  */
 int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
                   const double* const W[], double* const U_out[], double* const Z_out[]);
+
+/*
+ * tucker_sketch_static -- the sketch pass of tucker_sketch alone (Z_n for
+ * every mode, no orthonormalisation), computed without allocating any memory.
+ * The paper has no counterpart: it is a deployment variant of the CUDA-core
+ * sketch kernel for callers that cannot allocate device memory.
+ *
+ *   desc   as tucker_sketch; prec must be TDK_PREC_SIMT (else TDK_ENOTSUP).
+ *   Y, W   as tucker_sketch.
+ *   Z_out  N device pointers, all non-NULL; Z_out[n] FP64 [I_n x Rt_n]
+ *          receives Z_n = Y_(n) Omega_n.
+ * Scratch: a file-scope device array of TDK_SKETCH_STATIC_MAX_BYTES bytes
+ * (converted W, per-CTA partial sketches, the packed FP64 sum).  No
+ * cudaMalloc/cudaFree or allocating library routine is called.  A problem
+ * whose converted W plus the packed sketch plus one CTA's partial sketch do
+ * not fit returns TDK_ESCRATCH before anything is launched; otherwise the grid
+ * is reduced until the partials fit, which only changes the order of the
+ * fixed-order FP64 sum.
+ * Sharing: every call on a device uses the same array.  Calls whose work
+ * overlaps on the GPU (other streams, other contexts, other threads) race
+ * and give wrong results; serialise them (one stream, or events).
+ * Set-up: the first call on each device resolves the array's address with
+ * cudaGetSymbolAddress (this may load the module); make that first call
+ * before any stream capture begins.
+ * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOTSUP, TDK_ESCRATCH,
+ * TDK_ECUDA.
+ */
+#define TDK_SKETCH_STATIC_MAX_BYTES ((size_t)16 << 20)
+int tucker_sketch_static(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
+                         const double* const W[], double* const Z_out[]);
 
 /*
  * tucker_core -- G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2 line

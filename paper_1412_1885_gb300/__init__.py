@@ -15,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdk.so")
 
 TDK_OK, TDK_EINVAL, TDK_ENOMEM, TDK_ECUDA, TDK_ETIMEOUT, TDK_ENOTSUP = 0, -1, -2, -3, -4, -5
+TDK_ESCRATCH = -6
+SKETCH_STATIC_MAX_BYTES = 16 << 20
 TDK_WRANKDEF, TDK_WNOCONV, TDK_WPINV = 1, 2, 4
 F64, F32, BF16 = 0, 1, 2
 PREC = {"simt": 0, "tc": 1}
@@ -25,7 +27,7 @@ MAX_RANK = 64
 # symbols the header declares (checked by the CPU tests)
 EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_sync_status",
            "tdk_ctx_launch_count", "tdk_strerror", "tdk_ctx_profile", "tdk_ctx_profile_read", "tucker_sketch",
-           "tucker_core", "ffcp_als"]
+           "tucker_core", "ffcp_als", "tucker_sketch_static"]
 
 
 class TuckerDesc(ctypes.Structure):
@@ -72,6 +74,7 @@ def lib():
         L.tdk_strerror.restype = ctypes.c_char_p
         L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp]
         L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
+        L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
         L.ffcp_als.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, ctypes.POINTER(AlsOpts), pp, pp, vp,
                                ctypes.POINTER(AlsReport)]
         L.tdk_ctx_profile.argtypes = [vp, ctypes.c_int]
@@ -205,6 +208,28 @@ def tucker_sketch(ctx: Context, Y, W, ranks, p, prec="simt", want_Z=False):
     return U, Z
 
 
+def tucker_sketch_static(ctx: Context, Y, W, ranks, p, Z_out=None):
+    """Sketch pass only (Z_n for every mode), through the allocation-free
+    entry point (CUDA-core form; scratch in a fixed static device array, see
+    include/tdk.h).  Z_out: optional preallocated FP64 device tensors
+    [I_n x (R_n + p)].  Returns the Z list."""
+    import torch
+
+    N = Y.dim()
+    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, "simt")
+    Rt = [int(r) + int(p) for r in ranks]
+    if Z_out is None:
+        Z_out = [torch.empty((Y.shape[n], Rt[n]), dtype=torch.float64, device=Y.device) for n in range(N)]
+    Wf = []
+    for n in range(N):
+        for k in range(N):
+            Wf.append(None if k == n else W[n][k].contiguous())
+    ctx._bind_stream()
+    _check(lib().tucker_sketch_static(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _ptrs(Wf),
+                                      _ptrs(Z_out)), "tucker_sketch_static")
+    return Z_out
+
+
 def tucker_core(ctx: Context, Y, U, ranks, p, prec="simt"):
     """G = Y x_1 U_1^T ... x_N U_N^T and ||Y||^2 (device FP64 scalar)."""
     import torch
@@ -268,5 +293,5 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
     return out
 
 
-__all__ = ["Context", "tucker_sketch", "tucker_core", "ffcp_als", "decompose", "lib", "make_desc", "TdkError",
+__all__ = ["Context", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib", "make_desc", "TdkError",
            "EXPORTS", "strerror"]

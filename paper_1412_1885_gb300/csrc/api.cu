@@ -66,6 +66,7 @@ const char* tdk_strerror(int code) {
     case TDK_ECUDA: return "CUDA call failed";
     case TDK_ETIMEOUT: return "bounded wait or time limit exceeded";
     case TDK_ENOTSUP: return "not supported for this configuration";
+    case TDK_ESCRATCH: return "problem exceeds the static scratch array (TDK_SKETCH_STATIC_MAX_BYTES)";
     case TDK_WRANKDEF: return "warning: rank-deficient sketch completed";
     case TDK_WNOCONV: return "warning: ALS stopped at max_sweeps";
     case TDK_WPINV: return "warning: pseudo-inverse used in an ALS solve";

@@ -324,3 +324,177 @@ int sketch_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const dou
 }
 
 }  // namespace tdk
+
+// ---- allocation-free variant of the sketch pass --------------------------------
+// The whole scratch of tucker_sketch_static (converted W, the per-CTA partial
+// sketches, the packed FP64 sum) lives in one file-scope device array, so the
+// call allocates nothing.  Every call on a device shares it: calls that
+// overlap on the GPU race.
+#include <mutex>
+
+namespace tdk {
+namespace {
+
+constexpr size_t SKETCH_STATIC_BYTES = TDK_SKETCH_STATIC_MAX_BYTES;  // 16 MiB
+constexpr int MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_sketch_scratch[SKETCH_STATIC_BYTES];
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[MAX_DEVICES];
+
+// address of the array on the current device; resolved once per device
+int static_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= MAX_DEVICES) return TDK_EINVAL;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sketch_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return TDK_ECUDA;
+    }
+    g_scratch_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+  return TDK_OK;
+}
+
+// byte carve of the static array with 256-byte aligned pieces
+struct StaticCarve {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t n) {
+    size_t o = (off + 255) & ~(size_t)255;
+    off = o + n * sizeof(T);
+    return o;
+  }
+};
+
+template <class TY, class T>
+int sketch_static_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double* const W[],
+                    double* const Z_out[]) {
+  const int N = g.N, last = N - 1;
+  SketchArgs a{};
+  a.N = N;
+  for (int n = 0; n < N; ++n) {
+    a.I[n] = g.I[n];
+    a.Rt[n] = g.Rt[n];
+  }
+  a.M = g.M;
+  a.L = g.L;
+  int C1 = 0;
+  for (int n = 0; n < N - 1; ++n) {
+    a.off[n] = C1;
+    C1 += g.Rt[n];
+  }
+  a.C1 = C1;
+  int TC = (C1 + 15) / 16;
+  int tcs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 28};
+  int TCc = 0;
+  for (int v : tcs)
+    if (v >= TC) { TCc = v; break; }
+  if (TCc == 0) return TDK_EINVAL;
+  a.C1p = 16 * TCc;
+  a.RtL = g.Rt[last];
+  a.RtLp = ((a.RtL + 7) / 8) * 8;
+  if (a.RtLp > 64) return TDK_EINVAL;
+  for (int n = 0; n <= N; ++n) a.zoff[n] = g.zoff[n];
+  a.ztot = g.zoff[N];
+  a.ntiles = (g.M + BM - 1) / BM;
+
+  size_t base_smem = sizeof(T) * ((size_t)BM * (BL + 1) + (size_t)BL * a.C1p + (size_t)BM * a.RtLp +
+                                  (size_t)BM * a.C1p);
+  size_t zl_bytes = sizeof(T) * (size_t)g.L * a.RtL;
+  a.zlast_smem = (base_smem + zl_bytes <= 100 * 1024) ? 1 : 0;
+  size_t smem = base_smem + (a.zlast_smem ? zl_bytes : 0);
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_EINVAL;
+  int per_sm = a.zlast_smem ? 1 : 2;
+  int64_t grid64 = (int64_t)ctx->num_sms * per_sm;
+  if (grid64 > a.ntiles) grid64 = a.ntiles;
+
+  // fixed pieces first; the per-CTA partials take what is left, and the grid
+  // shrinks to fit them (a different grid only changes the summation order)
+  StaticCarve sc;
+  const size_t o_wn = sc.take<T>((size_t)g.L * C1);
+  size_t o_wk[TDK_MAX_MODES][TDK_MAX_MODES] = {};
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k)
+      if (k != n && k != last) o_wk[n][k] = sc.take<T>((size_t)g.I[k] * g.Rt[n]);
+  const size_t o_z = sc.take<double>((size_t)a.ztot);
+  const size_t o_part = (sc.off + 255) & ~(size_t)255;
+  if (o_part >= SKETCH_STATIC_BYTES) return TDK_ESCRATCH;
+  const int64_t fit = (int64_t)((SKETCH_STATIC_BYTES - o_part) / (sizeof(T) * (size_t)a.ztot));
+  if (fit < 1) return TDK_ESCRATCH;
+  if (grid64 > fit) grid64 = fit;
+  const int grid = (int)grid64;
+
+  unsigned char* base = nullptr;
+  int rc = static_scratch(ctx->device, &base);
+  if (rc) return rc;
+  T* WN = reinterpret_cast<T*>(base + o_wn);
+  for (int n = 0; n < N - 1; ++n) {
+    convert_w_kernel<T><<<64, 256, 0, ctx->stream>>>(W[n * N + last], WN, g.L, g.Rt[n], C1, a.off[n]);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  a.WN = WN;
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k) {
+      a.Wk[n][k] = nullptr;
+      if (k == n || k == last) continue;
+      T* d = reinterpret_cast<T*>(base + o_wk[n][k]);
+      convert_w_kernel<T><<<64, 256, 0, ctx->stream>>>(W[n * N + k], d, g.I[k], g.Rt[n], g.Rt[n], 0);
+      TDK_LAUNCH_CHECK(ctx);
+      a.Wk[n][k] = d;
+    }
+  // the kernel zeroes its own partials before accumulating; the reduce
+  // overwrites every element of the packed sum: nothing needs clearing here
+  T* part = reinterpret_cast<T*>(base + o_part);
+  a.part = part;
+  switch (TCc) {
+    case 1: rc = launch_sketch<TY, T, 1>(ctx, a, Y, grid, smem); break;
+    case 2: rc = launch_sketch<TY, T, 2>(ctx, a, Y, grid, smem); break;
+    case 3: rc = launch_sketch<TY, T, 3>(ctx, a, Y, grid, smem); break;
+    case 4: rc = launch_sketch<TY, T, 4>(ctx, a, Y, grid, smem); break;
+    case 6: rc = launch_sketch<TY, T, 6>(ctx, a, Y, grid, smem); break;
+    case 8: rc = launch_sketch<TY, T, 8>(ctx, a, Y, grid, smem); break;
+    case 12: rc = launch_sketch<TY, T, 12>(ctx, a, Y, grid, smem); break;
+    case 16: rc = launch_sketch<TY, T, 16>(ctx, a, Y, grid, smem); break;
+    case 24: rc = launch_sketch<TY, T, 24>(ctx, a, Y, grid, smem); break;
+    case 28: rc = launch_sketch<TY, T, 28>(ctx, a, Y, grid, smem); break;
+    default: rc = TDK_EINVAL;
+  }
+  if (rc) return rc;
+  double* Z = reinterpret_cast<double*>(base + o_z);
+  z_reduce_kernel<T><<<256, 256, 0, ctx->stream>>>(part, a.ztot, grid, Z);
+  TDK_LAUNCH_CHECK(ctx);
+  for (int n = 0; n < N; ++n)
+    TDK_CUDA_TRY(cudaMemcpyAsync(Z_out[n], Z + g.zoff[n], sizeof(double) * (size_t)g.I[n] * g.Rt[n],
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+  return TDK_OK;
+}
+
+}  // namespace
+}  // namespace tdk
+
+extern "C" int tucker_sketch_static(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
+                                    const double* const W[], double* const Z_out[]) {
+  using namespace tdk;
+  if (!ctx || !desc || !Y || !W || !Z_out) return TDK_EINVAL;
+  Geom g;
+  int rc = make_geom(desc, &g);
+  if (rc) return rc;
+  if (desc->prec != TDK_PREC_SIMT) return TDK_ENOTSUP;
+  for (int n = 0; n < g.N; ++n) {
+    if (!Z_out[n]) return TDK_EINVAL;
+    for (int k = 0; k < g.N; ++k)
+      if (k != n && !W[n * g.N + k]) return TDK_EINVAL;
+  }
+  TDK_CUDA_TRY(cudaSetDevice(ctx->device));
+  switch (desc->dtype) {
+    case TDK_F64: return sketch_static_t<double, double>(ctx, g, Y, W, Z_out);
+    case TDK_F32: return sketch_static_t<float, float>(ctx, g, Y, W, Z_out);
+    case TDK_BF16: return sketch_static_t<__nv_bfloat16, float>(ctx, g, Y, W, Z_out);
+  }
+  return TDK_EINVAL;
+}

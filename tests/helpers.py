@@ -9,6 +9,12 @@ TORCH_DT = {"f64": "float64", "f32": "float32", "bf16": "bfloat16"}
 DT_CODE = {"f64": 0, "f32": 1, "bf16": 2}
 
 
+# element-wise sketch tolerance of the CUDA-core form, relative to the bound
+# sum |y| * prod |w| of each entry (FP64: rounding of FP64 FMAs; FP32
+# accumulation for F32 and BF16 data)
+TOL_SKETCH = {("f64", "simt"): 1e-12, ("f32", "simt"): 2e-5, ("bf16", "simt"): 2e-5}
+
+
 def dev_tensor(Y: np.ndarray, dtype: str, device="cuda"):
     import torch
 

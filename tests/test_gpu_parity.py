@@ -8,14 +8,15 @@ import pytest
 
 import oracle
 import synth
-from helpers import DT_CODE, core_abs_bound, dev_tensor, dev_W, host, recon_err, sketch_abs_bound, small_problem
+from helpers import (DT_CODE, TOL_SKETCH, core_abs_bound, dev_tensor, dev_W, host, recon_err, sketch_abs_bound,
+                     small_problem)
 
 pytestmark = pytest.mark.gpu
 
-# relative rounding unit of the accumulation per form, times a safety factor:
-# FP64: products and sums in FP64; FP32/BF16 data on CUDA cores: FP32 sums of
-# up to ~1e6 terms (errors grow like sqrt(terms) * u32 in practice).
-TOL_SKETCH = {("f64", "simt"): 1e-12, ("f32", "simt"): 2e-5, ("bf16", "simt"): 2e-5}
+# TOL_SKETCH (helpers): relative rounding unit of the accumulation per form,
+# times a safety factor: FP64: products and sums in FP64; FP32/BF16 data on
+# CUDA cores: FP32 sums of up to ~1e6 terms (errors grow like sqrt(terms) * u32
+# in practice).
 
 SHAPES = [
     (67, 45, 130),        # 3015 rows (47 tiles of 64 + tail), 130 columns (4 chunks of 32 + tail)

@@ -289,3 +289,112 @@ def test_ffcp_fit_within_paper_table1_band():
         fits.append(100 * (1 - np.linalg.norm(Ystar - Yh) / np.linalg.norm(Ystar)))
     for f in fits:
         assert mean - 2 * std <= f <= 100.0, fits
+
+
+# ---------------------------------------------------------------- learned initialiser (oracle/mlp.py)
+from oracle import mlp as omlp  # noqa: E402
+
+
+def _tiny_mlp_problem(seed, N=3, Rt=3, hidden=5, batch=3, R=(2, 3, 1)):
+    r = np.random.default_rng(seed)
+    sizes = omlp.param_sizes(N, Rt, hidden)
+    theta = r.standard_normal(sum(sizes)) * 0.5
+    din = Rt ** N
+    X = r.standard_normal((batch, din))
+    S = r.standard_normal((batch,) + (Rt,) * N)
+    T = [[r.standard_normal((Rt, R[s])) for _ in range(N)] for s in range(batch)]
+    return theta, X, S, np.array(R), T
+
+
+def test_mlp_backward_matches_central_differences():
+    # exact form: the analytic gradient of the batch loss through the whole
+    # network against central differences of the loss itself
+    N, Rt, hidden = 3, 3, 5
+    theta, X, S, R, T = _tiny_mlp_problem(7)
+    L, g, _ = omlp.loss_grad(theta, X, S, R, N, Rt, hidden, T=T, alpha=0.3, bf16=False)
+    h = 1e-6
+    idx = np.random.default_rng(8).choice(theta.size, 60, replace=False)
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        Op, _ = omlp.forward(tp, X, N, Rt, hidden, bf16=False)
+        Om, _ = omlp.forward(tm, X, N, Rt, hidden, bf16=False)
+        fd = (omlp.loss(Op, S, R, T, 0.3) - omlp.loss(Om, S, R, T, 0.3)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    # columns beyond a sample's rank R are outside the model: zero gradient
+    O, _ = omlp.forward(theta, X, N, Rt, hidden, bf16=False)
+    dO = omlp._dloss_dO(O, S, R, T, 0.3)
+    for s, Rs in enumerate(R):
+        for n in range(N):
+            blk = dO[s, n * Rt * Rt:(n + 1) * Rt * Rt].reshape(Rt, Rt)
+            assert np.all(blk[:, Rs:] == 0.0) and np.any(blk[:, :Rs] != 0.0)
+    assert np.isfinite(L)
+
+
+def test_mlp_loss_equals_gram_identity_form():
+    # ||S - [[B]]||^2 = ||S||^2 - 2 <S, [[B]]> + 1^T (HADAMARD_n B_n^T B_n) 1
+    N, Rt = 3, 4
+    r = np.random.default_rng(9)
+    S = r.standard_normal((1, Rt, Rt, Rt))
+    O = r.standard_normal((1, N * Rt * Rt))
+    R = np.array([3])
+    Bs = [O[0, n * Rt * Rt:(n + 1) * Rt * Rt].reshape(Rt, Rt)[:, :3] for n in range(N)]
+    inner = sum(float(np.einsum("ijk,i,j,k->", S[0], Bs[0][:, c], Bs[1][:, c], Bs[2][:, c])) for c in range(3))
+    gram = np.ones((3, 3))
+    for B in Bs:
+        gram = gram * (B.T @ B)
+    ref = float(np.sum(S * S)) - 2 * inner + float(gram.sum())
+    assert abs(omlp.loss(O, S, R) - ref) < 1e-10 * max(1.0, abs(ref))
+
+
+def test_canonical_core_independent_of_tucker_basis():
+    # a change of Tucker basis U_n -> U_n Q_n (Q_n orthogonal) turns the core
+    # into G x_n Q_n^T; the canonical core and the ambient bases U_n V_n must
+    # not change
+    r = np.random.default_rng(10)
+    Rt, I = 5, 30
+    G = r.standard_normal((Rt, Rt, Rt)) * np.array([5.0, 3, 2, 1, 0.5])[:, None, None]
+    Us = [np.linalg.qr(r.standard_normal((I, Rt)))[0] for _ in range(3)]
+    Qs = [np.linalg.qr(r.standard_normal((Rt, Rt)))[0] for _ in range(3)]
+    G2 = G
+    for n in range(3):
+        G2 = ttm(G2, Qs[n], n)  # G x_n Q_n^T
+    U2 = [U @ Q for U, Q in zip(Us, Qs)]
+    S1, V1, n1 = omlp.canonicalise(G, [U.sum(axis=0) for U in Us])
+    S2, V2, n2 = omlp.canonicalise(G2, [U.sum(axis=0) for U in U2])
+    assert abs(n1 - n2) < 1e-12 * n1
+    assert np.abs(S1 - S2).max() < 1e-10
+    for n in range(3):
+        assert np.abs(Us[n] @ V1[n] - U2[n] @ V2[n]).max() < 1e-10
+        assert np.all((Us[n] @ V1[n]).sum(axis=0) >= 0)
+    # S x_n V_n * ||G|| reconstructs G
+    back = S1 * n1
+    for n in range(3):
+        back = ttm(back, V1[n].T, n)
+    assert np.abs(back - G).max() < 1e-10 * np.abs(G).max()
+
+
+def test_gelu_closed_forms():
+    assert omlp.gelu(0.0) == 0.0
+    # gelu(1) = Phi(1); Phi(1) = 0.841344746068542948... (normal table value)
+    assert abs(float(omlp.gelu(1.0)) - 0.8413447460685429) < 1e-15
+    assert abs(float(omlp.gelu(-1.0)) + 1.0 - 0.8413447460685429) < 1e-15  # -1 * Phi(-1)
+    assert abs(float(omlp.gelu(12.0)) - 12.0) < 1e-12 and abs(float(omlp.gelu(-12.0))) < 1e-12
+    z = np.linspace(-4, 4, 33)
+    h = 1e-6
+    fd = (omlp.gelu(z + h) - omlp.gelu(z - h)) / (2 * h)
+    assert np.abs(fd - omlp.gelu_grad(z)).max() < 1e-8
+
+
+def test_adam_constant_gradient_closed_form():
+    # constant g: the bias-corrected moments are exactly g and g^2, so every
+    # step moves by lr * g / (|g| + eps)
+    g = np.array([0.3, -2.0, 1e-3])
+    th = np.zeros(3)
+    m = np.zeros(3)
+    v = np.zeros(3)
+    lr, eps = 0.01, 1e-8
+    for t in range(1, 26):
+        th, m, v = omlp.adam_step(th, m, v, g, t, lr, eps=eps)
+    assert np.abs(th - (-25 * lr * g / (np.abs(g) + eps))).max() < 1e-12

@@ -14,8 +14,8 @@
  *   ffcp_als        CP-ALS on the core with the lift A_n = U_n B_n
  *                   (Sec. III-B, Alg. 1; Eqs. 9, 11-13, 16), unconstrained or
  *                   with projected nonnegative updates (P_+ of Eq. 8).
- *   ffcp_predict_init  learned initial core-space factors (no counterpart in
- *                   the paper; see its comment).
+ *   ffcp_predict_init  learned initial core-space factors from a small MLP
+ *                   (no counterpart in the paper; see the tdk_mlp section).
  *
  * Conventions for every entry point:
  *   - Tensors and matrices are ROW-MAJOR, last index fastest.  The mode-n
@@ -234,6 +234,95 @@ int ffcp_als(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* G,
              const double* const U[], const double* normY2, const tdk_als_opts* opts,
              double* const B_io[], double* const A_io[], double* lambda_out,
              tdk_als_report* rep);
+
+/* ======================================================================
+ * Learned initialiser (no counterpart in the paper: its ALS starts from random
+ * or HOSVD factors, Alg. 1 "Initialize A").  A small MLP maps a Tucker core G
+ * (output of tucker_core, all sketch widths equal to Rt) to initial
+ * core-space factors B_n for ffcp_als.
+ *
+ * Canonical form of a core: V_n = eigenvectors of G_(n) G_(n)^T, by
+ * decreasing eigenvalue, column j negated when colsum_n . v_j < 0, where
+ * colsum_n = 1^T U_n (so that the ambient vector U_n v_j has a nonnegative
+ * entry sum: the rule does not depend on the basis U_n the sketch produced);
+ * S = G x_1 V_1^T ... x_N V_N^T / ||G||.
+ * Network: x = BF16(sqrt(Rt^N) vec S) (unit RMS) -> hidden -> hidden -> N*Rt*Rt, GELU
+ * activations, BF16 weights and activations on tcgen05 tensor cores with FP32
+ * accumulation, FP32 master weights.  Output O[(n*Rt + i)*Rt + r] =
+ * Bhat_n[i, r] in canonical coordinates; only the first R columns are used.
+ * Loss per sample: ||S - [[Bhat]]||^2 + alpha ||[[Bhat]] - [[T]]||^2 with
+ * T_n = V_n^T B*_n (B*_N / ||G||), the converged FFCP factors of the same
+ * core; both terms are invariant under a permutation of the R columns; the
+ * batch loss is the mean.  Training: back-propagation and Adam.
+ * ====================================================================== */
+typedef struct tdk_mlp tdk_mlp;
+
+typedef struct {
+  int N;          /* order of the cores, 2..4                               */
+  int Rt;         /* sketch width of every mode, 2..32; Rt^N <= 12288       */
+  int hidden;     /* width of the two hidden layers, 8..8192               */
+  int max_batch;  /* largest batch of tdk_mlp_train_step, 1..65536          */
+} tdk_mlp_desc;
+
+/* Parameter vector layout (FP32, row-major blocks in this order): W1
+   [hidden x Rt^N], b1 [hidden], W2 [hidden x hidden], b2 [hidden], W3
+   [N*Rt*Rt x hidden], b3 [N*Rt*Rt]. */
+enum {
+  TDK_MLP_PARAMS = 0,      /* the parameter vector                          */
+  TDK_MLP_GRADS = 1,       /* gradient of the last train step's batch loss   */
+  TDK_MLP_CANON_CORE = 2,  /* last batch: S, FP32 [batch x Rt^N]            */
+  TDK_MLP_ROTATIONS = 3,   /* last batch: V_n, FP32 [batch][N][Rt][Rt]      */
+  TDK_MLP_OUTPUT = 4       /* last batch: network output, FP32 [batch x N*Rt*Rt] */
+};
+
+typedef struct {
+  double alpha;   /* weight of the target term (used when Bstar != NULL)   */
+  double lr;      /* Adam step size                                        */
+  double beta1, beta2, eps;  /* Adam moments and denominator guard        */
+  int update;     /* 0: loss and gradients only; 1: also one Adam step      */
+  int reserved;
+} tdk_mlp_train_opts;
+
+/* Create a model (weights zero until tdk_mlp_set_params) with device
+   buffers for max_batch samples.  Errors: TDK_EINVAL, TDK_ENOMEM, TDK_ECUDA. */
+int tdk_mlp_create(tdk_ctx* ctx, const tdk_mlp_desc* desc, tdk_mlp** out);
+/* Free the model (waits for the device first). */
+int tdk_mlp_destroy(tdk_mlp* m);
+/* Number of FP32 parameters. */
+int64_t tdk_mlp_param_count(const tdk_mlp* m);
+/* Copy a host parameter vector in (layout above); resets Adam's moments and
+   step counter.  Synchronous. */
+int tdk_mlp_set_params(tdk_ctx* ctx, tdk_mlp* m, const float* host_params);
+/* Copy one of the TDK_MLP_* arrays out to host memory.  Synchronous. */
+int tdk_mlp_get(tdk_ctx* ctx, tdk_mlp* m, int what, float* host_out);
+/* colsum_n = 1^T U_n for every mode, FP64 [N][Rt] device output (the sign
+   rule's input; all Rt_n must be equal). */
+int tdk_mlp_colsums(tdk_ctx* ctx, const tdk_tucker_desc* desc, const double* const U[], double* out);
+/*
+ * One training step on a batch of cores (device inputs):
+ *   G        FP32 [batch][Rt^N] raw cores from tucker_core;
+ *   colsums  FP64 [batch][N][Rt] (tdk_mlp_colsums of each core's U);
+ *   R        int32 [batch], CP rank of each sample, 1..Rt;
+ *   Bstar    NULL or FP64 [batch][N][Rt][Rt]: converged FFCP factors of each
+ *            core (columns >= R ignored);
+ *   lambda   NULL or FP64 [batch][Rt]: weights of Bstar's columns, so that
+ *            G ~ [[lambda; B*]] (NULL: the weights are already absorbed).
+ * Computes the loss and its gradient (TDK_MLP_GRADS) and, with
+ * opts->update, one Adam step.  *loss_out (host, may be NULL) receives the
+ * batch loss, which makes the call synchronous.
+ */
+int tdk_mlp_train_step(tdk_ctx* ctx, tdk_mlp* m, int batch, const float* G, const double* colsums, const int* R,
+                       const double* Bstar, const double* lambda, const tdk_mlp_train_opts* opts,
+                       double* loss_out);
+/*
+ * ffcp_predict_init -- initial core-space factors for ffcp_als from the
+ * model: canonicalise G (desc->dtype F64 -> FP64 core, else FP32), run the
+ * network, B_out[n] = V_n Bhat_n[:, :R] as FP64 [Rt x R] (pass as B_io with
+ * init = TDK_INIT_GIVEN).  U: the Tucker factors of the core (for the sign
+ * rule).  Errors: TDK_EINVAL (shape mismatch with the model), TDK_ECUDA.
+ */
+int ffcp_predict_init(tdk_ctx* ctx, tdk_mlp* m, const tdk_tucker_desc* desc, const void* G,
+                      const double* const U[], int R, double* const B_out[]);
 
 #ifdef __cplusplus
 }

@@ -15,6 +15,8 @@ canonicalise(G, colsums)
     ambient vector U_n v_j then has a nonnegative entry sum, a rule that does
     not depend on the (random) basis U_n the sketch produced.
     S = G x_1 V_1^T ... x_N V_N^T / ||G||   (unit Frobenius norm).
+input(S)
+    x = sqrt(Rt^N) vec(S): the canonical core scaled to unit RMS.
 forward(params, x)
     Z1 = x W1^T + b1,  H1 = gelu(Z1),  Z2 = H1 W2^T + b2,  H2 = gelu(Z2),
     O  = H2 W3^T + b3,  gelu(z) = z Phi(z) (exact, via erf).
@@ -47,7 +49,8 @@ from scipy.special import erf
 from .tucker import fold, unfold
 from .cpals import cp_full
 
-__all__ = ["mlp_dims", "param_sizes", "unpack", "canonicalise", "canonical_target", "gelu", "gelu_grad",
+__all__ = ["mlp_dims", "param_sizes", "unpack", "canonicalise", "canonical_target", "network_input", "gelu",
+           "gelu_grad",
            "forward", "loss", "loss_grad", "adam_step", "decanonicalise"]
 
 
@@ -110,6 +113,14 @@ def canonical_target(Bs, Vs, normG):
     T = [V.T @ np.asarray(B, dtype=np.float64) for V, B in zip(Vs, Bs)]
     T[-1] = T[-1] / normG
     return T
+
+
+def network_input(S):
+    """x = sqrt(Rt^N) vec(S) for a batch of canonical cores [batch, Rt, ..., Rt]."""
+    S = np.asarray(S, dtype=np.float64)
+    b = S.shape[0]
+    X = S.reshape(b, -1)
+    return X * math.sqrt(X.shape[1])
 
 
 def decanonicalise(Bhat, Vs):

@@ -27,7 +27,10 @@ MAX_RANK = 64
 # symbols the header declares (checked by the CPU tests)
 EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_sync_status",
            "tdk_ctx_launch_count", "tdk_strerror", "tdk_ctx_profile", "tdk_ctx_profile_read", "tucker_sketch",
-           "tucker_core", "ffcp_als", "tucker_sketch_static"]
+           "tucker_core", "ffcp_als", "tucker_sketch_static", "tdk_mlp_create", "tdk_mlp_destroy",
+           "tdk_mlp_param_count", "tdk_mlp_set_params", "tdk_mlp_get", "tdk_mlp_colsums", "tdk_mlp_train_step",
+           "ffcp_predict_init"]
+MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
 
 
 class TuckerDesc(ctypes.Structure):
@@ -44,6 +47,16 @@ class AlsOpts(ctypes.Structure):
 class AlsReport(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("status", ctypes.c_int), ("fit_core", ctypes.c_double),
                 ("fit_Y", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("Rt", ctypes.c_int), ("hidden", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class MlpTrainOpts(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("update", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class TdkError(RuntimeError):
@@ -77,6 +90,20 @@ def lib():
         L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
         L.ffcp_als.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, ctypes.POINTER(AlsOpts), pp, pp, vp,
                                ctypes.POINTER(AlsReport)]
+        L.tdk_mlp_create.argtypes = [vp, ctypes.POINTER(MlpDesc), ctypes.POINTER(vp)]
+        L.tdk_mlp_destroy.argtypes = [vp]
+        L.tdk_mlp_param_count.argtypes = [vp]
+        L.tdk_mlp_param_count.restype = i64
+        L.tdk_mlp_set_params.argtypes = [vp, vp, vp]
+        L.tdk_mlp_get.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.tdk_mlp_colsums.argtypes = [vp, ctypes.POINTER(TuckerDesc), pp, vp]
+        L.tdk_mlp_train_step.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.POINTER(MlpTrainOpts),
+                                         ctypes.POINTER(ctypes.c_double)]
+        L.ffcp_predict_init.argtypes = [vp, vp, ctypes.POINTER(TuckerDesc), vp, pp, ctypes.c_int, pp]
+        if hasattr(L, "tdk_test_gemm_bf16"):
+            L.tdk_test_gemm_bf16.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                             ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                             ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int]
         L.tdk_ctx_profile.argtypes = [vp, ctypes.c_int]
         L.tdk_ctx_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
@@ -277,21 +304,122 @@ def ffcp_als(ctx: Context, G, U, shape, ranks, p, dtype_code, R, max_sweeps=1000
             "fit_Y": rep.fit_Y, "ms": rep.ms}
 
 
-def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sweeps=1000, tol=1e-7,
-              init="given", B0=None, A0=None, check_every=8):
-    """The whole path: sketch -> CholQR2 -> core -> FFCP -> lift.  Y may be a
-    host tensor (copied in) or a device tensor; results stay on the device."""
-    import torch
+class Mlp:
+    """Learned FFCP initialiser (see include/tdk.h, tdk_mlp section): an MLP
+    from a canonicalised Tucker core to initial core-space factors."""
 
+    def __init__(self, ctx: Context, N: int, Rt: int, hidden: int = 1024, max_batch: int = 256):
+        self.ctx = ctx
+        self.N, self.Rt, self.hidden, self.max_batch = int(N), int(Rt), int(hidden), int(max_batch)
+        self._h = ctypes.c_void_p()
+        d = MlpDesc(N=self.N, Rt=self.Rt, hidden=self.hidden, max_batch=self.max_batch)
+        ctx._bind_stream()
+        _check(lib().tdk_mlp_create(ctx.handle, ctypes.byref(d), ctypes.byref(self._h)), "tdk_mlp_create")
+        self.din = self.Rt ** self.N
+        self.dout = self.N * self.Rt * self.Rt
+        self._last = 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def param_count(self) -> int:
+        return int(lib().tdk_mlp_param_count(self._h))
+
+    def set_params(self, theta):
+        import numpy as np
+
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.param_count():
+            raise ValueError("parameter vector has the wrong size")
+        self.ctx._bind_stream()
+        _check(lib().tdk_mlp_set_params(self.ctx.handle, self._h, a.ctypes.data_as(ctypes.c_void_p)),
+               "tdk_mlp_set_params")
+
+    def get(self, what: int):
+        """A TDK_MLP_* array as float32 numpy (batch arrays of the last call)."""
+        import numpy as np
+
+        B, RR = self._last, self.Rt * self.Rt
+        n = {MLP_PARAMS: self.param_count(), MLP_GRADS: self.param_count(), MLP_CANON_CORE: B * self.din,
+             MLP_ROTATIONS: B * self.N * RR, MLP_OUTPUT: B * self.dout}[what]
+        out = np.empty(n, dtype=np.float32)
+        self.ctx._bind_stream()
+        _check(lib().tdk_mlp_get(self.ctx.handle, self._h, int(what), out.ctypes.data_as(ctypes.c_void_p)),
+               "tdk_mlp_get")
+        return out
+
+    def train_step(self, G, colsums, R, Bstar=None, alpha=0.0, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   update=True, lam=None):
+        """One step on a device batch: G FP32 [B, Rt^N], colsums FP64 [B, N, Rt],
+        R int32 [B], Bstar FP64 [B, N, Rt, Rt] or None, lam FP64 [B, Rt] or None
+        (weights of Bstar's columns).  Returns the batch loss."""
+        o = MlpTrainOpts(alpha=float(alpha), lr=float(lr), beta1=float(beta1), beta2=float(beta2), eps=float(eps),
+                         update=int(bool(update)), reserved=0)
+        loss = ctypes.c_double(0.0)
+        B = int(G.shape[0])
+        self.ctx._bind_stream()
+        _check(lib().tdk_mlp_train_step(self.ctx.handle, self._h, B, ctypes.c_void_p(G.data_ptr()),
+                                        ctypes.c_void_p(colsums.data_ptr()), ctypes.c_void_p(R.data_ptr()),
+                                        ctypes.c_void_p(Bstar.data_ptr() if Bstar is not None else None),
+                                        ctypes.c_void_p(lam.data_ptr() if lam is not None else None),
+                                        ctypes.byref(o), ctypes.byref(loss)), "tdk_mlp_train_step")
+        self._last = B
+        return loss.value
+
+    def colsums(self, U, shape, ranks, p):
+        """1^T U_n for every mode, FP64 device [N, Rt]."""
+        import torch
+
+        desc = make_desc(shape, F32, ranks, p)
+        out = torch.empty((len(shape), self.Rt), dtype=torch.float64, device=U[0].device)
+        self.ctx._bind_stream()
+        _check(lib().tdk_mlp_colsums(self.ctx.handle, ctypes.byref(desc), _ptrs([u.contiguous() for u in U]),
+                                     ctypes.c_void_p(out.data_ptr())), "tdk_mlp_colsums")
+        return out
+
+    def predict_init(self, G, U, shape, ranks, p, dtype_code, R):
+        """Initial core-space factors B_n (FP64 [Rt, R]) for ffcp_als."""
+        import torch
+
+        desc = make_desc(shape, dtype_code, ranks, p)
+        B = [torch.empty((self.Rt, int(R)), dtype=torch.float64, device=G.device) for _ in range(self.N)]
+        self.ctx._bind_stream()
+        _check(lib().ffcp_predict_init(self.ctx.handle, self._h, ctypes.byref(desc), ctypes.c_void_p(G.data_ptr()),
+                                       _ptrs([u.contiguous() for u in U]), int(R), _ptrs(B)), "ffcp_predict_init")
+        self._last = 1
+        return B
+
+    def close(self):
+        if self._h:
+            lib().tdk_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sweeps=1000, tol=1e-7,
+              init="given", B0=None, A0=None, check_every=8, model=None):
+    """The whole path: sketch -> CholQR2 -> core -> FFCP -> lift.  Y may be a
+    host tensor (copied in) or a device tensor; results stay on the device.
+    With `model` (an Mlp) and the unconstrained form, the ALS starts from the
+    learned initial factors instead of B0."""
     if not Y.is_cuda:
         Y = Y.to(f"cuda:{ctx.device}", non_blocking=True)
     U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
     G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
+    if model is not None and not nonneg:
+        B0 = model.predict_init(G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R)
+        init = "given"
     out = ffcp_als(ctx, G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R, max_sweeps, tol, nonneg, init, B0, A0,
                    nrm, check_every)
     out.update({"U": U, "G": G, "normY2": nrm})
     return out
 
 
-__all__ = ["Context", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib", "make_desc", "TdkError",
-           "EXPORTS", "strerror"]
+__all__ = ["Context", "Mlp", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
+           "make_desc", "TdkError", "EXPORTS", "strerror"]

@@ -149,6 +149,32 @@ def init_factors(dims, R: int, seed: int, dist: str = "normal"):
     return out
 
 
+TAG_MLP = 7
+
+
+def mlp_init_params(N: int, Rt: int, hidden: int, seed: int, hosvd_start: bool = False,
+                    out_scale: float = 1.0) -> np.ndarray:
+    """Initial parameter vector of the learned initialiser's MLP (layout
+    W1, b1, W2, b2, W3, b3 as in the C header): weights i.i.d.
+    N(0, 1 / fan_in), biases zero, as float32.  With hosvd_start the output
+    bias holds an identity block per mode (in canonical coordinates the
+    leading singular vectors of the core: the HOSVD start of ALS) and the
+    output weights are scaled by out_scale, so training starts from the HOSVD
+    initialisation and learns corrections to it."""
+    din, dout = Rt ** N, N * Rt * Rt
+    r = rng(seed, TAG_MLP)
+    parts = []
+    for li, (fan_in, fan_out) in enumerate(((din, hidden), (hidden, hidden), (hidden, dout))):
+        W = r.standard_normal((fan_out, fan_in)) / math.sqrt(fan_in)
+        b = np.zeros(fan_out)
+        if li == 2 and hosvd_start:
+            W = W * out_scale
+            b = np.concatenate([np.eye(Rt).ravel() for _ in range(N)]) * 0.5
+        parts.append(W.ravel())
+        parts.append(b)
+    return np.concatenate(parts).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # The five workloads (sizes, ranks and data model of the synthetic runs).
 # --------------------------------------------------------------------------

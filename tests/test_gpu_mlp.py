@@ -1,0 +1,290 @@
+"""GPU parity of the learned initialiser (tcgen05 GEMM, canonicalisation,
+loss and gradients, Adam, prediction) against the FP64 oracle (oracle/mlp.py)
+on the same seeded inputs, through the C ABI.
+
+Tolerances: GEMM products of BF16 values are exact in FP32, so an FP32 output
+differs from the FP64 sum by the FP32 accumulation only (bounded by
+K * 2^-23 * sum |a b|).  A BF16 output may differ by one BF16 unit
+(2^-7 relative) where the pre-rounding values straddle a rounding boundary.
+Through the network, such single-unit differences of a few stored
+activations bound the norm-wise differences stated per test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp as omlp
+from helpers import dev_tensor, dev_W, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tdk():
+    import paper_1412_1885_gb300 as t
+    from paper_1412_1885_gb300 import build
+
+    build.build()
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(tdk):
+    c = tdk.Context(0)
+    yield c
+    c.close()
+
+
+def _ru8(x):
+    return (x + 7) // 8 * 8
+
+
+def _bf16_dev(X, ld):
+    """Row-major BF16 device matrix with leading dimension ld; the padding
+    columns hold NaN so that any read outside the matrix shows."""
+    import torch
+
+    rows, cols = X.shape
+    buf = torch.full((rows, ld), float("nan"), dtype=torch.float32)
+    buf[:, :cols] = torch.as_tensor(X, dtype=torch.float32)
+    return buf.to(torch.bfloat16).cuda()
+
+
+GEMM_SHAPES = [(200, 150, 96), (37, 300, 1000), (128, 128, 64), (1, 70, 27), (130, 1200, 256)]
+
+
+@pytest.mark.parametrize("a_mn,b_mn", [(0, 0), (0, 1), (1, 1), (1, 0)])
+@pytest.mark.parametrize("shape", GEMM_SHAPES)
+def test_gemm_bf16_layouts_and_epilogues(tdk, ctx, shape, a_mn, b_mn):
+    import torch
+
+    M, N, K = shape
+    r = np.random.default_rng(M * 7 + N * 3 + K + 10 * a_mn + b_mn)
+    A = synth.round_bf16(r.standard_normal((M, K)))
+    B = synth.round_bf16(r.standard_normal((N, K)))
+    Ad = _bf16_dev(A.T, _ru8(M)) if a_mn else _bf16_dev(A, _ru8(K))
+    lda = _ru8(M) if a_mn else _ru8(K)
+    Bd = _bf16_dev(B.T, _ru8(N)) if b_mn else _bf16_dev(B, _ru8(K))
+    ldb = _ru8(N) if b_mn else _ru8(K)
+    bias = r.standard_normal(N).astype(np.float32)
+    zin = r.standard_normal((M, N)).astype(np.float32)
+    biasd = torch.as_tensor(bias).cuda()
+    zind = torch.as_tensor(zin).cuda()
+    D = A @ B.T
+    bound = K * 2.0 ** -23 * (np.abs(A) @ np.abs(B).T) + 1e-30
+    L = tdk.lib()
+    for mode in range(4):
+        outf = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+        outb = torch.full((M, _ru8(N)), float("nan"), dtype=torch.bfloat16, device="cuda")
+        rc = L.tdk_test_gemm_bf16(ctx.handle, M, N, K, Ad.data_ptr(), lda, a_mn, Bd.data_ptr(), ldb, b_mn, mode,
+                                  biasd.data_ptr(), zind.data_ptr(), N, outf.data_ptr(), N, outb.data_ptr(), _ru8(N))
+        assert rc == 0
+        torch.cuda.synchronize()
+        f = outf.cpu().double().numpy()
+        bo = outb.float().cpu().double().numpy()[:, :N]
+        if mode == 0:
+            assert np.all(np.abs(f - D) <= bound)
+        elif mode == 2:
+            assert np.all(np.abs(f - (D + bias)) <= bound + 1e-6 * np.abs(bias))
+        elif mode == 1:
+            Z = D + bias
+            assert np.all(np.abs(f - Z) <= bound + 1e-6 * np.abs(bias))
+            ref = omlp.gelu(f)  # the kernel rounds gelu of its own pre-activation
+            assert np.all(np.abs(bo - ref) <= 2.0 ** -7 * np.abs(ref) + 1e-6)
+        else:
+            ref = D * omlp.gelu_grad(zin)
+            assert np.all(np.abs(bo - ref) <= 2.0 ** -7 * np.abs(ref) + bound * 2 + 1e-6)
+    assert ctx.sync_status() == 0
+
+
+def _odeco_cores(batch, Rt, N, seed, noise=1e-3):
+    """Cores with well-separated spectra in every unfolding: sum_r w_r q1_r o
+    q2_r o q3_r with orthogonal Q_n and distinct weights, plus small noise."""
+    r = np.random.default_rng(seed)
+    out = []
+    for _ in range(batch):
+        Qs = [np.linalg.qr(r.standard_normal((Rt, Rt)))[0] for _ in range(N)]
+        w = np.linspace(2.0, 0.3, Rt) * (1.0 + 0.05 * r.random(Rt))
+        G = oracle.cp_full(w, Qs) + noise * r.standard_normal((Rt,) * N)
+        out.append(G)
+    return np.array(out)
+
+
+def _problem(batch, N, Rt, seed):
+    r = np.random.default_rng(seed + 1)
+    G = _odeco_cores(batch, Rt, N, seed)
+    cs = r.standard_normal((batch, N, Rt)) * 3.0
+    R = r.integers(2, Rt + 1, size=batch).astype(np.int32)
+    Bs = r.standard_normal((batch, N, Rt, Rt))
+    return G, cs, R, Bs
+
+
+def _dev_batch(G, cs, R, Bs):
+    import torch
+
+    b = G.shape[0]
+    return (torch.as_tensor(G.reshape(b, -1), dtype=torch.float32).cuda(), torch.as_tensor(cs).cuda(),
+            torch.as_tensor(R).cuda(), torch.as_tensor(Bs).cuda())
+
+
+def test_canonicalisation_matches_oracle(tdk, ctx):
+    N, Rt, hidden, batch = 3, 6, 32, 9
+    G, cs, R, Bs = _problem(batch, N, Rt, 21)
+    m = tdk.Mlp(ctx, N, Rt, hidden, max_batch=16)
+    m.set_params(synth.mlp_init_params(N, Rt, hidden, 1))
+    Gd, csd, Rd, Bd = _dev_batch(G, cs, R, Bs)
+    m.train_step(Gd, csd, Rd, Bd, alpha=0.5, update=False)
+    S = m.get(tdk.MLP_CANON_CORE).reshape((batch,) + (Rt,) * N)
+    V = m.get(tdk.MLP_ROTATIONS).reshape(batch, N, Rt, Rt)
+    for s in range(batch):
+        So, Vo, _ = omlp.canonicalise(G[s].astype(np.float32).astype(np.float64), cs[s])
+        assert np.abs(S[s] - So).max() < 1e-4, s
+        for n in range(N):
+            assert np.abs(V[s, n] - Vo[n]).max() < 1e-4, (s, n)
+    m.close()
+
+
+@pytest.mark.parametrize("batch", [37, 150])
+def test_loss_and_gradients_match_oracle(tdk, ctx, batch):
+    N, Rt, hidden = 3, 6, 64
+    alpha = 0.5
+    G, cs, R, Bs = _problem(batch, N, Rt, 5 + batch)
+    theta = synth.mlp_init_params(N, Rt, hidden, 2)
+    m = tdk.Mlp(ctx, N, Rt, hidden, max_batch=256)
+    m.set_params(theta)
+    Gd, csd, Rd, Bd = _dev_batch(G, cs, R, Bs)
+    import torch
+
+    lam = np.random.default_rng(batch).uniform(0.5, 2.0, (batch, Rt))
+    loss = m.train_step(Gd, csd, Rd, Bd, alpha=alpha, update=False, lam=torch.as_tensor(lam).cuda())
+    g = m.get(tdk.MLP_GRADS).astype(np.float64)
+    O = m.get(tdk.MLP_OUTPUT).reshape(batch, -1)
+    # oracle from the same FP32 cores
+    G32 = G.astype(np.float32).astype(np.float64)
+    Ss, Ts = [], []
+    for s in range(batch):
+        S, V, nrm = omlp.canonicalise(G32[s], cs[s])
+        Ss.append(S)
+        Bw = [Bs[s, n][:, :R[s]] * (lam[s, :R[s]] if n == N - 1 else 1.0) for n in range(N)]
+        Ts.append(omlp.canonical_target(Bw, V, nrm))
+    Ss = np.array(Ss)
+    X = omlp.network_input(Ss)
+    Lo, go, Oo = omlp.loss_grad(theta.astype(np.float64), X, Ss, R, N, Rt, hidden, T=Ts, alpha=alpha, bf16=True)
+    assert np.linalg.norm(O - Oo) <= 2e-3 * np.linalg.norm(Oo)
+    assert abs(loss - Lo) <= 2e-3 * abs(Lo)
+    sizes = omlp.param_sizes(N, Rt, hidden)
+    o = 0
+    for k, sz in enumerate(sizes):
+        gg, gr = g[o:o + sz], go[o:o + sz]
+        assert np.linalg.norm(gg - gr) <= 1e-2 * np.linalg.norm(gr) + 1e-12, (k, np.linalg.norm(gg - gr),
+                                                                             np.linalg.norm(gr))
+        o += sz
+    m.close()
+
+
+def test_adam_step_matches_oracle(tdk, ctx):
+    N, Rt, hidden, batch = 3, 6, 32, 20
+    G, cs, R, Bs = _problem(batch, N, Rt, 31)
+    theta = synth.mlp_init_params(N, Rt, hidden, 3)
+    m = tdk.Mlp(ctx, N, Rt, hidden, max_batch=32)
+    m.set_params(theta)
+    Gd, csd, Rd, Bd = _dev_batch(G, cs, R, Bs)
+    m.train_step(Gd, csd, Rd, None, lr=1e-3, update=False)
+    g = m.get(tdk.MLP_GRADS).astype(np.float64)
+    m.train_step(Gd, csd, Rd, None, lr=1e-3, update=True)  # same batch: same gradient, then the step
+    th = m.get(tdk.MLP_PARAMS).astype(np.float64)
+    ref, _, _ = omlp.adam_step(theta.astype(np.float64), np.zeros_like(g), np.zeros_like(g), g, 1, 1e-3)
+    assert np.abs(th - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+    m.close()
+
+
+def test_predict_init_matches_oracle(tdk, ctx):
+    import torch
+
+    N, Rt, hidden, R = 3, 6, 64, 4
+    shape = (30, 28, 26)
+    r = np.random.default_rng(41)
+    # tensor of exact multilinear rank Rt whose core has separated spectra
+    G0 = _odeco_cores(1, Rt, N, 42, noise=0.0)[0]
+    As = [np.linalg.qr(r.standard_normal((I, Rt)))[0] for I in shape]
+    Y = oracle.tucker_full(G0, As)
+    W = synth.sketch_matrices(shape, Rt, 43)
+    Yd = dev_tensor(Y, "f32")
+    U, _ = tdk.tucker_sketch(ctx, Yd, dev_W(W), [Rt] * N, 0, "simt")
+    Gd, _ = tdk.tucker_core(ctx, Yd, U, [Rt] * N, 0, "simt")
+    theta = synth.mlp_init_params(N, Rt, hidden, 4)
+    m = tdk.Mlp(ctx, N, Rt, hidden, max_batch=4)
+    m.set_params(theta)
+    B = m.predict_init(Gd, U, shape, [Rt] * N, 0, tdk.F32, R)
+    torch.cuda.synchronize()
+    Gh = host(Gd)
+    cs = [host(u).sum(axis=0) for u in U]
+    S, V, _ = omlp.canonicalise(Gh, cs)
+    O, _ = omlp.forward(theta.astype(np.float64), omlp.network_input(S[None]), N, Rt, hidden, bf16=True)
+    Bh = [O[0, n * Rt * Rt:(n + 1) * Rt * Rt].reshape(Rt, Rt)[:, :R] for n in range(N)]
+    ref = omlp.decanonicalise(Bh, V)
+    for n in range(N):
+        got = host(B[n])
+        assert got.shape == (Rt, R)
+        assert np.linalg.norm(got - ref[n]) <= 2e-3 * np.linalg.norm(ref[n])
+    m.close()
+
+
+def _method_problem(k, split, I, Rt, rmin):
+    """One seeded training / held-out tensor of the learned-initialiser
+    workload (3-way CP data, rank R ~ U{rmin..Rt}, column correlation
+    ~ U[0, 0.9], SNR ~ U[10, 40] dB), scaled to I^3 with sketch width Rt."""
+    import dataclasses
+
+    import torch
+
+    base = synth.WORKLOADS["c5"]
+    seed = base.seed + split * 1000000 + k
+    r = synth.rng(seed, 99)
+    R = int(r.integers(rmin, Rt + 1))
+    w = dataclasses.replace(base, shape=(I,) * 3, R_cp=R, rho=float(r.uniform(0, 0.9)), snr_db=float(r.uniform(10, 40)),
+                            seed=seed, ranks=(Rt,) * 3, p=0, als_R=R)
+    Y, _ = synth.device_tensor(w, device="cuda")
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
+    Wd = [[None if x is None else torch.as_tensor(x, device="cuda") for x in row] for row in W]
+    B0 = [torch.as_tensor(b, device="cuda") for b in synth.init_factors(w.Rt, R, w.seed)]
+    return w, Y, Wd, B0, R
+
+
+def test_learned_start_needs_fewer_sweeps(tdk, ctx):
+    """Train the initialiser on cores and converged factors that the method
+    generates, then compare ALS sweeps to convergence on held-out tensors from
+    the random start, the HOSVD start and the learned start."""
+    from paper_1412_1885_gb300 import learned_init as li
+
+    I, Rt, hidden, ntrain, ntest = 24, 8, 1024, 4096, 96
+    m = tdk.Mlp(ctx, 3, Rt, hidden, max_batch=128)
+    m.set_params(synth.mlp_init_params(3, Rt, hidden, 0, hosvd_start=True, out_scale=0.1))
+    items = []
+    for k in range(ntrain):
+        w, Y, Wd, B0, R = _method_problem(k, 1, I, Rt, 3)
+        items.append(li.method_sample(ctx, m, Y, Wd, [Rt] * 3, 0, R, B0, prec="simt", init="hosvd", max_sweeps=300))
+    data = li.stack(items)
+    assert data.G.shape[0] > 0.7 * ntrain
+    hist = li.train(m, data, epochs=40, batch=128, lr=1e-3, alpha=0.5)
+    assert hist[-1] < 0.5 * hist[0]
+    sw = {"random": [], "hosvd": [], "learned": []}
+    fit = {"random": [], "hosvd": [], "learned": []}
+    for k in range(ntest):
+        w, Y, Wd, B0, R = _method_problem(k, 2, I, Rt, 3)
+        U, _ = tdk.tucker_sketch(ctx, Y, Wd, [Rt] * 3, 0, "simt")
+        G, nrm = tdk.tucker_core(ctx, Y, U, [Rt] * 3, 0, "simt")
+        runs = {"random": dict(B0=B0), "hosvd": dict(init="hosvd"),
+                "learned": dict(B0=m.predict_init(G, U, w.shape, [Rt] * 3, 0, tdk.F32, R))}
+        for name, kw in runs.items():
+            o = tdk.ffcp_als(ctx, G, U, w.shape, [Rt] * 3, 0, tdk.F32, R, 1000, 1e-7, normY2=nrm, **kw)
+            sw[name].append(o["sweeps"])
+            fit[name].append(o["fit_Y"])
+    med = {k: float(np.median(v)) for k, v in sw.items()}
+    mean_fit = {k: float(np.mean(v)) for k, v in fit.items()}
+    assert med["learned"] < med["random"] and med["learned"] < med["hosvd"], med
+    # the same final fit: the learned start does not land in worse optima on average
+    assert mean_fit["learned"] >= max(mean_fit["random"], mean_fit["hosvd"]) - 2e-3, mean_fit
+    m.close()

@@ -173,6 +173,83 @@ def cpu_oracle_sample(w, seconds_target=10.0, max_block=200_000_000):
     return nbytes / total / 1e9, desc, total
 
 
+def _fit_run(fn):
+    """(device ms, result) of one call, CUDA events on the current stream."""
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def learned_setup(t, ctx, w, prec, n_train, n_eval, dev):
+    """Learned-initialiser workload: build a training set with the method
+    (compress, FFCP from the HOSVD start to convergence), train the MLP, then
+    compare ALS from the random, HOSVD and learned starts on held-out tensors
+    (sweeps, final fit, device time from the resident core to the factors).
+    Everything here is set-up and evaluation, outside the timed steps."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1412_1885_gb300 import learned_init as li
+
+    N, Rt, hidden = w.N, w.Rt[0], 1024
+    m = t.Mlp(ctx, N, Rt, hidden, max_batch=256)
+    m.set_params(synth.mlp_init_params(N, Rt, hidden, w.seed, hosvd_start=True, out_scale=0.1))
+
+    def tensor(k, split):
+        wk = synth.learned_init_workload(k, split, w.shape, Rt)
+        Y, _ = synth.device_tensor(wk, device=dev)
+        W = synth.sketch_matrices(wk.shape, wk.Rt, wk.seed)
+        Wd = [[None if x is None else torch.as_tensor(x, device=dev) for x in row] for row in W]
+        B0 = [torch.as_tensor(b, device=dev) for b in synth.init_factors(wk.Rt, wk.als_R, wk.seed)]
+        return wk, Y, Wd, B0
+
+    t0 = time.perf_counter()
+    items = []
+    for k in range(n_train):
+        wk, Y, Wd, B0 = tensor(k, 1)
+        it = li.method_sample(ctx, m, Y, Wd, list(wk.ranks), 0, wk.als_R, B0, prec=prec, init="hosvd",
+                              max_sweeps=300)
+        items.append({kk: v for kk, v in it.items() if kk not in ("U", "Gc")})
+        del Y
+    data = li.stack(items)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = li.train(m, data, epochs=40, batch=128, lr=2e-4 if Rt > 12 else 1e-3, alpha=0.5)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    res = {k: {"sweeps": [], "fit": [], "ms": []} for k in ("random", "hosvd", "learned")}
+    for k in range(n_eval):
+        wk, Y, Wd, B0 = tensor(k, 2)
+        U, _ = t.tucker_sketch(ctx, Y, Wd, list(wk.ranks), 0, prec)
+        G, nrm = t.tucker_core(ctx, Y, U, list(wk.ranks), 0, prec)
+        args = (ctx, G, U, wk.shape, list(wk.ranks), 0, t._dtype_code(Y), wk.als_R, wk.als_max_sweeps, wk.als_tol)
+        runs = {"random": lambda: t.ffcp_als(*args, B0=B0, normY2=nrm),
+                "hosvd": lambda: t.ffcp_als(*args, init="hosvd", normY2=nrm),
+                "learned": lambda: t.ffcp_als(*args, normY2=nrm, B0=m.predict_init(G, U, wk.shape, list(wk.ranks), 0,
+                                                                                  t._dtype_code(Y), wk.als_R))}
+        for name, fn in runs.items():
+            ms, o = _fit_run(fn)
+            res[name]["sweeps"].append(o["sweeps"])
+            res[name]["fit"].append(o["fit_Y"])
+            res[name]["ms"].append(ms)
+        del Y
+    ev = {k: {"sweeps_median": float(np.median(v["sweeps"])), "sweeps_mean": float(np.mean(v["sweeps"])),
+              "sweeps_p90": float(np.percentile(v["sweeps"], 90)), "ms_median": float(np.median(v["ms"])),
+              "ms_mean": float(np.mean(v["ms"])), "fit_Y_mean": float(np.mean(v["fit"]))} for k, v in res.items()}
+    info = {"train_tensors": int(data.G.shape[0]), "generated": n_train, "epochs": 40, "hidden": hidden,
+            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "gen_s": gen_s, "train_s": train_s,
+            "eval_tensors": n_eval, "eval": ev}
+    return m, info
+
+
 def run_reference(args, w):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -211,6 +288,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-ttf", action="store_true", help="skip the time-to-fit comparison of the forms")
+    ap.add_argument("--train", type=int, default=2048, help="learned-init workload: training tensors")
+    ap.add_argument("--eval", type=int, default=64, help="learned-init workload: held-out tensors")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -246,18 +326,23 @@ def main():
     t.lib()
 
     # ---- inputs (untimed): Y generated in HBM, W / init from the seeded generators
+    ctx = t.Context(local)
+    model, li_info = None, None
+    if args.config == "c5":
+        model, li_info = learned_setup(t, ctx, w, args.prec, args.train, args.eval, dev)
+        # the timed tensor: held-out tensor 0 of the learned-initialiser workload
+        w = synth.learned_init_workload(0, 2, w.shape, w.Rt[0])
     Y, A_true = synth.device_tensor(w, device=dev)
     W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
     Wd = [[None if x is None else torch.as_tensor(x, device=dev) for x in row] for row in W]
     B0 = [torch.as_tensor(b, device=dev) for b in synth.init_factors(w.Rt, w.als_R, w.seed)]
     A0 = [torch.as_tensor(a, device=dev) for a in synth.init_factors(w.shape, w.als_R, w.seed, dist="uniform")]
-    ctx = t.Context(local)
     torch.cuda.synchronize()
 
-    def step(Yin):
-        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, args.prec, nonneg=w.nonneg,
+    def step(Yin, prec=args.prec):
+        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, prec, nonneg=w.nonneg,
                            max_sweeps=w.als_max_sweeps, tol=w.als_tol, B0=None if w.nonneg else B0,
-                           A0=A0 if w.nonneg else None, check_every=16)
+                           A0=A0 if w.nonneg else None, check_every=16, model=model)
 
     for _ in range(args.warmup):
         out = step(Y)
@@ -324,6 +409,20 @@ def main():
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
         del Yh
 
+    # ---- FFCP time-to-fit: this form vs the plain CUDA-core form, same tensor
+    ttf = None
+    if not args.no_ttf and rank == 0:
+        forms = {}
+        for form in dict.fromkeys([args.prec, "simt"]):
+            step(Y, form)  # warm this form's kernels
+            ms_f, o = _fit_run(lambda: step(Y, form))
+            forms[form] = {"ms": ms_f, "fit_Y": o["fit_Y"], "sweeps": o["sweeps"]}
+        ttf = {"forms": forms, "note": "device ms from Y resident in HBM to the factors A_n, one run per form; "
+                                       "simt = the plain CUDA-core form (FP32 arithmetic for FP32/BF16 data)"}
+        if "simt" in forms and args.prec in forms and args.prec != "simt":
+            ttf["speedup_vs_simt"] = forms["simt"]["ms"] / forms[args.prec]["ms"]
+            ttf["fit_Y_diff"] = abs(forms["simt"]["fit_Y"] - forms[args.prec]["fit_Y"])
+
     peak, peak_kind = _peaks()
     sk_avg = sk_ms / max(sk_n, 1)
     achieved = y_bytes / (sk_avg * 1e-3) / 1e9 if sk_n else None
@@ -353,7 +452,10 @@ def main():
                 "gpu_launches": launches,
                 "als": {"sweeps": sweeps, "fit_core": out["fit_core"], "fit_Y": out["fit_Y"],
                         "ms_last": out["ms"]},
-                "sketch_ms": sk_avg, "core_ms": co_ms / max(co_n, 1)}
+                "sketch_ms": sk_avg, "core_ms": co_ms / max(co_n, 1), "time_to_fit": ttf}
+        if li_info is not None:
+            line["learned_init"] = li_info
+            line["config"]["train_tensors"] = li_info["train_tensors"]
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:

@@ -175,6 +175,26 @@ def mlp_init_params(N: int, Rt: int, hidden: int, seed: int, hosvd_start: bool =
     return np.concatenate(parts).astype(np.float32)
 
 
+TAG_LEARNED = 99
+
+
+def learned_init_workload(k: int, split: int, shape=None, Rt: int | None = None, rmin: int = 8) -> "Workload":
+    """Sample k of the learned-initialiser workload (split 1: training, 2:
+    held out): 3-way CP data with rank R ~ U{rmin..Rt}, column correlation
+    ~ U[0, 0.9], SNR ~ U[10, 40] dB; Tucker ranks Rt with p = 0; ALS rank R."""
+    import dataclasses
+
+    base = WORKLOADS["c5"]
+    shape = tuple(base.shape if shape is None else shape)
+    Rt = base.Rt[0] if Rt is None else int(Rt)
+    seed = base.seed + split * 1000000 + k
+    r = rng(seed, TAG_LEARNED)
+    R = int(r.integers(rmin, Rt + 1))
+    return dataclasses.replace(base, name=f"{base.name}_{split}_{k}", shape=shape, R_cp=R,
+                               rho=float(r.uniform(0, 0.9)), snr_db=float(r.uniform(10, 40)), seed=seed,
+                               ranks=(Rt,) * len(shape), p=0, als_R=R)
+
+
 # --------------------------------------------------------------------------
 # The five workloads (sizes, ranks and data model of the synthetic runs).
 # --------------------------------------------------------------------------

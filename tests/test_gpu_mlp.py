@@ -233,24 +233,15 @@ def test_predict_init_matches_oracle(tdk, ctx):
 
 
 def _method_problem(k, split, I, Rt, rmin):
-    """One seeded training / held-out tensor of the learned-initialiser
-    workload (3-way CP data, rank R ~ U{rmin..Rt}, column correlation
-    ~ U[0, 0.9], SNR ~ U[10, 40] dB), scaled to I^3 with sketch width Rt."""
-    import dataclasses
-
+    """Tensor k of the learned-initialiser workload at I^3, sketch width Rt."""
     import torch
 
-    base = synth.WORKLOADS["c5"]
-    seed = base.seed + split * 1000000 + k
-    r = synth.rng(seed, 99)
-    R = int(r.integers(rmin, Rt + 1))
-    w = dataclasses.replace(base, shape=(I,) * 3, R_cp=R, rho=float(r.uniform(0, 0.9)), snr_db=float(r.uniform(10, 40)),
-                            seed=seed, ranks=(Rt,) * 3, p=0, als_R=R)
+    w = synth.learned_init_workload(k, split, (I,) * 3, Rt, rmin)
     Y, _ = synth.device_tensor(w, device="cuda")
     W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
     Wd = [[None if x is None else torch.as_tensor(x, device="cuda") for x in row] for row in W]
-    B0 = [torch.as_tensor(b, device="cuda") for b in synth.init_factors(w.Rt, R, w.seed)]
-    return w, Y, Wd, B0, R
+    B0 = [torch.as_tensor(b, device="cuda") for b in synth.init_factors(w.Rt, w.als_R, w.seed)]
+    return w, Y, Wd, B0, w.als_R
 
 
 def test_learned_start_needs_fewer_sweeps(tdk, ctx):

@@ -798,11 +798,56 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
                      const tdk_als_opts* o, double* const B_io[], double* const A_io[], double* lambda_out,
                      tdk_als_report* rep);
 
+// HOSVD start written into the caller's B_io (nonnegative form: |U_n B_n|
+// into A_io), on the context's stream, so that either ALS form can then
+// start from it as a given initialisation
+template <class T>
+int hosvd_into(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], const tdk_als_opts* o,
+               double* const B_io[], double* const A_io[]) {
+  AlsArgs<T> a{};
+  a.N = g.N;
+  a.R = o->R;
+  int64_t Rtmax = 0, s = 1;
+  for (int n = g.N - 1; n >= 0; --n) {
+    a.Rt[n] = g.Rt[n];
+    a.I[n] = g.I[n];
+    a.stride[n] = s;
+    s *= g.Rt[n];
+    Rtmax = g.Rt[n] > Rtmax ? g.Rt[n] : Rtmax;
+  }
+  a.gnumel = g.core_numel;
+  a.G = G;
+  double* tmp = nullptr;
+  if (o->nonneg) {
+    int rc = ws_reserve(ctx, sizeof(double) * (size_t)Rtmax * o->R + 256);
+    if (rc) return rc;
+    tmp = reinterpret_cast<double*>(ctx->ws);
+  }
+  for (int n = 0; n < g.N; ++n) {
+    hosvd_init_kernel<T><<<1, 128, 0, ctx->stream>>>(a, n, o->nonneg ? tmp : B_io[n]);
+    TDK_LAUNCH_CHECK(ctx);
+    if (o->nonneg) {
+      abs_lift_kernel<<<64, 256, 0, ctx->stream>>>(U[n], tmp, g.I[n], g.Rt[n], o->R, A_io[n]);
+      TDK_LAUNCH_CHECK(ctx);
+    }
+  }
+  return TDK_OK;
+}
+
 int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double* const U[], const double* normY2,
-            const tdk_als_opts* o, double* const B_io[], double* const A_io[], double* lambda_out,
+            const tdk_als_opts* o_in, double* const B_io[], double* const A_io[], double* lambda_out,
             tdk_als_report* rep) {
   // one persistent cooperative kernel when the core fits; otherwise (or when a
-  // normal equation needs the pseudo-inverse) the kernel-per-step form
+  // normal equation needs the pseudo-inverse) the kernel-per-step form.  A
+  // HOSVD start is computed first and handed to either form as a given start.
+  tdk_als_opts oo = *o_in;
+  const tdk_als_opts* o = &oo;
+  if (oo.init == TDK_INIT_HOSVD && !ctx->als_multi_kernel && !(oo.timeout_s > 0)) {
+    const int rc0 = (dtype == TDK_F64) ? hosvd_into<double>(ctx, g, reinterpret_cast<const double*>(G), U, o, B_io, A_io)
+                                       : hosvd_into<float>(ctx, g, reinterpret_cast<const float*>(G), U, o, B_io, A_io);
+    if (rc0) return rc0;
+    oo.init = TDK_INIT_GIVEN;
+  }
   int rc = TDK_ENOTSUP;
   if (!ctx->als_multi_kernel) {
     rc = (dtype == TDK_F64)

@@ -163,6 +163,33 @@ def test_nonneg_als_matches_oracle(tdk, ctx, als_form):
         assert np.allclose(Ah[n], Ao[n], atol=1e-8)
 
 
+def test_als_hosvd_start_matches_oracle(tdk, ctx, als_form):
+    # HOSVD start (leading R left singular vectors of every G_(n), largest
+    # entry positive), then 60 sweeps, FP64
+    shape, ranks, p, R = (40, 36, 32), (5, 5, 5), 3, 4
+    Y, W, _ = small_problem(shape, ranks, p, seed=12, dtype="f64", snr=25.0, R_cp=R)
+    ref = oracle.rand_tucker(Y, W)
+    o = oracle.cp_als(ref["G"], oracle.hosvd_init(ref["G"], R), max_sweeps=60, tol=0.0)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], "f64"), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, 0, R, max_sweeps=60, tol=0.0, init="hosvd")
+    assert out["sweeps"] == 60
+    assert abs(out["fit_core"] - o["fit"]) < 1e-10
+    for n in range(3):
+        assert np.allclose(host(out["B"][n]), o["B"][n], atol=1e-8)
+
+
+def test_nonneg_als_hosvd_start_matches_oracle(tdk, ctx, als_form):
+    # nonnegative form from |U_n B_n^hosvd|
+    shape, ranks, p, R = (24, 22, 20), (5, 5, 5), 3, 4
+    Y, W, _ = small_problem(shape, ranks, p, seed=13, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
+    ref = oracle.rand_tucker(Y, W)
+    A0 = [np.abs(u @ b) for u, b in zip(ref["U"], oracle.hosvd_init(ref["G"], R))]
+    o = oracle.cp_als_nonneg(ref["G"], ref["U"], A0, max_sweeps=30, tol=0.0)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], "f64"), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, 0, R, max_sweeps=30, tol=0.0, nonneg=True, init="hosvd")
+    assert abs(out["fit_core"] - o["fit"]) < 1e-10
+
+
 def test_end_to_end_c1_fp64(tdk, ctx):
     """Workload 1 at full size (100^3 FP64, CP rank 5, SNR 30 dB, p = 5, ALS
     rank 5, <= 100 sweeps, relative fit change < 1e-9)."""

@@ -70,7 +70,11 @@ enum {
                         BF16 data): the plain form                        */
   TDK_PREC_TC = 1    /* tcgen05 tensor cores, BF16 operands, FP32
                         accumulation; FP32 data is split hi+lo so products
-                        keep ~16 significant bits (F64 data: not supported) */
+                        keep ~16 significant bits, except that the
+                        Khatri-Rao rows of the last mode's sketch are rounded
+                        once to BF16 when its width exceeds 32 (the sketch is
+                        then exact for a test matrix within 2^-9 of Omega_N);
+                        F64 data: not supported                            */
 };
 
 typedef struct tdk_ctx tdk_ctx;

@@ -141,6 +141,97 @@ __global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, in
   }
 }
 
+// Same contraction for wide FP32 slabs (Rt and Bd above 32): a 64 x 64 output
+// tile per CTA, 64 threads with 8 x 8 outputs each (two 4-wide groups 32 apart
+// in each direction), K staged 32 deep through
+// double-buffered shared memory with the next slice prefetched in registers.
+// grid (A, ceil(Bd / 64))
+__global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__ X, int64_t Ic, int64_t Bd,
+                                                       const float* __restrict__ U, int Rt, float* __restrict__ Xo) {
+  constexpr int KC = 32;
+  __shared__ __align__(16) float Xs[2][KC][64];
+  __shared__ __align__(16) float Us[2][KC][64];
+  const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
+  const int64_t a = blockIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.y * 64;
+  const float* Xa = X + a * Ic * Bd;
+  const bool bok = b0 + t < Bd, rok = t < Rt;
+  float rx[KC], ru[KC];
+  // thread t loads column t of the slice: 32 rows of X (coalesced along b) and of U
+  auto load = [&](int64_t i0) {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      const int64_t i = i0 + j;
+      rx[j] = (i < Ic && bok) ? __ldg(Xa + i * Bd + b0 + t) : 0.f;
+      ru[j] = (i < Ic && rok) ? __ldg(U + i * Rt + t) : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      Xs[buf][j][t] = rx[j];
+      Us[buf][j][t] = ru[j];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
+  load(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int64_t i0 = 0; i0 < Ic; i0 += KC) {
+    const bool more = i0 + KC < Ic;
+    if (more) load(i0 + KC);
+#pragma unroll 4
+    for (int k = 0; k < KC; ++k) {
+      // rows ty*4 + {0..3} and 32 + ty*4 + {0..3}; columns likewise with tx:
+      // a quarter-warp's float4 reads cover 32 distinct banks
+      const float4 u0 = *reinterpret_cast<const float4*>(&Us[buf][k][ty * 4]);
+      const float4 u1 = *reinterpret_cast<const float4*>(&Us[buf][k][32 + ty * 4]);
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[buf][k][tx * 4]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[buf][k][32 + tx * 4]);
+      const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(u[p], x[q], acc[p][q]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* Xoa = Xo + a * (int64_t)Rt * Bd;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int r = (p < 4) ? ty * 4 + p : 32 + ty * 4 + (p - 4);
+    if (r >= Rt) continue;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t b = b0 + ((q < 4) ? tx * 4 + q : 32 + tx * 4 + (q - 4));
+      if (b < Bd) Xoa[(int64_t)r * Bd + b] = acc[p][q];
+    }
+  }
+}
+
+template <class T>
+void launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo) {
+  dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
+  ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
+}
+template <>
+void launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, int64_t Bd, const float* U, int Rt,
+                           float* Xo) {
+  dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
+  if (Rt > 32 && Bd > 32)
+    ttm_mid64_kernel<<<grid, 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
+  else
+    ttm_mid_kernel<float><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
+}
+
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
   __shared__ double red[32];
   double s = 0.0;
@@ -185,8 +276,7 @@ int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* 
     int64_t A = 1;
     for (int k = 0; k < m; ++k) A *= g.I[k];
     T* out = (m == 0) ? G : ((m % 2) ? tmp0 : tmp1);
-    dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
-    ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(cur, g.I[m], Bd, Ut[m], g.Rt[m], out);
+    launch_ttm_mid<T>(ctx, cur, A, g.I[m], Bd, Ut[m], g.Rt[m], out);
     TDK_LAUNCH_CHECK(ctx);
     cur = out;
     Bd *= g.Rt[m];

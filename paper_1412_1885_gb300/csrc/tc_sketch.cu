@@ -69,6 +69,7 @@ using namespace tc;
 
 constexpr int KB = 1024;
 constexpr uint32_t BOX_BYTES = 16 * KB;  // one 128-row x 128-byte box
+constexpr int SK_SMAX = 4;               // deepest stage ring of the sketch
 
 // =====================================================================
 //                               SKETCH
@@ -106,11 +107,17 @@ struct SkLayout {
   static constexpr uint32_t KT_BYTES = 16 * KB;                        // K_p tile [128 j][64 r] BF16
 };
 
+// epilogue warp groups: two for BF16 data (the epilogue bounds the pass),
+// one for FP32 data (whose converter warps take the other four slots)
+template <bool F32>
+constexpr int sketch_groups() { return F32 ? 1 : 2; }
+
 template <bool F32, int RW>
-__global__ void __launch_bounds__(F32 ? 320 : 192, 1)
+__global__ void __launch_bounds__(320, 1)
     tc_sketch_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmW,
                      const SkArgs a) {
   using Lay = SkLayout<F32>;
+  constexpr int EG = sketch_groups<F32>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned start, by offset so that the pointer stays in the shared space
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -119,21 +126,21 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
   const uint32_t wn_box = (uint32_t)a.N1 * 128u;
   unsigned char* kt_base = wn_base + ((2 * a.KS * wn_box + 1023) & ~1023u);  // 2 x KT_BYTES
   uint64_t* bars = reinterpret_cast<uint64_t*>(kt_base + 2 * Lay::KT_BYTES);
-  const int S = a.S;               // stage ring depth (<= 3)
-  uint64_t* full = bars;           // [3]
-  uint64_t* empty = bars + 3;      // [3]
-  uint64_t* cfull = bars + 6;      // [3] (FP32: converted)
-  uint64_t* d1full = bars + 9;     // [2]
-  uint64_t* d1empty = bars + 11;   // [2]
-  uint64_t* ktfull = bars + 13;    // [2]
-  uint64_t* ktempty = bars + 15;   // [2]
-  uint64_t* wnfull = bars + 17;
-  uint64_t* wnempty = bars + 18;
-  uint64_t* d2full = bars + 19;
-  uint64_t* d2empty = bars + 20;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 22);
-  float* red = reinterpret_cast<float*>(bars + 24);                // [4][64]
-  float* coef = red + 4 * 64;                                      // [3][4][64]
+  const int S = a.S;               // stage ring depth (<= SK_SMAX)
+  uint64_t* full = bars;                     // [SK_SMAX]
+  uint64_t* empty = bars + SK_SMAX;          // [SK_SMAX]
+  uint64_t* cfull = bars + 2 * SK_SMAX;      // [SK_SMAX] (FP32: converted)
+  uint64_t* d1full = bars + 3 * SK_SMAX;     // [2]
+  uint64_t* d1empty = d1full + 2;            // [2]
+  uint64_t* ktfull = d1full + 4;             // [2]
+  uint64_t* ktempty = d1full + 6;            // [2]
+  uint64_t* wnfull = d1full + 8;
+  uint64_t* wnempty = d1full + 9;
+  uint64_t* d2full = d1full + 10;
+  uint64_t* d2empty = d1full + 11;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(d1full + 13);
+  float* red = reinterpret_cast<float*>(d1full + 15);              // [2 groups][4][64]
+  float* coef = red + 2 * 4 * 64;                                  // [3][4][64]
   volatile int* abort_flag = reinterpret_cast<volatile int*>(coef + 3 * 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -145,14 +152,14 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&d1full[i]), 1);
-      mbar_init(smem_u32(&d1empty[i]), 4);
-      mbar_init(smem_u32(&ktfull[i]), 4);
+      mbar_init(smem_u32(&d1empty[i]), 4 * EG);
+      mbar_init(smem_u32(&ktfull[i]), 4 * EG);
       mbar_init(smem_u32(&ktempty[i]), 1);
     }
     mbar_init(smem_u32(wnfull), 1);
     mbar_init(smem_u32(wnempty), 1);
     mbar_init(smem_u32(d2full), 1);
-    mbar_init(smem_u32(d2empty), 4);
+    mbar_init(smem_u32(d2empty), 4 * EG);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -283,15 +290,24 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
       }
       if (!ok) *abort_flag = 1;
     }
-  } else if (warp < 6) {
-    // ------------------------------------------------------------ epilogue (4 warps)
-    constexpr int HW = RW / 2;
+  } else if (warp < 2 + 4 * EG) {
+    // ------------------------------------------------------------ epilogue (EG groups of 4 warps)
+    // Group g owns the channels [g*CH, (g+1)*CH) of every mode; the two groups
+    // read the same TMEM lanes (warp w reads lanes 32*(w%4)), so each warp's
+    // dependent chains are half as long and two warps share each scheduler.
+    constexpr int CH = RW / EG;
+    constexpr int HW = CH / 2;
+    constexpr int NE = 128 * EG;       // epilogue threads
+    constexpr int NSLOT = 256 / NE;    // coefficient slots per thread
     const int q = warp & 3;
-    const int jl = 32 * q + lane;  // TMEM lane = tile row j (D1) / column k (D2)
+    const int grp = (warp - 2) >> 2;
+    const int cg = grp * CH;           // first channel of this group
+    const int jl = 32 * q + lane;      // TMEM lane = tile row j (D1) / column k (D2)
+    const int et = grp * 128 + jl;     // epilogue thread index
     const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
     const int Nm = a.N;
-    const int nj = Nm - 2;         // tile row mode
-    const int nl = Nm - 1;         // contiguous mode
+    const int nj = Nm - 2;             // tile row mode
+    const int nl = Nm - 1;             // contiguous mode
     const int Rj = a.Rt[nj];
     // Per-p coefficient vectors, products of W rows over the outer indices of p
     // (four vectors of 64: [0] Khatri-Rao rows of the contiguous mode, [1] the
@@ -309,8 +325,8 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         }
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int slot = jl + 128 * h;
+      for (int h = 0; h < NSLOT; ++h) {
+        const int slot = et + NE * h;
         const int vec = slot >> 6, r = slot & 63;
         const int n = vec == 0 ? nl : (vec == 1 ? nj : vec - 2);
         const bool live = (vec < 2 || vec - 2 < nj) && r < a.Rt[n];
@@ -328,8 +344,8 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
     };
     auto coef_store = [&](uint32_t pidx, const float (*cr)[2]) {
       float* cb = coef + (pidx % 3) * 256;
-      cb[jl] = cr[0][0] * cr[0][1];
-      cb[jl + 128] = cr[1][0] * cr[1][1];
+#pragma unroll
+      for (int h = 0; h < NSLOT; ++h) cb[et + NE * h] = cr[h][0] * cr[h][1];
     };
     auto unpack = [](uint32_t w, int e) -> float {
       return e ? __uint_as_float(w & 0xFFFF0000u) : __uint_as_float(w << 16);
@@ -345,13 +361,14 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
       const int jj = j0 + jl;
       const bool vj = jj < a.J;
       float* up = a.part + u * a.ustride;
-      // this lane's row of W_{N-1}^(N) and of W_{N-1}^(m) (m < N-2), packed BF16
-      // (the test matrices hold BF16 values, so the packing is exact)
+      // this lane's row of W_{N-1}^(N) and of W_{N-1}^(m) (m < N-2) over the
+      // group's channels, packed BF16 (the test matrices hold BF16 values, so
+      // the packing is exact)
       uint32_t wk[HW], wn0[HW], wn1[HW];
 #pragma unroll
       for (int i = 0; i < HW; ++i) {
         float k0v = 0.f, k1v = 0.f, a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-        const int r = 2 * i;
+        const int r = cg + 2 * i;
         if (vj) {
           const float* wkr = a.Wf[nl][nj] + (int64_t)jj * a.RtL;
           if (r < a.RtL) k0v = __ldg(wkr + r);
@@ -371,31 +388,30 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         wn0[i] = pack_bf16x2(a0, a1);
         wn1[i] = pack_bf16x2(b0, b1);
       }
-      float accj[RW];
+      float accj[CH];
 #pragma unroll
-      for (int r = 0; r < RW; ++r) accj[r] = 0.f;
-      // K_p rows for G2 (row j of the tile), MN-major [j][r], 128-byte swizzle
+      for (int r = 0; r < CH; ++r) accj[r] = 0.f;
+      // K_p rows for G2 (row j of the tile), MN-major [j][r], 128-byte swizzle;
+      // group g writes the 16-byte chunks of its channels
       auto gen_k = [&](uint32_t pidx) -> bool {
         const int kb = pidx & 1;
         if (!mbar_wait(smem_u32(&ktempty[kb]), ((pidx >> 1) & 1) ^ 1, status)) return false;
         const float* cK = coef + (pidx % 3) * 256;
         unsigned char* row = kt_base + kb * SkLayout<F32>::KT_BYTES + jl * 128;
         const int ph = jl & 7;
+        auto put = [&](int c, const uint32_t* w4) {
+          *reinterpret_cast<uint4*>(row + ((c ^ ph) << 4)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        };
+        if (a.hilo) {
+          // single group: chunks 0-3 hold hi, 4-7 lo of channels 0..31
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint32_t w4[4];
+          for (int c = 0; c < 8; ++c) {
+            uint32_t w4[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float v0 = 0.f, v1 = 0.f;
-            if (!a.hilo) {
-              const int r = 8 * c + 2 * e;
-              if (r < RW) {
-                v0 = unpack(wk[r / 2], 0) * cK[r];
-                v1 = unpack(wk[r / 2], 1) * cK[r + 1];
-              }
-            } else {
+            for (int e = 0; e < 4; ++e) {
+              float v0 = 0.f, v1 = 0.f;
               const int r = 8 * (c & 3) + 2 * e;
-              if (r < RW) {
+              if (r < CH) {
                 const float s0 = unpack(wk[r / 2], 0) * cK[r];
                 const float s1 = unpack(wk[r / 2], 1) * cK[r + 1];
                 if (c < 4) {
@@ -406,10 +422,30 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
                   v1 = s1 - __bfloat162float(__float2bfloat16_rn(s1));
                 }
               }
+              w4[e] = pack_bf16x2(v0, v1);
             }
-            w4[e] = pack_bf16x2(v0, v1);
+            put(c, w4);
           }
-          *reinterpret_cast<uint4*>(row + ((c ^ ph) << 4)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        } else {
+          // the chunks of this group's channels, then its share of the zero
+          // chunks beyond RW (the G2 operand is 64 channels wide)
+          constexpr int OWN = CH / 8;
+          constexpr int ZERO = (8 - RW / 8) / EG;
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int rl = 8 * cc + 2 * e;  // channel within the group
+              w4[e] = pack_bf16x2(unpack(wk[rl / 2], 0) * cK[cg + rl], unpack(wk[rl / 2], 1) * cK[cg + rl + 1]);
+            }
+            put(cg / 8 + cc, w4);
+          }
+#pragma unroll
+          for (int cc = 0; cc < ZERO; ++cc) {
+            const uint32_t z4[4] = {0u, 0u, 0u, 0u};
+            put(RW / 8 + grp * ZERO + cc, z4);
+          }
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -417,7 +453,7 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         return true;
       };
       {
-        float cr[2][2];
+        float cr[NSLOT][2];
         coef_load(p0, cr);
         coef_store(pi, cr);
         if (p0 + 1 < p1) {
@@ -425,11 +461,13 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
           coef_store(pi + 1, cr);
         }
       }
-      named_bar(1, 128);
+      named_bar(1, NE);
       if (!gen_k(pi)) { ok = false; break; }
       for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
         const int db = pi & 1;
-        float cr2[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        float cr2[NSLOT][2];
+#pragma unroll
+        for (int h = 0; h < NSLOT; ++h) cr2[h][0] = cr2[h][1] = 0.f;
         const bool have2 = p + 2 < p1;
         if (have2) coef_load(p + 2, cr2);
         pmark(8);
@@ -443,23 +481,24 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
         const uint32_t d1 = tmem + db * a.d1_cols + lane_addr;
         // row mode: per-lane accumulation weighted by the outer coefficients
 #pragma unroll
-        for (int c16 = 0; c16 < RW / 16; ++c16) {
-          if (c16 * 16 < a.Rtp[nj]) {
+        for (int c16 = 0; c16 < CH / 16; ++c16) {
+          if (cg + c16 * 16 < a.Rtp[nj]) {
             float v[16];
-            tmem_ld16(d1 + a.off[nj] + c16 * 16, v);
+            tmem_ld16(d1 + a.off[nj] + cg + c16 * 16, v);
             tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 16; ++e) accj[c16 * 16 + e] = fmaf(v[e], cb[64 + c16 * 16 + e], accj[c16 * 16 + e]);
+            for (int e = 0; e < 16; ++e)
+              accj[c16 * 16 + e] = fmaf(v[e], cb[64 + cg + c16 * 16 + e], accj[c16 * 16 + e]);
           }
         }
         pmark(11);  // row mode
         // modes constant over the tile: weight by W_{N-1}^(m)[j], reduce over 128 lanes
         for (int m = 0; m < nj; ++m) {
-          float v[RW];
+          float v[CH];
 #pragma unroll
-          for (int c16 = 0; c16 < RW / 16; ++c16) {
-            if (c16 * 16 < a.Rtp[m]) {
-              tmem_ld16(d1 + a.off[m] + c16 * 16, v + c16 * 16);
+          for (int c16 = 0; c16 < CH / 16; ++c16) {
+            if (cg + c16 * 16 < a.Rtp[m]) {
+              tmem_ld16(d1 + a.off[m] + cg + c16 * 16, v + c16 * 16);
             } else {
 #pragma unroll
               for (int e = 0; e < 16; ++e) v[c16 * 16 + e] = 0.f;
@@ -472,50 +511,55 @@ __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
             v[2 * i] *= unpack(w, 0);
             v[2 * i + 1] *= unpack(w, 1);
           }
-          // butterfly transpose-reduce: each lane ends with RW/32 of the RW sums
-#pragma unroll
-          for (int o = 16, h = RW / 2; o >= 1; o >>= 1, h >>= 1) {
-            const bool upper = (lane & o) != 0;
-#pragma unroll
-            for (int i = 0; i < RW / 2; ++i) {
-              if (i < h) {
-                const float send = upper ? v[i] : v[i + h];
-                const float keep = upper ? v[i + h] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-              }
-            }
-          }
+          // butterfly transpose-reduce: each lane ends with max(1, CH/32) of
+          // the CH sums (CH < 32: the last rounds add the partner's partial)
           int bse = 0;
 #pragma unroll
-          for (int o = 16, h = RW / 2; o >= 1; o >>= 1, h >>= 1) bse += (lane & o) ? h : 0;
-          red[q * 64 + bse] = v[0];
-          if (RW == 64) red[q * 64 + bse + 1] = v[1];
-          named_bar(1, 128);
-          const int Rm = a.Rt[m];
-          if (jl < Rm) {
-            const float s = red[jl] + red[64 + jl] + red[128 + jl] + red[192 + jl];
-            up[a.poff_p[m] + (p - p0) * Rm + jl] = s * cb[128 + 64 * m + jl];
+          for (int o = 16, h = CH / 2; o >= 1; o >>= 1, h >>= 1) {
+            if (h >= 1) {
+              const bool upper = (lane & o) != 0;
+#pragma unroll
+              for (int i = 0; i < CH / 2; ++i) {
+                if (i < h) {
+                  const float send = upper ? v[i] : v[i + h];
+                  const float keep = upper ? v[i + h] : v[i];
+                  v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+              }
+              bse += upper ? h : 0;
+            } else {
+              v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+            }
           }
-          named_bar(1, 128);
+          float* rg = red + grp * 4 * 64;
+          rg[q * 64 + bse] = v[0];
+          if (CH == 64) rg[q * 64 + bse + 1] = v[1];
+          named_bar(1, NE);
+          const int Rm = a.Rt[m];
+          if (jl < CH && cg + jl < Rm) {
+            const float s = rg[jl] + rg[64 + jl] + rg[128 + jl] + rg[192 + jl];
+            up[a.poff_p[m] + (p - p0) * Rm + cg + jl] = s * cb[128 + 64 * m + cg + jl];
+          }
+          named_bar(1, NE);
         }
         pmark(12);  // reductions
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&d1empty[db]));
         if (have2) coef_store(pi + 2, cr2);
-        named_bar(1, 128);
+        named_bar(1, NE);
         pmark(13);  // tail barrier
       }
       if (!ok) break;
       // ---- unit end: row-mode partial and the contiguous mode from D2
       if (vj) {
 #pragma unroll
-        for (int r = 0; r < RW; ++r)
-          if (r < Rj) up[a.poff_j + (int64_t)jl * Rj + r] = accj[r];
+        for (int r = 0; r < CH; ++r)
+          if (cg + r < Rj) up[a.poff_j + (int64_t)jl * Rj + cg + r] = accj[r];
       }
       if (!mbar_wait(smem_u32(d2full), un & 1, status)) { ok = false; break; }
       tc_fence_after();
-      for (int st = 0; st < a.KS; ++st) {
+      for (int st = grp; st < a.KS; st += EG) {
         float v[64];
 #pragma unroll
         for (int c16 = 0; c16 < 4; ++c16) tmem_ld16(tmem + 2 * a.d1_cols + st * 64 + c16 * 16 + lane_addr, v + c16 * 16);
@@ -657,7 +701,7 @@ static int launch_sketch(tdk_ctx* ctx, const CUtensorMap& tmY, const CUtensorMap
                          size_t smem) {
   auto k = tc_sketch_kernel<F32, RW>;
   TDK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k<<<grid, F32 ? 320 : 192, smem, ctx->stream>>>(tmY, tmW, a);
+  k<<<grid, 320, smem, ctx->stream>>>(tmY, tmW, a);
   TDK_LAUNCH_CHECK(ctx);
   return TDK_OK;
 }
@@ -688,23 +732,31 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   a.hilo = (f32 && a.RtL <= 32) ? 1 : 0;
   if (!f32 && a.RtL > 64) return TDK_ENOTSUP;
   a.d1_cols = (N1 + 31) / 32 * 32;
-  // columns per unit (KS blocks of 128): the widest that TMEM (two D1 buffers +
-  // KS D2 blocks) and shared memory (ring + resident W block) allow, then the
-  // deepest ring; wider units amortise the per-p epilogue over more bytes
+  // columns per unit (KS blocks of 128): among the widths that TMEM (two D1
+  // buffers + KS D2 blocks) and shared memory (ring of at least two stages +
+  // resident W block) allow, the one that pads the contiguous mode least (a
+  // padded column costs a full column of work), ties to the widest (the per-p
+  // epilogue is amortised over more bytes); then the deepest ring that fits
   {
     const uint32_t stage_b = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
     a.KS = 0;
-    for (int ks = 4; ks >= 1 && !a.KS; --ks) {
+    int64_t best_cols = 0;
+    for (int ks = 4; ks >= 1; --ks) {
       if (ks > (a.L + 127) / 128 && ks > 1) continue;
       if (2 * a.d1_cols + ks * 64 > 512) continue;
-      for (int st = 3; st >= 2; --st) {
+      int fit_st = 0;
+      for (int st = SK_SMAX; st >= 2 && !fit_st; --st) {
         const size_t need = 1024 + (size_t)st * stage_b + ((2 * ks * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB +
-                            256 + 4 * 64 * 4 + 3 * 256 * 4 + 64;
-        if (need <= (size_t)ctx->max_smem_optin) {
-          a.KS = ks;
-          a.S = st;
-          break;
-        }
+                            256 + 2 * 4 * 64 * 4 + 3 * 256 * 4 + 64;
+        if (need <= (size_t)ctx->max_smem_optin) fit_st = st;
+      }
+      if (!fit_st) continue;
+      const int64_t w = 128LL * ks;
+      const int64_t cols = (a.L + w - 1) / w * w;
+      if (!a.KS || cols < best_cols) {
+        a.KS = ks;
+        a.S = fit_st;
+        best_cols = cols;
       }
     }
     if (!a.KS) return TDK_ENOTSUP;
@@ -784,7 +836,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   }
   const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
   size_t smem = 1024 + (size_t)a.S * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 +
-                4 * 64 * 4 + 3 * 256 * 4 + 64;
+                2 * 4 * 64 * 4 + 3 * 256 * 4 + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
   {

@@ -104,6 +104,24 @@ def test_core_matches_oracle(tdk, ctx, shape, dtype):
     assert math.isclose(float(nrm.item()), ref["normY2"], rel_tol=1e-12 if dtype == "f64" else 1e-6)
 
 
+@pytest.mark.parametrize("prec,dtype", [("simt", "f32"), ("tc", "f32"), ("tc", "bf16"), ("simt", "f64")])
+def test_core_wide_ranks_matches_oracle(tdk, ctx, prec, dtype):
+    # sketch widths above 32 (the shrunk contractions take their wide-tile
+    # form for FP32 cores): 3-way with ragged 64-tiles in every mode, and a
+    # 4-way case whose middle contractions see Bd = 40 * 36 and 40 * 36 * 34
+    for shape, ranks, p in [((70, 66, 72), (36, 40, 38), 2), ((38, 44, 40, 48), (34, 33, 36, 38), 2)]:
+        Y, W, _ = small_problem(shape, ranks, p, seed=23, dtype=dtype)
+        U = [np.linalg.qr(np.random.default_rng(24 + n).standard_normal((I, r + p)))[0]
+             for n, (I, r) in enumerate(zip(shape, ranks))]
+        Gref = oracle.tucker_core(Y, U)
+        G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), [dev_tensor(u, "f64") for u in U], ranks, p, prec)
+        assert ctx.sync_status() == 0
+        bnd = core_abs_bound(Y, U)
+        tol = 1e-12 if dtype == "f64" else 2e-5 + (2.0 ** -16 if prec == "tc" else 0.0)
+        err = np.abs(host(G) - Gref)
+        assert np.all(err <= tol * bnd), (shape, float((err / bnd).max()))
+
+
 @pytest.fixture(params=["persistent", "multi"])
 def als_form(request, ctx):
     ctx.set_als_form(request.param == "multi")
@@ -238,7 +256,8 @@ TC_SHAPES = [
     (3, 130, 512),
 ]
 # rounding of one BF16 operand (RNE): 2^-9 relative; FP32 data split hi+lo and
-# KRP rows split hi+lo (sketch width <= 32): residual below 2^-17.
+# KRP rows split hi+lo (sketch width <= 32): residual below 2^-17; KRP rows of
+# a last mode wider than 32 are rounded once (2^-9), for either data type.
 U_BF16 = 2.0 ** -9
 
 
@@ -246,7 +265,9 @@ def _tc_tol(dtype, mode_is_last, Rt_last):
     acc = 2e-5  # FP32 accumulation, as for the CUDA-core form
     if dtype == "bf16":
         return acc + (U_BF16 if mode_is_last else 0.0)
-    return acc + (2.0 ** -15 if (mode_is_last and Rt_last > 32) else 2.0 ** -16)
+    # FP32 data: hi + lo everywhere, except the KRP rows of the last mode when
+    # its sketch width exceeds 32 (no room for their lo half): one BF16 rounding
+    return acc + (U_BF16 if (mode_is_last and Rt_last > 32) else 2.0 ** -16)
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f32"])
@@ -255,6 +276,25 @@ def test_tc_sketch_matches_oracle(tdk, ctx, shape, dtype):
     ranks = [min(5, s - 2) for s in shape]
     p = 2
     Y, W, _ = small_problem(shape, ranks, p, seed=13, dtype=dtype)
+    U, Z = tdk.tucker_sketch(ctx, dev_tensor(Y, dtype), dev_W(W), ranks, p, "tc", want_Z=True)
+    assert ctx.sync_status() == 0
+    Zo, _ = oracle.sketch(Y, W)
+    bnd = sketch_abs_bound(Y, W)
+    N = len(shape)
+    for n in range(N):
+        tol = _tc_tol(dtype, n == N - 1, ranks[-1] + p)
+        err = np.abs(host(Z[n]) - Zo[n])
+        assert np.all(err <= tol * bnd[n] + 1e-30), (n, float((err / bnd[n]).max()), tol)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("shape,ranks", [((40, 130, 264), (20, 18, 22)), ((48, 200, 256), (40, 38, 44)),
+                                         ((6, 9, 140, 136), (4, 7, 26, 30))])
+def test_tc_sketch_wide_ranks_matches_oracle(tdk, ctx, shape, ranks, dtype):
+    # sketch widths 17..32 and above 32: every channel block of the epilogue
+    # (both warp groups, all K_p chunks) carries data
+    p = 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=14, dtype=dtype)
     U, Z = tdk.tucker_sketch(ctx, dev_tensor(Y, dtype), dev_W(W), ranks, p, "tc", want_Z=True)
     assert ctx.sync_status() == 0
     Zo, _ = oracle.sketch(Y, W)

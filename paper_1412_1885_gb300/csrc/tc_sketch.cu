@@ -70,6 +70,8 @@ using namespace tc;
 constexpr int KB = 1024;
 constexpr uint32_t BOX_BYTES = 16 * KB;  // one 128-row x 128-byte box
 constexpr int SK_SMAX = 4;               // deepest stage ring of the sketch
+constexpr int SK_KTB = 3;                // K_p tiles in flight (built two p ahead)
+constexpr int SK_CB = 4;                 // per-p coefficient buffers (loaded three p ahead)
 
 // =====================================================================
 //                               SKETCH
@@ -124,24 +126,24 @@ __global__ void __launch_bounds__(320, 1)
   unsigned char* st_base = base;                                   // STAGES x STAGE_BYTES
   unsigned char* wn_base = st_base + a.S * Lay::STAGE_BYTES;  // 2*KS boxes of N1 rows x 128 B
   const uint32_t wn_box = (uint32_t)a.N1 * 128u;
-  unsigned char* kt_base = wn_base + ((2 * a.KS * wn_box + 1023) & ~1023u);  // 2 x KT_BYTES
-  uint64_t* bars = reinterpret_cast<uint64_t*>(kt_base + 2 * Lay::KT_BYTES);
+  unsigned char* kt_base = wn_base + ((2 * a.KS * wn_box + 1023) & ~1023u);  // SK_KTB x KT_BYTES
+  uint64_t* bars = reinterpret_cast<uint64_t*>(kt_base + SK_KTB * Lay::KT_BYTES);
   const int S = a.S;               // stage ring depth (<= SK_SMAX)
   uint64_t* full = bars;                     // [SK_SMAX]
   uint64_t* empty = bars + SK_SMAX;          // [SK_SMAX]
   uint64_t* cfull = bars + 2 * SK_SMAX;      // [SK_SMAX] (FP32: converted)
   uint64_t* d1full = bars + 3 * SK_SMAX;     // [2]
   uint64_t* d1empty = d1full + 2;            // [2]
-  uint64_t* ktfull = d1full + 4;             // [2]
-  uint64_t* ktempty = d1full + 6;            // [2]
-  uint64_t* wnfull = d1full + 8;
-  uint64_t* wnempty = d1full + 9;
-  uint64_t* d2full = d1full + 10;
-  uint64_t* d2empty = d1full + 11;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(d1full + 13);
-  float* red = reinterpret_cast<float*>(d1full + 15);              // [2 groups][4][64]
-  float* coef = red + 2 * 4 * 64;                                  // [3][4][64]
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(coef + 3 * 256);
+  uint64_t* ktfull = d1full + 4;             // [SK_KTB]
+  uint64_t* ktempty = ktfull + SK_KTB;       // [SK_KTB]
+  uint64_t* wnfull = ktempty + SK_KTB;
+  uint64_t* wnempty = wnfull + 1;
+  uint64_t* d2full = wnfull + 2;
+  uint64_t* d2empty = wnfull + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wnfull + 5);
+  float* red = reinterpret_cast<float*>(wnfull + 7);               // [2 groups][4][64]
+  float* coef = red + 2 * 4 * 64;                                  // [SK_CB][4][64]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(coef + SK_CB * 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -153,6 +155,8 @@ __global__ void __launch_bounds__(320, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&d1full[i]), 1);
       mbar_init(smem_u32(&d1empty[i]), 4 * EG);
+    }
+    for (int i = 0; i < SK_KTB; ++i) {
       mbar_init(smem_u32(&ktfull[i]), 4 * EG);
       mbar_init(smem_u32(&ktempty[i]), 1);
     }
@@ -243,11 +247,11 @@ __global__ void __launch_bounds__(320, 1)
         tc_fence_after();
         bool first_p = true;
         for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
-          const int db = pi & 1, kb = pi & 1;
+          const int db = pi & 1, kb = pi % SK_KTB;
           pmark(0);
           if (!mbar_wait(smem_u32(&d1empty[db]), ((pi >> 1) & 1) ^ 1, status)) { ok = false; break; }
           pmark(1);  // MMA waits for the epilogue to free D1
-          if (!mbar_wait(smem_u32(&ktfull[kb]), (pi >> 1) & 1, status)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&ktfull[kb]), (pi / SK_KTB) & 1, status)) { ok = false; break; }
           pmark(2);  // MMA waits for the K_p tile
           tc_fence_after();
           const uint32_t d1 = tmem + db * a.d1_cols;
@@ -312,8 +316,8 @@ __global__ void __launch_bounds__(320, 1)
     // Per-p coefficient vectors, products of W rows over the outer indices of p
     // (four vectors of 64: [0] Khatri-Rao rows of the contiguous mode, [1] the
     // row mode, [2], [3] modes 0 and 1 when they are outer modes), kept in
-    // three shared buffers so that p+2 is loaded while p is in use.
-    // raw factors only: the loads are issued two p ahead and multiplied when
+    // four shared buffers so that p+3 is loaded while p is in use.
+    // raw factors only: the loads are issued three p ahead and multiplied when
     // stored, so their latency overlaps the work on p
     auto coef_load = [&](int64_t pp, float (*cr)[2]) {
       int kidx[2] = {0, 0};
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(320, 1)
       }
     };
     auto coef_store = [&](uint32_t pidx, const float (*cr)[2]) {
-      float* cb = coef + (pidx % 3) * 256;
+      float* cb = coef + (pidx % SK_CB) * 256;
 #pragma unroll
       for (int h = 0; h < NSLOT; ++h) cb[et + NE * h] = cr[h][0] * cr[h][1];
     };
@@ -394,9 +398,9 @@ __global__ void __launch_bounds__(320, 1)
       // K_p rows for G2 (row j of the tile), MN-major [j][r], 128-byte swizzle;
       // group g writes the 16-byte chunks of its channels
       auto gen_k = [&](uint32_t pidx) -> bool {
-        const int kb = pidx & 1;
-        if (!mbar_wait(smem_u32(&ktempty[kb]), ((pidx >> 1) & 1) ^ 1, status)) return false;
-        const float* cK = coef + (pidx % 3) * 256;
+        const int kb = pidx % SK_KTB;
+        if (!mbar_wait(smem_u32(&ktempty[kb]), ((pidx / SK_KTB) & 1) ^ 1, status)) return false;
+        const float* cK = coef + (pidx % SK_CB) * 256;
         unsigned char* row = kt_base + kb * SkLayout<F32>::KT_BYTES + jl * 128;
         const int ph = jl & 7;
         auto put = [&](int c, const uint32_t* w4) {
@@ -454,26 +458,28 @@ __global__ void __launch_bounds__(320, 1)
       };
       {
         float cr[NSLOT][2];
-        coef_load(p0, cr);
-        coef_store(pi, cr);
-        if (p0 + 1 < p1) {
-          coef_load(p0 + 1, cr);
-          coef_store(pi + 1, cr);
-        }
+        for (int d = 0; d < 3; ++d)
+          if (p0 + d < p1) {
+            coef_load(p0 + d, cr);
+            coef_store(pi + d, cr);
+          }
       }
       named_bar(1, NE);
+      // K tiles run two p ahead of the MMAs, so that the MMA issuer never
+      // waits for the epilogue's work on the previous D1
       if (!gen_k(pi)) { ok = false; break; }
+      if (p0 + 1 < p1 && !gen_k(pi + 1)) { ok = false; break; }
       for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
         const int db = pi & 1;
         float cr2[NSLOT][2];
 #pragma unroll
         for (int h = 0; h < NSLOT; ++h) cr2[h][0] = cr2[h][1] = 0.f;
-        const bool have2 = p + 2 < p1;
-        if (have2) coef_load(p + 2, cr2);
+        const bool have3 = p + 3 < p1;
+        if (have3) coef_load(p + 3, cr2);
         pmark(8);
-        if (p + 1 < p1 && !gen_k(pi + 1)) { ok = false; break; }
+        if (p + 2 < p1 && !gen_k(pi + 2)) { ok = false; break; }
         pmark(9);  // epilogue: K tile (incl. waiting for the MMA to free it)
-        const float* cb = coef + (pi % 3) * 256;
+        const float* cb = coef + (pi % SK_CB) * 256;
         // ---- D1 -> sketches of modes < N
         if (!mbar_wait(smem_u32(&d1full[db]), (pi >> 1) & 1, status)) { ok = false; break; }
         pmark(10);  // epilogue waits for D1
@@ -546,7 +552,7 @@ __global__ void __launch_bounds__(320, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&d1empty[db]));
-        if (have2) coef_store(pi + 2, cr2);
+        if (have3) coef_store(pi + 3, cr2);
         named_bar(1, NE);
         pmark(13);  // tail barrier
       }
@@ -746,8 +752,8 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
       if (2 * a.d1_cols + ks * 64 > 512) continue;
       int fit_st = 0;
       for (int st = SK_SMAX; st >= 2 && !fit_st; --st) {
-        const size_t need = 1024 + (size_t)st * stage_b + ((2 * ks * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB +
-                            256 + 2 * 4 * 64 * 4 + 3 * 256 * 4 + 64;
+        const size_t need = 1024 + (size_t)st * stage_b + ((2 * ks * N1 * 128 + 1023) & ~1023) + SK_KTB * 16 * KB +
+                            256 + 2 * 4 * 64 * 4 + SK_CB * 256 * 4 + 64;
         if (need <= (size_t)ctx->max_smem_optin) fit_st = st;
       }
       if (!fit_st) continue;
@@ -835,8 +841,8 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     if (rc) return rc;
   }
   const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
-  size_t smem = 1024 + (size_t)a.S * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + 2 * 16 * KB + 256 +
-                2 * 4 * 64 * 4 + 3 * 256 * 4 + 64;
+  size_t smem = 1024 + (size_t)a.S * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + SK_KTB * 16 * KB + 256 +
+                2 * 4 * 64 * 4 + SK_CB * 256 * 4 + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
   {

@@ -115,25 +115,6 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return s;
 }
 
-// x <- x L^{-T} L^{-1} for T = L L^T (lower L in Tm, 1/L_jj in invd), one warp
-__device__ __forceinline__ void warp_chol_solve(const double* Tm, const double* invd, int R, double* x) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < R; ++j) {
-    const double xj = x[j] * invd[j];
-    __syncwarp();
-    if (lane == 0) x[j] = xj;
-    for (int r = j + 1 + lane; r < R; r += 32) x[r] = fma(-Tm[r * R + j], xj, x[r]);
-    __syncwarp();
-  }
-  for (int j = R - 1; j >= 0; --j) {
-    const double xj = x[j] * invd[j];
-    __syncwarp();
-    if (lane == 0) x[j] = xj;
-    for (int r = lane; r < j; r += 32) x[r] = fma(-Tm[j * R + r], xj, x[r]);
-    __syncwarp();
-  }
-}
-
 #define PROF_MARK(ph)                                                            \
   do {                                                                           \
     if (a.prof && blockIdx.x == 0) {                                             \
@@ -149,8 +130,8 @@ __device__ __forceinline__ void warp_chol_solve(const double* Tm, const double* 
 // shared-memory plan of the persistent kernel, every region 16-byte aligned
 template <class T>
 struct PLayout {
-  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_invf, o_yf, o_lamt, o_ilamt,
-      o_slice, o_work, total;
+  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_invf, o_yf,
+      o_lamt, o_ilamt, o_slice, o_work, total;
   __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -168,6 +149,8 @@ struct PLayout {
     o_hrow = take(sizeof(double) * RMAXP);
     o_red = take(sizeof(double) * 32);
     o_lf = take(sizeof(float) * R * R);
+    o_tid = take(sizeof(double) * R * R);
+    o_gjs = take(sizeof(double) * 2 * RMAXP);
     o_invf = take(sizeof(float) * RMAXP);
     o_yf = take(sizeof(float) * RMAXP);
     o_lamt = take(sizeof(T) * RMAXP);
@@ -178,23 +161,39 @@ struct PLayout {
   }
 };
 
-// y <- y L^{-T} L^{-1} for an FP32 Cholesky factor (lower Lf, 1/L_jj in invf), one warp
-__device__ __forceinline__ void warp_solve32(const float* Lf, const float* invf, int R, float* y) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < R; ++j) {
-    const float yj = y[j] * invf[j];
-    __syncwarp();
-    if (lane == 0) y[j] = yj;
-    for (int r = j + 1 + lane; r < R; r += 32) y[r] = fmaf(-Lf[r * R + j], yj, y[r]);
-    __syncwarp();
+// In-place inverse of a symmetric positive definite R x R matrix (row-major)
+// by Gauss-Jordan elimination without pivoting, spread over a group of nt
+// threads (named barrier bar_id); a pivot is the Schur complement a Cholesky
+// factorisation would meet, so the breakdown test (pivot not above
+// R * eps * max diag) is the same: per pivot, the pivot row and column are copied, then every
+// thread updates its share of the R x R entries.  rowk, colk: R entries each.
+template <class F>
+__device__ int group_gj_inverse(F* A, F* rowk, F* colk, int R, F eps, int t, int nt, int bar_id) {
+  F mx = F(0);
+  for (int j = 0; j < R; ++j) mx = A[j * R + j] > mx ? A[j * R + j] : mx;
+  const F tiny = (F)R * eps * mx;
+  const int RR = R * R;
+  const float invR = 1.0f / (float)R;
+  for (int k = 0; k < R; ++k) {
+    if (t < R) {
+      rowk[t] = A[k * R + t];
+      colk[t] = A[t * R + k];
+    }
+    tc::named_bar(bar_id, nt);
+    const F p = rowk[k];
+    if (!(p > tiny)) return 0;  // same value in every thread of the group
+    const F ip = F(1) / p;
+    for (int e = t; e < RR; e += nt) {
+      const int i = __float2int_rz(((float)e + 0.5f) * invR);  // e / R (exact for e < 4096)
+      const int j = e - i * R;
+      F v;
+      if (i == k) v = (j == k) ? ip : rowk[j] * ip;
+      else v = (j == k) ? -colk[i] * ip : fma(-colk[i], rowk[j] * ip, A[e]);
+      A[e] = v;
+    }
+    tc::named_bar(bar_id, nt);
   }
-  for (int j = R - 1; j >= 0; --j) {
-    const float yj = y[j] * invf[j];
-    __syncwarp();
-    if (lane == 0) y[j] = yj;
-    for (int r = lane; r < j; r += 32) y[r] = fmaf(-Lf[j * R + r], yj, y[r]);
-    __syncwarp();
-  }
+  return 1;
 }
 
 template <class T>
@@ -219,14 +218,15 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   double* xrow = reinterpret_cast<double*>(sm + L.o_xrow);
   double* hrow = reinterpret_cast<double*>(sm + L.o_hrow);  // right-hand side
   double* red = reinterpret_cast<double*>(sm + L.o_red);    // [32]
-  float* Lf = reinterpret_cast<float*>(sm + L.o_lf);        // [R*R] FP32 Cholesky factor
+  float* Lf = reinterpret_cast<float*>(sm + L.o_lf);        // [R*R] FP32 inverse of T_n
+  double* Tid = reinterpret_cast<double*>(sm + L.o_tid);   // [R*R] FP64 inverse (fallback)
+  double* gjs = reinterpret_cast<double*>(sm + L.o_gjs);   // Gauss-Jordan pivot row / column
   float* invf = reinterpret_cast<float*>(sm + L.o_invf);
   float* yf = reinterpret_cast<float*>(sm + L.o_yf);
   T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
   T* ilamT = reinterpret_cast<T*>(sm + L.o_ilamt);
   T* slice = reinterpret_cast<T*>(sm + L.o_slice);   // [Qmax]
   T* work = reinterpret_cast<T*>(sm + L.o_work);     // [Amax * R]
-  __shared__ int s_bad;
 
   const int tid = threadIdx.x;
   const int G = gridDim.x, c = blockIdx.x;
@@ -289,95 +289,55 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         for (int p = 0; p < N; ++p)
           if (p != n) v *= (double)gram[p * R * R + e];
         Tm[e] = v;
-      }
-      if (tid == 0) s_bad = 0;
-      __syncthreads();
-      bool use32 = true;
-      {
-        float mx = 0.f;
-        for (int j = 0; j < R; ++j) mx = fmaxf(mx, Lf[j * R + j]);
-        const float tiny = R * 1.1920929e-7f * mx;
-        for (int j = 0; j < R; ++j) {
-          const float d = Lf[j * R + j];
-          if (!(d > tiny)) {
-            use32 = false;
-            break;
-          }
-          const float ljj = sqrtf(d), il = 1.0f / ljj;
-          __syncthreads();
-          if (tid == 0) {
-            Lf[j * R + j] = ljj;
-            invf[j] = il;
-          }
-          for (int r = j + 1 + tid; r < R; r += NTP) Lf[r * R + j] *= il;
-          __syncthreads();
-          const int m = R - j - 1;
-          for (int e = tid; e < m * m; e += NTP) {
-            const int r = j + 1 + e / m, cc = j + 1 + e % m;
-            if (cc <= r) Lf[r * R + cc] = fmaf(-Lf[r * R + j], Lf[cc * R + j], Lf[r * R + cc]);
-          }
-          __syncthreads();
-        }
+        Tid[e] = v;
       }
       __syncthreads();
-      if (!use32) {
-        double mx = 0.0;
-        for (int j = 0; j < R; ++j) mx = fmax(mx, Tm[j * R + j]);
-        const double tiny = R * 2.220446049250313e-16 * mx;
-        for (int j = 0; j < R; ++j) {
-          const double d = Tm[j * R + j];
-          if (!(d > tiny)) {
-            if (tid == 0) s_bad = 1;
-            break;
-          }
-          const double ljj = sqrt(d), il = 1.0 / ljj;
-          __syncthreads();
-          if (tid == 0) {
-            Tm[j * R + j] = ljj;
-            invd[j] = il;
-          }
-          for (int r = j + 1 + tid; r < R; r += NTP) Tm[r * R + j] *= il;
-          __syncthreads();
-          const int m = R - j - 1;
-          for (int e = tid; e < m * m; e += NTP) {
-            const int r = j + 1 + e / m, cc = j + 1 + e % m;
-            if (cc <= r) Tm[r * R + cc] = fma(-Tm[r * R + j], Tm[cc * R + j], Tm[r * R + cc]);
-          }
-          __syncthreads();
-        }
-        __syncthreads();
-      }
-      if (s_bad) {
+      // ---- 1b. inverse of T_n: FP32 by default (the solves are refined against
+      //          T_n in FP64), FP64 if an FP32 pivot breaks down
+      bool use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), reinterpret_cast<float*>(gjs) + RMAXP,
+                                           R, 1.1920929e-7f, tid, NTP, 1) != 0;
+      if (!use32 && !group_gj_inverse<double>(Tid, gjs, gjs + RMAXP, R, 2.220446049250313e-16, tid, NTP, 1)) {
         needpinv = 1;
         ok = false;  // identical in every CTA: all leave here
         break;
       }
-      // x <- x T_n^{-1} for the row in xrow (one warp)
+      __syncthreads();
+      // x <- x T_n^{-1} for the row in xrow, block-parallel: one product with the
+      // inverse, then two refinement steps against T_n in FP64 (invd: residual)
       auto solve_row = [&]() {
-        if (tid >= 32) return;
-        if (!use32) {
-          warp_chol_solve(Tm, invd, R, xrow);
-          return;
-        }
-        const int lane = tid;
-        for (int r = lane; r < R; r += 32) {
-          hrow[r] = xrow[r];
-          yf[r] = (float)xrow[r];
-          xrow[r] = 0.0;
-        }
-        __syncwarp();
-        for (int it = 0; it < 3; ++it) {
-          warp_solve32(Lf, invf, R, yf);
-          for (int r = lane; r < R; r += 32) xrow[r] += (double)yf[r];
-          __syncwarp();
-          if (it == 2) break;
-          // residual of the FP64 system: h - x T_n
-          for (int k = lane; k < R; k += 32) {
-            double rr = hrow[k];
-            for (int j = 0; j < R; ++j) rr = fma(-xrow[j], Tm[j * R + k], rr);
-            yf[k] = (float)rr;
+        for (int r = tid; r < R; r += NTP) hrow[r] = xrow[r];
+        __syncthreads();
+        for (int r = tid; r < R; r += NTP) {
+          double acc = 0.0;
+          if (use32) {
+            float af = 0.f;
+            for (int q = 0; q < R; ++q) af = fmaf((float)hrow[q], Lf[q * R + r], af);
+            acc = af;
+          } else {
+            for (int q = 0; q < R; ++q) acc = fma(hrow[q], Tid[q * R + r], acc);
           }
-          __syncwarp();
+          xrow[r] = acc;
+        }
+        __syncthreads();
+        for (int it = 0; it < 2; ++it) {
+          for (int q = tid; q < R; q += NTP) {
+            double rr = hrow[q];
+            for (int r = 0; r < R; ++r) rr = fma(-xrow[r], Tm[r * R + q], rr);
+            invd[q] = rr;
+          }
+          __syncthreads();
+          for (int r = tid; r < R; r += NTP) {
+            double acc = 0.0;
+            if (use32) {
+              float af = 0.f;
+              for (int q = 0; q < R; ++q) af = fmaf((float)invd[q], Lf[q * R + r], af);
+              acc = af;
+            } else {
+              for (int q = 0; q < R; ++q) acc = fma(invd[q], Tid[q * R + r], acc);
+            }
+            xrow[r] += acc;
+          }
+          __syncthreads();
         }
       };
 
@@ -392,6 +352,52 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       const int Rl = a.Rt[last];
       const int64_t A1 = Q / Rl;
       for (int i = c; i < Rn; i += G) {
+        if (N == 3) {
+          // slice S[a1, l] = G(i at n, a1 at p, l at q) without index decoding,
+          // then work = S B_q in 4 x 4 register tiles, then H[i, :] = sum_a1 work * B_p
+          const int p = oth[0], q = oth[1];
+          const int Rp = a.Rt[p], Rq = a.Rt[q];
+          const int64_t sp = a.stride[p], sq = a.stride[q];
+          const T* Gi = a.G + (int64_t)i * a.stride[n];
+          for (int a1 = tid >> 5; a1 < Rp; a1 += NTP / 32)
+            for (int l = tid & 31; l < Rq; l += 32) slice[a1 * Rq + l] = Gi[a1 * sp + l * sq];
+          __syncthreads();
+          const T* Bq = Bs + boff[q];
+          const int ta = (Rp + 3) / 4, tr = (R + 3) / 4;
+          for (int tile = tid; tile < ta * tr; tile += NTP) {
+            const int a0 = (tile / tr) * 4, r0 = (tile % tr) * 4;
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+            for (int l = 0; l < Rq; ++l) {
+              T s4[4], b4[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) s4[u] = (a0 + u < Rp) ? slice[(a0 + u) * Rq + l] : T(0);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) b4[v] = (r0 + v < R) ? Bq[l * R + r0 + v] : T(0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(s4[u], b4[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                if (a0 + u < Rp && r0 + v < R) work[(a0 + u) * R + r0 + v] = acc[u][v];
+          }
+          __syncthreads();
+          const T* Bp = Bs + boff[p];
+          for (int r = tid; r < R; r += NTP) {
+            T acc = T(0);
+            for (int a1 = 0; a1 < Rp; ++a1) acc = fma(work[a1 * R + r], Bp[a1 * R + r], acc);
+            a.H[(int64_t)i * R + r] = acc;
+            xrow[r] = (double)acc;
+          }
+          __syncthreads();
+        } else {
 #pragma unroll 4
         for (int e = tid; e < (int)Q; e += NTP) {
           int rem = e;
@@ -442,6 +448,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           xrow[r] = (double)in[r];
         }
         __syncthreads();
+        }
         if (!a.nonneg) {
           solve_row();
           __syncthreads();
@@ -541,9 +548,56 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           // FP32 forms: ||G - [[lambda; B]]||^2 summed explicitly over this CTA's
           // share of the core (the Gram identity cancels to rounding noise near
           // convergence in FP32)
+          T sacc = T(0), scmp = T(0);
+          if (N == 3) {
+            // slab i of mode 1: P[j, r] = lambda_r B_1[i, r] B_2[j, r], then the
+            // model slab P B_3^T in 4 x 4 register tiles against G[i, :, :]
+            const int R0 = a.Rt[0], R1 = a.Rt[1], R2 = a.Rt[2];
+            const T* B0 = Bs + boff[0];
+            const T* B1 = Bs + boff[1];
+            const T* B2 = Bs + boff[2];
+            for (int i = c; i < R0; i += G) {
+              __syncthreads();
+              for (int e = tid; e < R1 * R; e += NTP) {
+                const int j = e / R, r = e % R;
+                work[e] = lamT[r] * B0[i * R + r] * B1[j * R + r];
+              }
+              __syncthreads();
+              const int tj = (R1 + 3) / 4, tk = (R2 + 3) / 4;
+              for (int tile = tid; tile < tj * tk; tile += NTP) {
+                const int j0 = (tile / tk) * 4, k0 = (tile % tk) * 4;
+                T acc[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                  for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+                for (int r = 0; r < R; ++r) {
+                  T p4[4], b4[4];
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) p4[u] = (j0 + u < R1) ? work[(j0 + u) * R + r] : T(0);
+#pragma unroll
+                  for (int v = 0; v < 4; ++v) b4[v] = (k0 + v < R2) ? B2[(k0 + v) * R + r] : T(0);
+#pragma unroll
+                  for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(p4[u], b4[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                  for (int v = 0; v < 4; ++v)
+                    if (j0 + u < R1 && k0 + v < R2) {
+                      const T d = a.G[(int64_t)i * a.stride[0] + (int64_t)(j0 + u) * a.stride[1] + k0 + v] - acc[u][v];
+                      const T y = d * d - scmp;  // Kahan
+                      const T tt = sacc + y;
+                      scmp = (tt - sacc) - y;
+                      sacc = tt;
+                    }
+              }
+            }
+          } else {
           const int64_t chunk = (a.gnumel + G - 1) / G;
           const int64_t e0 = (int64_t)c * chunk, e1 = e0 + chunk < a.gnumel ? e0 + chunk : a.gnumel;
-          T sacc = T(0), scmp = T(0);
           for (int64_t e = e0 + tid; e < e1; e += NTP) {
             int rem = (int)e;
             int ix[TDK_MAX_MODES];
@@ -562,6 +616,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             const T t = sacc + y;
             scmp = (t - sacc) - y;
             sacc = t;
+          }
           }
           double s2 = block_sum_d((double)sacc - (double)scmp, red);
           if (tid == 0) a.rpart[c] = s2;
@@ -621,6 +676,383 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       a.st->fit = fit;
       a.st->fitY = fitY;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Whole FFCP on one CTA for 3-way cores that fit in shared memory (the core,
+// the factors and one intermediate of Rt_1 Rt_2 x R stay resident).  Same
+// steps and stopping rule as the grid-wide kernel, without grid barriers:
+//   mode 1: W[(i1,i2), r] = sum_i3 G[i1,i2,i3] B_3[i3, r], H_1 = sum_i2 W B_2;
+//   mode 2: H_2 = sum_i1 W B_1 (W unchanged: B_3 has not moved);
+//   mode 3: V[(i1,i3), r] = sum_i2 G[i1,i2,i3] B_2[i2, r], H_3 = sum_i1 V B_1;
+// T_n is inverted by warps 0-7 (Gauss-Jordan) while warps 8-15 form H_n; the
+// solve B_n = H_n T_n^-1 is one product plus two FP64 refinement steps.
+constexpr int NTS = 512;
+
+template <class T>
+struct SLayout {
+  size_t o_g, o_b0, o_b1, o_b2, o_gram, o_w, o_h, o_x, o_res, o_tm, o_ld, o_lid, o_lf, o_lif, o_lam, o_lamt, o_red,
+      total;
+  __host__ __device__ void plan(int R0, int R1, int R2, int R) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      const size_t o = (off + 15) & ~size_t(15);
+      off = o + bytes;
+      return o;
+    };
+    const int Rtm = R0 > R1 ? (R0 > R2 ? R0 : R2) : (R1 > R2 ? R1 : R2);
+    const size_t RR = (size_t)R * R;
+    o_g = take(sizeof(T) * (size_t)R0 * R1 * R2);
+    o_b0 = take(sizeof(T) * (size_t)R0 * R);
+    o_b1 = take(sizeof(T) * (size_t)R1 * R);
+    o_b2 = take(sizeof(T) * (size_t)R2 * R);
+    o_gram = take(sizeof(T) * 3 * RR);
+    o_w = take(sizeof(T) * (size_t)R0 * (R1 > R2 ? R1 : R2) * R);
+    o_h = take(sizeof(T) * (size_t)Rtm * R);
+    o_x = take(sizeof(double) * (size_t)Rtm * R);
+    o_res = take(sizeof(double) * (size_t)Rtm * R);
+    o_tm = take(sizeof(double) * RR);
+    o_ld = take(sizeof(double) * RR);
+    o_lid = take(sizeof(double) * (RR > 128 ? RR : 128));
+    o_lf = take(sizeof(float) * RR);
+    o_lif = take(sizeof(float) * (RR > 128 ? RR : 128));
+    o_lam = take(sizeof(double) * 64);
+    o_lamt = take(sizeof(T) * 64);
+    o_red = take(sizeof(double) * 32);
+    total = (off + 15) & ~size_t(15);
+  }
+};
+
+template <class T>
+__global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int R = a.R, RR = R * R;
+  const int Rt[3] = {a.Rt[0], a.Rt[1], a.Rt[2]};
+  const int M01 = Rt[0] * Rt[1];
+  const int nel = M01 * Rt[2];
+  SLayout<T> L;
+  L.plan(Rt[0], Rt[1], Rt[2], R);
+  T* Gc = reinterpret_cast<T*>(sm + L.o_g);
+  T* B[3] = {reinterpret_cast<T*>(sm + L.o_b0), reinterpret_cast<T*>(sm + L.o_b1), reinterpret_cast<T*>(sm + L.o_b2)};
+  T* gram = reinterpret_cast<T*>(sm + L.o_gram);
+  T* W = reinterpret_cast<T*>(sm + L.o_w);
+  T* H = reinterpret_cast<T*>(sm + L.o_h);
+  double* X = reinterpret_cast<double*>(sm + L.o_x);
+  double* Res = reinterpret_cast<double*>(sm + L.o_res);
+  double* Tm = reinterpret_cast<double*>(sm + L.o_tm);
+  double* Ld = reinterpret_cast<double*>(sm + L.o_ld);
+  double* Lid = reinterpret_cast<double*>(sm + L.o_lid);
+  float* Lf = reinterpret_cast<float*>(sm + L.o_lf);
+  float* Lif = reinterpret_cast<float*>(sm + L.o_lif);
+  double* lam = reinterpret_cast<double*>(sm + L.o_lam);
+  T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
+  double* red = reinterpret_cast<double*>(sm + L.o_red);
+  __shared__ int s_mode;  // 1: FP32 factor, 2: FP64 factor, 0: singular
+  __shared__ unsigned long long s_prof[10];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr bool F64 = sizeof(T) == 8;
+  // optional cycle accounting per phase (block-wide phases; thread 0 records)
+  const bool prof_on = a.prof != nullptr;
+  unsigned long long prof_t = clock64();
+  if (tid < 10) s_prof[tid] = 0;
+  auto pms = [&](int k) {
+    if (prof_on) {
+      __syncthreads();
+      if (tid == 0) {
+        const unsigned long long t = clock64();
+        s_prof[k] += t - prof_t;
+        prof_t = t;
+      }
+    }
+  };
+
+  for (int e = tid; e < nel; e += NTS) Gc[e] = a.G[e];
+  for (int n = 0; n < 3; ++n)
+    for (int e = tid; e < Rt[n] * R; e += NTS) B[n][e] = (T)a.init[n][e];
+  for (int r = tid; r < R; r += NTS) {
+    lam[r] = 1.0;
+    lamT[r] = T(1);
+  }
+  __syncthreads();
+  for (int n = 0; n < 3; ++n)
+    for (int e = tid; e < RR; e += NTS) {
+      const int r = e / R, c = e % R;
+      T acc = T(0);
+      for (int q = 0; q < Rt[n]; ++q) acc = fma(B[n][q * R + r], B[n][q * R + c], acc);
+      gram[n * RR + e] = acc;
+    }
+  __syncthreads();
+  const double nG2 = *a.nG2;
+  const double nY2 = a.nY2 ? *a.nY2 : 0.0;
+  double fit_old = 0.0, fit = 0.0, fitY = nan("");
+  int sweep = 0, converged = 0, singular = 0;
+  for (sweep = 1; sweep <= a.max_sweeps; ++sweep) {
+    for (int n = 0; n < 3; ++n) {
+      const int Rn = Rt[n];
+      pms(7);
+      // ---- T_n (FP64 and FP32 copies)
+      for (int e = tid; e < RR; e += NTS) {
+        double v = 1.0;
+        for (int p = 0; p < 3; ++p)
+          if (p != n) v *= (double)gram[p * RR + e];
+        Tm[e] = v;
+        Ld[e] = v;
+        Lf[e] = (float)v;
+      }
+      __syncthreads();
+      pms(0);
+      if (warp < 8) {
+        // ---- invert T_n (FP32 for FP32 cores, FP64 otherwise / as fallback), warps 0-7
+        const unsigned long long pt0 = clock64();
+        int mode = 0;
+        if (!F64 && group_gj_inverse<float>(Lf, Lif, Lif + 64, R, 1.1920929e-7f, tid, 256, 2)) {
+          mode = 1;
+        } else if (group_gj_inverse<double>(Ld, Lid, Lid + 64, R, 2.220446049250313e-16, tid, 256, 2)) {
+          mode = 2;
+        }
+        if (tid == 0) {
+          s_mode = mode;
+          if (prof_on) s_prof[8] += clock64() - pt0;
+        }
+      } else {
+        // ---- H_n, warps 8-15
+        const unsigned long long pt1 = clock64();
+        const int t = tid - 256, nt = NTS - 256;
+        if (n == 0) {
+          // W = G_(12) B_3 in 4 x 4 register tiles
+          const int tm = (M01 + 3) / 4, tr = (R + 3) / 4;
+          for (int tile = t; tile < tm * tr; tile += nt) {
+            const int m0 = (tile / tr) * 4, r0 = (tile % tr) * 4;
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+            for (int k = 0; k < Rt[2]; ++k) {
+              T g4[4], b4[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) g4[u] = (m0 + u < M01) ? Gc[(m0 + u) * Rt[2] + k] : T(0);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) b4[v] = (r0 + v < R) ? B[2][k * R + r0 + v] : T(0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(g4[u], b4[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                if (m0 + u < M01 && r0 + v < R) W[(m0 + u) * R + r0 + v] = acc[u][v];
+          }
+          tc::named_bar(1, nt);
+          for (int e = t; e < Rt[0] * R; e += nt) {
+            const int i = e / R, r = e % R;
+            T acc = T(0);
+            for (int j = 0; j < Rt[1]; ++j) acc = fma(W[(i * Rt[1] + j) * R + r], B[1][j * R + r], acc);
+            H[e] = acc;
+          }
+        } else if (n == 1) {
+          for (int e = t; e < Rt[1] * R; e += nt) {
+            const int j = e / R, r = e % R;
+            T acc = T(0);
+            for (int i = 0; i < Rt[0]; ++i) acc = fma(W[(i * Rt[1] + j) * R + r], B[0][i * R + r], acc);
+            H[e] = acc;
+          }
+        } else {
+          // V[(i1, i3), r] = sum_i2 G[i1, i2, i3] B_2[i2, r] in 4 x 4 tiles (4
+          // consecutive i3 of one i1), then H_3 = sum_i1 V B_1
+          const int tq = (Rt[2] + 3) / 4, tm = Rt[0] * tq, tr = (R + 3) / 4;
+          for (int tile = t; tile < tm * tr; tile += nt) {
+            const int mt = tile / tr, r0 = (tile % tr) * 4;
+            const int i0 = mt / tq, k0 = (mt % tq) * 4;
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+            for (int j = 0; j < Rt[1]; ++j) {
+              T g4[4], b4[4];
+              const T* gr = Gc + (i0 * Rt[1] + j) * Rt[2] + k0;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) g4[u] = (k0 + u < Rt[2]) ? gr[u] : T(0);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) b4[v] = (r0 + v < R) ? B[1][j * R + r0 + v] : T(0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(g4[u], b4[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                if (k0 + u < Rt[2] && r0 + v < R) W[(i0 * Rt[2] + k0 + u) * R + r0 + v] = acc[u][v];
+          }
+          tc::named_bar(1, nt);
+          for (int e = t; e < Rt[2] * R; e += nt) {
+            const int k = e / R, r = e % R;
+            T acc = T(0);
+            for (int i = 0; i < Rt[0]; ++i) acc = fma(W[(i * Rt[2] + k) * R + r], B[0][i * R + r], acc);
+            H[e] = acc;
+          }
+        }
+        if (prof_on && tid == 256) s_prof[9] += clock64() - pt1;
+      }
+      __syncthreads();
+      pms(1);
+      if (s_mode == 0) {
+        singular = 1;
+        break;
+      }
+      // ---- B_n = H_n T_n^-1, refined twice against T_n in FP64
+      const bool f32 = s_mode == 1;
+      for (int e = tid; e < Rn * R; e += NTS) {
+        const int i = e / R, c = e % R;
+        double acc = 0.0;
+        if (f32) {
+          float af = 0.f;
+          for (int r = 0; r < R; ++r) af = fmaf((float)H[i * R + r], Lf[r * R + c], af);
+          acc = af;
+        } else {
+          for (int r = 0; r < R; ++r) acc = fma((double)H[i * R + r], Ld[r * R + c], acc);
+        }
+        X[e] = acc;
+      }
+      __syncthreads();
+      pms(2);
+      for (int it = 0; it < 2; ++it) {
+        for (int e = tid; e < Rn * R; e += NTS) {
+          const int i = e / R, c = e % R;
+          double rr = (double)H[e];
+          for (int r = 0; r < R; ++r) rr = fma(-X[i * R + r], Tm[r * R + c], rr);
+          Res[e] = rr;
+        }
+        __syncthreads();
+        for (int e = tid; e < Rn * R; e += NTS) {
+          const int i = e / R, c = e % R;
+          double acc = 0.0;
+          if (f32) {
+            float af = 0.f;
+            for (int r = 0; r < R; ++r) af = fmaf((float)Res[i * R + r], Lf[r * R + c], af);
+            acc = af;
+          } else {
+            for (int r = 0; r < R; ++r) acc = fma(Res[i * R + r], Ld[r * R + c], acc);
+          }
+          X[e] += acc;
+        }
+        __syncthreads();
+      }
+      pms(3);
+      // ---- lambda (column norms), normalised B_n and its Gram
+      for (int r = warp; r < R; r += NTS / 32) {
+        double s2 = 0.0;
+        for (int i = tid & 31; i < Rn; i += 32) s2 = fma(X[i * R + r], X[i * R + r], s2);
+        s2 = warp_sum(s2);
+        if ((tid & 31) == 0) {
+          lam[r] = sqrt(s2);
+          lamT[r] = (T)lam[r];
+          Res[r] = lam[r] > 0.0 ? 1.0 / lam[r] : 0.0;  // reciprocal (Res is free here)
+        }
+      }
+      __syncthreads();
+      const T inv_rows = (T)(1.0 / sqrt((double)Rn));
+      for (int e = tid; e < Rn * R; e += NTS) {
+        const int r = e % R;
+        B[n][e] = lam[r] > 0.0 ? (T)(X[e] * Res[r]) : inv_rows;
+      }
+      __syncthreads();
+      for (int e = tid; e < RR; e += NTS) {
+        const int r = e / R, c = e % R;
+        T acc = T(0);
+        for (int q = 0; q < Rn; ++q) acc = fma(B[n][q * R + r], B[n][q * R + c], acc);
+        gram[n * RR + e] = acc;
+      }
+      __syncthreads();
+      pms(4);
+    }
+    if (singular) break;
+    // ---- fit
+    double m2 = 0.0;
+    for (int e = tid; e < RR; e += NTS) {
+      double v = lam[e / R] * lam[e % R];
+      for (int p = 0; p < 3; ++p) v *= (double)gram[p * RR + e];
+      m2 += v;
+    }
+    const double model2 = block_sum_d(m2, red);
+    double res2;
+    if (F64) {
+      // <G, [[lambda; B]]> from H_3 (Gram identity, as the FP64 oracle)
+      double in = 0.0;
+      for (int e = tid; e < Rt[2] * R; e += NTS) in += (double)H[e] * lam[e % R] * (double)B[2][e];
+      const double inner = block_sum_d(in, red);
+      res2 = fmax(0.0, nG2 - 2.0 * inner + model2);
+    } else {
+      // explicit ||G - [[lambda; B]]||^2: model (B_1 (.) B_2) diag(lambda) B_3^T, tile by tile
+      T sacc = T(0), scmp = T(0);
+      const int tm = (M01 + 3) / 4, tk = (Rt[2] + 3) / 4;
+      for (int tile = tid; tile < tm * tk; tile += NTS) {
+        const int m0 = (tile / tk) * 4, k0 = (tile % tk) * 4;
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        int ia[4], ib[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int m = m0 + u < M01 ? m0 + u : 0;
+          ia[u] = (m / Rt[1]) * R;
+          ib[u] = (m % Rt[1]) * R;
+        }
+        for (int r = 0; r < R; ++r) {
+          T w4[4], b4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w4[u] = (m0 + u < M01) ? B[0][ia[u] + r] * B[1][ib[u] + r] * lamT[r] : T(0);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) b4[v] = (k0 + v < Rt[2]) ? B[2][(k0 + v) * R + r] : T(0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(w4[u], b4[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (m0 + u < M01 && k0 + v < Rt[2]) {
+              const T d = Gc[(m0 + u) * Rt[2] + k0 + v] - acc[u][v];
+              const T y = d * d - scmp;  // Kahan
+              const T tt = sacc + y;
+              scmp = (tt - sacc) - y;
+              sacc = tt;
+            }
+      }
+      res2 = block_sum_d((double)sacc - (double)scmp, red);
+    }
+    pms(5);
+    fit_old = fit;
+    fit = 1.0 - sqrt(res2) / sqrt(nG2);
+    if (a.nY2) fitY = 1.0 - sqrt(fmax(0.0, nY2 - nG2 + res2)) / sqrt(nY2);
+    if (tid == 0 && sweep - 1 < a.hist_cap) a.hist[sweep - 1] = fit;
+    if (sweep > 1 && fabs(fit - fit_old) < a.tol * fabs(fit_old)) {
+      converged = 1;
+      break;
+    }
+    pms(6);
+  }
+  if (prof_on && tid < 10) a.prof[tid] = s_prof[tid];
+  if (sweep > a.max_sweeps) sweep = a.max_sweeps;
+  for (int n = 0; n < 3; ++n)
+    for (int e = tid; e < Rt[n] * R; e += NTS) a.Bout[n][e] = B[n][e];
+  for (int r = tid; r < R; r += NTS) a.lam_out[r] = lam[r];
+  if (tid == 0) {
+    a.st->sweeps = sweep;
+    a.st->converged = converged;
+    a.st->status = singular ? ST_NEEDPINV : 0;
+    a.st->fit = fit;
+    a.st->fitY = fitY;
   }
 }
 
@@ -754,9 +1186,20 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   norm2_core<T><<<1, 1024, 0, s>>>(G, g.core_numel, nG2);
   TDK_LAUNCH_CHECK(ctx);
   TDK_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s));
-  void* args[] = {&a};
-  TDK_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(NTP), args, smem, s));
-  ctx->launches++;
+  // 3-way unconstrained cores that fit in one SM: the single-CTA kernel
+  SLayout<T> sl;
+  sl.plan(g.Rt[0], g.Rt[N > 1 ? 1 : 0], g.Rt[N > 2 ? 2 : 0], R);
+  const bool small = N == 3 && !a.nonneg && sl.total + 64 <= (size_t)ctx->max_smem_optin;
+  if (small) {
+    auto ks = als_small_kernel<T>;
+    TDK_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sl.total + 64)));
+    ks<<<1, NTS, sl.total + 64, s>>>(a);
+    TDK_LAUNCH_CHECK(ctx);
+  } else {
+    void* args[] = {&a};
+    TDK_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(NTP), args, smem, s));
+    ctx->launches++;
+  }
   PState hs{};
   TDK_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(PState), cudaMemcpyDeviceToHost, s));
   TDK_CUDA_TRY(cudaStreamSynchronize(s));
@@ -765,10 +1208,17 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
     TDK_CUDA_TRY(cudaMemcpyAsync(hp, prof, sizeof(hp), cudaMemcpyDeviceToHost, s));
     TDK_CUDA_TRY(cudaStreamSynchronize(s));
     cudaFree(prof);
-    const char* names[7] = {"chol", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
-                            "barrier3", "fit"};
-    fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);
-    for (int i = 0; i < 7; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
+    if (small) {
+      const char* names[10] = {"T_n", "inverse|H", "solve", "refine", "normalise+gram", "fit", "check", "loop",
+                               "[warp0 inverse]", "[warp1 H]"};
+      fprintf(stderr, "tdk ALS profile (single CTA, Mcycles over %d sweeps):", hs.sweeps);
+      for (int i = 0; i < 10; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
+    } else {
+      const char* names[7] = {"chol", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
+                              "barrier3", "fit"};
+      fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);
+      for (int i = 0; i < 7; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
+    }
     fprintf(stderr, "\n");
   }
   if (hs.status & ST_NEEDPINV) return TDK_ENOTSUP;  // the multi-kernel form has the pseudo-inverse

@@ -217,6 +217,39 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
   }
 }
 
+// Same contraction for narrow FP32 slabs (Rt <= 32, Bd <= 32): the whole
+// Rt x Bd output of one a per CTA; K staged 64 deep, each slice of X and U a
+// contiguous run of memory read by all threads; 4 outputs per thread.
+__global__ void __launch_bounds__(256) ttm_mid32_kernel(const float* __restrict__ X, int64_t Ic, int Bd,
+                                                        const float* __restrict__ U, int Rt, float* __restrict__ Xo) {
+  constexpr int KC = 64;
+  __shared__ float Xs[KC * 32];
+  __shared__ float Us[KC * 32];
+  const int t = threadIdx.x;
+  const int64_t a = blockIdx.x;
+  const float* Xa = X + a * Ic * Bd;
+  const int b = t & 31, r0 = (t >> 5) * 4;  // column b, rows r0..r0+3
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t i0 = 0; i0 < Ic; i0 += KC) {
+    const int rows = (int)((Ic - i0) < KC ? (Ic - i0) : KC);
+    __syncthreads();
+    for (int e = t; e < rows * Bd; e += 256) Xs[(e / Bd) * 32 + e % Bd] = __ldg(Xa + i0 * Bd + e);
+    for (int e = t; e < rows * Rt; e += 256) Us[(e / Rt) * 32 + e % Rt] = __ldg(U + i0 * Rt + e);
+    __syncthreads();
+    if (b < Bd)
+      for (int k = 0; k < rows; ++k) {
+        const float x = Xs[k * 32 + b];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(Us[k * 32 + r0 + u], x, acc[u]);
+      }
+  }
+  float* Xoa = Xo + a * (int64_t)Rt * Bd;
+  if (b < Bd)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r0 + u < Rt) Xoa[(int64_t)(r0 + u) * Bd + b] = acc[u];
+}
+
 template <class T>
 void launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo) {
   dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
@@ -228,6 +261,8 @@ void launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, 
   dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
   if (Rt > 32 && Bd > 32)
     ttm_mid64_kernel<<<grid, 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
+  else if (Rt <= 32 && Bd <= 32)
+    ttm_mid32_kernel<<<(unsigned)A, 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, Xo);
   else
     ttm_mid_kernel<float><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
 }

@@ -115,6 +115,24 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, pg, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself without a process group."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(alg_bytes_per_replica: int, world: int, ms: float) -> float:
+    """Whole-job GB/s: every rank processes its own replica of the workload
+    (weak scaling), timed by the slowest rank."""
+    return world * alg_bytes_per_replica / (ms * 1e-3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -374,13 +392,10 @@ def main():
     sk_ms, sk_n = ctx.profile_read(0)
     co_ms, co_n = ctx.profile_read(1)
     ctx.profile(False)
-    if pg:
-        tt = torch.tensor([ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, pg, dev)
     y_bytes = w.itemsize * w.numel
     alg_bytes = 2 * y_bytes
-    value = ws * alg_bytes / (ms * 1e-3) / 1e9
+    value = job_value(alg_bytes, ws, ms)
 
     # ---- end to end: Y from pinned host memory each step, factors read back
     e2e = None
@@ -400,12 +415,8 @@ def main():
             host = [a.to("cpu") for a in o["A"]]
             d2h = sum(a.numel() * a.element_size() for a in host)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        if pg:
-            tt = torch.tensor([dt], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            dt = float(tt.item())
-        e2e = {"value": ws * alg_bytes / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, pg, dev)
+        e2e = {"value": job_value(alg_bytes, ws, dt * 1e3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
         del Yh
 

@@ -109,6 +109,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int64)]
         if hasattr(L, "tdk_ctx_test_fail_alloc"):
             L.tdk_ctx_test_fail_alloc.argtypes = [vp, ctypes.c_int]
+        if hasattr(L, "tdk_test_bounded_wait"):
+            L.tdk_test_bounded_wait.argtypes = [vp, ctypes.c_ulonglong]
         if hasattr(L, "tdk_ctx_test_als_form"):
             L.tdk_ctx_test_als_form.argtypes = [vp, ctypes.c_int]
         _lib = L

@@ -884,3 +884,38 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
 }
 
 }  // namespace tdk
+
+// ---- test hook (not in the public header): a bounded wait that cannot be
+// satisfied.  One thread waits for the first phase of an mbarrier that nothing
+// arrives at; after limit_ns it raises the timeout bit in the context's status
+// word and returns, exactly as the waits of the passes above do.
+namespace tdk {
+namespace {
+__global__ void wait_probe_kernel(unsigned* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = tc::globaltimer();
+    while (!tc::mbar_try_wait(tc::smem_u32(&bar), 0)) {
+      if (tc::globaltimer() - t0 > limit_ns) {
+        atomicOr(status, TDK_STATUS_TIMEOUT);
+        break;
+      }
+    }
+  }
+}
+}  // namespace
+}  // namespace tdk
+
+extern "C" int tdk_test_bounded_wait(tdk_ctx* ctx, unsigned long long limit_ns) {
+  using namespace tdk;
+  if (!ctx || limit_ns == 0 || limit_ns > 100000000ull) return TDK_EINVAL;  // at most 0.1 s
+  cudaSetDevice(ctx->device);
+  wait_probe_kernel<<<1, 32, 0, ctx->stream>>>(ctx->d_status, limit_ns);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}

@@ -60,6 +60,7 @@ struct PArgs {
   const double* init[TDK_MAX_MODES];  // B0 (Rt_n x R) or, nonneg, A0 (I_n x R)
   T* Bnew;                      // [max(Rt,I) x R] update rows (unnormalised)
   T* H;                         // [Rtmax x R]
+  T* Hpart;                     // [grid x R] partial rows of H_n
   T* Bout[TDK_MAX_MODES];       // final normalised B_n (CTA 0)
   double* Aout[TDK_MAX_MODES];  // nonneg: final normalised A_n (CTA 0)
   double* lam_out;
@@ -342,39 +343,56 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       };
 
       PROF_MARK(0);
-      // ---- 2. rows of H_n (unconstrained: and of B_n)
+      // ---- 2. rows of H_n (unconstrained: and of B_n).  Each row is split over
+      //         Pn CTAs by ranges of the slowest other mode; the partial rows
+      //         are summed in a fixed order after one more grid barrier.
       int oth[TDK_MAX_MODES];
       int no = 0;
       for (int p = 0; p < N; ++p)
         if (p != n) oth[no++] = p;
-      const int64_t Q = a.gnumel / Rn;
       const int last = oth[no - 1];
       const int Rl = a.Rt[last];
-      const int64_t A1 = Q / Rl;
-      for (int i = c; i < Rn; i += G) {
-        if (N == 3) {
-          // slice S[a1, l] = G(i at n, a1 at p, l at q) without index decoding,
-          // then work = S B_q in 4 x 4 register tiles, then H[i, :] = sum_a1 work * B_p
-          const int p = oth[0], q = oth[1];
-          const int Rp = a.Rt[p], Rq = a.Rt[q];
-          const int64_t sp = a.stride[p], sq = a.stride[q];
-          const T* Gi = a.G + (int64_t)i * a.stride[n];
-          for (int a1 = tid >> 5; a1 < Rp; a1 += NTP / 32)
-            for (int l = tid & 31; l < Rq; l += 32) slice[a1 * Rq + l] = Gi[a1 * sp + l * sq];
-          __syncthreads();
-          const T* Bq = Bs + boff[q];
-          const int ta = (Rp + 3) / 4, tr = (R + 3) / 4;
-          for (int tile = tid; tile < ta * tr; tile += NTP) {
-            const int a0 = (tile / tr) * 4, r0 = (tile % tr) * 4;
+      const int64_t sl = a.stride[last];
+      const int R0o = a.Rt[oth[0]];
+      const int64_t A1 = a.gnumel / Rn / Rl;  // slice rows: all other modes but the last
+      const int64_t per0 = A1 / R0o;          // slice rows per index of the slowest other mode
+      int Pn = G / Rn;
+      Pn = Pn < 1 ? 1 : (Pn > R0o ? R0o : Pn);
+      for (int wk = c; wk < Rn * Pn; wk += G) {
+        const int i = wk % Rn, part = wk / Rn;
+        const int lo = (int)((int64_t)part * R0o / Pn), hi = (int)((int64_t)(part + 1) * R0o / Pn);
+        const int64_t rows0 = (int64_t)(hi - lo) * per0;
+        // slice S[a1, l] of this part, one index decode per slice row
+        const T* Gi = a.G + (int64_t)i * a.stride[n];
+        for (int64_t a1 = tid >> 5; a1 < rows0; a1 += NTP / 32) {
+          int64_t rem = a1 + (int64_t)lo * per0;
+          int64_t off = 0;
+          for (int k = no - 2; k >= 0; --k) {
+            const int p = oth[k];
+            off += (rem % a.Rt[p]) * a.stride[p];
+            rem /= a.Rt[p];
+          }
+          const T* src = Gi + off;
+          for (int l = tid & 31; l < Rl; l += 32) slice[a1 * Rl + l] = src[l * sl];
+        }
+        __syncthreads();
+        // work[a1, r] = sum_l S[a1, l] B_last[l, r] in 4 x 4 register tiles
+        {
+          const T* Bq = Bs + boff[last];
+          const int64_t ta = (rows0 + 3) / 4;
+          const int tr = (R + 3) / 4;
+          for (int64_t tile = tid; tile < ta * tr; tile += NTP) {
+            const int64_t a0 = (tile / tr) * 4;
+            const int r0 = (int)(tile % tr) * 4;
             T acc[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
               for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-            for (int l = 0; l < Rq; ++l) {
+            for (int l = 0; l < Rl; ++l) {
               T s4[4], b4[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) s4[u] = (a0 + u < Rp) ? slice[(a0 + u) * Rq + l] : T(0);
+              for (int u = 0; u < 4; ++u) s4[u] = (a0 + u < rows0) ? slice[(a0 + u) * Rl + l] : T(0);
 #pragma unroll
               for (int v = 0; v < 4; ++v) b4[v] = (r0 + v < R) ? Bq[l * R + r0 + v] : T(0);
 #pragma unroll
@@ -386,50 +404,20 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             for (int u = 0; u < 4; ++u)
 #pragma unroll
               for (int v = 0; v < 4; ++v)
-                if (a0 + u < Rp && r0 + v < R) work[(a0 + u) * R + r0 + v] = acc[u][v];
+                if (a0 + u < rows0 && r0 + v < R) work[(a0 + u) * R + r0 + v] = acc[u][v];
           }
-          __syncthreads();
-          const T* Bp = Bs + boff[p];
-          for (int r = tid; r < R; r += NTP) {
-            T acc = T(0);
-            for (int a1 = 0; a1 < Rp; ++a1) acc = fma(work[a1 * R + r], Bp[a1 * R + r], acc);
-            a.H[(int64_t)i * R + r] = acc;
-            xrow[r] = (double)acc;
-          }
-          __syncthreads();
-        } else {
-#pragma unroll 4
-        for (int e = tid; e < (int)Q; e += NTP) {
-          int rem = e;
-          int64_t off = (int64_t)i * a.stride[n];
-          for (int k = no - 1; k >= 0; --k) {
-            const int p = oth[k];
-            off += (int64_t)(rem % a.Rt[p]) * a.stride[p];
-            rem /= a.Rt[p];
-          }
-          slice[e] = a.G[off];
         }
         __syncthreads();
-        // first contraction (last other mode): work[a1, r] = sum_l S[a1, l] B_last[l, r]
-        const T* Bl = Bs + boff[last];
-        for (int64_t e = tid; e < A1 * R; e += NTP) {
-          const int64_t a1 = e / R;
-          const int r = (int)(e % R);
-          const T* srow = slice + a1 * Rl;
-          T acc = T(0);
-          for (int l = 0; l < Rl; ++l) acc = fma(srow[l], Bl[l * R + r], acc);
-          work[e] = acc;
-        }
-        __syncthreads();
-        // remaining other modes, last to first: out[b, r] = sum_m in[b*Rp + m, r] B_p[m, r]
+        // remaining other modes, last to first: out[b, r] = sum_m in[b*Rp + m, r] B_p[m, r];
+        // the slowest one only over this part's range
         T* in = work;
         T* out = slice;
-        int64_t rows = A1;
+        int64_t rows = rows0;
         for (int k = no - 2; k >= 0; --k) {
           const int p = oth[k];
-          const int Rp = a.Rt[p];
+          const int Rp = (k == 0) ? (hi - lo) : a.Rt[p];
           const int64_t nrows = rows / Rp;
-          const T* Bp = Bs + boff[p];
+          const T* Bp = Bs + boff[p] + (k == 0 ? (int64_t)lo * R : 0);
           for (int64_t e = tid; e < nrows * R; e += NTP) {
             const int64_t b = e / R;
             const int r = (int)(e % R);
@@ -438,23 +426,44 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             out[e] = acc;
           }
           __syncthreads();
-          T* t = in;
+          T* tt = in;
           in = out;
-          out = t;
+          out = tt;
           rows = nrows;
         }
-        for (int r = tid; r < R; r += NTP) {
-          a.H[(int64_t)i * R + r] = in[r];
-          xrow[r] = (double)in[r];
-        }
-        __syncthreads();
-        }
-        if (!a.nonneg) {
-          solve_row();
+        if (Pn == 1) {
+          for (int r = tid; r < R; r += NTP) {
+            a.H[(int64_t)i * R + r] = in[r];
+            xrow[r] = (double)in[r];
+          }
           __syncthreads();
-          for (int r = tid; r < R; r += NTP) a.Bnew[(int64_t)i * R + r] = (T)xrow[r];
+          if (!a.nonneg) {
+            solve_row();
+            __syncthreads();
+            for (int r = tid; r < R; r += NTP) a.Bnew[(int64_t)i * R + r] = (T)xrow[r];
+          }
+        } else {
+          for (int r = tid; r < R; r += NTP) a.Hpart[((int64_t)part * Rn + i) * R + r] = in[r];
         }
         __syncthreads();
+      }
+      if (Pn > 1) {
+        if (!grid_sync(a.bar, a.status)) { ok = false; break; }
+        for (int i = c; i < Rn; i += G) {
+          for (int r = tid; r < R; r += NTP) {
+            T sum = T(0);
+            for (int part = 0; part < Pn; ++part) sum += __ldcg(a.Hpart + ((int64_t)part * Rn + i) * R + r);
+            a.H[(int64_t)i * R + r] = sum;
+            xrow[r] = (double)sum;
+          }
+          __syncthreads();
+          if (!a.nonneg) {
+            solve_row();
+            __syncthreads();
+            for (int r = tid; r < R; r += NTP) a.Bnew[(int64_t)i * R + r] = (T)xrow[r];
+          }
+          __syncthreads();
+        }
       }
       PROF_MARK(1);
       if (!grid_sync(a.bar, a.status)) { ok = false; break; }
@@ -1131,11 +1140,17 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   int per_sm = 0;
   TDK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTP, smem));
   if (per_sm < 1) return TDK_ENOTSUP;
-  int grid = (int)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, a.nonneg ? std::max(Rtmax, Imax) : Rtmax);
+  // rows of H_n are split over several CTAs (by ranges of the slowest other
+  // mode) when the whole GPU gives at least four per row; otherwise one CTA per
+  // row keeps the grid barriers cheap
+  const int grid_all = per_sm * ctx->num_sms;
+  const int64_t rows_cap = a.nonneg ? std::max(Rtmax, Imax) : Rtmax;
+  int grid = (grid_all >= 4 * Rtmax) ? grid_all : (int)std::min<int64_t>(grid_all, rows_cap);
 
   Planner pl;
   pl.take<T>((size_t)(a.nonneg ? std::max(Rtmax, Imax) : Rtmax) * R);
   pl.take<T>((size_t)Rtmax * R);
+  pl.take<T>((size_t)grid * R);
   for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.Rt[n] * R);
   for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.I[n] * g.Rt[n]);
   if (a.nonneg)
@@ -1151,6 +1166,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   Carver cv(ctx->ws);
   a.Bnew = cv.take<T>((size_t)(a.nonneg ? std::max(Rtmax, Imax) : Rtmax) * R);
   a.H = cv.take<T>((size_t)Rtmax * R);
+  a.Hpart = cv.take<T>((size_t)grid * R);
   for (int n = 0; n < N; ++n) a.Bout[n] = cv.take<T>((size_t)g.Rt[n] * R);
   T* uf[TDK_MAX_MODES];
   for (int n = 0; n < N; ++n) uf[n] = cv.take<T>((size_t)g.I[n] * g.Rt[n]);

@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
     if (lane == 0) {
       prefetch_tmap(&tmY);
       prefetch_tmap(&tmU);
-      const uint64_t pol = policy_evict_first();
       uint32_t it = 0;
       for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         for (int kc = 0; kc < a.KC; ++kc, ++it) {
@@ -111,8 +110,8 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
           for (int m = 0; m < MT; ++m) {
             const int row = (int)(t * 128 * MT + 128 * m);
             unsigned char* sub = dst + m * Lay::SUB_BYTES;
-            tma_load_3d_hint(smem_u32(sub), &tmY, kc * 64, row, 0, smem_u32(&full[s]), pol);
-            if (F32) tma_load_3d_hint(smem_u32(sub + BOX_BYTES), &tmY, kc * 64 + 32, row, 0, smem_u32(&full[s]), pol);
+            tma_load_3d(smem_u32(sub), &tmY, kc * 64, row, 0, smem_u32(&full[s]));
+            if (F32) tma_load_3d(smem_u32(sub + BOX_BYTES), &tmY, kc * 64 + 32, row, 0, smem_u32(&full[s]));
           }
           tma_load_3d(smem_u32(dst + Lay::Y_BYTES), &tmU, kc * 64, 0, 0, smem_u32(&full[s]));
         }

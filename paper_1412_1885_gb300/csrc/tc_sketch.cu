@@ -55,7 +55,7 @@ int encode_tmap(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* 
   }
   CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     fprintf(stderr, "tdk: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
     return TDK_EINVAL;
@@ -193,7 +193,6 @@ __global__ void __launch_bounds__(320, 1)
     if (lane == 0) {
       prefetch_tmap(&tmY);
       prefetch_tmap(&tmW);
-      const uint64_t pol = policy_evict_first();
       uint32_t it = 0, un = 0;
       for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
         const int pc = (int)(u % a.PC);
@@ -219,12 +218,10 @@ __global__ void __launch_bounds__(320, 1)
             const int kc = k0 + 128 * st;
             if (F32) {
               for (int q = 0; q < 4; ++q)
-                tma_load_3d_hint(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 32 * q, j0, (int)p, smem_u32(&full[s]),
-                                 pol);
+                tma_load_3d(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 32 * q, j0, (int)p, smem_u32(&full[s]));
             } else {
               for (int q = 0; q < 2; ++q)
-                tma_load_3d_hint(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 64 * q, j0, (int)p, smem_u32(&full[s]),
-                                 pol);
+                tma_load_3d(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 64 * q, j0, (int)p, smem_u32(&full[s]));
             }
           }
         }

@@ -27,6 +27,7 @@ sys.path.insert(0, ROOT)
 METRIC = "dense-tensor GB/s (sketch+core) vs HBM peak; FFCP time-to-fit vs plain FP32"
 DEFAULT_CONFIG = "c4"
 DEFAULT_PREC = "tc"
+DEFAULT_SKETCH = "independent"
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -309,6 +310,8 @@ def main():
     ap.add_argument("--no-ttf", action="store_true", help="skip the time-to-fit comparison of the forms")
     ap.add_argument("--train", type=int, default=2048, help="learned-init workload: training tensors")
     ap.add_argument("--eval", type=int, default=64, help="learned-init workload: held-out tensors")
+    ap.add_argument("--sketch", default=DEFAULT_SKETCH, choices=["shared", "independent"],
+                    help="sketch family: Khatri-Rao factors shared between the modes, or drawn per mode")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -351,8 +354,8 @@ def main():
         # the timed tensor: held-out tensor 0 of the learned-initialiser workload
         w = synth.learned_init_workload(0, 2, w.shape, w.Rt[0])
     Y, A_true = synth.device_tensor(w, device=dev)
-    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
-    Wd = [[None if x is None else torch.as_tensor(x, device=dev) for x in row] for row in W]
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed, shared=args.sketch == "shared")
+    Wd = synth.device_sketch(W, dev)
     B0 = [torch.as_tensor(b, device=dev) for b in synth.init_factors(w.Rt, w.als_R, w.seed)]
     A0 = [torch.as_tensor(a, device=dev) for a in synth.init_factors(w.shape, w.als_R, w.seed, dist="uniform")]
     torch.cuda.synchronize()
@@ -456,7 +459,7 @@ def main():
                 "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16"}[w.dtype],
                 "data": "synthetic",
                 "config": {"workload": w.name, "shape": list(w.shape), "ranks": list(w.ranks), "p": w.p,
-                           "R": w.als_R, "prec": args.prec, "nonneg": w.nonneg,
+                           "R": w.als_R, "prec": args.prec, "nonneg": w.nonneg, "sketch": args.sketch,
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -491,13 +491,28 @@ __global__ void lift_kernel(const double* __restrict__ U, const T* __restrict__ 
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * R; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / R;
     int r = (int)(e % R);
-    double s = 0.0;
-    for (int64_t q = 0; q < Rt; ++q) s = fma(U[i * Rt + q], (double)B[q * R + r], s);
+    double s;
+    if (sizeof(T) == 8) {
+      s = 0.0;
+      for (int64_t q = 0; q < Rt; ++q) s = fma(U[i * Rt + q], (double)B[q * R + r], s);
+    } else {
+      // FP32 factors B: the product in FP32 (U rounded to FP32 adds one
+      // rounding of the same size as B's own), FP64 arithmetic being scarce
+      float sf = 0.f;
+      for (int64_t q = 0; q < Rt; ++q) sf = fmaf((float)U[i * Rt + q], (float)B[q * R + r], sf);
+      s = (double)sf;
+    }
     A[e] = lam ? s * lam[r] : s;
   }
   if (Bout)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Rt * R; e += (int64_t)gridDim.x * blockDim.x)
       Bout[e] = (double)B[e];
+}
+
+// one thread per entry of A_n, capped
+static inline unsigned lift_grid(int64_t I, int R) {
+  const int64_t b = (I * R + 255) / 256;
+  return (unsigned)(b < 1 ? 1 : (b > 2048 ? 2048 : b));
 }
 
 __global__ void scale_cols_kernel(const double* __restrict__ A, int64_t I, int R, const double* __restrict__ lam,
@@ -727,7 +742,7 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
   for (int n = 0; n < N; ++n) {
     const double* lamp = (n == N - 1) ? a.lam : nullptr;
     if (!a.nonneg) {
-      lift_kernel<T><<<128, 256, 0, s>>>(U[n], a.B[n], g.I[n], g.Rt[n], R, lamp, A_io[n], B_io[n]);
+      lift_kernel<T><<<lift_grid(g.I[n], R), 256, 0, s>>>(U[n], a.B[n], g.I[n], g.Rt[n], R, lamp, A_io[n], B_io[n]);
       TDK_LAUNCH_CHECK(ctx);
     } else {
       scale_cols_kernel<<<128, 256, 0, s>>>(a.A[n], g.I[n], R, lamp, A_io[n]);
@@ -768,10 +783,10 @@ int als_finish(tdk_ctx* ctx, const Geom& g, int R, bool dbl, const void* const* 
     const double* lamp = (n == g.N - 1) ? lam : nullptr;
     if (!Aw) {
       if (dbl)
-        lift_kernel<double><<<128, 256, 0, s>>>(U[n], reinterpret_cast<const double*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
+        lift_kernel<double><<<lift_grid(g.I[n], R), 256, 0, s>>>(U[n], reinterpret_cast<const double*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
                                                 A_io[n], B_io[n]);
       else
-        lift_kernel<float><<<128, 256, 0, s>>>(U[n], reinterpret_cast<const float*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
+        lift_kernel<float><<<lift_grid(g.I[n], R), 256, 0, s>>>(U[n], reinterpret_cast<const float*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
                                                A_io[n], B_io[n]);
       TDK_LAUNCH_CHECK(ctx);
     } else {

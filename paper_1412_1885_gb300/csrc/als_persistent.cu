@@ -1069,9 +1069,26 @@ template <class T>
 __global__ void norm2_core(const T* __restrict__ G, int64_t n, double* __restrict__ out) {
   __shared__ double red[32];
   double s = 0.0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-    const double v = (double)G[e];
-    s = fma(v, v, s);
+  if (sizeof(T) == 8) {
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const double v = (double)G[e];
+      s = fma(v, v, s);
+    }
+  } else {
+    // FP32 core: each square is split exactly into hi + lo (an FMA gives the
+    // rounding error of the product) and both are summed with compensation in
+    // FP32, since FP64 arithmetic is scarce on this GPU; FP64 only across threads
+    float hs = 0.f, c = 0.f;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const float v = (float)G[e];
+      const float sq = v * v;
+      const float sq_lo = fmaf(v, v, -sq);
+      const float y = sq - c;
+      const float t = hs + y;
+      c = ((t - hs) - y) - sq_lo;
+      hs = t;
+    }
+    s = (double)hs - (double)c;
   }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;

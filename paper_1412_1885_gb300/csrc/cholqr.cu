@@ -68,58 +68,83 @@ __global__ void gram_reduce_kernel(QRArgs q, const double* __restrict__ gp, cons
   gram[(int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK + e] = s;
 }
 
-// Cholesky of the Gram (upper R, Gram = R^T R) -> Rinv; one CTA per mode
+// Cholesky of the Gram (upper R, Gram = R^T R) -> Rinv; one CTA per mode.
+// FP64 arithmetic is scarce on this GPU (about two FMAs per clock per SM), so
+// every FP64 value is computed by one thread only: each pivot's reciprocal
+// and breakdown test by the thread that finalises that pivot, each row
+// multiplier by lane 0 of the row's warp (then broadcast).
 __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* __restrict__ rinv,
                             int* __restrict__ fail) {
   const int n = blockIdx.x;
   const int Rt = q.Rt[n];
   __shared__ double A[TDK_MAX_RANK * TDK_MAX_RANK];
   __shared__ double Ri[TDK_MAX_RANK * TDK_MAX_RANK];
+  __shared__ double inv_d[TDK_MAX_RANK], dsq[TDK_MAX_RANK], idsq[TDK_MAX_RANK];
+  __shared__ double tiny_s;
   __shared__ int bad;
   if (fail[n]) return;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  if (tid == 0) bad = 0;
   for (int e = tid; e < Rt * Rt; e += nth) A[e] = gram[(int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK + e];
   __syncthreads();
-  double mx = 0.0;
-  for (int j = 0; j < Rt; ++j) mx = fmax(mx, A[j * Rt + j]);
-  const double tiny = Rt * 2.220446049250313e-16 * mx;
-  // right-looking Cholesky on the upper triangle: A = R^T R; the trailing
-  // update runs on a (threadIdx.y, threadIdx.x) = (row, column) grid
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < Rt; ++j) mx = fmax(mx, A[j * Rt + j]);
+    tiny_s = Rt * 2.220446049250313e-16 * mx;
+    bad = !(A[0] > tiny_s);
+    inv_d[0] = 1.0 / A[0];
+  }
+  // right-looking Cholesky on the upper triangle, A = R^T R, one barrier per
+  // pivot: the trailing update uses the unscaled pivot row times 1/d, and every
+  // row is scaled by 1/sqrt(d) once at the end (a row is not read again after
+  // its own step).  Warp y updates rows a = j+1+y (step blockDim.y), lanes the
+  // columns b >= a.
   for (int j = 0; j < Rt; ++j) {
     __syncthreads();
-    double d = A[j * Rt + j];
-    if (!(d > tiny)) {
-      if (tid == 0) bad = 1;
-      break;
+    if (bad) break;
+    const double id = inv_d[j];
+    for (int a = j + 1 + (int)threadIdx.y; a < Rt; a += blockDim.y) {
+      double aja = 0.0;
+      if (threadIdx.x == 0) aja = A[j * Rt + a] * id;
+      aja = __shfl_sync(0xffffffffu, aja, 0);
+      for (int b = a + (int)threadIdx.x; b < Rt; b += blockDim.x) {
+        const double v = fma(-aja, A[j * Rt + b], A[a * Rt + b]);
+        A[a * Rt + b] = v;
+        if (b == a && a == j + 1) {  // the next pivot is final now
+          bad = !(v > tiny_s);
+          inv_d[a] = 1.0 / v;
+        }
+      }
     }
-    const double rjj = sqrt(d), irjj = 1.0 / rjj;
-    __syncthreads();
-    if (tid == 0) A[j * Rt + j] = rjj;
-    for (int b = j + 1 + tid; b < Rt; b += nth) A[j * Rt + b] *= irjj;
-    __syncthreads();
-    for (int a = j + 1 + (int)threadIdx.y; a < Rt; a += blockDim.y)
-      for (int b = a + (int)threadIdx.x; b < Rt; b += blockDim.x)
-        A[a * Rt + b] = fma(-A[j * Rt + a], A[j * Rt + b], A[a * Rt + b]);
   }
   __syncthreads();
   if (bad) {
     if (tid == 0) fail[n] = 1;
     return;
   }
-  // Rinv = R^{-1}: column b solves R x = e_b (x upper triangular)
-  for (int b = tid; b < Rt; b += nth) {
-    for (int a = Rt - 1; a >= 0; --a) {
-      double s = (a == b) ? 1.0 : 0.0;
-      if (a > b) {
-        Ri[a * Rt + b] = 0.0;
-        continue;
-      }
-      for (int c = a + 1; c <= b; ++c) s = fma(-A[a * Rt + c], Ri[c * Rt + b], s);
-      Ri[a * Rt + b] = s / A[a * Rt + a];
-    }
+  for (int j = tid; j < Rt; j += nth) {
+    dsq[j] = sqrt(A[j * Rt + j]);
+    idsq[j] = 1.0 / dsq[j];
   }
   __syncthreads();
+  for (int e = tid; e < Rt * Rt; e += nth) {
+    const int j = e / Rt, b = e % Rt;
+    if (b > j) A[e] *= idsq[j];
+    else if (b == j) A[e] = dsq[j];
+  }
+  // Rinv = R^{-1} by Gauss-Jordan back substitution, all threads: X = I, then
+  // for k from the last row up: X[k, :] /= R_kk, X[i, :] -= R_ik X[k, :] (i < k).
+  // R is never updated (each step only clears column k of R).
+  for (int e = tid; e < Rt * Rt; e += nth) Ri[e] = (e / Rt == e % Rt) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = Rt - 1; k >= 0; --k) {
+    for (int j = k + tid; j < Rt; j += nth) Ri[k * Rt + j] *= idsq[k];
+    __syncthreads();
+    for (int i = threadIdx.y; i < k; i += blockDim.y) {
+      const double rik = A[i * Rt + k];
+      for (int j = k + (int)threadIdx.x; j < Rt; j += blockDim.x) Ri[i * Rt + j] = fma(-rik, Ri[k * Rt + j], Ri[i * Rt + j]);
+    }
+    __syncthreads();
+  }
   double* out = rinv + (int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK;
   for (int e = tid; e < Rt * Rt; e += nth) out[e] = Ri[e];
 }

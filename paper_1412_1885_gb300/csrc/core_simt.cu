@@ -90,28 +90,33 @@ __global__ void __launch_bounds__(NT) ttm_last_kernel(const TY* __restrict__ Y, 
   }
 }
 
-// Xo[a, r, b] = sum_i U[i, r] X[a, i, b];  grid (A, ceil(Bd/64)), Rt <= 64
+// Xo[a, r, b] = sum_i U[i, r] X[a, i, b];  grid (A, ceil(Bd/64), KS), Rt <= 64.
+// Split over the contracted index: CTA z sums i in [z kch, (z+1) kch) into
+// the z-th copy of the output (KS = 1: the output itself).
 template <class T>
 __global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, int64_t Ic, int64_t Bd,
-                                                     const T* __restrict__ U, int Rt, T* __restrict__ Xo) {
+                                                     const T* __restrict__ U, int Rt, T* __restrict__ Xo,
+                                                     int64_t kch) {
   __shared__ T Xs[32 * 64];
   __shared__ T Us[32 * 64];
   const int t = threadIdx.x, tb = t & 15, tr = t >> 4;
   const int64_t a = blockIdx.x;
   const int64_t b0 = (int64_t)blockIdx.y * 64;
+  const int64_t k0 = (int64_t)blockIdx.z * kch, k1 = k0 + kch < Ic ? k0 + kch : Ic;
   const T* Xa = X + a * Ic * Bd;
+  Xo += (int64_t)blockIdx.z * gridDim.x * (int64_t)Rt * Bd;
   T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  for (int64_t i0 = 0; i0 < Ic; i0 += 32) {
+  for (int64_t i0 = k0; i0 < k1; i0 += 32) {
     __syncthreads();
     for (int e = t; e < 32 * 64; e += NT) {
       int ii = e / 64, c = e % 64;
       int64_t i = i0 + ii;
-      Xs[e] = (i < Ic && b0 + c < Bd) ? Xa[i * Bd + b0 + c] : T(0);
-      Us[e] = (i < Ic && c < Rt) ? U[i * Rt + c] : T(0);
+      Xs[e] = (i < k1 && b0 + c < Bd) ? Xa[i * Bd + b0 + c] : T(0);
+      Us[e] = (i < k1 && c < Rt) ? U[i * Rt + c] : T(0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -147,14 +152,17 @@ __global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, in
 // double-buffered shared memory with the next slice prefetched in registers.
 // grid (A, ceil(Bd / 64))
 __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__ X, int64_t Ic, int64_t Bd,
-                                                       const float* __restrict__ U, int Rt, float* __restrict__ Xo) {
+                                                       const float* __restrict__ U, int Rt, float* __restrict__ Xo,
+                                                       int64_t kch) {
   constexpr int KC = 32;
   __shared__ __align__(16) float Xs[2][KC][64];
   __shared__ __align__(16) float Us[2][KC][64];
   const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
   const int64_t a = blockIdx.x;
   const int64_t b0 = (int64_t)blockIdx.y * 64;
+  const int64_t k0 = (int64_t)blockIdx.z * kch, k1 = k0 + kch < Ic ? k0 + kch : Ic;
   const float* Xa = X + a * Ic * Bd;
+  Xo += (int64_t)blockIdx.z * gridDim.x * (int64_t)Rt * Bd;
   const bool bok = b0 + t < Bd, rok = t < Rt;
   float rx[KC], ru[KC];
   // thread t loads column t of the slice: 32 rows of X (coalesced along b) and of U
@@ -162,8 +170,8 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
       const int64_t i = i0 + j;
-      rx[j] = (i < Ic && bok) ? __ldg(Xa + i * Bd + b0 + t) : 0.f;
-      ru[j] = (i < Ic && rok) ? __ldg(U + i * Rt + t) : 0.f;
+      rx[j] = (i < k1 && bok) ? __ldg(Xa + i * Bd + b0 + t) : 0.f;
+      ru[j] = (i < k1 && rok) ? __ldg(U + i * Rt + t) : 0.f;
     }
   };
   auto stash = [&](int buf) {
@@ -178,12 +186,12 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
   for (int p = 0; p < 8; ++p)
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
-  load(0);
+  load(k0);
   stash(0);
   __syncthreads();
   int buf = 0;
-  for (int64_t i0 = 0; i0 < Ic; i0 += KC) {
-    const bool more = i0 + KC < Ic;
+  for (int64_t i0 = k0; i0 < k1; i0 += KC) {
+    const bool more = i0 + KC < k1;
     if (more) load(i0 + KC);
 #pragma unroll 4
     for (int k = 0; k < KC; ++k) {
@@ -221,17 +229,20 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
 // Rt x Bd output of one a per CTA; K staged 64 deep, each slice of X and U a
 // contiguous run of memory read by all threads; 4 outputs per thread.
 __global__ void __launch_bounds__(256) ttm_mid32_kernel(const float* __restrict__ X, int64_t Ic, int Bd,
-                                                        const float* __restrict__ U, int Rt, float* __restrict__ Xo) {
+                                                        const float* __restrict__ U, int Rt, float* __restrict__ Xo,
+                                                        int64_t kch) {
   constexpr int KC = 64;
   __shared__ float Xs[KC * 32];
   __shared__ float Us[KC * 32];
   const int t = threadIdx.x;
   const int64_t a = blockIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.z * kch, k1 = k0 + kch < Ic ? k0 + kch : Ic;
   const float* Xa = X + a * Ic * Bd;
+  Xo += (int64_t)blockIdx.z * gridDim.x * (int64_t)Rt * Bd;
   const int b = t & 31, r0 = (t >> 5) * 4;  // column b, rows r0..r0+3
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int64_t i0 = 0; i0 < Ic; i0 += KC) {
-    const int rows = (int)((Ic - i0) < KC ? (Ic - i0) : KC);
+  for (int64_t i0 = k0; i0 < k1; i0 += KC) {
+    const int rows = (int)((k1 - i0) < KC ? (k1 - i0) : KC);
     __syncthreads();
     for (int e = t; e < rows * Bd; e += 256) Xs[(e / Bd) * 32 + e % Bd] = __ldg(Xa + i0 * Bd + e);
     for (int e = t; e < rows * Rt; e += 256) Us[(e / Rt) * 32 + e % Rt] = __ldg(U + i0 * Rt + e);
@@ -250,21 +261,57 @@ __global__ void __launch_bounds__(256) ttm_mid32_kernel(const float* __restrict_
       if (r0 + u < Rt) Xoa[(int64_t)(r0 + u) * Bd + b] = acc[u];
 }
 
+// fixed-order sum of the KS partial outputs of a split contraction
 template <class T>
-void launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo) {
-  dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
-  ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
+__global__ void sum_split_kernel(const T* __restrict__ part, int ks, int64_t n, T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    T v = part[e];
+    for (int z = 1; z < ks; ++z) v += part[z * n + e];
+    out[e] = v;
+  }
+}
+
+// Number of slices of the contracted index: the contractions at the end of
+// the chain have few output tiles (A = 1 at the last one), so their CTAs
+// would leave most SMs idle; slices of at least 128 indices each, partials in
+// `part` (capacity in elements), summed in a fixed order.
+static int split_count(tdk_ctx* ctx, int64_t ctas, int per_sm, int64_t Ic, int64_t out_n, int64_t part_cap) {
+  if (!part_cap) return 1;
+  int64_t ks = (per_sm * (int64_t)ctx->num_sms + ctas - 1) / ctas;
+  ks = std::min<int64_t>(ks, Ic / 128);
+  ks = std::min<int64_t>(ks, part_cap / std::max<int64_t>(out_n, 1));
+  return ks < 2 ? 1 : (int)std::min<int64_t>(ks, 64);
+}
+
+template <class T>
+void launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo,
+                    T* part, int64_t part_cap) {
+  const int64_t nb = (Bd + 63) / 64, out_n = A * Rt * Bd;
+  const int ks = split_count(ctx, A * nb, 2, Ic, out_n, part_cap);
+  const int64_t kch = (Ic + ks - 1) / ks;
+  dim3 grid((unsigned)A, (unsigned)nb, (unsigned)ks);
+  ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, ks > 1 ? part : Xo, kch);
+  if (ks > 1) sum_split_kernel<T><<<(unsigned)std::min<int64_t>((out_n + 255) / 256, 1024), 256, 0, ctx->stream>>>(part, ks, out_n, Xo);
 }
 template <>
 void launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, int64_t Bd, const float* U, int Rt,
-                           float* Xo) {
-  dim3 grid((unsigned)A, (unsigned)((Bd + 63) / 64));
-  if (Rt > 32 && Bd > 32)
-    ttm_mid64_kernel<<<grid, 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
-  else if (Rt <= 32 && Bd <= 32)
-    ttm_mid32_kernel<<<(unsigned)A, 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, Xo);
+                           float* Xo, float* part, int64_t part_cap) {
+  const int64_t nb = (Bd + 63) / 64, out_n = A * Rt * Bd;
+  const bool wide = Rt > 32 && Bd > 32, narrow = Rt <= 32 && Bd <= 32;
+  const int ks = wide ? split_count(ctx, A * nb, 6, Ic, out_n, part_cap)
+                      : split_count(ctx, narrow ? A : A * nb, 2, Ic, out_n, part_cap);
+  const int64_t kch = (Ic + ks - 1) / ks;
+  float* dst = ks > 1 ? part : Xo;
+  if (wide)
+    ttm_mid64_kernel<<<dim3((unsigned)A, (unsigned)nb, (unsigned)ks), 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, dst, kch);
+  else if (narrow)
+    ttm_mid32_kernel<<<dim3((unsigned)A, 1, (unsigned)ks), 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
   else
-    ttm_mid_kernel<float><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo);
+    ttm_mid_kernel<float><<<dim3((unsigned)A, (unsigned)nb, (unsigned)ks), NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt,
+                                                                                                 dst, kch);
+  if (ks > 1)
+    sum_split_kernel<float><<<(unsigned)std::min<int64_t>((out_n + 255) / 256, 1024), 256, 0, ctx->stream>>>(
+        part, ks, out_n, Xo);
 }
 
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
@@ -300,27 +347,39 @@ int launch_last(tdk_ctx* ctx, const void* Y, int64_t M, int64_t L, const T* U, i
 
 }  // namespace
 
-// core chain shared by both forms once X_1 exists (modes N-2 .. 0)
+// core chain from a partly contracted tensor X with dims I_0..I_{m0},
+// Rt_{m0+1}..Rt_{N-1} (modes m0 .. 0 remain); X is neither tmp0 nor tmp1
 template <class T>
-int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1) {
+int core_chain_from(tdk_ctx* ctx, const Geom& g, const T* X, int m0, T* const Ut[], T* G, T* tmp0, T* tmp1,
+                    T* part, int64_t part_cap) {
   const int N = g.N;
-  // dims of the current tensor: I_0..I_{m}, Rt_{m+1}..Rt_{N-1}
-  const T* cur = X1;
-  int64_t Bd = g.Rt[N - 1];
-  for (int m = N - 2; m >= 0; --m) {
+  const T* cur = X;
+  int64_t Bd = 1;
+  for (int k = m0 + 1; k < N; ++k) Bd *= g.Rt[k];
+  for (int m = m0; m >= 0; --m) {
     int64_t A = 1;
     for (int k = 0; k < m; ++k) A *= g.I[k];
     T* out = (m == 0) ? G : ((m % 2) ? tmp0 : tmp1);
-    launch_ttm_mid<T>(ctx, cur, A, g.I[m], Bd, Ut[m], g.Rt[m], out);
+    launch_ttm_mid<T>(ctx, cur, A, g.I[m], Bd, Ut[m], g.Rt[m], out, part, part_cap);
     TDK_LAUNCH_CHECK(ctx);
     cur = out;
     Bd *= g.Rt[m];
   }
   return TDK_OK;
 }
-template int core_chain_rest<float>(tdk_ctx*, const Geom&, const float*, float* const[], float*, float*, float*);
+template int core_chain_from<float>(tdk_ctx*, const Geom&, const float*, int, float* const[], float*, float*,
+                                    float*, float*, int64_t);
+
+// core chain shared by both forms once X_1 exists (modes N-2 .. 0)
+template <class T>
+int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1, T* part,
+                    int64_t part_cap) {
+  return core_chain_from<T>(ctx, g, X1, g.N - 2, Ut, G, tmp0, tmp1, part, part_cap);
+}
+template int core_chain_rest<float>(tdk_ctx*, const Geom&, const float*, float* const[], float*, float*, float*,
+                                    float*, int64_t);
 template int core_chain_rest<double>(tdk_ctx*, const Geom&, const double*, double* const[], double*, double*,
-                                     double*);
+                                     double*, double*, int64_t);
 
 template <class TY, class T>
 static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double* const U[], void* Gv,
@@ -348,6 +407,8 @@ static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double*
   pl.take<T>((size_t)tmpsz);
   pl.take<T>((size_t)tmpsz);
   pl.take<double>((size_t)grid);
+  const int64_t pcap = chain_split_cap(g);
+  pl.take<T>((size_t)pcap);
   int rc = ws_reserve(ctx, pl.off);
   if (rc) return rc;
   Carver cv(ctx->ws);
@@ -361,6 +422,7 @@ static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double*
   T* tmp0 = cv.take<T>((size_t)tmpsz);
   T* tmp1 = cv.take<T>((size_t)tmpsz);
   double* parts = cv.take<double>((size_t)grid);
+  T* spl = cv.take<T>((size_t)pcap);
   switch (TC) {
     case 1: rc = launch_last<TY, T, 1>(ctx, Y, g.M, g.L, Ut[N - 1], RtL, X1, parts, grid); break;
     case 2: rc = launch_last<TY, T, 2>(ctx, Y, g.M, g.L, Ut[N - 1], RtL, X1, parts, grid); break;
@@ -373,7 +435,7 @@ static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double*
     sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(parts, grid, normY2);
     TDK_LAUNCH_CHECK(ctx);
   }
-  return core_chain_rest<T>(ctx, g, X1, Ut, reinterpret_cast<T*>(Gv), tmp0, tmp1);
+  return core_chain_rest<T>(ctx, g, X1, Ut, reinterpret_cast<T*>(Gv), tmp0, tmp1, spl, pcap);
 }
 
 int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* G,

@@ -16,7 +16,11 @@
 namespace tdk {
 
 template <class T>
-int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1);
+int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1, T* part,
+                    int64_t part_cap);
+template <class T>
+int core_chain_from(tdk_ctx* ctx, const Geom& g, const T* X, int m0, T* const Ut[], T* G, T* tmp0, T* tmp1,
+                    T* part, int64_t part_cap);
 
 namespace {
 
@@ -264,6 +268,373 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused first two contractions (BF16 data).  Y is read as [P][J][L] (L = I_N,
+// J = I_{N-1}, P = prod of the other modes); a work item is one p, its tiles
+// the 128-row blocks of j.  Per tile, D1 = X_1 rows (as above) and then a
+// second product on the tensor cores,
+//   D2[s, r] += sum_j U_{N-1}[j, s] X_1[p, j, r],
+// accumulated in TMEM over the tiles of p, so X_1 never leaves the SM.  Both
+// operands of the second product are split hi + lo (A: rows 0..63 the hi and
+// 64..127 the lo part of U_{N-1}^T; B: columns 0..63 hi and 64..127 lo of the
+// X_1 tile, written by the epilogue), so D2 holds the four partial products
+// and X_2[p, s, r] is their sum.  The second product of a tile is issued after
+// the first product of the next tile, so the MMA issuer never waits for the
+// epilogue.
+struct FuArgs {
+  int L, KC, NB, Rt, Rtp;  // contiguous mode, as CoArgs
+  int J, JT;               // I_{N-1} and its 128-row tiles
+  int P;                   // work items
+  int Rt2;                 // sketch width of mode N-1
+  float* X2;               // [P][Rt2][Rt]
+  double* nrm_part;
+  unsigned* status;
+};
+
+constexpr int FU_S = 4;                 // stage ring
+constexpr uint32_t FU_Y = 16 * KB;      // 128 rows x 64 columns BF16
+constexpr int FU_THREADS = 192;
+constexpr int FU_SCR_LD = 65;           // padded row of the exchange buffer (floats)
+
+inline size_t fused_smem_bytes(int NB) {
+  const size_t stage = FU_Y + ((size_t)(NB * 128 + 1023) & ~size_t(1023));
+  return 1024 + FU_S * stage + 64 * KB + (size_t)64 * FU_SCR_LD * 4 + 256;
+}
+
+__global__ void __launch_bounds__(FU_THREADS, 1)
+    tc_core_fused_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmU,
+                         const __grid_constant__ CUtensorMap tmV, const FuArgs a) {
+  constexpr int S = FU_S;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t b_bytes = (uint32_t)a.NB * 128u;
+  const uint32_t stage_bytes = FU_Y + ((b_bytes + 1023) & ~1023u);
+  unsigned char* st_base = base;                      // S x (Y tile | U_N tile)
+  unsigned char* v_base = base + S * stage_bytes;     // U_{N-1} rows of the tile: two 16 KB boxes (hi, lo)
+  unsigned char* x_base = v_base + 32 * KB;           // X_1 tile: two 16 KB boxes (hi, lo)
+  float* scr = reinterpret_cast<float*>(x_base + 32 * KB);  // [64][FU_SCR_LD] lo-row partials of D2
+  uint64_t* bars = reinterpret_cast<uint64_t*>(scr + 64 * FU_SCR_LD);
+  uint64_t* full = bars;           // [S]
+  uint64_t* empty = bars + S;      // [S]
+  uint64_t* dfull = bars + 2 * S;  // [2]
+  uint64_t* dempty = dfull + 2;    // [2]
+  uint64_t* vfull = dfull + 4;
+  uint64_t* vempty = vfull + 1;
+  uint64_t* xfull = vfull + 2;
+  uint64_t* xempty = vfull + 3;
+  uint64_t* d2full = vfull + 4;
+  uint64_t* d2empty = vfull + 5;
+  uint64_t* sfull = vfull + 6;
+  uint64_t* sempty = vfull + 7;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(vfull + 8);
+  double* nred = reinterpret_cast<double*>(vfull + 10);  // [6]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 5);  // the MMA commit and the four epilogue warps (||Y||^2)
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&dfull[i]), 1);
+      mbar_init(smem_u32(&dempty[i]), 4);
+    }
+    mbar_init(smem_u32(vfull), 1);
+    mbar_init(smem_u32(vempty), 1);
+    mbar_init(smem_u32(xfull), 4);
+    mbar_init(smem_u32(xempty), 1);
+    mbar_init(smem_u32(d2full), 1);
+    mbar_init(smem_u32(d2empty), 4);
+    mbar_init(smem_u32(sfull), 2);
+    mbar_init(smem_u32(sempty), 2);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t d2col = 256;  // D1 buffers at columns [0, NB) and [NB, 2 NB), NB <= 128
+  unsigned* status = a.status;
+  bool ok = true;
+  float nrm = 0.f, nrm_c = 0.f;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmY);
+      prefetch_tmap(&tmU);
+      prefetch_tmap(&tmV);
+      // the U_{N-1} rows of tile t are loaded while the next tile streams in,
+      // once the second product of tile t-1 has read the single V buffer: after
+      // stage vk of the next tile, whose slot was freed by an MMA issued after
+      // that product, so the wait is normally already satisfied
+      auto load_v = [&](uint32_t t, int jt) -> bool {
+        if (!mbar_wait(smem_u32(vempty), (t & 1) ^ 1, status)) return false;
+        mbar_expect_tx(smem_u32(vfull), 32 * KB);
+        tma_load_3d(smem_u32(v_base), &tmV, 0, jt * 128, 0, smem_u32(vfull));
+        tma_load_3d(smem_u32(v_base + 16 * KB), &tmV, 64, jt * 128, 0, smem_u32(vfull));
+        return true;
+      };
+      const int vk = a.KC - 1 < S ? a.KC - 1 : S;
+      bool vp = false;
+      uint32_t vtl = 0;
+      int vjt = 0;
+      uint32_t it = 0, tl = 0;
+      for (int p = blockIdx.x; p < a.P && ok; p += gridDim.x) {
+        for (int jt = 0; jt < a.JT; ++jt, ++tl) {
+          for (int kc = 0; kc < a.KC; ++kc, ++it) {
+            const int s = it % S;
+            const uint32_t n = it / S;
+            if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
+            unsigned char* dst = st_base + s * stage_bytes;
+            mbar_expect_tx(smem_u32(&full[s]), FU_Y + b_bytes);
+            tma_load_3d(smem_u32(dst), &tmY, kc * 64, jt * 128, p, smem_u32(&full[s]));
+            tma_load_3d(smem_u32(dst + FU_Y), &tmU, kc * 64, 0, 0, smem_u32(&full[s]));
+            if (kc == vk && vp) {
+              if (!load_v(vtl, vjt)) { ok = false; break; }
+              vp = false;
+            }
+          }
+          if (!ok) break;
+          vp = true;
+          vtl = tl;
+          vjt = jt;
+        }
+      }
+      if (ok && vp && !load_v(vtl, vjt)) ok = false;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(128, a.NB, 0, 0);
+      const uint32_t id2 = idesc_bf16(128, 128, 1, 1);
+      // second product of tile t2 (of item number u2): D2 += V^T X
+      auto second = [&](uint32_t t2, uint32_t u2, bool first, bool last) -> bool {
+        if (first && !mbar_wait(smem_u32(d2empty), (u2 & 1) ^ 1, status)) return false;
+        if (!mbar_wait(smem_u32(vfull), t2 & 1, status)) return false;
+        if (!mbar_wait(smem_u32(xfull), t2 & 1, status)) return false;
+        tc_fence_after();
+        const uint32_t va = smem_u32(v_base), xa = smem_u32(x_base);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+          mma_bf16(tmem + d2col, smem_desc(va + kk * 2048, 16 * KB, 1024, SW128),
+                   smem_desc(xa + kk * 2048, 16 * KB, 1024, SW128), id2, !(first && kk == 0));
+        umma_commit(smem_u32(vempty));
+        umma_commit(smem_u32(xempty));
+        if (last) umma_commit(smem_u32(d2full));
+        return true;
+      };
+      uint32_t it = 0, tl = 0, ui = 0;
+      bool pend = false, pfirst = false, plast = false;
+      uint32_t ptl = 0, pui = 0;
+      for (int p = blockIdx.x; p < a.P && ok; p += gridDim.x, ++ui) {
+        for (int jt = 0; jt < a.JT; ++jt, ++tl) {
+          const int db = tl & 1;
+          if (!mbar_wait(smem_u32(&dempty[db]), ((tl >> 1) & 1) ^ 1, status)) { ok = false; break; }
+          tc_fence_after();
+          for (int kc = 0; kc < a.KC; ++kc, ++it) {
+            const int s = it % S;
+            const uint32_t n = it / S;
+            if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sb = smem_u32(st_base + s * stage_bytes);
+            const uint32_t bb = sb + FU_Y;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(tmem + db * a.NB, smem_desc(sb + kk * 32, 16, 1024, SW128),
+                       smem_desc(bb + kk * 32, 16, 1024, SW128), id1, (kc | kk) != 0);
+            umma_commit(smem_u32(&empty[s]));
+          }
+          if (!ok) break;
+          umma_commit(smem_u32(&dfull[db]));
+          if (pend && !second(ptl, pui, pfirst, plast)) { ok = false; break; }
+          pend = true;
+          ptl = tl;
+          pui = ui;
+          pfirst = jt == 0;
+          plast = jt == a.JT - 1;
+        }
+      }
+      if (ok && pend && !second(ptl, pui, pfirst, plast)) ok = false;
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2-5)
+    const int q = warp & 3;
+    const int rl = 32 * q + lane;  // TMEM lane: tile row j (D1), row of V^T (D2)
+    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    const bool upper = q >= 2;     // D2 rows 64..127: the lo part of U_{N-1}
+    // X_2[p] = the four quadrants of D2 (rows s (hi) and 64 + s (lo), columns r
+    // and 64 + r).  Run after the next tile's stages have been read, so that the
+    // stage ring keeps moving while the issuer still has the first product of
+    // that tile ahead of this item's last second product.
+    auto finalise = [&](int fp, uint32_t fu) -> bool {
+      if (!mbar_wait(smem_u32(d2full), fu & 1, status)) return false;
+      tc_fence_after();
+      float y[64];  // this row's hi-column plus lo-column products
+#pragma unroll
+      for (int c16 = 0; c16 < 4; ++c16) {
+        float t0[16], t1[16];
+        tmem_ld16(tmem + d2col + c16 * 16 + lane_addr, t0);
+        tmem_ld16(tmem + d2col + 64 + c16 * 16 + lane_addr, t1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) y[c16 * 16 + e] = t0[e] + t1[e];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(d2empty));
+      if (upper) {
+        if (!mbar_wait(smem_u32(sempty), (fu & 1) ^ 1, status)) return false;
+        float* sr = scr + (rl - 64) * FU_SCR_LD;
+#pragma unroll
+        for (int r = 0; r < 64; ++r) sr[r] = y[r];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(sfull));
+      } else {
+        if (!mbar_wait(smem_u32(sfull), fu & 1, status)) return false;
+        const float* sr = scr + rl * FU_SCR_LD;
+        if (rl < a.Rt2) {
+          float* out = a.X2 + ((int64_t)fp * a.Rt2 + rl) * a.Rt;
+#pragma unroll
+          for (int r = 0; r < 64; ++r)
+            if (r < a.Rt) out[r] = y[r] + sr[r];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(sempty));
+      }
+      return true;
+    };
+    bool fin = false;
+    int fin_p = 0;
+    uint32_t fin_u = 0;
+    uint32_t it = 0, tl = 0, ui = 0;
+    for (int p = blockIdx.x; p < a.P && ok; p += gridDim.x, ++ui) {
+      for (int jt = 0; jt < a.JT; ++jt, ++tl) {
+        // ||Y||^2 from the staged tiles
+        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t n = it / S;
+          if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
+          float part = 0.f;
+          const unsigned char* row = st_base + s * stage_bytes + rl * 128;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint4 w = *reinterpret_cast<const uint4*>(row + ((c ^ (rl & 7)) << 4));
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
+              part = fmaf(lo, lo, part);
+              part = fmaf(hi, hi, part);
+            }
+          }
+          const float y = part - nrm_c;
+          const float tt = nrm + y;
+          nrm_c = (tt - nrm) - y;
+          nrm = tt;
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        if (fin) {
+          if (!finalise(fin_p, fin_u)) { ok = false; break; }
+          fin = false;
+        }
+        // X_1 row j = rl of this tile (sum of the U_hi and U_lo columns of D1)
+        const int db = tl & 1;
+        if (!mbar_wait(smem_u32(&dfull[db]), (tl >> 1) & 1, status)) { ok = false; break; }
+        tc_fence_after();
+        float xr[128];  // D1 row; its first 64 entries become the X_1 row
+#pragma unroll
+        for (int c16 = 0; c16 < 8; ++c16)
+          if (c16 * 16 < a.NB) tmem_ld16(tmem + db * a.NB + c16 * 16 + lane_addr, xr + c16 * 16);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&dempty[db]));
+        // in increasing r, so that each read column Rtp + r > r is still unwritten
+#pragma unroll
+        for (int r = 0; r < 64; ++r) {
+          float x = 0.f;
+          if (r < a.Rt) {
+            x = xr[r];
+#pragma unroll
+            for (int h = 16; h <= 64; h += 16)
+              if (a.Rtp == h) x += xr[h + r];
+          }
+          xr[r] = x;
+        }
+        // B operand of the second product: row j, hi part in box 0, lo part in box 1
+        if (!mbar_wait(smem_u32(xempty), (tl & 1) ^ 1, status)) { ok = false; break; }
+        {
+          unsigned char* rowh = x_base + rl * 128;
+          const int ph = rl & 7;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float x0 = xr[8 * c + 2 * e], x1 = xr[8 * c + 2 * e + 1];
+              const float h0 = __bfloat162float(__float2bfloat16_rn(x0));
+              const float h1 = __bfloat162float(__float2bfloat16_rn(x1));
+              wh[e] = pack_bf16x2(h0, h1);
+              wl[e] = pack_bf16x2(x0 - h0, x1 - h1);
+            }
+            *reinterpret_cast<uint4*>(rowh + ((c ^ ph) << 4)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            *reinterpret_cast<uint4*>(rowh + 16 * KB + ((c ^ ph) << 4)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(xfull));
+        if (jt == a.JT - 1) {
+          fin = true;
+          fin_p = p;
+          fin_u = ui;
+        }
+      }
+    }
+    if (ok && fin && !finalise(fin_p, fin_u)) ok = false;
+  }
+  double mine = (double)nrm - (double)nrm_c;
+  mine = warp_sum(mine);
+  if (lane == 0) nred[warp] = mine;
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += nred[w];
+    a.nrm_part[blockIdx.x] = s;
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// U_{N-1} as the A operand rows of the second product: row j holds the
+// nearest BF16 of U[j, s] at column s and the remainder at column 64 + s
+__global__ void build_v_bf16(const double* __restrict__ U, int J, int Rt, __nv_bfloat16* __restrict__ out) {
+  const int64_t total = (int64_t)J * 128;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / 128;
+    const int c = (int)(e % 128);
+    const int s = c & 63;
+    float v = 0.f;
+    if (s < Rt) {
+      const double x = U[j * Rt + s];
+      const float hi = __bfloat162float(__float2bfloat16_rn((float)x));
+      v = (c < 64) ? hi : (float)(x - (double)hi);
+    }
+    out[e] = __float2bfloat16_rn(v);
+  }
+}
+
 // U_N^T as BF16 rows (channel-major, columns = L padded to ldu): rows [0, Rtp)
 // hold the nearest BF16 of U; with hilo, rows [Rtp, 2 Rtp) hold the remainder
 __global__ void build_u_bf16(const double* __restrict__ U, int L, int Rt, int Rtp, int hilo, int ldu,
@@ -318,9 +689,110 @@ int launch_core(tdk_ctx* ctx, const CUtensorMap& tmY, const CUtensorMap& tmU, co
 
 }  // namespace
 
+// BF16 data, N >= 3: the fused first two contractions, then the rest of the
+// chain from X_2 on CUDA cores
+static int core_tc_fused(tdk_ctx* ctx, const Geom& g, const void* Y, const double* const U[], void* Gv,
+                         double* normY2) {
+  const int N = g.N;
+  FuArgs a{};
+  a.L = (int)g.L;
+  a.KC = (a.L + 63) / 64;
+  a.Rt = g.Rt[N - 1];
+  a.Rtp = (a.Rt + 15) / 16 * 16;
+  a.NB = 2 * a.Rtp;  // U_N split hi + lo
+  a.J = (int)g.I[N - 2];
+  a.JT = (a.J + 127) / 128;
+  int64_t P = 1;
+  for (int k = 0; k < N - 2; ++k) P *= g.I[k];
+  if (P > (int64_t)0x7fffffff) return TDK_ENOTSUP;
+  a.P = (int)P;
+  a.Rt2 = g.Rt[N - 2];
+  a.status = ctx->d_status;
+  const size_t smem = fused_smem_bytes(a.NB);
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
+  const int grid = (int)std::min<int64_t>(P, ctx->num_sms);
+  const int ldu = (a.L + 7) / 8 * 8;
+  int64_t tmpsz = 1;
+  {
+    int64_t Bd = (int64_t)a.Rt * a.Rt2;
+    for (int m = N - 3; m >= 1; --m) {
+      int64_t A = 1;
+      for (int k = 0; k < m; ++k) A *= g.I[k];
+      tmpsz = std::max<int64_t>(tmpsz, A * g.Rt[m] * Bd);
+      Bd *= g.Rt[m];
+    }
+  }
+  Planner pl;
+  pl.take<__nv_bfloat16>((size_t)a.NB * ldu);
+  pl.take<__nv_bfloat16>((size_t)a.J * 128);
+  for (int n = 0; n < N; ++n) pl.take<float>((size_t)g.I[n] * g.Rt[n]);
+  pl.take<float>((size_t)P * a.Rt2 * a.Rt);
+  pl.take<float>((size_t)tmpsz);
+  pl.take<float>((size_t)tmpsz);
+  pl.take<double>((size_t)grid);
+  const int64_t pcap = chain_split_cap(g);
+  pl.take<float>((size_t)pcap);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  __nv_bfloat16* ub = cv.take<__nv_bfloat16>((size_t)a.NB * ldu);
+  build_u_bf16<<<128, 256, 0, ctx->stream>>>(U[N - 1], a.L, a.Rt, a.Rtp, 1, ldu, ub);
+  TDK_LAUNCH_CHECK(ctx);
+  __nv_bfloat16* vb = cv.take<__nv_bfloat16>((size_t)a.J * 128);
+  build_v_bf16<<<128, 256, 0, ctx->stream>>>(U[N - 2], a.J, a.Rt2, vb);
+  TDK_LAUNCH_CHECK(ctx);
+  float* Ut[TDK_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    Ut[n] = cv.take<float>((size_t)g.I[n] * g.Rt[n]);
+    if (n < N - 2) {
+      cvt_u<<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
+      TDK_LAUNCH_CHECK(ctx);
+    }
+  }
+  a.X2 = cv.take<float>((size_t)P * a.Rt2 * a.Rt);
+  float* tmp0 = cv.take<float>((size_t)tmpsz);
+  float* tmp1 = cv.take<float>((size_t)tmpsz);
+  a.nrm_part = cv.take<double>((size_t)grid);
+  float* spl = cv.take<float>((size_t)pcap);
+
+  CUtensorMap tmY, tmU, tmV;
+  {
+    uint64_t dims[3] = {(uint64_t)a.L, (uint64_t)a.J, (uint64_t)P};
+    uint64_t str[2] = {(uint64_t)a.L * 2, (uint64_t)a.L * 2 * (uint64_t)a.J};
+    uint32_t box[3] = {64u, 128u, 1u};
+    rc = encode_tmap(&tmY, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims, str, box, true);
+    if (rc) return rc;
+    uint64_t ud[3] = {(uint64_t)a.L, (uint64_t)a.NB, 1};
+    uint64_t us[2] = {(uint64_t)ldu * 2, (uint64_t)ldu * 2 * a.NB};
+    uint32_t ubx[3] = {64u, (uint32_t)a.NB, 1u};
+    rc = encode_tmap(&tmU, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ub, ud, us, ubx, true);
+    if (rc) return rc;
+    uint64_t vd[3] = {128, (uint64_t)a.J, 1};
+    uint64_t vs[2] = {256, 256 * (uint64_t)a.J};
+    uint32_t vbx[3] = {64u, 128u, 1u};
+    rc = encode_tmap(&tmV, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, vb, vd, vs, vbx, true);
+    if (rc) return rc;
+  }
+  {
+    TDK_CUDA_TRY(cudaFuncSetAttribute(tc_core_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(ctx, 1);
+    tc_core_fused_kernel<<<grid, FU_THREADS, smem, ctx->stream>>>(tmY, tmU, tmV, a);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  if (normY2) {
+    sum_doubles<<<1, 256, 0, ctx->stream>>>(a.nrm_part, grid, normY2);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  return core_chain_from<float>(ctx, g, a.X2, N - 3, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1, spl, pcap);
+}
+
 int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* Gv,
             double* normY2) {
   if (!tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
+  if (dtype == TDK_BF16 && g.N >= 3) {
+    const int rc = core_tc_fused(ctx, g, Y, U, Gv, normY2);
+    if (rc != TDK_ENOTSUP) return rc;
+  }
   const bool f32 = dtype == TDK_F32;
   constexpr int MT_BF16 = 2, MT_F32 = 1;
   const int MT = f32 ? MT_F32 : MT_BF16;
@@ -360,6 +832,8 @@ int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double*
   pl.take<float>((size_t)tmpsz);
   pl.take<float>((size_t)tmpsz);
   pl.take<double>((size_t)grid);
+  const int64_t pcap = chain_split_cap(g);
+  pl.take<float>((size_t)pcap);
   int rc = ws_reserve(ctx, pl.off);
   if (rc) return rc;
   Carver cv(ctx->ws);
@@ -376,6 +850,7 @@ int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double*
   float* tmp0 = cv.take<float>((size_t)tmpsz);
   float* tmp1 = cv.take<float>((size_t)tmpsz);
   a.nrm_part = cv.take<double>((size_t)grid);
+  float* spl = cv.take<float>((size_t)pcap);
 
   CUtensorMap tmY, tmU;
   {
@@ -398,7 +873,7 @@ int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double*
     sum_doubles<<<1, 256, 0, ctx->stream>>>(a.nrm_part, grid, normY2);
     TDK_LAUNCH_CHECK(ctx);
   }
-  return core_chain_rest<float>(ctx, g, a.X, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1);
+  return core_chain_rest<float>(ctx, g, a.X, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1, spl, pcap);
 }
 
 }  // namespace tdk

@@ -16,7 +16,7 @@
 // row mode) accumulates per TMEM lane across p; modes < N-1 are constant over
 // the tile and need a 128-lane reduction.  Each work unit (j-tile, column
 // range, p-range) writes its own partial block (the blockwise sums of Eq. 21);
-// a fixed-order FP64 reduction produces Z.
+// a fixed-order compensated FP32 reduction produces Z.
 //
 // CORE (Alg. 2, the first "Y <- Y x_n U^T", contiguous mode): X_1 = Y_(rows) U_N
 // with U split hi+lo into one B operand [U_hi | U_lo]; ||Y||^2 on the side.
@@ -618,7 +618,8 @@ __global__ void __launch_bounds__(320, 1)
   }
 }
 
-// fixed-order FP64 reduction of the unit partials into Z (packed by zoff)
+// fixed-order reduction of the unit partials into Z (packed by zoff): a
+// compensated (Kahan) FP32 sum, since FP64 arithmetic would bound this pass
 struct RedArgs {
   SkArgs s;
   int64_t zoff[TDK_MAX_MODES + 1];
@@ -635,14 +636,20 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
     const int Rn = a.Rt[n];
     const int64_t i = (e - ra.zoff[n]) / Rn;
     const int r = (int)((e - ra.zoff[n]) % Rn);
-    double s = 0.0;
+    float s = 0.f, cmp = 0.f;  // compensated FP32 sum of FP32 partials, fixed order
+    auto add = [&](float v) {
+      const float y = v - cmp;
+      const float t = s + y;
+      cmp = (t - s) - y;
+      s = t;
+    };
     if (n == nl) {
       const int kr = (int)(i / a.KRW);
       const int64_t kl = i - (int64_t)kr * a.KRW;
       for (int jt = 0; jt < a.JT; ++jt)
         for (int pc = 0; pc < a.PC; ++pc) {
           const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
-          s += (double)a.part[u * a.ustride + a.poff_last + kl * Rn + r];
+          add(a.part[u * a.ustride + a.poff_last + kl * Rn + r]);
         }
     } else if (n == nj) {
       const int jt = (int)(i / 128);
@@ -650,7 +657,7 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
       for (int kr = 0; kr < a.KR; ++kr)
         for (int pc = 0; pc < a.PC; ++pc) {
           const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
-          s += (double)a.part[u * a.ustride + a.poff_j + jl * Rn + r];
+          add(a.part[u * a.ustride + a.poff_j + jl * Rn + r]);
         }
     } else {
       // every p with i_n(p) = i: enumerate the other outer indices
@@ -667,11 +674,11 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
         for (int jt = 0; jt < a.JT; ++jt)
           for (int kr = 0; kr < a.KR; ++kr) {
             const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
-            s += (double)a.part[u * a.ustride + a.poff_p[n] + pl * Rn + r];
+            add(a.part[u * a.ustride + a.poff_p[n] + pl * Rn + r]);
           }
       }
     }
-    Z[e] = s;
+    Z[e] = (double)s - (double)cmp;
   }
 }
 
@@ -680,7 +687,8 @@ __global__ void w_to_f32(const double* __restrict__ s, float* __restrict__ d, in
     d[e] = (float)s[e];
 }
 
-// WN^T block: rows = channels of modes < N-1 (each padded to 16), columns = L
+// WN^T block: rows = channels of modes < N-1 (each padded to 16; one block for
+// all of them when they share W_{N-1}), columns = L
 __global__ void build_wn(const double* const* __restrict__ Wl, SkArgs a, int ldw, __nv_bfloat16* __restrict__ out) {
   const int64_t total = (int64_t)a.N1 * ldw;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -724,10 +732,17 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   a.J = (int)g.I[nj];
   a.P = 1;
   for (int k = 0; k < nj; ++k) a.P *= g.I[k];
+  // G1 channels: one block per mode n < N-1 holding W_{N-1}^(n).  When every
+  // such mode passes the same matrix (a sketch family whose Khatri-Rao factors
+  // are shared between the modes, W_k^(n) = W_k), one block serves them all and
+  // the G1 contraction is done once for all of them.
+  bool shared = true;
+  for (int n = 1; n <= nj; ++n)
+    if (W[n * N + nl] != W[nl] || g.Rt[n] != g.Rt[0]) shared = false;
   int N1 = 0;
   for (int n = 0; n <= nj; ++n) {
-    a.off[n] = N1;
-    N1 += a.Rtp[n];
+    a.off[n] = shared ? 0 : N1;
+    if (!shared || n == 0) N1 += a.Rtp[n];
   }
   a.N1 = N1;
   if (N1 > 256) return TDK_ENOTSUP;
@@ -862,7 +877,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
       s *= g.I[k];
     }
   }
-  sketch_tc_reduce<<<256, 256, 0, ctx->stream>>>(ra, Zdst);
+  sketch_tc_reduce<<<(unsigned)std::min<int64_t>((g.zoff[N] + 255) / 256, 65535), 256, 0, ctx->stream>>>(ra, Zdst);
   TDK_LAUNCH_CHECK(ctx);
   if (want_prof) {
     unsigned long long hp[16];

@@ -115,6 +115,11 @@ struct Geom {
 };
 int make_geom(const tdk_tucker_desc* d, Geom* g);
 
+// elements of the buffer for the partial outputs of split contractions in
+// the core chain: eight copies of the largest contraction output that can
+// be split (the core itself bounds the last ones)
+inline int64_t chain_split_cap(const Geom& g) { return 8 * g.core_numel; }
+
 // ---- entry points of the translation units --------------------------------
 // sketch (SIMT): writes FP64 Z_n for all modes into Zdst (packed by zoff)
 int sketch_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],

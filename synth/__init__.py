@@ -32,6 +32,7 @@ TAG_SKETCH = 3
 TAG_INIT = 4
 TAG_TUCKER = 5
 TAG_MASK = 6
+TAG_SKETCH_SHARED = 8
 
 OMEGA_SEED_XOR = 0x9E3779B97F4A7C15
 
@@ -118,16 +119,29 @@ def tucker_dense(shape, ranks, seed: int) -> np.ndarray:
     return out
 
 
-def sketch_matrices(shape, Rt, seed: int):
+def sketch_matrices(shape, Rt, seed: int, shared: bool = False):
     """W[n][k] (k != n): I_k x Rt[n] i.i.d. N(0,1), rounded to BF16 values.
 
     Omega_n is the Khatri-Rao product of W[n][k] over k != n (never formed by
     the CUDA path).  W[n][n] is None.
+
+    shared=True draws one matrix W_k (I_k x max Rt) per mode and uses it for
+    every sketch: W[n][k] = W_k (its first Rt[n] columns where Rt[n] is
+    narrower).  Every Omega_n is still a Khatri-Rao product of independent
+    N(0,1) matrices, so each sketch has the distribution of the independent
+    family; only the sketches of different modes become dependent.  Entries
+    of equal width are the same array object (`device_sketch` uploads such an
+    object once).
     """
     N = len(shape)
     if np.isscalar(Rt):
         Rt = [int(Rt)] * N
     base = int(seed) ^ OMEGA_SEED_XOR
+    if shared:
+        wmax = max(int(r) for r in Rt)
+        Wk = [round_bf16(rng(base, TAG_SKETCH_SHARED, k).standard_normal((shape[k], wmax))) for k in range(N)]
+        return [[None if k == n else (Wk[k] if int(Rt[n]) == wmax else np.ascontiguousarray(Wk[k][:, :Rt[n]]))
+                 for k in range(N)] for n in range(N)]
     W = []
     for n in range(N):
         row = []
@@ -138,6 +152,26 @@ def sketch_matrices(shape, Rt, seed: int):
                 row.append(round_bf16(rng(base, TAG_SKETCH, n, k).standard_normal((shape[k], Rt[n]))))
         W.append(row)
     return W
+
+
+def device_sketch(W, device):
+    """W[n][k] as torch tensors on `device`; an array object that occurs more
+    than once (a shared family) becomes one tensor."""
+    import torch
+
+    seen = {}
+    out = []
+    for row in W:
+        r = []
+        for x in row:
+            if x is None:
+                r.append(None)
+                continue
+            if id(x) not in seen:
+                seen[id(x)] = torch.as_tensor(x, device=device)
+            r.append(seen[id(x)])
+        out.append(r)
+    return out
 
 
 def init_factors(dims, R: int, seed: int, dist: str = "normal"):

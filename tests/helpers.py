@@ -23,9 +23,9 @@ def dev_tensor(Y: np.ndarray, dtype: str, device="cuda"):
 
 
 def dev_W(W, device="cuda"):
-    import torch
-
-    return [[None if w is None else torch.as_tensor(w, dtype=torch.float64, device=device) for w in row] for row in W]
+    """Device copies of the sketch matrices; an array shared between modes
+    (synth.sketch_matrices(shared=True)) stays one tensor."""
+    return synth.device_sketch(W, device)
 
 
 def host(t) -> np.ndarray:
@@ -48,10 +48,11 @@ def recon_err(normY2: float, G: np.ndarray) -> float:
     return float(np.sqrt(max(0.0, normY2 - float(np.sum(np.asarray(G, dtype=np.float64) ** 2))) / normY2))
 
 
-def small_problem(shape, ranks, p, seed, dtype="f32", snr=20.0, R_cp=None, dist="normal", clip0=False):
+def small_problem(shape, ranks, p, seed, dtype="f32", snr=20.0, R_cp=None, dist="normal", clip0=False,
+                  shared=False):
     R_cp = R_cp or min(ranks)
     A = synth.cp_factors(shape, R_cp, seed, dist)
     Y = synth.add_noise(synth.cp_dense(A), snr, seed, clip0)
     Y = synth.to_storage(Y, dtype)
-    W = synth.sketch_matrices(shape, [r + p for r in ranks], seed)
+    W = synth.sketch_matrices(shape, [r + p for r in ranks], seed, shared=shared)
     return Y, W, A

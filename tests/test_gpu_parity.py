@@ -117,9 +117,28 @@ def test_core_wide_ranks_matches_oracle(tdk, ctx, prec, dtype):
         G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), [dev_tensor(u, "f64") for u in U], ranks, p, prec)
         assert ctx.sync_status() == 0
         bnd = core_abs_bound(Y, U)
-        tol = 1e-12 if dtype == "f64" else 2e-5 + (2.0 ** -16 if prec == "tc" else 0.0)
+        tol = 1e-12 if dtype == "f64" else 2e-5 + (_tc_core_split(dtype) if prec == "tc" else 0.0)
         err = np.abs(host(G) - Gref)
         assert np.all(err <= tol * bnd), (shape, float((err / bnd).max()))
+
+
+@pytest.mark.parametrize("prec,dtype", [("simt", "f64"), ("simt", "f32"), ("tc", "f32")])
+@pytest.mark.parametrize("shape,ranks", [((600, 40, 64), (10, 12, 14)), ((300, 72, 64), (40, 36, 44)),
+                                         ((520, 9, 10, 16), (6, 5, 7, 8))])
+def test_core_split_contraction_matches_oracle(tdk, ctx, prec, dtype, shape, ranks):
+    # a first mode of several hundred: the last contraction of the chain (one
+    # output slab) is split over that mode and the partials summed in order
+    p = 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=31, dtype=dtype)
+    U = [np.linalg.qr(np.random.default_rng(32 + n).standard_normal((I, r + p)))[0]
+         for n, (I, r) in enumerate(zip(shape, ranks))]
+    Gref = oracle.tucker_core(Y, U)
+    G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), [dev_tensor(u, "f64") for u in U], ranks, p, prec)
+    assert ctx.sync_status() == 0
+    bnd = core_abs_bound(Y, U)
+    tol = 1e-12 if dtype == "f64" else 2e-5 + (_tc_core_split(dtype) if prec == "tc" else 0.0)
+    err = np.abs(host(G) - Gref)
+    assert np.all(err <= tol * bnd), (shape, float((err / bnd).max()))
 
 
 @pytest.fixture(params=["persistent", "multi"])
@@ -307,6 +326,40 @@ def test_tc_sketch_wide_ranks_matches_oracle(tdk, ctx, shape, ranks, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("shape,ranks", [((67, 45, 136), (5, 5, 5)), ((40, 130, 264), (20, 20, 20)),
+                                         ((48, 200, 256), (40, 40, 40)), ((6, 9, 140, 136), (4, 4, 4, 4)),
+                                         ((9, 11, 7, 16), (5, 5, 5, 5))])
+def test_tc_sketch_shared_family_matches_oracle(tdk, ctx, shape, ranks, dtype):
+    # W_k^(n) = W_k for every n: the kernel contracts the shared last-mode
+    # block once for all modes < N-1 (same pointer, same width); the result is
+    # the oracle's sketch of the same matrices, and the same as when the
+    # shared matrices are passed as separate copies (independent blocks)
+    p = 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=15, dtype=dtype, shared=True)
+    N = len(shape)
+    assert all(W[n][N - 1] is W[0][N - 1] for n in range(N - 1))
+    Yd = dev_tensor(Y, dtype)
+    Zo, _ = oracle.sketch(Y, W)
+    bnd = sketch_abs_bound(Y, W)
+    copies = [[None if w is None else w.copy() for w in row] for row in W]
+    for Win in (dev_W(W), dev_W(copies)):
+        U, Z = tdk.tucker_sketch(ctx, Yd, Win, ranks, p, "tc", want_Z=True)
+        assert ctx.sync_status() == 0
+        for n in range(N):
+            tol = _tc_tol(dtype, n == N - 1, ranks[-1] + p)
+            err = np.abs(host(Z[n]) - Zo[n])
+            assert np.all(err <= tol * bnd[n] + 1e-30), (n, float((err / bnd[n]).max()), tol)
+
+
+def _tc_core_split(dtype):
+    """Relative error bound of the hi + lo splits in the tensor-core core pass
+    (each split leaves a residual below 2^-17 of the value).  FP32 data: U_N
+    and Y split (2 x 2^-17).  BF16 data (Y exact): U_N, then in the fused
+    second contraction X_1 and U_{N-1} (3 x 2^-17)."""
+    return 2 * 2.0 ** -17 if dtype == "f32" else 3 * 2.0 ** -17
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
 @pytest.mark.parametrize("shape", TC_SHAPES)
 def test_tc_core_matches_oracle(tdk, ctx, shape, dtype):
     ranks = [min(5, s - 2) for s in shape]
@@ -317,11 +370,32 @@ def test_tc_core_matches_oracle(tdk, ctx, shape, dtype):
     G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, dtype), Ud, ranks, p, "tc")
     assert ctx.sync_status() == 0
     bnd = core_abs_bound(Y, ref["U"])
-    # U split hi + lo (residual < 2^-17); FP32 data split hi + lo as well
-    tol = 2e-5 + (2.0 ** -16 if dtype == "f32" else 2.0 ** -17)
+    tol = 2e-5 + _tc_core_split(dtype)
     err = np.abs(host(G) - ref["G"])
     assert np.all(err <= tol * bnd), float((err / bnd).max())
     assert math.isclose(float(nrm.item()), ref["normY2"], rel_tol=1e-6)
+
+
+@pytest.mark.parametrize("shape,ranks", [((320, 140, 72), (6, 7, 8)), ((160, 257, 384), (40, 38, 44)),
+                                         ((6, 40, 30, 136), (4, 5, 6, 7)), ((200, 128, 64), (3, 60, 60)),
+                                         ((600, 40, 64), (10, 12, 14)), ((300, 136, 64), (40, 40, 40))])
+def test_tc_core_fused_matches_oracle(tdk, ctx, shape, ranks):
+    # BF16 data: the fused first two contractions.  More work items (outer
+    # indices) than SMs, ragged and exact 128-row tiles of the second mode,
+    # fewer and more 64-column chunks than ring stages, sketch widths from 8
+    # to 62, and a 4-way case (outer index over two modes)
+    p = 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=29, dtype="bf16")
+    U = [np.linalg.qr(np.random.default_rng(30 + n).standard_normal((I, r + p)))[0]
+         for n, (I, r) in enumerate(zip(shape, ranks))]
+    Gref = oracle.tucker_core(Y, U)
+    G, nrm = tdk.tucker_core(ctx, dev_tensor(Y, "bf16"), [dev_tensor(u, "f64") for u in U], ranks, p, "tc")
+    assert ctx.sync_status() == 0
+    bnd = core_abs_bound(Y, U)
+    tol = 2e-5 + _tc_core_split("bf16")
+    err = np.abs(host(G) - Gref)
+    assert np.all(err <= tol * bnd), (shape, float((err / bnd).max()))
+    assert math.isclose(float(nrm.item()), float(np.sum(Y.astype(np.float64) ** 2)), rel_tol=1e-6)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])

@@ -134,11 +134,15 @@ def test_projection_pythagoras():
     assert math.isclose(lhs, rhs, rel_tol=1e-12)
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("shape,ranks,p", [((30, 25, 20), (3, 4, 5), 5), ((12, 11, 10, 9), (2, 3, 2, 3), 2)])
-def test_rand_tucker_exact_recovery(shape, ranks, p):
+def test_rand_tucker_exact_recovery(shape, ranks, p, shared):
+    # exact multilinear rank: range(Z_n) = range(Y_(n)) almost surely for
+    # either sketch family (each Omega_n is a Khatri-Rao product of
+    # independent Gaussians), so the Tucker model is recovered exactly
     Y = synth.tucker_dense(shape, ranks, 3)
     Rt = [r + p for r in ranks]
-    W = synth.sketch_matrices(shape, Rt, 5)
+    W = synth.sketch_matrices(shape, Rt, 5, shared=shared)
     out = oracle.rand_tucker(Y, W)
     for U in out["U"]:
         assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-13

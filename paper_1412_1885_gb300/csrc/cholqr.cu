@@ -69,21 +69,22 @@ __global__ void gram_reduce_kernel(QRArgs q, const double* __restrict__ gp, cons
 }
 
 // Cholesky of the Gram (upper R, Gram = R^T R) -> Rinv; one CTA per mode.
-// FP64 arithmetic is scarce on this GPU (about two FMAs per clock per SM), so
-// every FP64 value is computed by one thread only: each pivot's reciprocal
-// and breakdown test by the thread that finalises that pivot, each row
-// multiplier by lane 0 of the row's warp (then broadcast).
+// FP64 arithmetic is scarce on this GPU (about two FMAs per clock per SM) and
+// slow to return, so each step spreads its update over all threads (one
+// element each, no serial chains) and every FP64 value is computed once: the
+// pivot reciprocal and breakdown test by the thread that finalises the pivot,
+// the pivot row scaled once per step.
 __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* __restrict__ rinv,
                             int* __restrict__ fail) {
   const int n = blockIdx.x;
   const int Rt = q.Rt[n];
   __shared__ double A[TDK_MAX_RANK * TDK_MAX_RANK];
   __shared__ double Ri[TDK_MAX_RANK * TDK_MAX_RANK];
-  __shared__ double inv_d[TDK_MAX_RANK], dsq[TDK_MAX_RANK], idsq[TDK_MAX_RANK];
+  __shared__ double inv_d[TDK_MAX_RANK], srow[TDK_MAX_RANK], dsq[TDK_MAX_RANK], idsq[TDK_MAX_RANK];
   __shared__ double tiny_s;
   __shared__ int bad;
   if (fail[n]) return;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
   for (int e = tid; e < Rt * Rt; e += nth) A[e] = gram[(int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK + e];
   __syncthreads();
   if (tid == 0) {
@@ -93,26 +94,24 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* _
     bad = !(A[0] > tiny_s);
     inv_d[0] = 1.0 / A[0];
   }
-  // right-looking Cholesky on the upper triangle, A = R^T R, one barrier per
-  // pivot: the trailing update uses the unscaled pivot row times 1/d, and every
-  // row is scaled by 1/sqrt(d) once at the end (a row is not read again after
-  // its own step).  Warp y updates rows a = j+1+y (step blockDim.y), lanes the
-  // columns b >= a.
+  // right-looking Cholesky on the upper triangle, A = R^T R: step j scales the
+  // pivot row once (srow = A[j, :] / d_j) and updates the trailing triangle
+  // A[a, b] -= srow[a] A[j, b] (j < a <= b), one element per thread; rows are
+  // scaled by 1/sqrt(d) at the end (a row is not read again after its step)
   for (int j = 0; j < Rt; ++j) {
     __syncthreads();
     if (bad) break;
-    const double id = inv_d[j];
-    for (int a = j + 1 + (int)threadIdx.y; a < Rt; a += blockDim.y) {
-      double aja = 0.0;
-      if (threadIdx.x == 0) aja = A[j * Rt + a] * id;
-      aja = __shfl_sync(0xffffffffu, aja, 0);
-      for (int b = a + (int)threadIdx.x; b < Rt; b += blockDim.x) {
-        const double v = fma(-aja, A[j * Rt + b], A[a * Rt + b]);
-        A[a * Rt + b] = v;
-        if (b == a && a == j + 1) {  // the next pivot is final now
-          bad = !(v > tiny_s);
-          inv_d[a] = 1.0 / v;
-        }
+    const int m = Rt - j - 1;
+    for (int a = j + 1 + tid; a < Rt; a += nth) srow[a] = A[j * Rt + a] * inv_d[j];
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nth) {
+      const int a = j + 1 + e / m, b = j + 1 + e % m;
+      if (b < a) continue;
+      const double v = fma(-srow[a], A[j * Rt + b], A[a * Rt + b]);
+      A[a * Rt + b] = v;
+      if (b == a && a == j + 1) {  // the next pivot is final now
+        bad = !(v > tiny_s);
+        inv_d[a] = 1.0 / v;
       }
     }
   }
@@ -131,17 +130,19 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* _
     if (b > j) A[e] *= idsq[j];
     else if (b == j) A[e] = dsq[j];
   }
-  // Rinv = R^{-1} by Gauss-Jordan back substitution, all threads: X = I, then
-  // for k from the last row up: X[k, :] /= R_kk, X[i, :] -= R_ik X[k, :] (i < k).
-  // R is never updated (each step only clears column k of R).
+  // Rinv = R^{-1} by Gauss-Jordan back substitution: X = I, then for k from
+  // the last row up: X[k, :] /= R_kk, X[i, :] -= R_ik X[k, :] (i < k), over the
+  // k x (Rt - k) block of columns >= k (X is upper triangular), one element per
+  // thread.  R is never updated (each step only clears column k of R).
   for (int e = tid; e < Rt * Rt; e += nth) Ri[e] = (e / Rt == e % Rt) ? 1.0 : 0.0;
   __syncthreads();
   for (int k = Rt - 1; k >= 0; --k) {
+    const int w = Rt - k;
     for (int j = k + tid; j < Rt; j += nth) Ri[k * Rt + j] *= idsq[k];
     __syncthreads();
-    for (int i = threadIdx.y; i < k; i += blockDim.y) {
-      const double rik = A[i * Rt + k];
-      for (int j = k + (int)threadIdx.x; j < Rt; j += blockDim.x) Ri[i * Rt + j] = fma(-rik, Ri[k * Rt + j], Ri[i * Rt + j]);
+    for (int e = tid; e < k * w; e += nth) {
+      const int i = e / w, j = k + e % w;
+      Ri[i * Rt + j] = fma(-A[i * Rt + k], Ri[k * Rt + j], Ri[i * Rt + j]);
     }
     __syncthreads();
   }
@@ -295,7 +296,7 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   const dim3 agrid(64, g.N);
   // round 1: Z -> Q1
   const dim3 rgrid((TDK_MAX_RANK * TDK_MAX_RANK + 255) / 256, g.N);
-  const dim3 cblk(32, 8);
+  const int cblk = 256;
   gram_partial_kernel<<<ggrid, 256, 0, ctx->stream>>>(Z, q, gpart, fail);
   TDK_LAUNCH_CHECK(ctx);
   gram_reduce_kernel<<<rgrid, 256, 0, ctx->stream>>>(q, gpart, fail, gram);

@@ -284,18 +284,24 @@ static int split_count(tdk_ctx* ctx, int64_t ctas, int per_sm, int64_t Ic, int64
 }
 
 template <class T>
-void launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo,
-                    T* part, int64_t part_cap) {
+int launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo,
+                   T* part, int64_t part_cap) {
   const int64_t nb = (Bd + 63) / 64, out_n = A * Rt * Bd;
   const int ks = split_count(ctx, A * nb, 2, Ic, out_n, part_cap);
   const int64_t kch = (Ic + ks - 1) / ks;
   dim3 grid((unsigned)A, (unsigned)nb, (unsigned)ks);
   ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, ks > 1 ? part : Xo, kch);
-  if (ks > 1) sum_split_kernel<T><<<(unsigned)std::min<int64_t>((out_n + 255) / 256, 1024), 256, 0, ctx->stream>>>(part, ks, out_n, Xo);
+  TDK_LAUNCH_CHECK(ctx);
+  if (ks > 1) {
+    sum_split_kernel<T><<<(unsigned)std::min<int64_t>((out_n + 255) / 256, 1024), 256, 0, ctx->stream>>>(
+        part, ks, out_n, Xo);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  return TDK_OK;
 }
 template <>
-void launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, int64_t Bd, const float* U, int Rt,
-                           float* Xo, float* part, int64_t part_cap) {
+int launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, int64_t Bd, const float* U, int Rt,
+                          float* Xo, float* part, int64_t part_cap) {
   const int64_t nb = (Bd + 63) / 64, out_n = A * Rt * Bd;
   const bool wide = Rt > 32 && Bd > 32, narrow = Rt <= 32 && Bd <= 32;
   const int ks = wide ? split_count(ctx, A * nb, 6, Ic, out_n, part_cap)
@@ -309,9 +315,13 @@ void launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, 
   else
     ttm_mid_kernel<float><<<dim3((unsigned)A, (unsigned)nb, (unsigned)ks), NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt,
                                                                                                  dst, kch);
-  if (ks > 1)
+  TDK_LAUNCH_CHECK(ctx);
+  if (ks > 1) {
     sum_split_kernel<float><<<(unsigned)std::min<int64_t>((out_n + 255) / 256, 1024), 256, 0, ctx->stream>>>(
         part, ks, out_n, Xo);
+    TDK_LAUNCH_CHECK(ctx);
+  }
+  return TDK_OK;
 }
 
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
@@ -360,8 +370,8 @@ int core_chain_from(tdk_ctx* ctx, const Geom& g, const T* X, int m0, T* const Ut
     int64_t A = 1;
     for (int k = 0; k < m; ++k) A *= g.I[k];
     T* out = (m == 0) ? G : ((m % 2) ? tmp0 : tmp1);
-    launch_ttm_mid<T>(ctx, cur, A, g.I[m], Bd, Ut[m], g.Rt[m], out, part, part_cap);
-    TDK_LAUNCH_CHECK(ctx);
+    const int rc = launch_ttm_mid<T>(ctx, cur, A, g.I[m], Bd, Ut[m], g.Rt[m], out, part, part_cap);
+    if (rc) return rc;
     cur = out;
     Bd *= g.Rt[m];
   }

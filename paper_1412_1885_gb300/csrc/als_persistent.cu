@@ -104,14 +104,21 @@ __device__ bool grid_sync(unsigned* bar, unsigned* status) {
   return fail == 0;
 }
 
+// block-wide FP64 sum, the same value (same order) in every thread; the warp
+// partials are added by one thread (FP64 arithmetic is scarce on this GPU)
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    red[0] = s;
+  }
+  __syncthreads();
+  const double s = red[0];
   __syncthreads();
   return s;
 }
@@ -151,7 +158,7 @@ struct PLayout {
     o_red = take(sizeof(double) * 32);
     o_lf = take(sizeof(float) * R * R);
     o_tid = take(sizeof(double) * R * R);
-    o_gjs = take(sizeof(double) * 2 * RMAXP);
+    o_gjs = take(sizeof(double) * 4 * RMAXP);
     o_invf = take(sizeof(float) * RMAXP);
     o_yf = take(sizeof(float) * RMAXP);
     o_lamt = take(sizeof(T) * RMAXP);
@@ -164,25 +171,32 @@ struct PLayout {
 
 // In-place inverse of a symmetric positive definite R x R matrix (row-major)
 // by Gauss-Jordan elimination without pivoting, spread over a group of nt
-// threads (named barrier bar_id); a pivot is the Schur complement a Cholesky
+// threads (named barrier bar_id).  A pivot is the Schur complement a Cholesky
 // factorisation would meet, so the breakdown test (pivot not above
-// R * eps * max diag) is the same: per pivot, the pivot row and column are copied, then every
-// thread updates its share of the R x R entries.  rowk, colk: R entries each.
+// R * eps * max diag) is the same.  One barrier per pivot: the threads that
+// update row k+1 and column k+1 also copy them into the other half of `buf`
+// (4 R entries), from which pivot k+1 reads.  Returns the same value in
+// every thread of the group.
 template <class F>
-__device__ int group_gj_inverse(F* A, F* rowk, F* colk, int R, F eps, int t, int nt, int bar_id) {
+__device__ int group_gj_inverse(F* A, F* buf, int R, F eps, int t, int nt, int bar_id) {
+  tc::named_bar(bar_id, nt);  // `buf` may still be read by a previous call
   F mx = F(0);
   for (int j = 0; j < R; ++j) mx = A[j * R + j] > mx ? A[j * R + j] : mx;
   const F tiny = (F)R * eps * mx;
   const int RR = R * R;
   const float invR = 1.0f / (float)R;
+  if (t < R) {
+    buf[t] = A[t];
+    buf[R + t] = A[t * R];
+  }
+  tc::named_bar(bar_id, nt);
   for (int k = 0; k < R; ++k) {
-    if (t < R) {
-      rowk[t] = A[k * R + t];
-      colk[t] = A[t * R + k];
-    }
-    tc::named_bar(bar_id, nt);
+    const F* rowk = buf + (k & 1) * 2 * R;
+    const F* colk = rowk + R;
+    F* rown = buf + ((k + 1) & 1) * 2 * R;
+    F* coln = rown + R;
     const F p = rowk[k];
-    if (!(p > tiny)) return 0;  // same value in every thread of the group
+    if (!(p > tiny)) return 0;
     const F ip = F(1) / p;
     for (int e = t; e < RR; e += nt) {
       const int i = __float2int_rz(((float)e + 0.5f) * invR);  // e / R (exact for e < 4096)
@@ -191,6 +205,8 @@ __device__ int group_gj_inverse(F* A, F* rowk, F* colk, int R, F eps, int t, int
       if (i == k) v = (j == k) ? ip : rowk[j] * ip;
       else v = (j == k) ? -colk[i] * ip : fma(-colk[i], rowk[j] * ip, A[e]);
       A[e] = v;
+      if (i == k + 1) rown[j] = v;
+      if (j == k + 1) coln[i] = v;
     }
     tc::named_bar(bar_id, nt);
   }
@@ -201,6 +217,7 @@ template <class T>
 __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   unsigned long long prof_t = clock64();
   extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ double s_irows[TDK_MAX_MODES];  // 1 / sqrt(rows of the updated factor of mode n)
   const int N = a.N, R = a.R;
   int boff[TDK_MAX_MODES];
   int btot = 0;
@@ -221,7 +238,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   double* red = reinterpret_cast<double*>(sm + L.o_red);    // [32]
   float* Lf = reinterpret_cast<float*>(sm + L.o_lf);        // [R*R] FP32 inverse of T_n
   double* Tid = reinterpret_cast<double*>(sm + L.o_tid);   // [R*R] FP64 inverse (fallback)
-  double* gjs = reinterpret_cast<double*>(sm + L.o_gjs);   // Gauss-Jordan pivot row / column
+  double* gjs = reinterpret_cast<double*>(sm + L.o_gjs);   // Gauss-Jordan pivot rows / columns (two pairs)
   float* invf = reinterpret_cast<float*>(sm + L.o_invf);
   float* yf = reinterpret_cast<float*>(sm + L.o_yf);
   T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
@@ -232,6 +249,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   const int tid = threadIdx.x;
   const int G = gridDim.x, c = blockIdx.x;
   bool ok = true;
+  if (tid < N) s_irows[tid] = 1.0 / sqrt((double)(a.nonneg ? a.I[tid] : a.Rt[tid]));
 
   // ---- initial factors (raw) and their Grams
   for (int n = 0; n < N; ++n) {
@@ -272,7 +290,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   const double nG2 = *a.nG2;
   const double nY2 = a.nY2 ? *a.nY2 : 0.0;
 
-  double fit_old = 0.0, fit = 0.0, fitY = nan("");
+  double fit = 0.0, fitY = nan("");
   int sweep = 0, converged = 0, needpinv = 0;
   for (sweep = 1; sweep <= a.max_sweeps && ok; ++sweep) {
     double inner = 0.0;
@@ -295,9 +313,8 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       __syncthreads();
       // ---- 1b. inverse of T_n: FP32 by default (the solves are refined against
       //          T_n in FP64), FP64 if an FP32 pivot breaks down
-      bool use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), reinterpret_cast<float*>(gjs) + RMAXP,
-                                           R, 1.1920929e-7f, tid, NTP, 1) != 0;
-      if (!use32 && !group_gj_inverse<double>(Tid, gjs, gjs + RMAXP, R, 2.220446049250313e-16, tid, NTP, 1)) {
+      const bool use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
+      if (!use32 && !group_gj_inverse<double>(Tid, gjs, R, 2.220446049250313e-16, tid, NTP, 1)) {
         needpinv = 1;
         ok = false;  // identical in every CTA: all leave here
         break;
@@ -512,7 +529,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         }
       }
       __syncthreads();
-      const T inv_rows = (T)(1.0 / sqrt((double)rows));
+      const T inv_rows = (T)s_irows[n];
       for (int64_t e = tid; e < rows * R; e += NTP) {
         const int r = (int)(e % R);
         nb[e] = lamT[r] > T(0) ? nb[e] * ilamT[r] : inv_rows;
@@ -650,25 +667,32 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       mb2 += vb;
     }
     const double model2 = block_sum_d((double)m2, red);
-    double res2;
-    if (sizeof(T) == 8) {
-      res2 = fmax(0.0, nG2 - 2.0 * inner + model2);
-    } else {
-      res2 = 0.0;
-      for (int q = 0; q < G; ++q) res2 += __ldcg(a.rpart + q);
-      if (a.nonneg) {
-        // [[A]] leaves the Tucker subspace: add ||[[A]]||^2 - ||P [[A]]||^2,
-        // P [[A]] = [[U B]] with B_p = U_p^T A_p
-        const double mb = block_sum_d((double)mb2, red);
-        res2 += fmax(0.0, model2 - mb);
-      }
-    }
+    // [[A]] leaves the Tucker subspace (nonneg): add ||[[A]]||^2 - ||P [[A]]||^2,
+    // P [[A]] = [[U B]] with B_p = U_p^T A_p
+    const double mb = (sizeof(T) != 8 && a.nonneg) ? block_sum_d((double)mb2, red) : 0.0;
     PROF_MARK(6);
-    fit_old = fit;
-    fit = 1.0 - sqrt(res2) / sqrt(nG2);
-    if (a.nY2) fitY = 1.0 - sqrt(fmax(0.0, nY2 - nG2 + res2)) / sqrt(nY2);
-    if (c == 0 && tid == 0 && sweep - 1 < a.hist_cap) a.hist[sweep - 1] = fit;
-    if (sweep > 1 && fabs(fit - fit_old) < a.tol * fabs(fit_old)) {
+    // the scalar tail by one thread, shared through `red` (same value in every CTA)
+    if (tid == 0) {
+      double res2;
+      if (sizeof(T) == 8) {
+        res2 = fmax(0.0, nG2 - 2.0 * inner + model2);
+      } else {
+        res2 = 0.0;
+        for (int q = 0; q < G; ++q) res2 += __ldcg(a.rpart + q);
+        if (a.nonneg) res2 += fmax(0.0, model2 - mb);
+      }
+      const double f = 1.0 - sqrt(res2) / sqrt(nG2);
+      red[0] = f;
+      red[1] = a.nY2 ? 1.0 - sqrt(fmax(0.0, nY2 - nG2 + res2)) / sqrt(nY2) : fitY;
+      red[2] = (sweep > 1 && fabs(f - fit) < a.tol * fabs(fit)) ? 1.0 : 0.0;
+      if (c == 0 && sweep - 1 < a.hist_cap) a.hist[sweep - 1] = f;
+    }
+    __syncthreads();
+    fit = red[0];
+    fitY = red[1];
+    const bool conv = red[2] != 0.0;
+    __syncthreads();
+    if (conv) {
       converged = 1;
       break;
     }
@@ -758,6 +782,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
   double* red = reinterpret_cast<double*>(sm + L.o_red);
   __shared__ int s_mode;  // 1: FP32 factor, 2: FP64 factor, 0: singular
+  __shared__ T s_irows[3];  // 1 / sqrt(Rt_n): the column a zero column is replaced by
   __shared__ unsigned long long s_prof[10];
   const int tid = threadIdx.x, warp = tid >> 5;
   constexpr bool F64 = sizeof(T) == 8;
@@ -776,6 +801,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
     }
   };
 
+  if (tid < 3) s_irows[tid] = (T)(1.0 / sqrt((double)Rt[tid]));
   for (int e = tid; e < nel; e += NTS) Gc[e] = a.G[e];
   for (int n = 0; n < 3; ++n)
     for (int e = tid; e < Rt[n] * R; e += NTS) B[n][e] = (T)a.init[n][e];
@@ -794,7 +820,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   __syncthreads();
   const double nG2 = *a.nG2;
   const double nY2 = a.nY2 ? *a.nY2 : 0.0;
-  double fit_old = 0.0, fit = 0.0, fitY = nan("");
+  double fit = 0.0, fitY = nan("");
   int sweep = 0, converged = 0, singular = 0;
   for (sweep = 1; sweep <= a.max_sweeps; ++sweep) {
     for (int n = 0; n < 3; ++n) {
@@ -815,9 +841,9 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
         // ---- invert T_n (FP32 for FP32 cores, FP64 otherwise / as fallback), warps 0-7
         const unsigned long long pt0 = clock64();
         int mode = 0;
-        if (!F64 && group_gj_inverse<float>(Lf, Lif, Lif + 64, R, 1.1920929e-7f, tid, 256, 2)) {
+        if (!F64 && group_gj_inverse<float>(Lf, Lif, R, 1.1920929e-7f, tid, 256, 2)) {
           mode = 1;
-        } else if (group_gj_inverse<double>(Ld, Lid, Lid + 64, R, 2.220446049250313e-16, tid, 256, 2)) {
+        } else if (group_gj_inverse<double>(Ld, Lid, R, 2.220446049250313e-16, tid, 256, 2)) {
           mode = 2;
         }
         if (tid == 0) {
@@ -966,7 +992,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
         }
       }
       __syncthreads();
-      const T inv_rows = (T)(1.0 / sqrt((double)Rn));
+      const T inv_rows = s_irows[n];
       for (int e = tid; e < Rn * R; e += NTS) {
         const int r = e % R;
         B[n][e] = lam[r] > 0.0 ? (T)(X[e] * Res[r]) : inv_rows;
@@ -1041,11 +1067,20 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       res2 = block_sum_d((double)sacc - (double)scmp, red);
     }
     pms(5);
-    fit_old = fit;
-    fit = 1.0 - sqrt(res2) / sqrt(nG2);
-    if (a.nY2) fitY = 1.0 - sqrt(fmax(0.0, nY2 - nG2 + res2)) / sqrt(nY2);
-    if (tid == 0 && sweep - 1 < a.hist_cap) a.hist[sweep - 1] = fit;
-    if (sweep > 1 && fabs(fit - fit_old) < a.tol * fabs(fit_old)) {
+    // the scalar tail by one thread, shared through `red`
+    if (tid == 0) {
+      const double f = 1.0 - sqrt(res2) / sqrt(nG2);
+      red[0] = f;
+      red[1] = a.nY2 ? 1.0 - sqrt(fmax(0.0, nY2 - nG2 + res2)) / sqrt(nY2) : fitY;
+      red[2] = (sweep > 1 && fabs(f - fit) < a.tol * fabs(fit)) ? 1.0 : 0.0;
+      if (sweep - 1 < a.hist_cap) a.hist[sweep - 1] = f;
+    }
+    __syncthreads();
+    fit = red[0];
+    fitY = red[1];
+    const bool conv = red[2] != 0.0;
+    __syncthreads();
+    if (conv) {
       converged = 1;
       break;
     }

@@ -11,6 +11,8 @@
 // Gram-Schmidt, and a column whose projected norm falls below 1e-12 of its
 // original norm is replaced by a fixed pseudo-random vector, itself
 // orthogonalised twice.  The status bit TDK_STATUS_RANKDEF is raised.
+#include <algorithm>
+
 #include "tdk_internal.cuh"
 
 namespace tdk {
@@ -166,10 +168,20 @@ __global__ void apply_rinv_kernel(const double* __restrict__ Z, QRArgs q, const 
   __syncthreads();
   const double* Zn = Z + q.zoff[n];
   double* Qn = dst.p[n];
+  // (row, column) by 32-bit division where the mode fits (64-bit division is
+  // a long instruction sequence next to the dot product)
+  const bool small = I * Rt < 0x7fffffffLL;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * Rt;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / Rt;
-    int b = (int)(e % Rt);
+    int64_t i;
+    int b;
+    if (small) {
+      i = (int)e / Rt;
+      b = (int)e - (int)i * Rt;
+    } else {
+      i = e / Rt;
+      b = (int)(e % Rt);
+    }
     double s = 0.0;
     for (int a = 0; a <= b; ++a) s = fma(Zn[i * Rt + a], Ri[a * Rt + b], s);
     Qn[e] = s;
@@ -293,7 +305,9 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
     d2.p[n] = U_out[n];
   }
   const dim3 ggrid(maxchunk, g.N);
-  const dim3 agrid(64, g.N);
+  // the products are FP64-bound (about one FP64 FMA per clock per SM): the
+  // same number of CTAs per mode, a multiple of the SM count in all
+  const dim3 agrid((unsigned)std::max(1, 2 * ctx->num_sms), g.N);
   // round 1: Z -> Q1
   const dim3 rgrid((TDK_MAX_RANK * TDK_MAX_RANK + 255) / 256, g.N);
   const int cblk = 256;

@@ -414,3 +414,42 @@ def test_tc_end_to_end_scaled(tdk, ctx, dtype):
     e_gpu = recon_err(float(nrm.item()), host(G))
     e_or = recon_err(ref["normY2"], ref["G"])
     assert abs(e_gpu - e_or) <= (1e-5 if dtype == "f32" else 1e-3), (e_gpu, e_or)
+
+
+@pytest.mark.parametrize("cfg", ["c4", "c2"])
+def test_full_size_sketch_rows_match_oracle(tdk, ctx, cfg):
+    """The bench workloads at full size (3000^3 BF16, 1000^3 FP32) through
+    the bench's tensor-core path: sampled rows Z_n[i, :] against the oracle's
+    row-by-row sketch of the same slab, with the tolerance of the small-size
+    tests; U_n orthonormal; ||G|| <= ||Y|| (orthogonal projection)."""
+    import torch
+
+    w = synth.WORKLOADS[cfg]
+    N = len(w.shape)
+    Y, _ = synth.device_tensor(w, device="cuda")
+    W = synth.sketch_matrices(w.shape, w.Rt, w.seed)
+    Wabs = [[None if x is None else np.abs(x) for x in row] for row in W]
+    try:
+        U, Z = tdk.tucker_sketch(ctx, Y, dev_W(W), w.ranks, w.p, "tc", want_Z=True)
+        G, nrm = tdk.tucker_core(ctx, Y, U, w.ranks, w.p, "tc")
+        assert ctx.sync_status() == 0
+        rng = np.random.default_rng(7)
+        for n in range(N):
+            tol = _tc_tol(w.dtype, n == N - 1, w.Rt[-1])
+            rows = [0, w.shape[n] - 1] + [int(i) for i in rng.choice(w.shape[n], 2, replace=False)]
+            Zn = host(Z[n])
+            for i in rows:
+                idx = [slice(None)] * N
+                idx[n] = i
+                slab = Y[tuple(idx)].to(torch.float64).cpu().numpy()
+                ref = oracle.sketch_row(slab, n, W)
+                bnd = oracle.sketch_row(np.abs(slab), n, Wabs)
+                err = np.abs(Zn[i] - ref)
+                assert np.all(err <= tol * bnd + 1e-30), (cfg, n, i, float((err / bnd).max()), tol)
+            Un = host(U[n])
+            assert np.abs(Un.T @ Un - np.eye(Un.shape[1])).max() < 1e-12
+        g2 = float(np.sum(host(G) ** 2))
+        assert 0.0 < g2 <= float(nrm.item()) * (1.0 + 1e-5)
+    finally:
+        del Y
+        torch.cuda.empty_cache()

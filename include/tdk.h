@@ -118,6 +118,15 @@ typedef struct {
                                TDK_MAX_RANK)                                */
 } tdk_tucker_desc;
 
+/* Host-only check of a descriptor, the one every entry point applies before
+   any CUDA call: 2 <= N <= TDK_MAX_MODES, a known dtype and prec, p >= 0,
+   every I_n >= 1 and R_n >= 1, R_n + p <= min(I_n, TDK_MAX_RANK), and the
+   element count below 2^62.  Returns TDK_OK or TDK_EINVAL.  Forms that do
+   not cover a valid problem return TDK_ENOTSUP at the entry point: the
+   tensor-core sketch wants 3 <= N <= 4, no tensor-core form takes FP64 data,
+   and both want the contiguous mode's row pitch a multiple of 16 bytes. */
+int tdk_tucker_check(const tdk_tucker_desc* desc);
+
 /*
  * tucker_sketch -- all-mode randomized range finder (Sec. IV-A; Alg. 2 lines
  * "Z = Y_(n) Omega" and "U = orth(Z)"; Eq. 21 for the blockwise sums).

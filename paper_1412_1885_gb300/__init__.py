@@ -29,7 +29,7 @@ EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_s
            "tdk_ctx_launch_count", "tdk_strerror", "tdk_ctx_profile", "tdk_ctx_profile_read", "tucker_sketch",
            "tucker_core", "ffcp_als", "tucker_sketch_static", "tdk_mlp_create", "tdk_mlp_destroy",
            "tdk_mlp_param_count", "tdk_mlp_set_params", "tdk_mlp_get", "tdk_mlp_colsums", "tdk_mlp_train_step",
-           "ffcp_predict_init"]
+           "ffcp_predict_init", "tdk_tucker_check"]
 MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
 
 
@@ -85,6 +85,7 @@ def lib():
         L.tdk_ctx_launch_count.restype = i64
         L.tdk_strerror.argtypes = [ctypes.c_int]
         L.tdk_strerror.restype = ctypes.c_char_p
+        L.tdk_tucker_check.argtypes = [ctypes.POINTER(TuckerDesc)]
         L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp]
         L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
         L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
@@ -155,6 +156,12 @@ def make_desc(shape, dtype_code, ranks, p, prec="simt") -> TuckerDesc:
         d.I[n] = int(I)
         d.R[n] = int(R)
     return d
+
+
+def tucker_check(shape, dtype_code, ranks, p, prec="simt") -> int:
+    """The library's own descriptor check (host only, no CUDA call): TDK_OK or
+    TDK_EINVAL."""
+    return int(lib().tdk_tucker_check(ctypes.byref(make_desc(shape, dtype_code, ranks, p, prec))))
 
 
 class Context:
@@ -423,5 +430,5 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
     return out
 
 
-__all__ = ["Context", "Mlp", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
+__all__ = ["Context", "Mlp", "tucker_check", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
            "make_desc", "TdkError", "EXPORTS", "strerror"]

@@ -1151,6 +1151,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   auto t0 = std::chrono::steady_clock::now();
   const int N = g.N, R = o->R;
   if (o->init != TDK_INIT_GIVEN || o->timeout_s > 0) return TDK_ENOTSUP;
+  // the row slices of H_n are indexed by the other modes but the last one:
+  // with two modes there are none, and the multi-kernel form takes over
+  if (N < 3) return TDK_ENOTSUP;
   PArgs<T> a{};
   a.N = N;
   a.R = R;

@@ -58,6 +58,11 @@ using namespace tdk;
 
 extern "C" {
 
+int tdk_tucker_check(const tdk_tucker_desc* desc) {
+  Geom g;
+  return make_geom(desc, &g);
+}
+
 const char* tdk_strerror(int code) {
   switch (code) {
     case TDK_OK: return "ok";

@@ -78,3 +78,26 @@ def test_desc_validation_rules():
     assert d.N == 3 and d.I[2] == 14 and d.R[1] == 3
     with pytest.raises(ValueError):
         t.make_desc((10, 12), t.F32, (3, 3, 3), 2)
+
+
+def test_descriptor_edge_cases_without_gpu(L):
+    """The descriptor rules every entry point applies before any CUDA call:
+    empty modes, ranks beyond the mode or the sketch-width limit, negative
+    oversampling, unknown types, orders outside 2..8, element-count overflow."""
+    import paper_1412_1885_gb300 as t
+
+    ok, bad = t.TDK_OK, t.TDK_EINVAL
+    chk = t.tucker_check
+    assert chk((10, 12, 14), t.F32, (3, 3, 3), 2) == ok
+    assert chk((5, 7), t.F64, (2, 3), 1) == ok                       # matrices (N = 2)
+    assert chk((3,) * 8, t.F32, (1,) * 8, 2) == ok                    # 8 modes, Rt = I
+    assert chk((70, 64, 80), t.BF16, (60, 60, 60), 4) == ok           # Rt = 64, the limit
+    assert chk((70, 64, 80), t.BF16, (60, 61, 60), 4) == bad          # Rt = 65
+    assert chk((10, 0, 14), t.F32, (3, 3, 3), 2) == bad               # empty mode
+    assert chk((10, 12, 14), t.F32, (3, 0, 3), 2) == bad              # zero rank
+    assert chk((10, 12, 4), t.F32, (3, 3, 3), 2) == bad               # Rt > I
+    assert chk((10, 12, 14), t.F32, (3, 3, 3), -1) == bad             # p < 0
+    assert chk((10,), t.F32, (3,), 2) == bad                          # N = 1
+    assert chk((10, 12, 14), 7, (3, 3, 3), 2) == bad                  # dtype
+    assert chk((10, 12, 14), t.F32, (3, 3, 3), 2, prec=5) == bad      # form
+    assert chk((1 << 21,) * 3, t.F32, (3, 3, 3), 2) == bad            # 2^63 elements

@@ -453,3 +453,64 @@ def test_full_size_sketch_rows_match_oracle(tdk, ctx, cfg):
     finally:
         del Y
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_matrix_case_matches_oracle(tdk, ctx, dtype, als_form):
+    """N = 2 (a matrix): the sketches are Y W and Y^T W, the core U_1^T Y U_2,
+    and FFCP is ALS on that small matrix.  Both ALS forms (the persistent
+    kernel hands N = 2 to the kernel-per-step form)."""
+    shape, ranks, p, R = (90, 70), (6, 5), 3, 4
+    Y, W, _ = small_problem(shape, ranks, p, seed=41, dtype=dtype, R_cp=R)
+    Yd = dev_tensor(Y, dtype)
+    U, Z = tdk.tucker_sketch(ctx, Yd, dev_W(W), ranks, p, "simt", want_Z=True)
+    Zo, _ = oracle.sketch(Y, W)
+    bnd = sketch_abs_bound(Y, W)
+    for n in range(2):
+        err = np.abs(host(Z[n]) - Zo[n])
+        assert np.all(err <= TOL_SKETCH[(dtype, "simt")] * bnd[n] + 1e-300), n
+    Uh = [host(u) for u in U]
+    G, nrm = tdk.tucker_core(ctx, Yd, U, ranks, p, "simt")
+    Gref = oracle.tucker_core(Y, Uh)
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    assert np.all(np.abs(host(G) - Gref) <= tol * core_abs_bound(Y, Uh))
+    Rt = [r + p for r in ranks]
+    B0 = synth.init_factors(Rt, R, 5)
+    ref_als = oracle.cp_als(Gref, B0, max_sweeps=40, tol=0.0)
+    out = tdk.ffcp_als(ctx, G, U, shape, ranks, p, DT_CODE[dtype], R, max_sweeps=40, tol=0.0,
+                       B0=[dev_tensor(b, "f64") for b in B0], normY2=nrm)
+    assert ctx.sync_status() == 0
+    assert out["sweeps"] == 40
+    assert abs(out["fit_core"] - ref_als["fit"]) < (1e-9 if dtype == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec,dtype", [("simt", "f64"), ("simt", "f32"), ("tc", "f32"), ("tc", "bf16")])
+def test_full_width_sketch_reconstructs_exactly(tdk, ctx, prec, dtype):
+    """Degenerate width R_n + p = I_n: every U_n is a square orthogonal
+    matrix, so the Tucker model reproduces Y and ||G|| = ||Y||."""
+    shape, ranks, p = (20, 24, 32), (18, 22, 30), 2
+    Y, W, _ = small_problem(shape, ranks, p, seed=43, dtype=dtype)
+    Yd = dev_tensor(Y, dtype)
+    U, _ = tdk.tucker_sketch(ctx, Yd, dev_W(W), ranks, p, prec)
+    G, nrm = tdk.tucker_core(ctx, Yd, U, ranks, p, prec)
+    assert ctx.sync_status() == 0
+    Uh = [host(u) for u in U]
+    for u in Uh:
+        assert u.shape[0] == u.shape[1]
+        assert np.abs(u.T @ u - np.eye(u.shape[0])).max() < 1e-12
+    Yr = oracle.tucker_full(host(G), Uh)
+    rel = np.linalg.norm(Yr - Y) / np.linalg.norm(Y)
+    assert rel < (1e-12 if dtype == "f64" else (2e-5 if prec == "simt" else 1e-4)), rel
+    assert math.isclose(float(np.sum(host(G) ** 2)), float(nrm.item()),
+                        rel_tol=1e-11 if dtype == "f64" else (1e-4 if prec == "simt" else 5e-4))
+
+
+def test_tensor_core_form_rejects_what_it_does_not_cover(tdk, ctx):
+    """N = 2 and FP64 data have no tensor-core form: TDK_ENOTSUP, nothing run."""
+    Y, W, _ = small_problem((40, 32), (4, 4), 2, seed=45, dtype="f32")
+    with pytest.raises(tdk.TdkError):
+        tdk.tucker_sketch(ctx, dev_tensor(Y, "f32"), dev_W(W), (4, 4), 2, "tc")
+    Y3, W3, _ = small_problem((12, 10, 16), (3, 3, 3), 2, seed=46, dtype="f64")
+    with pytest.raises(tdk.TdkError):
+        tdk.tucker_sketch(ctx, dev_tensor(Y3, "f64"), dev_W(W3), (3, 3, 3), 2, "tc")
+    assert ctx.sync_status() == 0

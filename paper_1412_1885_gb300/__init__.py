@@ -415,10 +415,14 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
               init="given", B0=None, A0=None, check_every=8, model=None):
     """The whole path: sketch -> CholQR2 -> core -> FFCP -> lift.  Y may be a
     host tensor (copied in) or a device tensor; results stay on the device.
+    Without a start (B0, or A0 for the nonnegative form) FFCP starts from the
+    HOSVD of the core.
     With `model` (an Mlp) and the unconstrained form, the ALS starts from the
     learned initial factors instead of B0."""
     if not Y.is_cuda:
         Y = Y.to(f"cuda:{ctx.device}", non_blocking=True)
+    if init == "given" and model is None and (A0 is None if nonneg else B0 is None):
+        init = "hosvd"  # no start given: the HOSVD start of the core
     U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
     G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
     if model is not None and not nonneg:

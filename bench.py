@@ -360,8 +360,8 @@ def main():
     A0 = [torch.as_tensor(a, device=dev) for a in synth.init_factors(w.shape, w.als_R, w.seed, dist="uniform")]
     torch.cuda.synchronize()
 
-    def step(Yin, prec=args.prec):
-        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, prec, nonneg=w.nonneg,
+    def step(Yin, Ydev=None, prec=args.prec):
+        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, prec, nonneg=w.nonneg, Y_dev=Ydev,
                            max_sweeps=w.als_max_sweeps, tol=w.als_tol, B0=None if w.nonneg else B0,
                            A0=A0 if w.nonneg else None, check_every=16, model=model)
 
@@ -413,9 +413,9 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            Y.copy_(Yh, non_blocking=True)
-            o = step(Y)
-            host = [a.to("cpu") for a in o["A"]]
+            # the public call on host data: Y crosses the link inside decompose (tdk_copy_in)
+            o = step(Yh, Y)
+            host = [t.copy_out(ctx, a) for a in o["A"]]
             d2h = sum(a.numel() * a.element_size() for a in host)
         torch.cuda.synchronize()
         dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, pg, dev)
@@ -428,8 +428,8 @@ def main():
     if not args.no_ttf and rank == 0:
         forms = {}
         for form in dict.fromkeys([args.prec, "simt"]):
-            step(Y, form)  # warm this form's kernels
-            ms_f, o = _fit_run(lambda: step(Y, form))
+            step(Y, prec=form)  # warm this form's kernels
+            ms_f, o = _fit_run(lambda: step(Y, prec=form))
             forms[form] = {"ms": ms_f, "fit_Y": o["fit_Y"], "sweeps": o["sweeps"]}
         ttf = {"forms": forms, "note": "device ms from Y resident in HBM to the factors A_n, one run per form; "
                                        "simt = the plain CUDA-core form (FP32 arithmetic for FP32/BF16 data)"}

@@ -102,6 +102,14 @@ int64_t tdk_ctx_launch_count(const tdk_ctx* ctx);
 int tdk_ctx_profile(tdk_ctx* ctx, int enable);
 int tdk_ctx_profile_read(tdk_ctx* ctx, int region, double* total_ms /* host */,
                          int64_t* launches /* host */);
+/* Host <-> device copies on the context's stream, for callers whose data
+   live in host memory (pinned memory for full link speed).  tdk_copy_in is
+   asynchronous: later calls on the stream see the data.  tdk_copy_out waits
+   for the stream, so *dst_host is valid on return.  Both buffers are
+   caller-owned; bytes = 0 is a no-op.  Errors: TDK_EINVAL (null context or
+   buffer), TDK_ECUDA. */
+int tdk_copy_in(tdk_ctx* ctx, void* dst /* device */, const void* src_host, size_t bytes);
+int tdk_copy_out(tdk_ctx* ctx, void* dst_host, const void* src /* device */, size_t bytes);
 /* Human-readable text for a return code. */
 const char* tdk_strerror(int code);
 

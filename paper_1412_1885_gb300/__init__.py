@@ -29,7 +29,7 @@ EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_s
            "tdk_ctx_launch_count", "tdk_strerror", "tdk_ctx_profile", "tdk_ctx_profile_read", "tucker_sketch",
            "tucker_core", "ffcp_als", "tucker_sketch_static", "tdk_mlp_create", "tdk_mlp_destroy",
            "tdk_mlp_param_count", "tdk_mlp_set_params", "tdk_mlp_get", "tdk_mlp_colsums", "tdk_mlp_train_step",
-           "ffcp_predict_init", "tdk_tucker_check"]
+           "ffcp_predict_init", "tdk_tucker_check", "tdk_copy_in", "tdk_copy_out"]
 MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
 
 
@@ -86,6 +86,8 @@ def lib():
         L.tdk_strerror.argtypes = [ctypes.c_int]
         L.tdk_strerror.restype = ctypes.c_char_p
         L.tdk_tucker_check.argtypes = [ctypes.POINTER(TuckerDesc)]
+        L.tdk_copy_in.argtypes = [vp, vp, vp, ctypes.c_size_t]
+        L.tdk_copy_out.argtypes = [vp, vp, vp, ctypes.c_size_t]
         L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp]
         L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
         L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
@@ -411,16 +413,47 @@ class Mlp:
             pass
 
 
+def copy_in(ctx: Context, dst, src_host):
+    """Host tensor -> device tensor of the same size, on the context's stream
+    (tdk_copy_in)."""
+    nbytes = src_host.numel() * src_host.element_size()
+    if dst.numel() * dst.element_size() != nbytes or not dst.is_cuda or src_host.is_cuda:
+        raise ValueError("copy_in: a host source and a device destination of equal size")
+    ctx._bind_stream()
+    _check(lib().tdk_copy_in(ctx.handle, ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(src_host.data_ptr()),
+                             nbytes), "tdk_copy_in")
+    return dst
+
+
+def copy_out(ctx: Context, src, dst_host=None):
+    """Device tensor -> host tensor (allocated when dst_host is None); waits
+    for the context's stream (tdk_copy_out)."""
+    import torch
+
+    if dst_host is None:
+        dst_host = torch.empty(src.shape, dtype=src.dtype)
+    nbytes = src.numel() * src.element_size()
+    ctx._bind_stream()
+    _check(lib().tdk_copy_out(ctx.handle, ctypes.c_void_p(dst_host.data_ptr()), ctypes.c_void_p(src.data_ptr()),
+                              nbytes), "tdk_copy_out")
+    return dst_host
+
+
 def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sweeps=1000, tol=1e-7,
-              init="given", B0=None, A0=None, check_every=8, model=None):
+              init="given", B0=None, A0=None, check_every=8, model=None, Y_dev=None):
     """The whole path: sketch -> CholQR2 -> core -> FFCP -> lift.  Y may be a
-    host tensor (copied in) or a device tensor; results stay on the device.
+    host tensor (copied in by tdk_copy_in, into Y_dev when given) or a device
+    tensor; results stay on the device.
     Without a start (B0, or A0 for the nonnegative form) FFCP starts from the
     HOSVD of the core.
     With `model` (an Mlp) and the unconstrained form, the ALS starts from the
     learned initial factors instead of B0."""
     if not Y.is_cuda:
-        Y = Y.to(f"cuda:{ctx.device}", non_blocking=True)
+        import torch
+
+        if Y_dev is None:
+            Y_dev = torch.empty(Y.shape, dtype=Y.dtype, device=f"cuda:{ctx.device}")
+        Y = copy_in(ctx, Y_dev, Y.contiguous())
     if init == "given" and model is None and (A0 is None if nonneg else B0 is None):
         init = "hosvd"  # no start given: the HOSVD start of the core
     U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
@@ -434,5 +467,5 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
     return out
 
 
-__all__ = ["Context", "Mlp", "tucker_check", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
+__all__ = ["Context", "Mlp", "tucker_check", "copy_in", "copy_out", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
            "make_desc", "TdkError", "EXPORTS", "strerror"]

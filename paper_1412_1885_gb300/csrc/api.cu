@@ -145,6 +145,23 @@ int tdk_ctx_sync_status(tdk_ctx* c, int* flags_out) {
 
 int64_t tdk_ctx_launch_count(const tdk_ctx* c) { return c ? c->launches : -1; }
 
+int tdk_copy_in(tdk_ctx* c, void* dst, const void* src_host, size_t bytes) {
+  if (!c || (bytes && (!dst || !src_host))) return TDK_EINVAL;
+  if (!bytes) return TDK_OK;
+  cudaSetDevice(c->device);
+  TDK_CUDA_TRY(cudaMemcpyAsync(dst, src_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  return TDK_OK;
+}
+
+int tdk_copy_out(tdk_ctx* c, void* dst_host, const void* src, size_t bytes) {
+  if (!c || (bytes && (!dst_host || !src))) return TDK_EINVAL;
+  if (!bytes) return TDK_OK;
+  cudaSetDevice(c->device);
+  TDK_CUDA_TRY(cudaMemcpyAsync(dst_host, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+  TDK_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return TDK_OK;
+}
+
 static void prof_drain(tdk_ctx* c, int r) {
   auto& v = c->prof_ev[r];
   for (size_t i = 0; i + 1 < v.size(); i += 2) {

@@ -514,3 +514,26 @@ def test_tensor_core_form_rejects_what_it_does_not_cover(tdk, ctx):
     with pytest.raises(tdk.TdkError):
         tdk.tucker_sketch(ctx, dev_tensor(Y3, "f64"), dev_W(W3), (3, 3, 3), 2, "tc")
     assert ctx.sync_status() == 0
+
+
+def test_host_data_through_the_abi_copies(tdk, ctx):
+    """decompose on a host tensor (copied in by tdk_copy_in) gives the same
+    result as on the device tensor; tdk_copy_out returns the factors."""
+    import torch
+
+    shape, ranks, p, R = (40, 36, 48), (4, 4, 4), 2, 3
+    Y, W, _ = small_problem(shape, ranks, p, seed=47, dtype="f32")
+    Yh = torch.as_tensor(Y, dtype=torch.float32).pin_memory()
+    Yd = Yh.to("cuda")
+    Wd = dev_W(W)
+    B0 = [dev_tensor(b, "f64") for b in synth.init_factors([r + p for r in ranks], R, 3)]
+    a = tdk.decompose(ctx, Yd, Wd, ranks, p, R, "tc", max_sweeps=30, tol=0.0, B0=B0)
+    buf = torch.empty_like(Yd)
+    b = tdk.decompose(ctx, Yh, Wd, ranks, p, R, "tc", max_sweeps=30, tol=0.0, B0=B0, Y_dev=buf)
+    assert torch.equal(buf, Yd)
+    for n in range(3):
+        ha = tdk.copy_out(ctx, a["A"][n])
+        hb = tdk.copy_out(ctx, b["A"][n])
+        assert ha.device.type == "cpu" and torch.equal(ha, hb)
+    assert a["fit_core"] == b["fit_core"]
+    assert ctx.sync_status() == 0

@@ -136,7 +136,31 @@ def cp_als(G: np.ndarray, B_init, max_sweeps: int = 1000, tol: float = 1e-9):
             "inner": inner, "model2": model2, "normG2": nG2, "pinv_used": npinv}
 
 
-def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float = 1e-7):
+def hals_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
+    """HALS update of A (Eq. 8): column by column, r = 1..R,
+        a_r <- P_+( a_r + (m_r - A t_r) / t_rr ),
+    with the columns already updated in this pass used for A (the projection
+    applied to the updated column: the exact minimiser of the objective over
+    column r with the others fixed)."""
+    A = np.array(A0, dtype=np.float64)
+    for r in range(A.shape[1]):
+        A[:, r] = np.maximum(0.0, A[:, r] + (M[:, r] - A @ T[:, r]) / T[r, r])
+    return A
+
+
+def mu_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
+    """Multiplicative update in the low-rank form (Eq. 14):
+        A <- A (*) P_+(M) (/) (A T),
+    elementwise; an entry whose denominator is not positive becomes 0."""
+    A0 = np.asarray(A0, dtype=np.float64)
+    D = A0 @ T
+    out = np.zeros_like(A0)
+    pos = D > 0.0
+    out[pos] = A0[pos] * np.maximum(M, 0.0)[pos] / D[pos]
+    return out
+
+
+def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float = 1e-7, rule: str = "ls"):
     """FFCP with projected nonnegative LS updates on the Tucker format.
 
     For every mode (Alg. 1 with the LS rule of Eq. 13 followed by P_+ of Eq. 8):
@@ -147,6 +171,11 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
     Columns of A_n are scaled to unit norm (lambda); an all-zero column is
     replaced by the constant unit vector with lambda_r = 0.  The fit is taken
     against Y~ = [[G; U]]:  <Y~, [[A]]> = <G, [[B]]>, ||[[A]]||^2 from A's Grams.
+
+    rule "hals" (Eq. 8) and "mu" (Eq. 14) replace the projected solve by one
+    pass of `hals_rows` / `mu_rows` from the current iterate of the mode,
+    A_n diag(lambda) (the model [[lambda; A]] with lambda on the factor being
+    updated), with the same M_n and T_n.
     """
     G = np.asarray(G, dtype=np.float64)
     N = G.ndim
@@ -165,8 +194,15 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
             H = mttkrp(G, Bs, n)
             M = Us[n] @ H
             T = hadamard_grams(As, n)
-            An, _ = solve_normal(M, T)
-            An = np.maximum(An, 0.0)
+            if rule == "ls":
+                An, _ = solve_normal(M, T)
+                An = np.maximum(An, 0.0)
+            elif rule == "hals":
+                An = hals_rows(As[n] * lam[None, :], M, T)
+            elif rule == "mu":
+                An = mu_rows(As[n] * lam[None, :], M, T)
+            else:
+                raise ValueError(rule)
             An, lam = _normalise(An)
             zero = lam == 0
             if np.any(zero):

@@ -250,6 +250,71 @@ def test_nonneg_ffcp_recovers_noise_free_nonnegative_cp():
     assert oracle.congruence(A, Ah) > 0.9999
 
 
+@pytest.mark.parametrize("rule,sweeps,tol", [("hals", 300, 1e-8), ("mu", 5000, 1e-5)])
+def test_nonneg_rules_recover_noise_free_nonnegative_cp(rule, sweeps, tol):
+    # the HALS (Eq. 8) and multiplicative (Eq. 14) updates reach the exact
+    # nonnegative CP model of a noise-free tensor through its Tucker format
+    shape, R = (30, 28, 26), 3
+    A = synth.cp_factors(shape, R, 8, dist="uniform")
+    Y = synth.cp_dense(A)
+    W = synth.sketch_matrices(shape, R + 3, 1)
+    tk = oracle.rand_tucker(Y, W)
+    A0 = synth.init_factors(shape, R, 2, dist="uniform")
+    out = oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=sweeps, tol=0.0, rule=rule)
+    Ah = [a.copy() for a in out["A"]]
+    Ah[-1] = Ah[-1] * out["lam"][None, :]
+    assert all(np.all(a >= 0) for a in Ah)
+    rel = np.linalg.norm(Y - oracle.cp_full(np.ones(R), Ah)) / np.linalg.norm(Y)
+    assert rel < tol, rel
+    assert oracle.congruence(A, Ah) > 0.9999
+
+
+def test_hals_column_is_the_nonnegative_columnwise_minimiser():
+    # brute force on the objective itself, ||X - A W^T||^2: each updated
+    # column, with the columns before it already updated and the ones after
+    # it as given, minimises the objective over that column on a fine grid
+    r_ = np.random.default_rng(3)
+    I, J, R = 5, 9, 4
+    X = r_.standard_normal((I, J))
+    Wm = r_.standard_normal((J, R))
+    A0 = np.abs(r_.standard_normal((I, R)))
+    A1 = oracle.hals_rows(A0, X @ Wm, Wm.T @ Wm)
+    assert np.all(A1 >= 0)
+    for r in range(R):
+        cur = np.concatenate([A1[:, :r], A0[:, r:]], axis=1)
+        rest = X - np.delete(cur, r, axis=1) @ np.delete(Wm, r, axis=1).T
+        grid = np.linspace(0.0, 5.0, 50001)
+        for i in range(I):
+            f = np.sum((rest[i][None, :] - grid[:, None] * Wm[:, r][None, :]) ** 2, axis=1)
+            fi = np.sum((rest[i] - A1[i, r] * Wm[:, r]) ** 2)
+            assert fi <= f.min() + 1e-9
+            assert A1[i, r] <= 5.0
+
+
+def test_mu_fixed_point_and_monotone_on_nonnegative_data():
+    r_ = np.random.default_rng(4)
+    I, J, R = 7, 11, 3
+    Wm = r_.random((J, R))
+    Astar = r_.random((I, R))
+    X = Astar @ Wm.T
+    T = Wm.T @ Wm
+    # an exact nonnegative factor is a fixed point of A <- A (*) M (/) (A T)
+    assert np.allclose(oracle.mu_rows(Astar, X @ Wm, T), Astar, rtol=1e-13, atol=0)
+    # on nonnegative data the update never raises ||X - A W^T|| (Lee and Seung)
+    Xn = r_.random((I, J))
+    A = r_.random((I, R)) + 0.1
+    obj = lambda a: np.sum((Xn - a @ Wm.T) ** 2)
+    for _ in range(20):
+        An = oracle.mu_rows(A, Xn @ Wm, T)
+        assert obj(An) <= obj(A) * (1 + 1e-12)
+        assert np.all(An >= 0)
+        A = An
+    # a row with a zero denominator stays zero
+    Z = A.copy()
+    Z[2] = 0.0
+    assert np.all(oracle.mu_rows(Z, Xn @ Wm, T)[2] == 0.0)
+
+
 def test_hosvd_init_spans_leading_subspace():
     G = _rand((6, 5, 4), 2)
     V = oracle.hosvd_init(G, 3)

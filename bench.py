@@ -141,7 +141,7 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(w, seconds_target=10.0, max_block=200_000_000):
+def cpu_oracle_sample(w, seconds_target=10.0, max_block=200_000_000, rule="ls"):
     """Time the FP64 oracle (as it stands) on a leading sub-block of the
     workload on the host cores: sketch + QR + core over the block, then ALS on
     its core.  A small block is timed first to size the measured block (at
@@ -172,7 +172,8 @@ def cpu_oracle_sample(w, seconds_target=10.0, max_block=200_000_000):
         t0 = time.perf_counter()
         tk = oracle.rand_tucker(Y, W)
         if sw.nonneg:
-            oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
+            oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol,
+                                 rule=rule)
         else:
             oracle.cp_als(tk["G"], B0, max_sweeps=min(sw.als_max_sweeps, 200), tol=sw.als_tol)
         return time.perf_counter() - t0
@@ -279,7 +280,7 @@ def run_reference(args, w):
     vals = []
     desc = ""
     for i in range(args.warmup + args.steps):
-        v, desc, _ = cpu_oracle_sample(w)
+        v, desc, _ = cpu_oracle_sample(w, rule=args.nonneg_rule)
         if i >= args.warmup:
             vals.append(v)
     vals.sort()
@@ -310,6 +311,8 @@ def main():
     ap.add_argument("--no-ttf", action="store_true", help="skip the time-to-fit comparison of the forms")
     ap.add_argument("--train", type=int, default=2048, help="learned-init workload: training tensors")
     ap.add_argument("--eval", type=int, default=64, help="learned-init workload: held-out tensors")
+    ap.add_argument("--nonneg-rule", default="ls", choices=["ls", "hals", "mu"],
+                    help="update rule of the nonnegative workloads: projected LS, HALS (Eq. 8), MU (Eq. 14)")
     ap.add_argument("--sketch", default=DEFAULT_SKETCH, choices=["shared", "independent"],
                     help="sketch family: Khatri-Rao factors shared between the modes, or drawn per mode")
     args = ap.parse_args()
@@ -361,7 +364,8 @@ def main():
     torch.cuda.synchronize()
 
     def step(Yin, Ydev=None, prec=args.prec):
-        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, prec, nonneg=w.nonneg, Y_dev=Ydev,
+        return t.decompose(ctx, Yin, Wd, w.ranks, w.p, w.als_R, prec, nonneg=args.nonneg_rule if w.nonneg else False,
+                           Y_dev=Ydev,
                            max_sweeps=w.als_max_sweeps, tol=w.als_tol, B0=None if w.nonneg else B0,
                            A0=A0 if w.nonneg else None, check_every=16, model=model)
 
@@ -451,7 +455,7 @@ def main():
                               "avg_launch_ms": co_ms / max(co_n, 1)}}
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cv, cdesc, _ = cpu_oracle_sample(w)
+        cv, cdesc, _ = cpu_oracle_sample(w, rule=args.nonneg_rule)
         cpu = {"value": cv, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle", "sample": cdesc}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -459,7 +463,8 @@ def main():
                 "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16"}[w.dtype],
                 "data": "synthetic",
                 "config": {"workload": w.name, "shape": list(w.shape), "ranks": list(w.ranks), "p": w.p,
-                           "R": w.als_R, "prec": args.prec, "nonneg": w.nonneg, "sketch": args.sketch,
+                           "R": w.als_R, "prec": args.prec, "nonneg": w.nonneg,
+                           "nonneg_rule": args.nonneg_rule if w.nonneg else None, "sketch": args.sketch,
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

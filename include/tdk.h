@@ -205,13 +205,20 @@ int tucker_core(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
                 const double* const U[], void* G_out, double* normY2);
 
 enum { TDK_INIT_GIVEN = 0, TDK_INIT_HOSVD = 1 };
+enum { TDK_NONNEG_NONE = 0, TDK_NONNEG_LS = 1, TDK_NONNEG_HALS = 2, TDK_NONNEG_MU = 3 };
 
 typedef struct {
   int R;            /* CP rank, 1 <= R <= min_n Rt_n                       */
   int max_sweeps;   /* >= 1                                                */
   double tol;       /* stop when |f_t - f_{t-1}| < tol * |f_{t-1}|, f the
                        fit of the core (Sec. V-A uses an absolute 1e-6)     */
-  int nonneg;       /* 0: LS update (Eq. 13); 1: projected nonnegative LS  */
+  int nonneg;       /* 0: LS update (Eq. 13); TDK_NONNEG_LS (1): projected
+                       nonnegative LS; TDK_NONNEG_HALS (2): column-wise
+                       HALS (Eq. 8); TDK_NONNEG_MU (3): multiplicative
+                       update in the low-rank form (Eq. 14).  HALS and MU
+                       start each mode from A_n diag(lambda) and need the
+                       persistent kernel (N >= 3, core fits on chip, no
+                       time limit): otherwise TDK_ENOTSUP                  */
   int init;         /* TDK_INIT_GIVEN: start from B_io (nonneg: A_io);
                        TDK_INIT_HOSVD: leading R left singular vectors of
                        every G_(n) (nonneg: their magnitudes lifted)        */

@@ -21,6 +21,8 @@ TDK_WRANKDEF, TDK_WNOCONV, TDK_WPINV = 1, 2, 4
 F64, F32, BF16 = 0, 1, 2
 PREC = {"simt": 0, "tc": 1}
 INIT = {"given": 0, "hosvd": 1}
+# nonnegative update rule: projected LS, HALS (Eq. 8), multiplicative (Eq. 14)
+NONNEG = {False: 0, True: 1, "ls": 1, "hals": 2, "mu": 3}
 MAX_MODES = 8
 MAX_RANK = 64
 
@@ -302,7 +304,7 @@ def ffcp_als(ctx: Context, G, U, shape, ranks, p, dtype_code, R, max_sweeps=1000
         for n in range(N):
             A[n].copy_(A0[n])
     lam = torch.empty(R, dtype=torch.float64, device=dev)
-    o = AlsOpts(R=int(R), max_sweeps=int(max_sweeps), tol=float(tol), nonneg=int(bool(nonneg)),
+    o = AlsOpts(R=int(R), max_sweeps=int(max_sweeps), tol=float(tol), nonneg=NONNEG[nonneg],
                 init=INIT[init], check_every=int(check_every), reserved=0, timeout_s=float(timeout_s))
     rep = AlsReport()
     ctx._bind_stream()
@@ -454,11 +456,11 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
         if Y_dev is None:
             Y_dev = torch.empty(Y.shape, dtype=Y.dtype, device=f"cuda:{ctx.device}")
         Y = copy_in(ctx, Y_dev, Y.contiguous())
-    if init == "given" and model is None and (A0 is None if nonneg else B0 is None):
+    if init == "given" and model is None and (A0 is None if NONNEG[nonneg] else B0 is None):
         init = "hosvd"  # no start given: the HOSVD start of the core
     U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
     G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
-    if model is not None and not nonneg:
+    if model is not None and not NONNEG[nonneg]:
         B0 = model.predict_init(G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R)
         init = "given"
     out = ffcp_als(ctx, G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R, max_sweeps, tol, nonneg, init, B0, A0,

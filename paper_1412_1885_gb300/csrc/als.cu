@@ -595,6 +595,8 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
   AlsArgs<T> a{};
   a.N = N;
   a.R = R;
+  // the HALS and multiplicative rules live in the persistent kernel only
+  if (o->nonneg == TDK_NONNEG_HALS || o->nonneg == TDK_NONNEG_MU) return TDK_ENOTSUP;
   a.nonneg = o->nonneg ? 1 : 0;
   a.max_sweeps = o->max_sweeps;
   a.tol = o->tol;

@@ -49,6 +49,7 @@ struct PState {
 template <class T>
 struct PArgs {
   int N, R, nonneg, max_sweeps;
+  int nn_rule;                  // nonneg: 0 projected LS, 1 HALS (Eq. 8), 2 multiplicative (Eq. 14)
   double tol;
   int Rt[TDK_MAX_MODES];
   int64_t I[TDK_MAX_MODES];
@@ -250,6 +251,11 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   const int G = gridDim.x, c = blockIdx.x;
   bool ok = true;
   if (tid < N) s_irows[tid] = 1.0 / sqrt((double)(a.nonneg ? a.I[tid] : a.Rt[tid]));
+  // the HALS and multiplicative rules start every mode from its running A_n:
+  // in the first sweep that is the given A0 (read after a grid barrier)
+  if (a.nonneg && a.nn_rule != 0 && c == 0)
+    for (int n = 0; n < N; ++n)
+      for (int64_t e = tid; e < a.I[n] * R; e += NTP) a.Aout[n][e] = a.init[n][e];
 
   // ---- initial factors (raw) and their Grams
   for (int n = 0; n < N; ++n) {
@@ -313,11 +319,15 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       __syncthreads();
       // ---- 1b. inverse of T_n: FP32 by default (the solves are refined against
       //          T_n in FP64), FP64 if an FP32 pivot breaks down
-      const bool use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
-      if (!use32 && !group_gj_inverse<double>(Tid, gjs, R, 2.220446049250313e-16, tid, NTP, 1)) {
-        needpinv = 1;
-        ok = false;  // identical in every CTA: all leave here
-        break;
+      // (the HALS and multiplicative rules use T_n itself, not its inverse)
+      bool use32 = true;
+      if (!(a.nonneg && a.nn_rule != 0)) {
+        use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
+        if (!use32 && !group_gj_inverse<double>(Tid, gjs, R, 2.220446049250313e-16, tid, NTP, 1)) {
+          needpinv = 1;
+          ok = false;  // identical in every CTA: all leave here
+          break;
+        }
       }
       __syncthreads();
       // x <- x T_n^{-1} for the row in xrow, block-parallel: one product with the
@@ -497,9 +507,36 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             xrow[r] = (double)m;
           }
           __syncthreads();
-          solve_row();
-          __syncthreads();
-          for (int r = tid; r < R; r += NTP) a.Bnew[i * R + r] = (T)fmax(xrow[r], 0.0);
+          if (a.nn_rule == 0) {
+            solve_row();
+            __syncthreads();
+            for (int r = tid; r < R; r += NTP) a.Bnew[i * R + r] = (T)fmax(xrow[r], 0.0);
+          } else {
+            // from the current iterate of the row, A_n[i, :] diag(lambda) (FP64)
+            for (int r = tid; r < R; r += NTP) hrow[r] = __ldcg(a.Aout[n] + i * R + r) * lam[r];
+            __syncthreads();
+            if (a.nn_rule == 2) {
+              // multiplicative: a <- a (*) P_+(m) (/) (a T_n); 0 where a T_n is not positive
+              for (int r = tid; r < R; r += NTP) {
+                double d = 0.0;
+                for (int q = 0; q < R; ++q) d = fma(hrow[q], Tm[q * R + r], d);
+                a.Bnew[i * R + r] = (T)(d > 0.0 ? hrow[r] * fmax(xrow[r], 0.0) / d : 0.0);
+              }
+            } else {
+              // HALS, column by column: a_r <- P_+(a_r + (m_r - a t_r) / t_rr), one warp
+              if (tid < 32) {
+                for (int r = 0; r < R; ++r) {
+                  double part = 0.0;
+                  for (int q = tid; q < R; q += 32) part = fma(hrow[q], Tm[q * R + r], part);
+                  part = warp_sum(part);
+                  if (tid == 0) hrow[r] = fmax(0.0, hrow[r] + (xrow[r] - part) / Tm[r * R + r]);
+                  __syncwarp();
+                }
+              }
+              __syncthreads();
+              for (int r = tid; r < R; r += NTP) a.Bnew[i * R + r] = (T)hrow[r];
+            }
+          }
           __syncthreads();
         }
         if (!grid_sync(a.bar, a.status)) { ok = false; break; }
@@ -1158,6 +1195,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   a.N = N;
   a.R = R;
   a.nonneg = o->nonneg ? 1 : 0;
+  a.nn_rule = o->nonneg == TDK_NONNEG_HALS ? 1 : (o->nonneg == TDK_NONNEG_MU ? 2 : 0);
   a.max_sweeps = o->max_sweeps;
   a.tol = o->tol;
   int64_t Rtmax = 0, Imax = 0, btot = 0;

@@ -537,3 +537,46 @@ def test_host_data_through_the_abi_copies(tdk, ctx):
         assert ha.device.type == "cpu" and torch.equal(ha, hb)
     assert a["fit_core"] == b["fit_core"]
     assert ctx.sync_status() == 0
+
+
+@pytest.mark.parametrize("rule", ["hals", "mu"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_nonneg_rules_match_oracle(tdk, ctx, rule, dtype):
+    """HALS (Eq. 8) and multiplicative (Eq. 14) nonnegative FFCP in the
+    persistent kernel against the oracle's rules on the same 4-way core."""
+    shape, ranks, p, R = (24, 22, 20, 18), (5, 5, 5, 5), 3, 4
+    Y, W, A = small_problem(shape, ranks, p, seed=7, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
+    ref = oracle.rand_tucker(Y, W)
+    A0 = synth.init_factors(shape, R, 6, dist="uniform")
+    o = oracle.cp_als_nonneg(ref["G"], ref["U"], A0, max_sweeps=40, tol=0.0, rule=rule)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], dtype), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, DT_CODE[dtype], R, max_sweeps=40, tol=0.0, nonneg=rule,
+                       A0=[dev_tensor(a, "f64") for a in A0])
+    assert ctx.sync_status() == 0
+    assert out["sweeps"] == 40
+    assert abs(out["fit_core"] - o["fit"]) < (1e-10 if dtype == "f64" else 1e-5), (out["fit_core"], o["fit"])
+    Ah = [host(a) for a in out["A"]]
+    assert all(np.all(a >= 0) for a in Ah)
+    Ao = [a.copy() for a in o["A"]]
+    Ao[-1] = Ao[-1] * o["lam"][None, :]
+    if dtype == "f64":
+        for n in range(4):
+            assert np.allclose(Ah[n], Ao[n], atol=1e-8)
+    else:
+        assert oracle.congruence(Ao, Ah) > 0.9999
+
+
+def test_nonneg_rules_need_the_persistent_form(tdk, ctx):
+    """HALS and MU have no kernel-per-step form: TDK_ENOTSUP there."""
+    shape, ranks, p, R = (24, 22, 20), (5, 5, 5), 3, 4
+    Y, W, _ = small_problem(shape, ranks, p, seed=8, dtype="f64", dist="uniform", clip0=True)
+    ref = oracle.rand_tucker(Y, W)
+    A0 = synth.init_factors(shape, R, 6, dist="uniform")
+    ctx.set_als_form(True)
+    try:
+        with pytest.raises(tdk.TdkError):
+            tdk.ffcp_als(ctx, dev_tensor(ref["G"], "f64"), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                         p, 0, R, max_sweeps=5, tol=0.0, nonneg="hals", A0=[dev_tensor(a, "f64") for a in A0])
+    finally:
+        ctx.set_als_form(False)
+    assert ctx.sync_status() == 0

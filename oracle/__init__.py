@@ -24,12 +24,12 @@ marks a function with no pin independent of itself.
 from .tucker import (unfold, fold, khatri_rao, sketch, sketch_row, householder_qr,
                      ttm, tucker_core, rand_tucker, tucker_full, norm2, hosvd_factors)
 from .cpals import (mttkrp, hadamard_grams, cp_full, cp_als, cp_als_nonneg, core_fit,
-                    lift, congruence, solve_normal, hosvd_init, hals_rows, mu_rows)
+                    lift, congruence, solve_normal, hosvd_init, hals_rows, mu_rows, soft_threshold)
 from . import mlp
 
 __all__ = [
     "unfold", "fold", "khatri_rao", "sketch", "sketch_row", "householder_qr", "ttm",
     "tucker_core", "rand_tucker", "hosvd_factors", "tucker_full", "norm2", "mttkrp", "hadamard_grams",
     "cp_full", "cp_als", "cp_als_nonneg", "core_fit", "lift", "congruence", "solve_normal",
-    "hosvd_init", "hals_rows", "mu_rows", "mlp",
+    "hosvd_init", "hals_rows", "mu_rows", "soft_threshold", "mlp",
 ]

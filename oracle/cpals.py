@@ -160,7 +160,15 @@ def mu_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
     return out
 
 
-def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float = 1e-7, rule: str = "ls"):
+def soft_threshold(X: np.ndarray, c: float) -> np.ndarray:
+    """S_c(x) = sign(x) max(|x| - c, 0), elementwise (Eq. 15): the minimiser
+    of (z - x)^2 / 2 + c |z| (pinned by brute force)."""
+    X = np.asarray(X, dtype=np.float64)
+    return np.sign(X) * np.maximum(np.abs(X) - c, 0.0)
+
+
+def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float = 1e-7, rule: str = "ls",
+                  l1: float = 0.0, clip: bool = True):
     """FFCP with projected nonnegative LS updates on the Tucker format.
 
     For every mode (Alg. 1 with the LS rule of Eq. 13 followed by P_+ of Eq. 8):
@@ -176,6 +184,10 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
     pass of `hals_rows` / `mu_rows` from the current iterate of the mode,
     A_n diag(lambda) (the model [[lambda; A]] with lambda on the factor being
     updated), with the same M_n and T_n.
+
+    l1 > 0 (rule "ls"): the l1-regularised update of Eq. 15, A_n <- S_c(A_n)
+    applied to the LS solution before the projection; clip=False drops the
+    projection P_+ (the sparse but signed form).
     """
     G = np.asarray(G, dtype=np.float64)
     N = G.ndim
@@ -196,7 +208,10 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
             T = hadamard_grams(As, n)
             if rule == "ls":
                 An, _ = solve_normal(M, T)
-                An = np.maximum(An, 0.0)
+                if l1 > 0.0:
+                    An = soft_threshold(An, l1)
+                if clip:
+                    An = np.maximum(An, 0.0)
             elif rule == "hals":
                 An = hals_rows(As[n] * lam[None, :], M, T)
             elif rule == "mu":

@@ -315,6 +315,32 @@ def test_mu_fixed_point_and_monotone_on_nonnegative_data():
     assert np.all(oracle.mu_rows(Z, Xn @ Wm, T)[2] == 0.0)
 
 
+def test_soft_threshold_is_the_l1_proximal_map():
+    # S_c(x) minimises (z - x)^2 / 2 + c |z| (Eq. 15): brute force on a grid
+    grid = np.linspace(-6.0, 6.0, 120001)
+    for x in (-3.7, -0.4, 0.0, 0.25, 1.3, 4.9):
+        for c in (0.0, 0.5, 2.0):
+            z = float(oracle.soft_threshold(np.array([x]), c)[0])
+            f = 0.5 * (grid - x) ** 2 + c * np.abs(grid)
+            assert 0.5 * (z - x) ** 2 + c * abs(z) <= f.min() + 1e-9
+            assert abs(z - grid[np.argmin(f)]) <= 2e-4
+
+
+def test_ambient_ls_without_penalty_equals_core_space_als():
+    # l1 = 0 without projection, started inside the Tucker subspace
+    # (A0 = U B0): the ambient-factor update equals FFCP's core-space LS
+    shape, ranks, p, R = (20, 18, 16), (4, 4, 4), 2, 3
+    Y = synth.cp_dense(synth.cp_factors(shape, R, 5))
+    Y = synth.add_noise(Y, 20.0, 5)
+    W = synth.sketch_matrices(shape, [r + p for r in ranks], 5)
+    tk = oracle.rand_tucker(Y, W)
+    B0 = synth.init_factors([r + p for r in ranks], R, 6)
+    A0 = [u @ b for u, b in zip(tk["U"], B0)]
+    a = oracle.cp_als_nonneg(tk["G"], tk["U"], A0, max_sweeps=15, tol=0.0, l1=0.0, clip=False)
+    c = oracle.cp_als(tk["G"], B0, max_sweeps=15, tol=0.0)
+    assert np.allclose(a["history"], c["history"], rtol=0, atol=1e-10)
+
+
 def test_hosvd_init_spans_leading_subspace():
     G = _rand((6, 5, 4), 2)
     V = oracle.hosvd_init(G, 3)

@@ -219,13 +219,20 @@ typedef struct {
                        start each mode from A_n diag(lambda) and need the
                        persistent kernel (N >= 3, core fits on chip, no
                        time limit): otherwise TDK_ENOTSUP                  */
-  int init;         /* TDK_INIT_GIVEN: start from B_io (nonneg: A_io);
+  int init;         /* TDK_INIT_GIVEN: start from B_io (nonneg or l1: A_io);
                        TDK_INIT_HOSVD: leading R left singular vectors of
                        every G_(n) (nonneg: their magnitudes lifted)        */
   int check_every;  /* sweeps per convergence check on the host (0 = 8)    */
   int reserved;
   double timeout_s; /* bound on the whole call, 0 = none; exceeded ->
                        TDK_ETIMEOUT with the last iterate in the outputs   */
+  double l1;        /* >= 0.  > 0: l1-regularised update of Eq. 15, the
+                       LS solution for A_n soft-thresholded, S_c(x) =
+                       sign(x) max(|x| - c, 0) with c = l1, then projected
+                       if nonneg = TDK_NONNEG_LS.  The factors are updated
+                       as A_n (start from A_io, or the HOSVD start lifted);
+                       needs the persistent kernel and nonneg NONE or LS,
+                       else TDK_ENOTSUP / TDK_EINVAL                        */
 } tdk_als_opts;
 
 typedef struct {

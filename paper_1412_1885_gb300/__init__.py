@@ -43,7 +43,7 @@ class TuckerDesc(ctypes.Structure):
 class AlsOpts(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
                 ("nonneg", ctypes.c_int), ("init", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+                ("reserved", ctypes.c_int), ("timeout_s", ctypes.c_double), ("l1", ctypes.c_double)]
 
 
 class AlsReport(ctypes.Structure):
@@ -287,7 +287,7 @@ def tucker_core(ctx: Context, Y, U, ranks, p, prec="simt"):
 
 
 def ffcp_als(ctx: Context, G, U, shape, ranks, p, dtype_code, R, max_sweeps=1000, tol=1e-7, nonneg=False,
-             init="given", B0=None, A0=None, normY2=None, check_every=8, timeout_s=0.0):
+             init="given", B0=None, A0=None, normY2=None, check_every=8, timeout_s=0.0, l1=0.0):
     """FFCP on the core (see include/tdk.h).  Returns dict(A, B, lam, report)."""
     import torch
 
@@ -305,7 +305,8 @@ def ffcp_als(ctx: Context, G, U, shape, ranks, p, dtype_code, R, max_sweeps=1000
             A[n].copy_(A0[n])
     lam = torch.empty(R, dtype=torch.float64, device=dev)
     o = AlsOpts(R=int(R), max_sweeps=int(max_sweeps), tol=float(tol), nonneg=NONNEG[nonneg],
-                init=INIT[init], check_every=int(check_every), reserved=0, timeout_s=float(timeout_s))
+                init=INIT[init], check_every=int(check_every), reserved=0, timeout_s=float(timeout_s),
+                l1=float(l1))
     rep = AlsReport()
     ctx._bind_stream()
     rc = _check(lib().ffcp_als(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(G.data_ptr()),
@@ -442,7 +443,7 @@ def copy_out(ctx: Context, src, dst_host=None):
 
 
 def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sweeps=1000, tol=1e-7,
-              init="given", B0=None, A0=None, check_every=8, model=None, Y_dev=None):
+              init="given", B0=None, A0=None, check_every=8, model=None, Y_dev=None, l1=0.0):
     """The whole path: sketch -> CholQR2 -> core -> FFCP -> lift.  Y may be a
     host tensor (copied in by tdk_copy_in, into Y_dev when given) or a device
     tensor; results stay on the device.
@@ -456,15 +457,16 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
         if Y_dev is None:
             Y_dev = torch.empty(Y.shape, dtype=Y.dtype, device=f"cuda:{ctx.device}")
         Y = copy_in(ctx, Y_dev, Y.contiguous())
-    if init == "given" and model is None and (A0 is None if NONNEG[nonneg] else B0 is None):
+    ambient = bool(NONNEG[nonneg]) or l1 > 0.0
+    if init == "given" and model is None and (A0 is None if ambient else B0 is None):
         init = "hosvd"  # no start given: the HOSVD start of the core
     U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
     G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
-    if model is not None and not NONNEG[nonneg]:
+    if model is not None and not ambient:
         B0 = model.predict_init(G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R)
         init = "given"
     out = ffcp_als(ctx, G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R, max_sweeps, tol, nonneg, init, B0, A0,
-                   nrm, check_every)
+                   nrm, check_every, l1=l1)
     out.update({"U": U, "G": G, "normY2": nrm})
     return out
 

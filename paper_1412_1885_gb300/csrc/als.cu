@@ -576,13 +576,13 @@ __global__ void __launch_bounds__(128) hosvd_init_kernel(AlsArgs<T> a, int n, do
 
 // |U_n B_n| as a nonnegative starting point
 __global__ void abs_lift_kernel(const double* __restrict__ U, const double* __restrict__ B, int64_t I, int64_t Rt,
-                                int R, double* __restrict__ A) {
+                                int R, double* __restrict__ A, bool take_abs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * R; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / R;
     int r = (int)(e % R);
     double s = 0.0;
     for (int64_t q = 0; q < Rt; ++q) s = fma(U[i * Rt + q], B[q * R + r], s);
-    A[e] = fabs(s);
+    A[e] = take_abs ? fabs(s) : s;
   }
 }
 
@@ -595,8 +595,8 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
   AlsArgs<T> a{};
   a.N = N;
   a.R = R;
-  // the HALS and multiplicative rules live in the persistent kernel only
-  if (o->nonneg == TDK_NONNEG_HALS || o->nonneg == TDK_NONNEG_MU) return TDK_ENOTSUP;
+  // the HALS, multiplicative and l1 rules live in the persistent kernel only
+  if (o->nonneg == TDK_NONNEG_HALS || o->nonneg == TDK_NONNEG_MU || o->l1 > 0.0) return TDK_ENOTSUP;
   a.nonneg = o->nonneg ? 1 : 0;
   a.max_sweeps = o->max_sweeps;
   a.tol = o->tol;
@@ -676,7 +676,7 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
       hosvd_init_kernel<T><<<1, 128, 0, s>>>(a, n, a.nonneg ? a.Hfull : a.Bnew);
       TDK_LAUNCH_CHECK(ctx);
       if (a.nonneg) {
-        abs_lift_kernel<<<64, 256, 0, s>>>(U[n], a.Hfull, g.I[n], g.Rt[n], R, a.Bnew);
+        abs_lift_kernel<<<64, 256, 0, s>>>(U[n], a.Hfull, g.I[n], g.Rt[n], R, a.Bnew, true);
         TDK_LAUNCH_CHECK(ctx);
       }
     }
@@ -834,17 +834,20 @@ int hosvd_into(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[],
   }
   a.gnumel = g.core_numel;
   a.G = G;
+  // factors updated as A_n (nonneg, l1): the start lifted, A_n = U_n B_n
+  // (its magnitudes for the nonnegative forms)
+  const bool ambient = o->nonneg || o->l1 > 0.0;
   double* tmp = nullptr;
-  if (o->nonneg) {
+  if (ambient) {
     int rc = ws_reserve(ctx, sizeof(double) * (size_t)Rtmax * o->R + 256);
     if (rc) return rc;
     tmp = reinterpret_cast<double*>(ctx->ws);
   }
   for (int n = 0; n < g.N; ++n) {
-    hosvd_init_kernel<T><<<1, 128, 0, ctx->stream>>>(a, n, o->nonneg ? tmp : B_io[n]);
+    hosvd_init_kernel<T><<<1, 128, 0, ctx->stream>>>(a, n, ambient ? tmp : B_io[n]);
     TDK_LAUNCH_CHECK(ctx);
-    if (o->nonneg) {
-      abs_lift_kernel<<<64, 256, 0, ctx->stream>>>(U[n], tmp, g.I[n], g.Rt[n], o->R, A_io[n]);
+    if (ambient) {
+      abs_lift_kernel<<<64, 256, 0, ctx->stream>>>(U[n], tmp, g.I[n], g.Rt[n], o->R, A_io[n], o->nonneg != 0);
       TDK_LAUNCH_CHECK(ctx);
     }
   }

@@ -50,6 +50,8 @@ template <class T>
 struct PArgs {
   int N, R, nonneg, max_sweeps;
   int nn_rule;                  // nonneg: 0 projected LS, 1 HALS (Eq. 8), 2 multiplicative (Eq. 14)
+  int clip;                     // nonneg path: project onto x >= 0 (0: the signed l1 form)
+  double l1;                    // soft threshold of the LS rows (Eq. 15), 0 = none
   double tol;
   int Rt[TDK_MAX_MODES];
   int64_t I[TDK_MAX_MODES];
@@ -510,7 +512,11 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           if (a.nn_rule == 0) {
             solve_row();
             __syncthreads();
-            for (int r = tid; r < R; r += NTP) a.Bnew[i * R + r] = (T)fmax(xrow[r], 0.0);
+            for (int r = tid; r < R; r += NTP) {
+              double x = xrow[r];
+              if (a.l1 > 0.0) x = copysign(fmax(fabs(x) - a.l1, 0.0), x);
+              a.Bnew[i * R + r] = (T)(a.clip ? fmax(x, 0.0) : x);
+            }
           } else {
             // from the current iterate of the row, A_n[i, :] diag(lambda) (FP64)
             for (int r = tid; r < R; r += NTP) hrow[r] = __ldcg(a.Aout[n] + i * R + r) * lam[r];
@@ -1194,8 +1200,11 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   PArgs<T> a{};
   a.N = N;
   a.R = R;
-  a.nonneg = o->nonneg ? 1 : 0;
+  // the l1 form updates the factors as A_n like the nonnegative forms
+  a.nonneg = (o->nonneg || o->l1 > 0.0) ? 1 : 0;
   a.nn_rule = o->nonneg == TDK_NONNEG_HALS ? 1 : (o->nonneg == TDK_NONNEG_MU ? 2 : 0);
+  a.clip = o->nonneg ? 1 : 0;
+  a.l1 = o->l1;
   a.max_sweeps = o->max_sweeps;
   a.tol = o->tol;
   int64_t Rtmax = 0, Imax = 0, btot = 0;

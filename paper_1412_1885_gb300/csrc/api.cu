@@ -276,6 +276,8 @@ int ffcp_als(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* G, const dou
   if (opts->R < 1 || opts->R > TDK_MAX_RANK || opts->max_sweeps < 1 || !(opts->tol >= 0.0)) return TDK_EINVAL;
   if (opts->init != TDK_INIT_GIVEN && opts->init != TDK_INIT_HOSVD) return TDK_EINVAL;
   if (opts->nonneg < TDK_NONNEG_NONE || opts->nonneg > TDK_NONNEG_MU) return TDK_EINVAL;
+  if (!(opts->l1 >= 0.0) || opts->l1 > 1e300) return TDK_EINVAL;
+  if (opts->l1 > 0.0 && opts->nonneg > TDK_NONNEG_LS) return TDK_EINVAL;
   for (int n = 0; n < g.N; ++n) {
     if (opts->R > g.Rt[n]) return TDK_EINVAL;
     if (!U[n] || !B_io[n] || !A_io[n]) return TDK_EINVAL;

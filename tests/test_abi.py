@@ -67,7 +67,7 @@ def test_struct_layouts_match_header():
 
     # int N, dtype, prec, p; int64 I[8]; int R[8]
     assert ctypes.sizeof(t.TuckerDesc) == 16 + 64 + 32
-    assert ctypes.sizeof(t.AlsOpts) == 4 + 4 + 8 + 4 * 4 + 8
+    assert ctypes.sizeof(t.AlsOpts) == 4 + 4 + 8 + 4 * 4 + 8 + 8
     assert ctypes.sizeof(t.AlsReport) == 4 + 4 + 8 * 3
 
 

@@ -580,3 +580,31 @@ def test_nonneg_rules_need_the_persistent_form(tdk, ctx):
     finally:
         ctx.set_als_form(False)
     assert ctx.sync_status() == 0
+
+
+@pytest.mark.parametrize("clip", [False, True])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_l1_rule_matches_oracle(tdk, ctx, clip, dtype):
+    """The l1-regularised update of Eq. 15 (soft threshold of the LS rows,
+    signed or projected) against the oracle on the same core."""
+    shape, ranks, p, R = (24, 22, 20), (5, 5, 5), 3, 4
+    dist = "uniform" if clip else "normal"
+    Y, W, _ = small_problem(shape, ranks, p, seed=9, dtype="f64", snr=25.0, R_cp=R, dist=dist, clip0=clip)
+    ref = oracle.rand_tucker(Y, W)
+    A0 = synth.init_factors(shape, R, 6, dist=dist)
+    c = 0.05
+    o = oracle.cp_als_nonneg(ref["G"], ref["U"], A0, max_sweeps=30, tol=0.0, l1=c, clip=clip)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], dtype), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, DT_CODE[dtype], R, max_sweeps=30, tol=0.0, nonneg="ls" if clip else False,
+                       A0=[dev_tensor(a, "f64") for a in A0], l1=c)
+    assert ctx.sync_status() == 0
+    assert out["sweeps"] == 30
+    assert abs(out["fit_core"] - o["fit"]) < (1e-10 if dtype == "f64" else 1e-4), (out["fit_core"], o["fit"])
+    if dtype == "f64":
+        Ah = [host(a) for a in out["A"]]
+        Ao = [a.copy() for a in o["A"]]
+        Ao[-1] = Ao[-1] * o["lam"][None, :]
+        for n in range(3):
+            assert np.allclose(Ah[n], Ao[n], atol=1e-8)
+        if clip:
+            assert all(np.all(a >= 0) for a in Ah)

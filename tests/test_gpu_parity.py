@@ -608,3 +608,47 @@ def test_l1_rule_matches_oracle(tdk, ctx, clip, dtype):
             assert np.allclose(Ah[n], Ao[n], atol=1e-8)
         if clip:
             assert all(np.all(a >= 0) for a in Ah)
+
+
+@pytest.mark.parametrize("nonneg", [False, True])
+def test_ffcp_on_tucker_format_input_at_large_dimension(tdk, ctx, nonneg):
+    """FFCP on a Tucker-format input with I_n = 10^4 and no dense Y (the
+    large-dimension experiment of Sec. V): a planted CP model is given by its
+    core and orthonormal factors; the lifted factors are compared with the
+    oracle's (unconstrained: the core-space ALS lifted; nonneg: the
+    ambient-row form, whose rows do not fit on chip and take the
+    kernel-per-step form)."""
+    I, Rt, R = 10000, 8, 3
+    shape, ranks, p = (I, I, I), (Rt - 2, Rt - 2, Rt - 2), 2
+    r_ = np.random.default_rng(51)
+    U = [np.linalg.qr(r_.standard_normal((I, Rt)))[0] for _ in range(3)]
+    if nonneg:
+        # a nonnegative planted model inside the span of U: A_n = |U_n C_n| projected back
+        C = [np.abs(r_.standard_normal((Rt, R))) for _ in range(3)]
+        A = [np.abs(u @ c) for u, c in zip(U, C)]
+        U = [np.linalg.qr(np.concatenate([a, r_.standard_normal((I, Rt - R))], axis=1))[0] for a in A]
+        B = [u.T @ a for u, a in zip(U, A)]
+    else:
+        B = [r_.standard_normal((Rt, R)) for _ in range(3)]
+    G = oracle.cp_full(np.ones(R), B) + 1e-3 * r_.standard_normal((Rt, Rt, Rt))
+    Gd = dev_tensor(G, "f64")
+    Ud = [dev_tensor(u, "f64") for u in U]
+    if nonneg:
+        A0 = [np.abs(r_.standard_normal((I, R))) for _ in range(3)]
+        o = oracle.cp_als_nonneg(G, U, A0, max_sweeps=25, tol=0.0)
+        out = tdk.ffcp_als(ctx, Gd, Ud, shape, ranks, p, 0, R, max_sweeps=25, tol=0.0, nonneg=True,
+                           A0=[dev_tensor(a, "f64") for a in A0])
+        Ao = [a.copy() for a in o["A"]]
+        Ao[-1] = Ao[-1] * o["lam"][None, :]
+    else:
+        B0 = [r_.standard_normal((Rt, R)) for _ in range(3)]
+        o = oracle.cp_als(G, B0, max_sweeps=25, tol=0.0)
+        out = tdk.ffcp_als(ctx, Gd, Ud, shape, ranks, p, 0, R, max_sweeps=25, tol=0.0,
+                           B0=[dev_tensor(b, "f64") for b in B0])
+        Ao = oracle.lift(U, o["B"], o["lam"])
+    assert ctx.sync_status() == 0
+    assert abs(out["fit_core"] - o["fit"]) < 1e-10
+    Ah = [host(a) for a in out["A"]]
+    assert all(a.shape == (I, R) for a in Ah)
+    for n in range(3):
+        assert np.allclose(Ah[n], Ao[n], atol=1e-8)

@@ -174,3 +174,34 @@ def rand_tucker(Y: np.ndarray, W) -> dict:
     U = [q for q, _ in QR]
     G = tucker_core(Y, U)
     return {"Z": Z, "U": U, "R": [r for _, r in QR], "G": G, "normY2": nY2}
+
+
+def refine_pass(Y: np.ndarray, Us, W) -> list:
+    """One pass of the RandTucker2i loop (Alg. 3, the body repeated twice),
+    modes in order, each using the factors already refined in this pass:
+        X   = Y x_{p != n} U_p^T                  (Alg. 3 prints U_p; read U_p^T)
+        Z_n = X_(n) Omega_n,  Omega_n = KRP_{k != n} W[n][k]   (W[n][k]: Rt_k x Rt_n)
+        U_n = orth(Z_n)                            (Householder QR, diag(R) >= 0)
+    Omega_n is drawn as a Khatri-Rao product of small Gaussians, as for the
+    first sketch.  Returns the new factor list."""
+    Y = np.asarray(Y, dtype=np.float64)
+    N = Y.ndim
+    Us = [np.asarray(u, dtype=np.float64) for u in Us]
+    for n in range(N):
+        X = Y
+        for p in range(N):
+            if p != n:
+                X = ttm(X, Us[p], p)
+        Z = unfold(X, n) @ khatri_rao([W[n][k] for k in range(N) if k != n])
+        Us[n], _ = householder_qr(Z)
+    return Us
+
+
+def rand_tucker_2i(Y: np.ndarray, U_init, W_passes) -> dict:
+    """RandTucker2i (Alg. 3): random starting factors, two refinement passes
+    (`refine_pass` with the sketch matrices of each pass), then the core."""
+    Us = [np.asarray(u, dtype=np.float64) for u in U_init]
+    for W in W_passes:
+        Us = refine_pass(Y, Us, W)
+    G = tucker_core(Y, Us)
+    return {"U": Us, "G": G, "normY2": float(np.sum(np.asarray(Y, dtype=np.float64) ** 2))}

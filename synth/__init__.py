@@ -33,6 +33,7 @@ TAG_INIT = 4
 TAG_TUCKER = 5
 TAG_MASK = 6
 TAG_SKETCH_SHARED = 8
+TAG_REFINE = 9
 
 OMEGA_SEED_XOR = 0x9E3779B97F4A7C15
 
@@ -152,6 +153,20 @@ def sketch_matrices(shape, Rt, seed: int, shared: bool = False):
                 row.append(round_bf16(rng(base, TAG_SKETCH, n, k).standard_normal((shape[k], Rt[n]))))
         W.append(row)
     return W
+
+
+def refine_matrices(Rt, seed: int, it: int):
+    """Sketch matrices of refinement pass `it` (RandTucker2i): W[n][k]
+    (k != n) is Rt[k] x Rt[n] i.i.d. N(0,1) rounded to BF16 values."""
+    N = len(Rt)
+    base = int(seed) ^ OMEGA_SEED_XOR
+    return [[None if k == n else round_bf16(rng(base, TAG_REFINE, it, n, k).standard_normal((Rt[k], Rt[n])))
+             for k in range(N)] for n in range(N)]
+
+
+def random_factors(shape, Rt, seed: int):
+    """RandTucker2i's starting factors: I_n x Rt_n i.i.d. N(0,1)."""
+    return [rng(seed, TAG_REFINE, 99, n).standard_normal((shape[n], Rt[n])) for n in range(len(shape))]
 
 
 def device_sketch(W, device):

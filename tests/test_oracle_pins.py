@@ -150,6 +150,35 @@ def test_rand_tucker_exact_recovery(shape, ranks, p, shared):
     assert rel < 1e-10
 
 
+def test_rand_tucker_2i_exact_recovery():
+    shape, ranks, p = (30, 25, 20), (3, 4, 5), 2
+    Y = synth.tucker_dense(shape, ranks, 3)
+    Rt = [r + p for r in ranks]
+    out = oracle.rand_tucker_2i(Y, synth.random_factors(shape, Rt, 4),
+                                [synth.refine_matrices(Rt, 4, it) for it in range(2)])
+    for U in out["U"]:
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-13
+    rel = np.linalg.norm(Y - tucker_full(out["G"], out["U"])) / np.linalg.norm(Y)
+    assert rel < 1e-10
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_rand_tucker_2i_is_near_hosvd_and_beats_one_pass(seed):
+    # Sec. IV-A, Fig. 5: with noise, the two refinement passes bring the
+    # randomized Tucker model close to the HOSVD one and well below the
+    # single randomized pass (same widths Rt for all three)
+    shape, ranks, p = (40, 36, 32), (5, 5, 5), 5
+    Rt = [r + p for r in ranks]
+    Y = synth.add_noise(synth.tucker_dense(shape, ranks, seed), 20.0, seed)
+    err = lambda G: math.sqrt(max(0.0, float(np.sum(Y ** 2) - np.sum(G ** 2))) / float(np.sum(Y ** 2)))
+    e1 = err(oracle.rand_tucker(Y, synth.sketch_matrices(shape, Rt, seed))["G"])
+    e2 = err(oracle.rand_tucker_2i(Y, synth.random_factors(shape, Rt, seed),
+                                   [synth.refine_matrices(Rt, seed, it) for it in range(2)])["G"])
+    eh = err(oracle.tucker_core(Y, oracle.hosvd_factors(Y, Rt)))
+    assert eh <= e2 < e1
+    assert e2 <= 1.25 * eh
+
+
 def test_mttkrp_matches_brute_force():
     G = _rand((3, 4, 5), 2)
     Bs = [_rand((3, 2), 3), _rand((4, 2), 4), _rand((5, 2), 5)]

@@ -191,6 +191,25 @@ int tucker_sketch_static(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* 
                          const double* const W[], double* const Z_out[]);
 
 /*
+ * tucker_refine -- one refinement pass of RandTucker2i (Alg. 3, the loop
+ * body; RandTucker2i is two passes from random factors, then tucker_core).
+ * For n = 1..N in order, each mode using the factors already refined:
+ *   X = Y x_{p != n} U_p^T (Alg. 3 prints U_p; read U_p^T),
+ *   Z_n = X_(n) Omega_n with Omega_n = KRP_{k != n} W[n*N + k],
+ *   U_n <- orthonormal basis of Z_n (CholQR2, FP64; rank-deficient Z_n
+ *   completed as in tucker_sketch).
+ *   Y      [I_1 x ... x I_N], desc->dtype FP64 or FP32 (CUDA-core form).
+ *   W      N*N device pointers; W[n*N + k] (k != n) FP64 [Rt_k x Rt_n],
+ *          a fresh draw per pass; W[n*N + n] is ignored.
+ *   U_io   N device pointers, FP64 [I_n x Rt_n]: the factors in (any full
+ *          rank start, e.g. Gaussian), refined in place.
+ * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOMEM, TDK_ENOTSUP
+ * (BF16 data).
+ */
+int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
+                  double* const U_io[]);
+
+/*
  * tucker_core -- G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2 line
  * "Y <- Y x_n U^T" for every n; Eq. 1), plus ||Y||_F^2.
  *

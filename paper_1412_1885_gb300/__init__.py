@@ -31,7 +31,7 @@ EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_s
            "tdk_ctx_launch_count", "tdk_strerror", "tdk_ctx_profile", "tdk_ctx_profile_read", "tucker_sketch",
            "tucker_core", "ffcp_als", "tucker_sketch_static", "tdk_mlp_create", "tdk_mlp_destroy",
            "tdk_mlp_param_count", "tdk_mlp_set_params", "tdk_mlp_get", "tdk_mlp_colsums", "tdk_mlp_train_step",
-           "ffcp_predict_init", "tdk_tucker_check", "tdk_copy_in", "tdk_copy_out"]
+           "ffcp_predict_init", "tdk_tucker_check", "tdk_copy_in", "tdk_copy_out", "tucker_refine"]
 MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
 
 
@@ -92,6 +92,7 @@ def lib():
         L.tdk_copy_out.argtypes = [vp, vp, vp, ctypes.c_size_t]
         L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp]
         L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
+        L.tucker_refine.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
         L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
         L.ffcp_als.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, ctypes.POINTER(AlsOpts), pp, pp, vp,
                                ctypes.POINTER(AlsReport)]
@@ -268,6 +269,33 @@ def tucker_sketch_static(ctx: Context, Y, W, ranks, p, Z_out=None):
     _check(lib().tucker_sketch_static(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _ptrs(Wf),
                                       _ptrs(Z_out)), "tucker_sketch_static")
     return Z_out
+
+
+def tucker_refine(ctx: Context, Y, W, U, ranks, p):
+    """One RandTucker2i refinement pass (see include/tdk.h): U (FP64 device
+    tensors [I_n x Rt_n]) refined in place with the pass matrices W[n][k]
+    (FP64 device [Rt_k x Rt_n]).  Returns U."""
+    N = Y.dim()
+    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, "simt")
+    Wf = []
+    for n in range(N):
+        for k in range(N):
+            Wf.append(None if k == n else W[n][k].contiguous())
+    ctx._bind_stream()
+    _check(lib().tucker_refine(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _ptrs(Wf), _ptrs(U)),
+           "tucker_refine")
+    return U
+
+
+def rand_tucker_2i(ctx: Context, Y, U0, W_passes, ranks, p, prec="simt"):
+    """RandTucker2i (Alg. 3): the starting factors U0 refined by one pass
+    per entry of W_passes (two in the paper), then the core.  Returns
+    (U, G, ||Y||^2)."""
+    U = [u.clone() for u in U0]
+    for W in W_passes:
+        tucker_refine(ctx, Y, W, U, ranks, p)
+    G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
+    return U, G, nrm
 
 
 def tucker_core(ctx: Context, Y, U, ranks, p, prec="simt"):
@@ -471,5 +499,6 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
     return out
 
 
-__all__ = ["Context", "Mlp", "tucker_check", "copy_in", "copy_out", "tucker_sketch", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
+__all__ = ["Context", "Mlp", "tucker_check", "copy_in", "copy_out", "tucker_sketch", "tucker_refine",
+           "rand_tucker_2i", "tucker_sketch_static", "tucker_core", "ffcp_als", "decompose", "lib",
            "make_desc", "TdkError", "EXPORTS", "strerror"]

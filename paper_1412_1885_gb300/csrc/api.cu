@@ -252,6 +252,22 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
   return rc;
 }
 
+int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
+                  double* const U_io[]) {
+  if (!ctx || !desc || !Y || !W || !U_io) return TDK_EINVAL;
+  Geom g;
+  int rc = make_geom(desc, &g);
+  if (rc) return rc;
+  for (int n = 0; n < g.N; ++n) {
+    if (!U_io[n]) return TDK_EINVAL;
+    for (int k = 0; k < g.N; ++k)
+      if (k != n && !W[n * g.N + k]) return TDK_EINVAL;
+  }
+  if (desc->dtype != TDK_F64 && desc->dtype != TDK_F32) return TDK_ENOTSUP;
+  cudaSetDevice(ctx->device);
+  return refine_pass(ctx, g, desc->dtype, Y, W, U_io);
+}
+
 int tucker_core(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const U[], void* G_out,
                 double* normY2) {
   if (!ctx || !desc || !Y || !U || !G_out) return TDK_EINVAL;

@@ -283,6 +283,39 @@ static int split_count(tdk_ctx* ctx, int64_t ctas, int per_sm, int64_t Ic, int64
   return ks < 2 ? 1 : (int)std::min<int64_t>(ks, 64);
 }
 
+__global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    *out = v;
+  }
+}
+
+template <class T>
+__global__ void cvt_f64_kernel(const double* __restrict__ s, T* __restrict__ d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (T)s[e];
+}
+
+template <class TY, class T, int TC>
+int launch_last(tdk_ctx* ctx, const void* Y, int64_t M, int64_t L, const T* U, int Rt, T* X,
+                double* parts, int grid) {
+  ProfScope ps(ctx, 1);
+  ttm_last_kernel<TY, T, TC><<<grid, NT, 0, ctx->stream>>>(reinterpret_cast<const TY*>(Y), M, L, U, Rt,
+                                                          X, parts);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
+}  // namespace
+
 template <class T>
 int launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo,
                    T* part, int64_t part_cap) {
@@ -324,38 +357,8 @@ int launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, i
   return TDK_OK;
 }
 
-__global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-    *out = v;
-  }
-}
-
-template <class T>
-__global__ void cvt_f64_kernel(const double* __restrict__ s, T* __restrict__ d, int64_t n) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    d[e] = (T)s[e];
-}
-
-template <class TY, class T, int TC>
-int launch_last(tdk_ctx* ctx, const void* Y, int64_t M, int64_t L, const T* U, int Rt, T* X,
-                double* parts, int grid) {
-  ProfScope ps(ctx, 1);
-  ttm_last_kernel<TY, T, TC><<<grid, NT, 0, ctx->stream>>>(reinterpret_cast<const TY*>(Y), M, L, U, Rt,
-                                                          X, parts);
-  TDK_LAUNCH_CHECK(ctx);
-  return TDK_OK;
-}
-
-}  // namespace
+template int launch_ttm_mid<double>(tdk_ctx*, const double*, int64_t, int64_t, int64_t, const double*, int, double*,
+                                    double*, int64_t);
 
 // core chain from a partly contracted tensor X with dims I_0..I_{m0},
 // Rt_{m0+1}..Rt_{N-1} (modes m0 .. 0 remain); X is neither tmp0 nor tmp1

@@ -134,6 +134,14 @@ int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
               void* G, double* normY2);
 int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[],
             void* G, double* normY2);
+// one refinement pass of RandTucker2i on CUDA cores (FP64/FP32 data)
+int refine_pass(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],
+                double* const U_io[]);
+// X_out[a, r, b] = sum_i U[i, r] X[a, i, b] (T = float or double), with an
+// optional buffer for split partial outputs (nullptr = no split)
+template <class T>
+int launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo,
+                   T* part, int64_t part_cap);
 int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double* const U[],
             const double* normY2, const tdk_als_opts* o, double* const B_io[],
             double* const A_io[], double* lambda_out, tdk_als_report* rep);

@@ -652,3 +652,31 @@ def test_ffcp_on_tucker_format_input_at_large_dimension(tdk, ctx, nonneg):
     assert all(a.shape == (I, R) for a in Ah)
     for n in range(3):
         assert np.allclose(Ah[n], Ao[n], atol=1e-8)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shape,ranks", [((40, 36, 32), (5, 6, 7)), ((14, 12, 10, 16), (3, 4, 3, 5))])
+def test_rand_tucker_2i_matches_oracle(tdk, ctx, dtype, shape, ranks):
+    """RandTucker2i (Alg. 3): two refinement passes from Gaussian factors,
+    then the core, against the oracle on the same inputs."""
+    p = 2
+    Rt = [r + p for r in ranks]
+    Y, _, _ = small_problem(shape, ranks, p, seed=53, dtype=dtype)
+    U0 = synth.random_factors(shape, Rt, 53)
+    Wp = [synth.refine_matrices(Rt, 53, it) for it in range(2)]
+    ref = oracle.rand_tucker_2i(Y, U0, Wp)
+    U, G, nrm = tdk.rand_tucker_2i(ctx, dev_tensor(Y, dtype), [dev_tensor(u, "f64") for u in U0],
+                                   [dev_W(W) for W in Wp], ranks, p)
+    assert ctx.sync_status() == 0
+    Uh = [host(u) for u in U]
+    for u in Uh:
+        assert np.abs(u.T @ u - np.eye(u.shape[1])).max() < 1e-12
+    if dtype == "f64":
+        for n in range(len(shape)):
+            assert np.abs(Uh[n] - ref["U"][n]).max() < 1e-8, n
+        bnd = core_abs_bound(Y, ref["U"])
+        assert np.all(np.abs(host(G) - ref["G"]) <= 1e-9 * bnd)
+    else:
+        e_gpu = recon_err(float(nrm.item()), host(G))
+        e_or = recon_err(ref["normY2"], ref["G"])
+        assert abs(e_gpu - e_or) <= 1e-5, (e_gpu, e_or)

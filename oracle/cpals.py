@@ -141,7 +141,9 @@ def hals_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
         a_r <- P_+( a_r + (m_r - A t_r) / t_rr ),
     with the columns already updated in this pass used for A (the projection
     applied to the updated column: the exact minimiser of the objective over
-    column r with the others fixed)."""
+    column r with the others fixed).  Pinned: brute-force minimisation of the
+    objective over each column on a grid; exact recovery of a noise-free
+    nonnegative CP model."""
     A = np.array(A0, dtype=np.float64)
     for r in range(A.shape[1]):
         A[:, r] = np.maximum(0.0, A[:, r] + (M[:, r] - A @ T[:, r]) / T[r, r])
@@ -151,7 +153,9 @@ def hals_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
 def mu_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
     """Multiplicative update in the low-rank form (Eq. 14):
         A <- A (*) P_+(M) (/) (A T),
-    elementwise; an entry whose denominator is not positive becomes 0."""
+    elementwise; an entry whose denominator is not positive becomes 0.
+    Pinned: an exact nonnegative factor is a fixed point; on nonnegative data
+    the objective never rises (Lee and Seung); exact recovery."""
     A0 = np.asarray(A0, dtype=np.float64)
     D = A0 @ T
     out = np.zeros_like(A0)

@@ -183,7 +183,8 @@ def refine_pass(Y: np.ndarray, Us, W) -> list:
         Z_n = X_(n) Omega_n,  Omega_n = KRP_{k != n} W[n][k]   (W[n][k]: Rt_k x Rt_n)
         U_n = orth(Z_n)                            (Householder QR, diag(R) >= 0)
     Omega_n is drawn as a Khatri-Rao product of small Gaussians, as for the
-    first sketch.  Returns the new factor list."""
+    first sketch.  Returns the new factor list.  Pinned through
+    `rand_tucker_2i`."""
     Y = np.asarray(Y, dtype=np.float64)
     N = Y.ndim
     Us = [np.asarray(u, dtype=np.float64) for u in Us]
@@ -199,7 +200,9 @@ def refine_pass(Y: np.ndarray, Us, W) -> list:
 
 def rand_tucker_2i(Y: np.ndarray, U_init, W_passes) -> dict:
     """RandTucker2i (Alg. 3): random starting factors, two refinement passes
-    (`refine_pass` with the sketch matrices of each pass), then the core."""
+    (`refine_pass` with the sketch matrices of each pass), then the core.
+    Pinned: exact recovery of exact multilinear-rank tensors; on noisy
+    tensors, HOSVD <= RandTucker2i < one randomized pass in error (Fig. 5)."""
     Us = [np.asarray(u, dtype=np.float64) for u in U_init]
     for W in W_passes:
         Us = refine_pass(Y, Us, W)

@@ -49,7 +49,7 @@ extern "C" {
 #define TDK_ENOMEM (-2)    /* workspace allocation failed                  */
 #define TDK_ECUDA (-3)     /* a CUDA runtime/driver call failed            */
 #define TDK_ETIMEOUT (-4)  /* a bounded device-side wait gave up           */
-#define TDK_ENOTSUP (-5)   /* supported by the ABI, not by this build/GPU  */
+#define TDK_ENOTSUP (-5)   /* a form or option that does not cover the case */
 #define TDK_ESCRATCH (-6)  /* problem needs more scratch than the fixed
                               static array of tucker_sketch_static holds   */
 #define TDK_WRANKDEF 1     /* a sketch was numerically rank deficient; the

@@ -308,7 +308,7 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   // the products are FP64-bound (about one FP64 FMA per clock per SM): the
   // same number of CTAs per mode, a multiple of the SM count in all
   const dim3 agrid((unsigned)std::max(1, 2 * ctx->num_sms), g.N);
-  // round 1: Z -> Q1
+  // first pass: Z -> Q1
   const dim3 rgrid((TDK_MAX_RANK * TDK_MAX_RANK + 255) / 256, g.N);
   const int cblk = 256;
   gram_partial_kernel<<<ggrid, 256, 0, ctx->stream>>>(Z, q, gpart, fail);
@@ -319,7 +319,7 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   TDK_LAUNCH_CHECK(ctx);
   apply_rinv_kernel<<<agrid, 256, 0, ctx->stream>>>(Z, q, rinv, fail, d1);
   TDK_LAUNCH_CHECK(ctx);
-  // round 2: Q1 -> U
+  // second pass: Q1 -> U
   gram_partial_kernel<<<ggrid, 256, 0, ctx->stream>>>(Q1, q, gpart, fail);
   TDK_LAUNCH_CHECK(ctx);
   gram_reduce_kernel<<<rgrid, 256, 0, ctx->stream>>>(q, gpart, fail, gram);

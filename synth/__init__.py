@@ -5,7 +5,9 @@ This module draws inputs only; it holds none of the decomposition arithmetic
 
 * CP-model data tensors with Gaussian noise at a given SNR, the data model of
   the paper's synthetic experiments (Sec. V-A, CP model of Eq. 2 plus i.i.d.
-  Gaussian noise; nonnegative variant with clipped values).
+  Gaussian noise; nonnegative variant with clipped values), and the sparse
+  nonnegative factors of its nonnegative CPD experiments (exponential
+  entries, a fixed share of them set to zero).
 * Exact multilinear-rank tensors (Tucker model, Eq. 1) for exact-recovery tests.
 * The small Gaussian matrices W_k^(n) whose Khatri-Rao product is the random
   test matrix Omega_n of the range finder (Sec. IV-A, step 1).  They are drawn
@@ -34,6 +36,7 @@ TAG_TUCKER = 5
 TAG_MASK = 6
 TAG_SKETCH_SHARED = 8
 TAG_REFINE = 9
+TAG_SPARSE_NN = 10
 
 OMEGA_SEED_XOR = 0x9E3779B97F4A7C15
 
@@ -77,6 +80,21 @@ def correlated_factor(r: np.random.Generator, I: int, R: int, rho: float,
 def cp_factors(shape, R: int, seed: int, dist: str = "normal", rho: float = 0.0):
     r = rng(seed, TAG_FACTORS)
     return [correlated_factor(r, I, R, rho, dist) for I in shape]
+
+
+def sparse_exponential_factors(shape, R: int, seed: int, mean: float = 10.0, zero_frac: float = 0.1):
+    """Nonnegative CP factors of the data model in Sec. V-A ("Simulations on
+    Nonnegative CPD"): entries i.i.d. exponential with the given mean, then
+    round(zero_frac * I * R) entries of each factor, chosen uniformly without
+    replacement, set to zero."""
+    out = []
+    for n, I in enumerate(shape):
+        r = rng(seed, TAG_SPARSE_NN, n)
+        A = r.exponential(mean, (I, R))
+        k = int(round(zero_frac * I * R))
+        A.reshape(-1)[r.choice(I * R, k, replace=False)] = 0.0
+        out.append(A)
+    return out
 
 
 def cp_dense(factors) -> np.ndarray:

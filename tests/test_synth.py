@@ -44,3 +44,15 @@ def test_device_sketch_keeps_shared_objects_as_one_tensor():
         for k in range(3):
             if k != n:
                 assert np.array_equal(Wd[n][k].numpy(), W[n][k])
+
+
+def test_sparse_exponential_factors_zero_share_and_mean():
+    A = synth.sparse_exponential_factors((200, 300), 10, 5, mean=10.0, zero_frac=0.1)
+    for I, a in zip((200, 300), A):
+        assert a.shape == (I, 10) and np.all(a >= 0.0)
+        assert int(np.sum(a == 0.0)) == round(0.1 * I * 10)
+        nz = a[a > 0.0]
+        # exponential(10): mean 10, std 10; nz has >= 1800 draws
+        assert abs(nz.mean() - 10.0) < 1.0
+    B = synth.sparse_exponential_factors((200, 300), 10, 5, mean=10.0, zero_frac=0.1)
+    assert all(np.array_equal(a, b) for a, b in zip(A, B))

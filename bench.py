@@ -40,13 +40,46 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def _code_without_comments(src: str) -> str:
+    """C++/CUDA source with its // and /* */ comments removed; string and
+    character literals are kept whole.  An edit of a comment alone then
+    leaves the kernel's hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def _kernel_source_sha(prec: str) -> str:
-    names = ["tc_sketch.cu", "tc_common.cuh"] if prec == "tc" else ["sketch_simt.cu"]
+    """Hash of the sketch kernel's code (comments excluded): the committed
+    ncu traffic figure applies only while it matches."""
+    return source_sha(["tc_sketch.cu", "tc_common.cuh"] if prec == "tc" else ["sketch_simt.cu"])
+
+
+def source_sha(names) -> str:
+    """First 16 hex digits of the SHA-256 of the named files under csrc/,
+    comments removed, in the given order."""
     h = hashlib.sha256()
     for n in names:
         p = os.path.join(ROOT, "paper_1412_1885_gb300", "csrc", n)
         if os.path.exists(p):
-            h.update(open(p, "rb").read())
+            h.update(_code_without_comments(open(p, encoding="utf-8").read()).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

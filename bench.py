@@ -345,7 +345,7 @@ def main():
     ap.add_argument("--train", type=int, default=2048, help="learned-init workload: training tensors")
     ap.add_argument("--eval", type=int, default=64, help="learned-init workload: held-out tensors")
     ap.add_argument("--nonneg-rule", default="ls", choices=["ls", "hals", "mu"],
-                    help="update rule of the nonnegative workloads: projected LS, HALS (Eq. 8), MU (Eq. 14)")
+                    help="update rule of the nonnegative workloads: projected LS, HALS (Eq. 8), MU (Eq. 15)")
     ap.add_argument("--sketch", default=DEFAULT_SKETCH, choices=["shared", "independent"],
                     help="sketch family: Khatri-Rao factors shared between the modes, or drawn per mode")
     args = ap.parse_args()

@@ -6,13 +6,13 @@
  *
  *   tucker_sketch   Z_n = Y_(n) Omega_n for every mode n in one pass over Y,
  *                   Omega_n = KRP_{k != n} W_k^(n) never formed (Sec. IV-A,
- *                   range-finder steps 1-2; Alg. 2; Eq. 21), then an
+ *                   range-finder steps 1-2; Alg. 2; Eq. 22), then an
  *                   orthonormal basis U_n of range(Z_n) (range-finder step 3;
- *                   Eq. 22 gives the Gram-based variant used in spirit here:
+ *                   Eq. 23 gives the Gram-based variant used in spirit here:
  *                   FP64 CholQR2).
  *   tucker_core     G = Y x_1 U_1^T ... x_N U_N^T (Alg. 2, TTM chain; Eq. 1).
  *   ffcp_als        CP-ALS on the core with the lift A_n = U_n B_n
- *                   (Sec. III-B, Alg. 1; Eqs. 9, 11-13, 16), unconstrained or
+ *                   (Sec. III-B, Alg. 1; Eqs. 9, 11-14, 17), unconstrained or
  *                   with projected nonnegative updates (P_+ of Eq. 8).
  *   ffcp_predict_init  learned initial core-space factors from a small MLP
  *                   (no counterpart in the paper; see the tdk_mlp section).
@@ -137,7 +137,7 @@ int tdk_tucker_check(const tdk_tucker_desc* desc);
 
 /*
  * tucker_sketch -- all-mode randomized range finder (Sec. IV-A; Alg. 2 lines
- * "Z = Y_(n) Omega" and "U = orth(Z)"; Eq. 21 for the blockwise sums).
+ * "Z = Y_(n) Omega" and "U = orth(Z)"; Eq. 22 for the blockwise sums).
  *
  *   Y      [I_1 x ... x I_N] in desc->dtype.
  *   W      array of N*N device pointers; W[n*N + k] (k != n) is the FP64
@@ -231,10 +231,10 @@ typedef struct {
   int max_sweeps;   /* >= 1                                                */
   double tol;       /* stop when |f_t - f_{t-1}| < tol * |f_{t-1}|, f the
                        fit of the core (Sec. V-A uses an absolute 1e-6)     */
-  int nonneg;       /* 0: LS update (Eq. 13); TDK_NONNEG_LS (1): projected
+  int nonneg;       /* 0: LS update (Eq. 14); TDK_NONNEG_LS (1): projected
                        nonnegative LS; TDK_NONNEG_HALS (2): column-wise
                        HALS (Eq. 8); TDK_NONNEG_MU (3): multiplicative
-                       update in the low-rank form (Eq. 14).  HALS and MU
+                       update in the low-rank form (Eq. 15).  HALS and MU
                        start each mode from A_n diag(lambda) and need the
                        persistent kernel (N >= 3, core fits on chip, no
                        time limit): otherwise TDK_ENOTSUP                  */
@@ -245,7 +245,7 @@ typedef struct {
   int reserved;
   double timeout_s; /* bound on the whole call, 0 = none; exceeded ->
                        TDK_ETIMEOUT with the last iterate in the outputs   */
-  double l1;        /* >= 0.  > 0: l1-regularised update of Eq. 15, the
+  double l1;        /* >= 0.  > 0: l1-regularised update of Eq. 16, the
                        LS solution for A_n soft-thresholded, S_c(x) =
                        sign(x) max(|x| - c, 0) with c = l1, then projected
                        if nonneg = TDK_NONNEG_LS.  The factors are updated
@@ -265,9 +265,9 @@ typedef struct {
 
 /*
  * ffcp_als -- FFCP (Alg. 1): CP-ALS on the core G with core-space factors
- * B_n = U_n^T A_n (Eq. 12); per mode H_n = G_(n) [KRP_{p != n} B_p]
- * (Eq. 11), T_n = HADAMARD_{p != n} B_p^T B_p (Eq. 9; A_p^T A_p for the
- * nonnegative form), B_n <- H_n T_n^-1 (Eq. 13; FP64 Cholesky, pseudo-inverse
+ * B_n = U_n^T A_n (Eq. 13); per mode H_n = G_(n) [KRP_{p != n} B_p]
+ * (Eq. 12), T_n = HADAMARD_{p != n} B_p^T B_p (Eq. 9; A_p^T A_p for the
+ * nonnegative form), B_n <- H_n T_n^-1 (Eq. 14; FP64 Cholesky, pseudo-inverse
  * with cutoff R*eps*lambda_max when a pivot is not above R*eps*max T_jj);
  * columns normalised to unit 2-norm with the norms in lambda.  Nonnegative
  * form: A_n <- max(0, U_n H_n T_n^-1), B_n <- U_n^T A_n.

@@ -3,11 +3,11 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 With orthonormal U_n, FFCP on Y~ = [[G; U]] is equivalent to CP of the core
-(Eq. 16): for every mode n
-  H_n = G_(n) [KRP_{p != n} B_p]                       (Alg. 1; Eq. 11)
+(Eq. 17): for every mode n
+  H_n = G_(n) [KRP_{p != n} B_p]                       (Alg. 1; Eq. 12)
   T_n = HADAMARD_{p != n} A_p^T A_p = ... B_p^T B_p     (Eq. 9)
-  B_n <- H_n T_n^{-1}                                  (Eq. 13 in core space)
-and finally A_n = U_n B_n (Eq. 12).  The textbook form on an explicit tensor
+  B_n <- H_n T_n^{-1}                                  (Eq. 14 in core space)
+and finally A_n = U_n B_n (Eq. 13).  The textbook form on an explicit tensor
 (Eq. 6) is the same function applied to Y~ itself, which the tests use to pin
 the core-space form.
 """
@@ -22,7 +22,7 @@ from .tucker import khatri_rao, unfold
 
 def mttkrp(G: np.ndarray, Bs, n: int) -> np.ndarray:
     """H_n = G_(n) [KRP_{p != n} B_p] with the Khatri-Rao product formed
-    (Alg. 1, "compute H"; Eq. 11).  Pinned by brute force in tests."""
+    (Alg. 1, "compute H"; Eq. 12).  Pinned by brute force in tests."""
     N = G.ndim
     return unfold(G, n) @ khatri_rao([Bs[p] for p in range(N) if p != n])
 
@@ -38,7 +38,7 @@ def hadamard_grams(Bs, n: int) -> np.ndarray:
 
 
 def solve_normal(H: np.ndarray, T: np.ndarray):
-    """X = H T^{-1} for symmetric positive semidefinite T (Eq. 6 / Eq. 13).
+    """X = H T^{-1} for symmetric positive semidefinite T (Eq. 6 / Eq. 14).
 
     Cholesky when every pivot exceeds R * eps * max_j T_jj; otherwise the
     pseudo-inverse from the eigendecomposition of T with cutoff
@@ -151,7 +151,7 @@ def hals_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
 
 
 def mu_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
-    """Multiplicative update in the low-rank form (Eq. 14):
+    """Multiplicative update in the low-rank form (Eq. 15):
         A <- A (*) P_+(M) (/) (A T),
     elementwise; an entry whose denominator is not positive becomes 0.
     Pinned: an exact nonnegative factor is a fixed point; on nonnegative data
@@ -165,7 +165,7 @@ def mu_rows(A0: np.ndarray, M: np.ndarray, T: np.ndarray) -> np.ndarray:
 
 
 def soft_threshold(X: np.ndarray, c: float) -> np.ndarray:
-    """S_c(x) = sign(x) max(|x| - c, 0), elementwise (Eq. 15): the minimiser
+    """S_c(x) = sign(x) max(|x| - c, 0), elementwise (Eq. 16): the minimiser
     of (z - x)^2 / 2 + c |z| (pinned by brute force)."""
     X = np.asarray(X, dtype=np.float64)
     return np.sign(X) * np.maximum(np.abs(X) - c, 0.0)
@@ -175,21 +175,21 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
                   l1: float = 0.0, clip: bool = True):
     """FFCP with projected nonnegative LS updates on the Tucker format.
 
-    For every mode (Alg. 1 with the LS rule of Eq. 13 followed by P_+ of Eq. 8):
-      H_n = G_(n) [KRP_{p != n} B_p]        with B_p = U_p^T A_p   (Eqs. 11, 12)
-      M_n = U_n H_n                          (~ Y_(n) B, Eq. 11)
+    For every mode (Alg. 1 with the LS rule of Eq. 14 followed by P_+ of Eq. 8):
+      H_n = G_(n) [KRP_{p != n} B_p]        with B_p = U_p^T A_p   (Eqs. 12, 13)
+      M_n = U_n H_n                          (~ Y_(n) B, Eq. 12)
       T_n = HADAMARD_{p != n} A_p^T A_p       (Eq. 9, the actual A_p)
       A_n <- max(0, M_n T_n^{-1}),  B_n <- U_n^T A_n
     Columns of A_n are scaled to unit norm (lambda); an all-zero column is
     replaced by the constant unit vector with lambda_r = 0.  The fit is taken
     against Y~ = [[G; U]]:  <Y~, [[A]]> = <G, [[B]]>, ||[[A]]||^2 from A's Grams.
 
-    rule "hals" (Eq. 8) and "mu" (Eq. 14) replace the projected solve by one
+    rule "hals" (Eq. 8) and "mu" (Eq. 15) replace the projected solve by one
     pass of `hals_rows` / `mu_rows` from the current iterate of the mode,
     A_n diag(lambda) (the model [[lambda; A]] with lambda on the factor being
     updated), with the same M_n and T_n.
 
-    l1 > 0 (rule "ls"): the l1-regularised update of Eq. 15, A_n <- S_c(A_n)
+    l1 > 0 (rule "ls"): the l1-regularised update of Eq. 16, A_n <- S_c(A_n)
     applied to the LS solution before the projection; clip=False drops the
     projection P_+ (the sparse but signed form).
 
@@ -248,7 +248,7 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
 
 
 def lift(Us, Bs, lam):
-    """A_n = U_n B_n (Eq. 12 / Eq. 16), lambda absorbed into A_N (Sec. II)."""
+    """A_n = U_n B_n (Eq. 13 / Eq. 17), lambda absorbed into A_N (Sec. II)."""
     A = [np.asarray(u, dtype=np.float64) @ np.asarray(b, dtype=np.float64) for u, b in zip(Us, Bs)]
     A[-1] = A[-1] * np.asarray(lam)[None, :]
     return A

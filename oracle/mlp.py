@@ -189,7 +189,7 @@ def _dloss_dO(O, S, R, T, alpha):
         if T is not None and alpha != 0.0:
             E = E + 2.0 * alpha * (M - cp_full(np.ones(T[s][0].shape[1]), T[s]))
         for n in range(N):
-            # d<E, [[B]]>/dB_n = E_(n) KRP_{p != n} B_p (Eq. 11 form)
+            # d<E, [[B]]>/dB_n = E_(n) KRP_{p != n} B_p (the Y_(n) B term of Eq. 5)
             others = [Bh[p] for p in range(N) if p != n]
             K = others[0]
             for P in others[1:]:

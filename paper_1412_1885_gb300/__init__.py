@@ -21,7 +21,7 @@ TDK_WRANKDEF, TDK_WNOCONV, TDK_WPINV = 1, 2, 4
 F64, F32, BF16 = 0, 1, 2
 PREC = {"simt": 0, "tc": 1}
 INIT = {"given": 0, "hosvd": 1}
-# nonnegative update rule: projected LS, HALS (Eq. 8), multiplicative (Eq. 14)
+# nonnegative update rule: projected LS, HALS (Eq. 8), multiplicative (Eq. 15)
 NONNEG = {False: 0, True: 1, "ls": 1, "hals": 2, "mu": 3}
 MAX_MODES = 8
 MAX_RANK = 64

@@ -1,4 +1,4 @@
-// FFCP: CP-ALS on the Tucker core (Sec. III-B, Alg. 1; Eqs. 9, 11-13, 16).
+// FFCP: CP-ALS on the Tucker core (Sec. III-B, Alg. 1; Eqs. 9, 11-14, 17).
 //
 // Per sweep, for every mode n (Gauss-Seidel order 1..N):
 //   H_n = G_(n) [KRP_{p != n} B_p]      (als_mttkrp: the Khatri-Rao product is
@@ -6,13 +6,13 @@
 //                                         multiplied by the product of the
 //                                         factor rows it touches, Sec. III-B)
 //   T_n = HADAMARD_{p != n} B_p^T B_p   (Eq. 9; A_p^T A_p for the nonneg form)
-//   B_n = H_n T_n^{-1}                  (Eq. 13 in core space; FP64 Cholesky,
+//   B_n = H_n T_n^{-1}                  (Eq. 14 in core space; FP64 Cholesky,
 //                                         pseudo-inverse on breakdown)
 //   lambda = column norms, B_n scaled to unit columns, Gram_n refreshed
 // then the fit from the Gram identities; the sweep loop runs on the device
 // (captured once as a CUDA graph) and the host checks the done flag every
 // `check_every` sweeps.  Nonnegative form: A_n = max(0, U_n H_n T_n^{-1}),
-// B_n = U_n^T A_n (Eq. 12; P_+ of Eq. 8).
+// B_n = U_n^T A_n (Eq. 13; P_+ of Eq. 8).
 #include <chrono>
 #include <cmath>
 

@@ -1,4 +1,4 @@
-// FFCP sweep loop as ONE persistent cooperative kernel (Alg. 1, Eqs. 9, 11-13).
+// FFCP sweep loop as ONE persistent cooperative kernel (Alg. 1, Eqs. 9, 12-14).
 //
 // Every CTA holds all normalised factors B_p and their Grams in shared memory.
 // Per mode n:
@@ -8,7 +8,7 @@
 //      from the core slice G[.., i, ..] staged in shared memory, contracting
 //      one mode at a time (the last other mode first as a small GEMM, then
 //      weighted sums over the others), and solves its rows of B_n = H_n T_n^{-1}
-//      in FP64 (Eq. 13);
+//      in FP64 (Eq. 14);
 //   3. grid barrier; every CTA reads the new rows, computes lambda, the
 //      normalised factor and its Gram -- identically, in the same order.
 // Nonnegative form: rows of H_n, barrier, rows of A_n = max(0, U_n H_n T_n^{-1})
@@ -49,9 +49,9 @@ struct PState {
 template <class T>
 struct PArgs {
   int N, R, nonneg, max_sweeps;
-  int nn_rule;                  // nonneg: 0 projected LS, 1 HALS (Eq. 8), 2 multiplicative (Eq. 14)
+  int nn_rule;                  // nonneg: 0 projected LS, 1 HALS (Eq. 8), 2 multiplicative (Eq. 15)
   int clip;                     // nonneg path: project onto x >= 0 (0: the signed l1 form)
-  double l1;                    // soft threshold of the LS rows (Eq. 15), 0 = none
+  double l1;                    // soft threshold of the LS rows (Eq. 16), 0 = none
   double tol;
   int Rt[TDK_MAX_MODES];
   int64_t I[TDK_MAX_MODES];

@@ -1,6 +1,6 @@
 // Orthonormal basis of every sketch Z_n (Sec. IV-A step 3; Alg. 2
 // "compute U as an orthonormal basis of Z").  The paper's distributed variant
-// (Eq. 22) forms the Gram sum_s Z_s^T Z_s from row blocks and whitens it;
+// (Eq. 23) forms the Gram sum_s Z_s^T Z_s from row blocks and whitens it;
 // here the same row-block Gram feeds a Cholesky factor instead of an EVD
 // (CholQR), applied twice (CholQR2) so that the result is orthonormal to
 // working precision.  All arithmetic is FP64.

@@ -14,7 +14,7 @@
 //                 by the Gram identities (no model tensor is formed):
 //                 ||[[B]]||^2 = 1^T (HADAMARD_n B_n^T B_n) 1 (Eq. 9 form) and
 //                 <S, [[B]]> = sum(B_1 * H_1), H_1 = S_(1) KRP_{p != 1} B_p
-//                 (Eq. 11 form).  T = V_n^T B*_n: converged FFCP factors.
+//                 (the Y_(n) B term of Eq. 5).  T = V_n^T B*_n: converged FFCP factors.
 //   training      back-propagation through the same GEMM kernel, Adam.
 //   inference     B_n = V_n Bhat_n, FP64, ready as ffcp_als's B_io.
 #include <cmath>

@@ -1,7 +1,7 @@
 // All-mode randomized sketch on CUDA cores (the plain form), and the first
 // contraction of the core chain in the same form.
 //
-// Sketch (Sec. IV-A step 2, Alg. 2, Eq. 21): for every mode n
+// Sketch (Sec. IV-A step 2, Alg. 2, Eq. 22): for every mode n
 //   Z_n[i_n, r] = sum_{i != i_n} y[i] * prod_{k != n} W_k^(n)[i_k, r].
 // Y is viewed as M rows x L columns (row = (i_1..i_{N-1}), column = i_N, the
 // contiguous mode).  One pass over Y computes, per row tile:
@@ -10,7 +10,7 @@
 //                Z_n[i_n(row), r] += P[row, c] * prod_{k<N, k != n} W_k^(n)[i_k, r];
 //   Z_N[col, r] += sum_row Y[row, col] * K[row, r],  K = KRP_{k<N} W_k^(N).
 // Partial sums live per CTA (the CTA-level blocks play the role of the
-// paper's sub-tensor workers, Eq. 21) and are reduced in a fixed order in
+// paper's sub-tensor workers, Eq. 22) and are reduced in a fixed order in
 // FP64, so results are bitwise reproducible.
 #include "tdk_internal.cuh"
 

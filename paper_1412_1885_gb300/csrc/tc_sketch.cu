@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) forms of the two passes over Y.
 //
-// SKETCH (Sec. IV-A step 2; Alg. 2; Eq. 21), N >= 3.  Y is read as a 3-D
+// SKETCH (Sec. IV-A step 2; Alg. 2; Eq. 22), N >= 3.  Y is read as a 3-D
 // array [P][J][L] with L = I_N (contiguous), J = I_{N-1}, P = prod_{k<N-1} I_k.
 // A tile is 128 consecutive j (one p) x 128 consecutive columns, staged by TMA
 // into shared memory with the 128-byte swizzle, and used twice:
@@ -15,7 +15,7 @@
 // The epilogue turns D1 into the sketches of modes < N: mode N-1 (the tile's
 // row mode) accumulates per TMEM lane across p; modes < N-1 are constant over
 // the tile and need a 128-lane reduction.  Each work unit (j-tile, column
-// range, p-range) writes its own partial block (the blockwise sums of Eq. 21);
+// range, p-range) writes its own partial block (the blockwise sums of Eq. 22);
 // a fixed-order compensated FP32 reduction produces Z.
 //
 // CORE (Alg. 2, the first "Y <- Y x_n U^T", contiguous mode): X_1 = Y_(rows) U_N

@@ -542,7 +542,7 @@ def test_host_data_through_the_abi_copies(tdk, ctx):
 @pytest.mark.parametrize("rule", ["hals", "mu"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_nonneg_rules_match_oracle(tdk, ctx, rule, dtype):
-    """HALS (Eq. 8) and multiplicative (Eq. 14) nonnegative FFCP in the
+    """HALS (Eq. 8) and multiplicative (Eq. 15) nonnegative FFCP in the
     persistent kernel against the oracle's rules on the same 4-way core."""
     shape, ranks, p, R = (24, 22, 20, 18), (5, 5, 5, 5), 3, 4
     Y, W, A = small_problem(shape, ranks, p, seed=7, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
@@ -585,7 +585,7 @@ def test_nonneg_rules_need_the_persistent_form(tdk, ctx):
 @pytest.mark.parametrize("clip", [False, True])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_l1_rule_matches_oracle(tdk, ctx, clip, dtype):
-    """The l1-regularised update of Eq. 15 (soft threshold of the LS rows,
+    """The l1-regularised update of Eq. 16 (soft threshold of the LS rows,
     signed or projected) against the oracle on the same core."""
     shape, ranks, p, R = (24, 22, 20), (5, 5, 5), 3, 4
     dist = "uniform" if clip else "normal"

@@ -209,7 +209,7 @@ def test_solve_normal_cholesky_and_pinv():
 
 
 def test_ffcp_core_space_equals_textbook_als_on_full_tensor():
-    """Eq. 16: with orthonormal U_n, ALS on Y~ = [[G; U]] from A0 = U B0 gives
+    """Eq. 17: with orthonormal U_n, ALS on Y~ = [[G; U]] from A0 = U B0 gives
     A_t = U B_t at every sweep (the core-space iteration lifted)."""
     G = _rand((4, 5, 3), 1)
     U = [_orth(9, 4, 2), _orth(8, 5, 3), _orth(7, 3, 4)]
@@ -281,7 +281,7 @@ def test_nonneg_ffcp_recovers_noise_free_nonnegative_cp():
 
 @pytest.mark.parametrize("rule,sweeps,tol", [("hals", 300, 1e-8), ("mu", 5000, 1e-5)])
 def test_nonneg_rules_recover_noise_free_nonnegative_cp(rule, sweeps, tol):
-    # the HALS (Eq. 8) and multiplicative (Eq. 14) updates reach the exact
+    # the HALS (Eq. 8) and multiplicative (Eq. 15) updates reach the exact
     # nonnegative CP model of a noise-free tensor through its Tucker format
     shape, R = (30, 28, 26), 3
     A = synth.cp_factors(shape, R, 8, dist="uniform")
@@ -345,7 +345,7 @@ def test_mu_fixed_point_and_monotone_on_nonnegative_data():
 
 
 def test_soft_threshold_is_the_l1_proximal_map():
-    # S_c(x) minimises (z - x)^2 / 2 + c |z| (Eq. 15): brute force on a grid
+    # S_c(x) minimises (z - x)^2 / 2 + c |z| (Eq. 16): brute force on a grid
     grid = np.linspace(-6.0, 6.0, 120001)
     for x in (-3.7, -0.4, 0.0, 0.25, 1.3, 4.9):
         for c in (0.0, 0.5, 2.0):

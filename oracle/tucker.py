@@ -9,6 +9,11 @@ The method computes, for every mode n from the ORIGINAL tensor Y,
   G   = Y x_1 U_1^T x_2 ... x_N U_N^T                            (Alg. 2, TTM)
 i.e. the range-finder sketch of every mode taken in one pass over Y with a
 Khatri-Rao structured Gaussian test matrix, then the Tucker core (Eq. 1).
+
+The forms the paper prints are here too, for comparison: the range finder
+with a dense Gaussian Omega (`rand_tucker_dense`), Alg. 2's sequential sketch
+on the shrinking tensor (`rand_tucker_seq`), the Gram-based basis of Eq. 23
+(`evd_orth`), and RandTucker2i (Alg. 3).
 """
 from __future__ import annotations
 
@@ -174,6 +179,57 @@ def rand_tucker(Y: np.ndarray, W) -> dict:
     U = [q for q, _ in QR]
     G = tucker_core(Y, U)
     return {"Z": Z, "U": U, "R": [r for _, r in QR], "G": G, "normY2": nY2}
+
+
+def evd_orth(Z: np.ndarray, slabs: int = 1) -> np.ndarray:
+    """Orthonormal basis of range(Z) by the Gram route of Sec. IV-B (Eq. 23):
+    the Gram sum_s Z_s^T Z_s over `slabs` row blocks Z_s of Z has the
+    eigendecomposition V Sigma V^T (eigenvalues decreasing), and every block
+    of the basis is U_s = Z_s V Sigma^{-1/2}.  Eq. 23 divides by Sigma^{1/2},
+    so Z must have full column rank (ValueError otherwise).  Pinned: U^T U = I,
+    the projector U U^T equals that of the Householder basis, and the slab
+    count changes only rounding."""
+    Z = np.asarray(Z, dtype=np.float64)
+    blocks = np.array_split(Z, slabs, axis=0)
+    C = np.zeros((Z.shape[1], Z.shape[1]))
+    for Zs in blocks:
+        C += Zs.T @ Zs
+    w, V = np.linalg.eigh(C)
+    order = np.argsort(-w, kind="stable")
+    w, V = w[order], V[:, order]
+    if not w[-1] > Z.shape[1] * np.finfo(np.float64).eps * w[0]:
+        raise ValueError("the Gram route needs Z of full column rank")
+    return np.vstack([Zs @ (V / np.sqrt(w)[None, :]) for Zs in blocks])
+
+
+def rand_tucker_dense(Y: np.ndarray, Omegas) -> dict:
+    """All-mode randomized Tucker with the dense Gaussian test matrices of the
+    range finder as printed (Sec. IV-A, step 1): Z_n = Y_(n) Omega_n with
+    Omega_n of (prod_{k != n} I_k) x Rt_n given in full, every Z_n from the
+    original Y, Householder bases, then the core.  The method's own sketch
+    replaces Omega_n by a Khatri-Rao product; this form measures what that
+    costs.  Pinned: exact recovery of exact multilinear-rank tensors."""
+    Y = np.asarray(Y, dtype=np.float64)
+    U = [householder_qr(unfold(Y, n) @ np.asarray(Omegas[n], dtype=np.float64))[0] for n in range(Y.ndim)]
+    return {"U": U, "G": tucker_core(Y, U)}
+
+
+def rand_tucker_seq(Y: np.ndarray, Omegas, orth: str = "qr") -> dict:
+    """Alg. 2 as printed: for n = 1..N in order, Z_n = Y_(n) Omega_n with a
+    dense Gaussian Omega_n, U_n an orthonormal basis of Z_n, then Y <- Y x_n
+    U_n^T (mode n shrinks to Rt_n before mode n + 1 is sketched); the last Y
+    is the core.  Omega_n therefore has prod_{k<n} Rt_k prod_{k>n} I_k rows.
+    orth "qr" takes the Householder basis (step 3's "e.g. QR"), "evd" the Gram
+    route of Eq. 23.  Pinned: exact recovery, and the core equals the TTM
+    chain of the original Y with the same factors."""
+    X = np.asarray(Y, dtype=np.float64)
+    U = []
+    for n in range(X.ndim):
+        Z = unfold(X, n) @ np.asarray(Omegas[n], dtype=np.float64)
+        Un = householder_qr(Z)[0] if orth == "qr" else evd_orth(Z)
+        U.append(Un)
+        X = ttm(X, Un, n)
+    return {"U": U, "G": X}
 
 
 def refine_pass(Y: np.ndarray, Us, W) -> list:

@@ -37,6 +37,7 @@ TAG_MASK = 6
 TAG_SKETCH_SHARED = 8
 TAG_REFINE = 9
 TAG_SPARSE_NN = 10
+TAG_DENSE_OMEGA = 11
 
 OMEGA_SEED_XOR = 0x9E3779B97F4A7C15
 
@@ -171,6 +172,22 @@ def sketch_matrices(shape, Rt, seed: int, shared: bool = False):
                 row.append(round_bf16(rng(base, TAG_SKETCH, n, k).standard_normal((shape[k], Rt[n]))))
         W.append(row)
     return W
+
+
+def dense_test_matrices(shape, Rt, seed: int, sequential: bool = False):
+    """Dense Gaussian test matrices Omega_n, i.i.d. N(0,1), for the range
+    finder as printed (Sec. IV-A, step 1): prod_{k != n} I_k rows for the
+    all-mode sketch, or prod_{k<n} Rt_k prod_{k>n} I_k rows for Alg. 2's
+    sequential form (modes before n already shrunk); Rt_n columns."""
+    N = len(shape)
+    out = []
+    for n in range(N):
+        rows = 1
+        for k in range(N):
+            if k != n:
+                rows *= Rt[k] if (sequential and k < n) else shape[k]
+        out.append(rng(seed, TAG_DENSE_OMEGA, n, int(sequential)).standard_normal((rows, Rt[n])))
+    return out
 
 
 def refine_matrices(Rt, seed: int, it: int):

@@ -25,13 +25,13 @@ from .tucker import (unfold, fold, khatri_rao, sketch, sketch_row, householder_q
                      ttm, tucker_core, rand_tucker, tucker_full, norm2, hosvd_factors, refine_pass,
                      rand_tucker_2i, evd_orth, rand_tucker_dense, rand_tucker_seq)
 from .cpals import (mttkrp, hadamard_grams, cp_full, cp_als, cp_als_nonneg, core_fit,
-                    lift, congruence, solve_normal, hosvd_init, hals_rows, mu_rows, soft_threshold)
+                    lift, congruence, sir_db, solve_normal, hosvd_init, hals_rows, mu_rows, soft_threshold)
 from . import mlp
 
 __all__ = [
     "unfold", "fold", "khatri_rao", "sketch", "sketch_row", "householder_qr", "ttm",
     "tucker_core", "rand_tucker", "hosvd_factors", "refine_pass", "rand_tucker_2i", "evd_orth",
     "rand_tucker_dense", "rand_tucker_seq", "tucker_full", "norm2", "mttkrp", "hadamard_grams",
-    "cp_full", "cp_als", "cp_als_nonneg", "core_fit", "lift", "congruence", "solve_normal",
+    "cp_full", "cp_als", "cp_als_nonneg", "core_fit", "lift", "congruence", "sir_db", "solve_normal",
     "hosvd_init", "hals_rows", "mu_rows", "soft_threshold", "mlp",
 ]

@@ -28,7 +28,8 @@ def mttkrp(G: np.ndarray, Bs, n: int) -> np.ndarray:
 
 
 def hadamard_grams(Bs, n: int) -> np.ndarray:
-    """T_n = HADAMARD_{p != n} B_p^T B_p (Eq. 9)."""
+    """T_n = HADAMARD_{p != n} B_p^T B_p (Eq. 9).  Pinned: equals the Gram of
+    the explicit Khatri-Rao product of the other factors."""
     R = Bs[0].shape[1]
     T = np.ones((R, R))
     for p, B in enumerate(Bs):
@@ -44,7 +45,8 @@ def solve_normal(H: np.ndarray, T: np.ndarray):
     pseudo-inverse from the eigendecomposition of T with cutoff
     R * eps * lambda_max (the paper writes the inverse; both thresholds are
     this implementation's reading for a singular Hadamard product of Grams).
-    Returns (X, used_pinv).
+    Returns (X, used_pinv).  Pinned: X T = H on an SPD T; LAPACK's pinv on a
+    singular one.
     """
     R = T.shape[0]
     L = np.zeros_like(T)
@@ -69,7 +71,7 @@ def solve_normal(H: np.ndarray, T: np.ndarray):
 
 
 def cp_full(lam, Bs) -> np.ndarray:
-    """Dense [[lambda; B_1, ..., B_N]] (Eq. 2)."""
+    """Dense [[lambda; B_1, ..., B_N]] (Eq. 2).  Pinned: brute-force sums."""
     Bs = [np.asarray(b, dtype=np.float64) for b in Bs]
     shape = tuple(b.shape[0] for b in Bs)
     R = Bs[0].shape[1]
@@ -90,7 +92,8 @@ def _normalise(B: np.ndarray):
 
 def core_fit(normG2: float, inner: float, model2: float) -> float:
     """Fit = 1 - ||X - X^||_F / ||X||_F (Sec. III-B) from the identity
-    ||X - X^||^2 = ||X||^2 - 2 <X, X^> + ||X^||^2."""
+    ||X - X^||^2 = ||X||^2 - 2 <X, X^> + ||X^||^2.  Pinned: against the
+    explicit residual of a converged run."""
     res2 = max(0.0, normG2 - 2.0 * inner + model2)
     return 1.0 - math.sqrt(res2) / math.sqrt(normG2)
 
@@ -103,6 +106,8 @@ def cp_als(G: np.ndarray, B_init, max_sweeps: int = 1000, tol: float = 1e-9):
     After each sweep the fit is evaluated from the last mode's H and the
     Grams; the loop stops when |f_t - f_{t-1}| < tol * |f_{t-1}| or after
     max_sweeps.  Returns dict(B=normalised factors, lam, fit, sweeps, history).
+    Pinned: textbook ALS on the explicit Y~ (Eq. 17), exact recovery of
+    noise-free CP tensors, the fit of Table II and the noise floor.
     """
     G = np.asarray(G, dtype=np.float64)
     N = G.ndim
@@ -248,7 +253,8 @@ def cp_als_nonneg(G: np.ndarray, Us, A_init, max_sweeps: int = 1000, tol: float 
 
 
 def lift(Us, Bs, lam):
-    """A_n = U_n B_n (Eq. 13 / Eq. 17), lambda absorbed into A_N (Sec. II)."""
+    """A_n = U_n B_n (Eq. 13 / Eq. 17), lambda absorbed into A_N (Sec. II).
+    Pinned: exact recovery of noise-free CP tensors by explicit residual."""
     A = [np.asarray(u, dtype=np.float64) @ np.asarray(b, dtype=np.float64) for u, b in zip(Us, Bs)]
     A[-1] = A[-1] * np.asarray(lam)[None, :]
     return A
@@ -257,7 +263,8 @@ def lift(Us, Bs, lam):
 def hosvd_init(G: np.ndarray, R: int):
     """Leading R left singular vectors of G_(n) for every n (HOSVD of the core,
     Sec. II), each column's sign fixed so its largest-magnitude entry is
-    positive.  Needs R <= R_n."""
+    positive.  Needs R <= R_n.  Pinned: spans the leading eigenvectors of
+    G_(n) G_(n)^T."""
     out = []
     for n in range(G.ndim):
         Un, _, _ = np.linalg.svd(unfold(G, n), full_matrices=False)
@@ -272,7 +279,8 @@ def hosvd_init(G: np.ndarray, R: int):
 def congruence(A_true, A_est) -> float:
     """Factor congruence after permutation / scale alignment: columns are
     matched by the Hungarian method on prod_n |cos(a_nr, a^_ns)| and the
-    minimum over matched pairs is returned."""
+    minimum over matched pairs is returned.  Pinned: 1 under column
+    permutation and scaling; cos(theta) for one column turned by theta."""
     from scipy.optimize import linear_sum_assignment
 
     R = A_true[0].shape[1]

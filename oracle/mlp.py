@@ -34,10 +34,13 @@ BF16 storage (the `bf16=True` form): the input x, the weights and the stored
     store them; all arithmetic between those points is exact here (FP64).
 
 Pins (tests/test_oracle_pins.py): central finite differences of `loss`
-against `loss_grad` in the exact form; the loss against a direct evaluation
+against `loss_grad` in the exact form (which covers `forward`, `gelu_grad`
+and the parameter layout of `unpack`); the loss against a direct evaluation
 of the Gram-identity formula; the invariance of `canonicalise` under a change
-of Tucker basis (U_n -> U_n Q_n, G -> G x_n Q_n^T); `gelu` against closed
-forms and limits; Adam against its closed form for a constant gradient.
+of Tucker basis (U_n -> U_n Q_n, G -> G x_n Q_n^T); for an exact CP core,
+[[canonical_target]] equals the canonical core and `decanonicalise` undoes
+the rotation; `network_input` has unit RMS; `gelu` against closed forms and
+limits; Adam against its closed form for a constant gradient.
 """
 from __future__ import annotations
 

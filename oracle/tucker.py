@@ -21,7 +21,8 @@ import numpy as np
 
 
 def norm2(Y) -> float:
-    """||Y||_F^2 (used by the fit, Sec. III-B)."""
+    """||Y||_F^2 (used by the fit, Sec. III-B).  Pinned: the explicit sum of
+    squares in the sketch's brute-force test."""
     Y = np.asarray(Y, dtype=np.float64)
     return float(np.sum(Y * Y))
 
@@ -33,7 +34,8 @@ def unfold(Y: np.ndarray, n: int) -> np.ndarray:
 
 
 def fold(M: np.ndarray, n: int, shape) -> np.ndarray:
-    """Inverse of unfold for a tensor of the given shape."""
+    """Inverse of unfold for a tensor of the given shape.  Pinned: the
+    round trip of the index-loop unfolding test, and through the TTM pins."""
     shape = list(shape)
     lead = [shape[n]] + shape[:n] + shape[n + 1:]
     return np.moveaxis(M.reshape(lead), 0, n)
@@ -73,7 +75,8 @@ def sketch_row(slab: np.ndarray, n: int, W, chunk: int = 32) -> np.ndarray:
     """One row Z_n[i, :] from the slab Y[..., i_n = i, ...] (shape: the other
     modes in order).  Same definition as `sketch`; Omega_n is formed a block of
     its rows at a time (the first remaining index in chunks) so that rows of
-    full-size problems fit in host memory.
+    full-size problems fit in host memory.  Pinned: equals the rows of the
+    brute-force-pinned `sketch`.
     """
     slab = np.asarray(slab, dtype=np.float64)
     N = slab.ndim + 1
@@ -137,7 +140,9 @@ def ttm(Y: np.ndarray, U: np.ndarray, n: int) -> np.ndarray:
 
 
 def tucker_core(Y: np.ndarray, Us) -> np.ndarray:
-    """G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2, final core; Eq. 1)."""
+    """G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2, final core; Eq. 1).
+    Pinned: recovers the core of an exact Tucker tensor in any mode order;
+    Pythagoras ||Y - [[G; U]]||^2 = ||Y||^2 - ||G||^2."""
     G = np.asarray(Y, dtype=np.float64)
     for n, U in enumerate(Us):
         G = ttm(G, U, n)
@@ -145,7 +150,8 @@ def tucker_core(Y: np.ndarray, Us) -> np.ndarray:
 
 
 def tucker_full(G: np.ndarray, Us) -> np.ndarray:
-    """[[G; U_1, ..., U_N]] = G x_1 U_1 ... x_N U_N (Eq. 1)."""
+    """[[G; U_1, ..., U_N]] = G x_1 U_1 ... x_N U_N (Eq. 1).  Pinned with
+    `tucker_core` (exact Tucker tensors, Pythagoras)."""
     X = np.asarray(G, dtype=np.float64)
     for n, U in enumerate(Us):
         shape = list(X.shape)
@@ -157,7 +163,9 @@ def tucker_full(G: np.ndarray, Us) -> np.ndarray:
 def hosvd_factors(Y: np.ndarray, ranks):
     """HOSVD factors: the leading R_n left singular vectors of every Y_(n)
     (Sec. II).  The full-tensor SVD is exactly the cost the randomized method
-    avoids; the oracle keeps it as the deterministic reference compression."""
+    avoids; the oracle keeps it as the deterministic reference compression.
+    Pinned: exact recovery of exact multilinear-rank tensors, and the
+    Eckart-Young residual against the eigenvalues of Y_(n) Y_(n)^T."""
     out = []
     for n, Rn in enumerate(ranks):
         Un, _, _ = np.linalg.svd(unfold(Y, n), full_matrices=False)
@@ -173,6 +181,9 @@ def rand_tucker(Y: np.ndarray, W) -> dict:
     the tensor already projected on modes < n; here every Z_n comes from the
     original Y (one pass for all modes), with Omega_n a Khatri-Rao product of
     small Gaussians instead of a dense Gaussian matrix.
+    Pinned: exact recovery of exact multilinear-rank tensors (independent and
+    shared sketch families); its accuracy against the printed forms is
+    measured in the tests.
     """
     Z, nY2 = sketch(Y, W)
     QR = [householder_qr(z) for z in Z]

@@ -31,6 +31,7 @@ def test_unfold_matches_index_loops(shape):
             for k in others:  # row-major over the remaining modes, slowest first
                 col = col * shape[k] + idx[k]
             assert M[idx[n], col] == Y[idx]
+        assert np.array_equal(oracle.fold(M, n, shape), Y)
 
 
 def test_khatri_rao_entries_and_gram_identity():
@@ -248,6 +249,54 @@ def test_accuracy_cost_of_the_one_pass_khatri_rao_sketch():
     assert m["shared"] <= 1.10 * m["krp"], m
     assert m["seq"] <= 0.85 * min(m["krp"], m["dense"]), m
     assert m["2i"] < m["seq"] and m["hosvd"] < m["2i"], m
+
+
+def test_hosvd_factors_exact_recovery_and_eckart_young():
+    # exact multilinear rank: HOSVD reproduces Y; on any tensor the mode-n
+    # residual ||(I - U U^T) Y_(n)||^2 is the sum of the trailing eigenvalues
+    # of Y_(n) Y_(n)^T (Eckart-Young), computed here by eigh, not by SVD
+    Y = synth.tucker_dense((12, 11, 10), (3, 4, 2), 6)
+    U = oracle.hosvd_factors(Y, [3, 4, 2])
+    assert np.linalg.norm(tucker_full(tucker_core(Y, U), U) - Y) < 1e-12 * np.linalg.norm(Y)
+    X = _rand((9, 8, 7), 12)
+    for n, Rn in enumerate(oracle.hosvd_factors(X, [4, 3, 5])):
+        M = unfold(X, n)
+        w = np.sort(np.linalg.eigvalsh(M @ M.T))[::-1]
+        res = np.sum((M - Rn @ (Rn.T @ M)) ** 2)
+        assert math.isclose(res, float(np.sum(w[Rn.shape[1]:])), rel_tol=1e-10)
+        assert np.allclose(Rn.T @ Rn, np.eye(Rn.shape[1]), atol=1e-13)
+
+
+def test_cp_full_brute_force_and_hadamard_grams_identity():
+    lam = np.array([0.5, -2.0])
+    Bs = [_rand((3, 2), 1), _rand((4, 2), 2), _rand((2, 2), 3)]
+    X = oracle.cp_full(lam, Bs)
+    for i, j, k in itertools.product(range(3), range(4), range(2)):
+        ref = sum(lam[r] * Bs[0][i, r] * Bs[1][j, r] * Bs[2][k, r] for r in range(2))
+        assert math.isclose(X[i, j, k], ref, rel_tol=1e-13, abs_tol=1e-14)
+    # Eq. 9: the Hadamard product of the other Grams is the Gram of their
+    # Khatri-Rao product (khatri_rao is pinned by brute force above)
+    for n in range(3):
+        K = khatri_rao([Bs[p] for p in range(3) if p != n])
+        assert np.allclose(oracle.hadamard_grams(Bs, n), K.T @ K, rtol=1e-13, atol=1e-13)
+
+
+def test_congruence_invariances_and_planted_angle():
+    A = [_rand((20, 3), 1), _rand((15, 3), 2), _rand((10, 3), 3)]
+    perm = [1, 2, 0]
+    sc = np.array([2.0, -0.5, 7.0])
+    Ap = [a[:, perm] * sc[None, :] for a in A]
+    assert math.isclose(oracle.congruence(A, Ap), 1.0, rel_tol=1e-12)
+    # turn column 1 of mode 0 by theta towards a unit vector orthogonal to it:
+    # the matched product for that column is |cos theta|, the others stay 1
+    theta = 0.3
+    a = A[0][:, 1] / np.linalg.norm(A[0][:, 1])
+    w = _rand(20, 4)
+    w -= a * (a @ w)
+    w /= np.linalg.norm(w)
+    B0 = A[0].copy()
+    B0[:, 1] = np.linalg.norm(A[0][:, 1]) * (math.cos(theta) * a + math.sin(theta) * w)
+    assert math.isclose(oracle.congruence(A, [B0, A[1], A[2]]), math.cos(theta), rel_tol=1e-12)
 
 
 def test_mttkrp_matches_brute_force():
@@ -657,6 +706,24 @@ def test_canonical_core_independent_of_tucker_basis():
     for n in range(3):
         back = ttm(back, V1[n].T, n)
     assert np.abs(back - G).max() < 1e-10 * np.abs(G).max()
+
+
+def test_canonical_target_reproduces_the_canonical_core_of_an_exact_cp_core():
+    # G = [[B]] exactly: [[T]] with T = canonical_target(B) equals S, and
+    # decanonicalise(T) undoes the rotation (V_n is square orthogonal)
+    r = np.random.default_rng(4)
+    Rt, R = 4, 3
+    B = [r.standard_normal((Rt, R)) for _ in range(3)]
+    G = oracle.cp_full(np.ones(R), B)
+    S, V, nrm = omlp.canonicalise(G, [r.standard_normal(Rt) for _ in range(3)])
+    T = omlp.canonical_target(B, V, nrm)
+    assert np.allclose(oracle.cp_full(np.ones(R), T), S, atol=1e-13)
+    Bb = omlp.decanonicalise(T, V)
+    assert np.allclose(Bb[0], B[0], atol=1e-13) and np.allclose(Bb[1], B[1], atol=1e-13)
+    assert np.allclose(Bb[2] * nrm, B[2], atol=1e-12)
+    # network_input scales the canonical core to unit RMS
+    x = omlp.network_input(S[None])
+    assert math.isclose(float(np.sqrt(np.mean(x * x))), 1.0, rel_tol=1e-13)
 
 
 def test_gelu_closed_forms():

@@ -555,6 +555,26 @@ def test_ffcp_fit_within_paper_table2_band():
     assert min(abs(f - floor) for f in fits) < 0.05, (fits, floor)
 
 
+def test_order6_ffcp_reaches_paper_table2_band_and_noise_floor():
+    """Table II, third column (N=6, I=20, R=5, SNR 10 dB): FFCP fit 93.4 +-
+    8.6 %.  At order 6 the stop rule of Sec. V-A (fit change below 1e-6)
+    ends some runs on a plateau, which the paper's spread reflects; this pin
+    runs one seeded case to convergence (relative change below 1e-12) and
+    requires the paper's band (mean - 2 std .. 100 %) and the first-order
+    noise floor within 0.05 points.  Compression: HOSVD with R_n = R + 2."""
+    N, I, R, mean, std, _t = _golden("paper_table2_cpd_ffcp.txt")[2]
+    N, I, R, mean, std = int(N), int(I), int(R), float(mean), float(std)
+    A = synth.cp_factors((I,) * N, R, 300)
+    Ystar = synth.cp_dense(A)
+    Y = synth.add_noise(Ystar, 10.0, 300)
+    U = oracle.hosvd_factors(Y, [R + 2] * N)
+    G = tucker_core(Y, U)
+    als = oracle.cp_als(G, synth.init_factors([R + 2] * N, R, 0), max_sweeps=3000, tol=1e-12)
+    f = _fit_pct(Ystar, oracle.cp_full(np.ones(R), oracle.lift(U, als["B"], als["lam"])))
+    assert mean - 2 * std <= f <= 100.0, f
+    assert abs(f - _noise_floor_fit((I,) * N, R, 10.0)) < 0.05, f
+
+
 @pytest.mark.parametrize("rule", ["hals", "mu"])
 def test_nonneg_ffcp_fit_within_paper_table3_band(rule):
     """Table III (nonnegative CPD of synthetic data), N=3 I=200 R=10 at SNR

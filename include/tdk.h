@@ -241,10 +241,12 @@ typedef struct {
   int init;         /* TDK_INIT_GIVEN: start from B_io (nonneg or l1: A_io);
                        TDK_INIT_HOSVD: leading R left singular vectors of
                        every G_(n) (nonneg: their magnitudes lifted)        */
-  int check_every;  /* sweeps per convergence check on the host (0 = 8)    */
+  int check_every;  /* sweeps per convergence check on the host (<= 0: 8) */
   int reserved;
-  double timeout_s; /* bound on the whole call, 0 = none; exceeded ->
-                       TDK_ETIMEOUT with the last iterate in the outputs   */
+  double timeout_s; /* bound on the whole call in seconds; <= 0 or NaN =
+                       none; exceeded -> TDK_ETIMEOUT with the last
+                       iterate in the outputs.  A limit selects the
+                       one-kernel-per-step form                            */
   double l1;        /* >= 0.  > 0: l1-regularised update of Eq. 16, the
                        LS solution for A_n soft-thresholded, S_c(x) =
                        sign(x) max(|x| - c, 0) with c = l1, then projected

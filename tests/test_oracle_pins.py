@@ -328,6 +328,26 @@ def test_solve_normal_cholesky_and_pinv():
     assert np.allclose(X2, H @ np.linalg.pinv(T2, rcond=4 * np.finfo(float).eps), atol=1e-8)
 
 
+def test_als_mode_update_is_the_least_squares_solution():
+    # Eq. 6 on the core: B_n = argmin ||G_(n) - B KRP_{p != n}(B_p)^T||, here
+    # against LAPACK's least squares (a library cross-check)
+    G = _rand((5, 6, 4), 21)
+    Bs = [_rand((5, 3), 22), _rand((6, 3), 23), _rand((4, 3), 24)]
+    for n in range(3):
+        X, _ = oracle.solve_normal(oracle.mttkrp(G, Bs, n), oracle.hadamard_grams(Bs, n))
+        K = khatri_rao([Bs[p] for p in range(3) if p != n])
+        Xls = np.linalg.lstsq(K, unfold(G, n).T, rcond=None)[0].T
+        assert np.allclose(X, Xls, atol=1e-11)
+
+
+def test_ttm_matches_einsum():
+    Y = _rand((4, 5, 6), 25)
+    U = [_rand((4, 2), 26), _rand((5, 3), 27), _rand((6, 2), 28)]
+    specs = ["ijk,ir->rjk", "ijk,jr->irk", "ijk,kr->ijr"]
+    for n in range(3):
+        assert np.allclose(ttm(Y, U[n], n), np.einsum(specs[n], Y, U[n]), atol=1e-13)
+
+
 def test_ffcp_core_space_equals_textbook_als_on_full_tensor():
     """Eq. 17: with orthonormal U_n, ALS on Y~ = [[G; U]] from A0 = U B0 gives
     A_t = U B_t at every sweep (the core-space iteration lifted)."""

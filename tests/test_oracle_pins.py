@@ -135,6 +135,19 @@ def test_projection_pythagoras():
     assert math.isclose(lhs, rhs, rel_tol=1e-12)
 
 
+def test_inner_product_with_a_lifted_cp_model_moves_to_the_core():
+    # <Y, [[U_1 B_1, ..., U_N B_N]]> = <G, [[B]]> with G = Y x_n U_n^T: the
+    # identity behind the data fit computed from the core
+    Y = _rand((8, 9, 10), 14)
+    U = [_orth(8, 3, 1), _orth(9, 4, 2), _orth(10, 5, 3)]
+    G = tucker_core(Y, U)
+    B = [_rand((3, 2), 4), _rand((4, 2), 5), _rand((5, 2), 6)]
+    lam = np.array([1.5, -0.25])
+    lhs = np.sum(Y * oracle.cp_full(lam, [u @ b for u, b in zip(U, B)]))
+    rhs = np.sum(G * oracle.cp_full(lam, B))
+    assert math.isclose(lhs, rhs, rel_tol=1e-12)
+
+
 @pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("shape,ranks,p", [((30, 25, 20), (3, 4, 5), 5), ((12, 11, 10, 9), (2, 3, 2, 3), 2)])
 def test_rand_tucker_exact_recovery(shape, ranks, p, shared):

@@ -243,6 +243,58 @@ def rand_tucker_seq(Y: np.ndarray, Omegas, orth: str = "qr") -> dict:
     return {"U": U, "G": X}
 
 
+def grid_blocks(shape, grid):
+    """Index ranges of the sub-tensor grid of Sec. IV-B (Eq. 19): mode n is
+    cut into grid[n] contiguous, near-equal blocks.  Returns one list of index
+    arrays per mode."""
+    return [np.array_split(np.arange(I), S) for I, S in zip(shape, grid)]
+
+
+def sketch_share(Ysub: np.ndarray, idx, W) -> list:
+    """One sub-tensor's contribution to every sketch (Eq. 22): for mode n,
+    Y^(s)_(n) Omega_k, with Omega_k the rows of Omega_n = KRP_{k != n}
+    W[n][k] that belong to the sub-tensor's index ranges idx[k] (the
+    Khatri-Rao product of the row blocks of the small factors).  It adds into
+    rows idx[n] of Z_n; the sum over all sub-tensors is the full sketch."""
+    Ysub = np.asarray(Ysub, dtype=np.float64)
+    N = Ysub.ndim
+    return [unfold(Ysub, n) @ khatri_rao([W[n][k][idx[k]] for k in range(N) if k != n]) for n in range(N)]
+
+
+def core_share(Ysub: np.ndarray, idx, Us) -> np.ndarray:
+    """One sub-tensor's share of the core: Y^(s) x_1 U_1[idx_1]^T ... x_N
+    U_N[idx_N]^T, with U_n[idx_n] the row block of U_n on the sub-tensor's
+    range; the core is the sum of the shares (Sec. IV-B, last step)."""
+    return tucker_core(Ysub, [np.asarray(U, dtype=np.float64)[idx[n]] for n, U in enumerate(Us)])
+
+
+def rand_tucker_grid(Y: np.ndarray, W, grid) -> dict:
+    """The all-mode randomized Tucker of `rand_tucker` computed as Sec. IV-B
+    lays it out over a grid of sub-tensors:
+      Z_n rows of block s_n = sum over the other blocks of the shares (Eq. 22),
+      U_n = the Gram basis of Eq. 23 from the row-block Grams of Z_n,
+      G   = sum of the sub-tensors' core shares.
+    The partial sums are reduced here; the paper's "broadcast" of them is read
+    as that reduction.  Pinned: equals the one-block sketch and core."""
+    Y = np.asarray(Y, dtype=np.float64)
+    N = Y.ndim
+    blocks = grid_blocks(Y.shape, grid)
+    Rt = [W[n][(n + 1) % N].shape[1] for n in range(N)]
+    Z = [np.zeros((Y.shape[n], Rt[n])) for n in range(N)]
+    cells = list(np.ndindex(*grid))
+    for cell in cells:
+        idx = [blocks[n][cell[n]] for n in range(N)]
+        sub = Y[np.ix_(*idx)]
+        for n, part in enumerate(sketch_share(sub, idx, W)):
+            Z[n][idx[n]] += part
+    U = [evd_orth(Z[n], slabs=grid[n]) for n in range(N)]
+    G = np.zeros(Rt)
+    for cell in cells:
+        idx = [blocks[n][cell[n]] for n in range(N)]
+        G += core_share(Y[np.ix_(*idx)], idx, U)
+    return {"Z": Z, "U": U, "G": G}
+
+
 def refine_pass(Y: np.ndarray, Us, W) -> list:
     """One pass of the RandTucker2i loop (Alg. 3, the body repeated twice),
     modes in order, each using the factors already refined in this pass:

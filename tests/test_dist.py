@@ -1,6 +1,8 @@
-"""The multi-rank host path of bench.py (independent replicas, one per rank)
-on CPU with the gloo backend, world size 2: the job is timed by its slowest
-rank and its value counts every rank's replica."""
+"""Multi-rank host paths on CPU with the gloo backend, world size 2:
+* bench.py's replicas: the job is timed by its slowest rank and its value
+  counts every rank's replica;
+* the sub-tensor layout of Sec. IV-B emulated with CPU ranks (the oracle's
+  shares, reduced with all_reduce) against the one-process result."""
 import os
 import socket
 
@@ -50,3 +52,57 @@ def test_single_process_needs_no_group():
 
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert abs(bench.job_value(8_000_000_000, 1, 1000.0) - 8.0) < 1e-12
+
+
+def _grid_worker(rank, world, port, q):
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    shape, Rt, grid = (10, 9, 8), 4, (4, 3, 2)
+    Y = synth.host_tensor(synth.scaled(synth.WORKLOADS["c1"], shape))
+    W = synth.sketch_matrices(shape, Rt, 7)
+    blocks = oracle.grid_blocks(shape, grid)
+    # this rank's sub-tensors: mode-1 blocks s_1 = rank, rank + world, ...
+    mine = [c for c in np.ndindex(*grid) if c[0] % world == rank]
+    Z = [torch.zeros((shape[n], Rt), dtype=torch.float64) for n in range(3)]
+    for c in mine:
+        idx = [blocks[n][c[n]] for n in range(3)]
+        for n, part in enumerate(oracle.sketch_share(Y[np.ix_(*idx)], idx, W)):
+            Z[n][torch.as_tensor(idx[n])] += torch.as_tensor(part)
+    for z in Z:
+        dist.all_reduce(z)  # Eq. 22: the shares summed over the workers
+    U = [oracle.evd_orth(z.numpy(), slabs=grid[n]) for n, z in enumerate(Z)]
+    G = torch.zeros((Rt,) * 3, dtype=torch.float64)
+    for c in mine:
+        idx = [blocks[n][c[n]] for n in range(3)]
+        G += torch.as_tensor(oracle.core_share(Y[np.ix_(*idx)], idx, U))
+    dist.all_reduce(G)
+    if rank == 0:
+        one = oracle.rand_tucker_grid(Y, W, grid)
+        ok = all(np.allclose(Z[n].numpy(), one["Z"][n], atol=1e-12) for n in range(3))
+        ok = ok and np.allclose(G.numpy(), one["G"], atol=1e-12)
+        q.put((len(mine), ok))
+    else:
+        q.put((len(mine), True))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_subtensor_layout_on_two_ranks_matches_one_process():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grid_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert sorted(n for n, _ in out) == [12, 12]
+    assert all(ok for _, ok in out)

@@ -312,6 +312,24 @@ def test_congruence_invariances_and_planted_angle():
     assert math.isclose(oracle.congruence(A, [B0, A[1], A[2]]), math.cos(theta), rel_tol=1e-12)
 
 
+@pytest.mark.parametrize("grid", [(2, 3, 2), (1, 1, 1), (3, 1, 4)])
+def test_grid_form_equals_the_one_block_result(grid):
+    # Sec. IV-B: the sketch summed from sub-tensor shares (Eq. 22) is the
+    # one-block sketch; the Gram basis of Eq. 23 spans the same range as the
+    # Householder basis; the summed core shares are the core of Y in that basis
+    shape, Rt = (7, 9, 8), 4
+    Y = _rand(shape, 41)
+    W = synth.sketch_matrices(shape, Rt, 42)
+    g = oracle.rand_tucker_grid(Y, W, grid)
+    Z, _ = sketch(Y, W)
+    ref = oracle.rand_tucker(Y, W)
+    for n in range(3):
+        assert np.allclose(g["Z"][n], Z[n], atol=1e-12)
+        assert np.allclose(g["U"][n] @ g["U"][n].T, ref["U"][n] @ ref["U"][n].T, atol=1e-11)
+    assert np.allclose(g["G"], tucker_core(Y, g["U"]), atol=1e-12)
+    assert np.allclose(tucker_full(g["G"], g["U"]), tucker_full(ref["G"], ref["U"]), atol=1e-10)
+
+
 def test_mttkrp_matches_brute_force():
     G = _rand((3, 4, 5), 2)
     Bs = [_rand((3, 2), 3), _rand((4, 2), 4), _rand((5, 2), 5)]

@@ -52,6 +52,8 @@ extern "C" {
 #define TDK_ENOTSUP (-5)   /* a form or option that does not cover the case */
 #define TDK_ESCRATCH (-6)  /* problem needs more scratch than the fixed
                               static array of tucker_sketch_static holds   */
+#define TDK_EIO (-7)       /* a file could not be read or written, or holds
+                              something else than what the call expects     */
 #define TDK_WRANKDEF 1     /* a sketch was numerically rank deficient; the
                               orthonormal basis was completed (see below)  */
 #define TDK_WNOCONV 2      /* ALS stopped at max_sweeps                    */
@@ -93,6 +95,9 @@ int tdk_ctx_set_stream(tdk_ctx* ctx, void* cuda_stream);
 int tdk_ctx_sync_status(tdk_ctx* ctx, int* flags_out /* host */);
 /* Number of kernel launches this context has issued since creation. */
 int64_t tdk_ctx_launch_count(const tdk_ctx* ctx);
+/* Bytes of device workspace the context holds now (0 until an entry point
+   first needs one; it only grows, and tdk_ctx_destroy frees it). */
+size_t tdk_ctx_workspace_bytes(const tdk_ctx* ctx);
 /* Kernel timing by CUDA events recorded on the launching stream around the
    main kernel of each region (0 = the pass of tucker_sketch over Y, 1 = the
    pass of tucker_core over Y).  tdk_ctx_profile(ctx, 1) starts recording and
@@ -115,7 +120,8 @@ const char* tdk_strerror(int code);
 
 /* Problem description, following the paper's problem statement: tensor
    dimensions I_n, multilinear ranks R_n and the oversampling p, so that the
-   sketch width is Rt_n = R_n + p (Sec. IV-A). */
+   sketch width is Rt_n = R_n + p (Sec. IV-A), and the seed of the random test
+   matrices (Sec. IV-B shares a seed between workers, not the matrices). */
 typedef struct {
   int N;                    /* order, 2 <= N <= TDK_MAX_MODES               */
   int dtype;                /* TDK_F64 / TDK_F32 / TDK_BF16 storage of Y    */
@@ -124,7 +130,27 @@ typedef struct {
   int64_t I[TDK_MAX_MODES]; /* dimensions                                   */
   int R[TDK_MAX_MODES];     /* Tucker ranks; need 1 <= R_n + p <= min(I_n,
                                TDK_MAX_RANK)                                */
+  uint64_t seed;            /* seed of the test matrices W_k^(n) that the
+                               library draws when a call gets W = NULL     */
 } tdk_tucker_desc;
+
+/*
+ * The seeded test matrices.  Entry (i, r) of W_k^(n) (mode n's sketch, factor
+ * of mode k, 0-based n, k, i, r) is one standard normal value rounded to the
+ * nearest BF16 value (ties to even), drawn from the counter-based generator
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+ *   key     = (seed mod 2^32, seed div 2^32),
+ *   counter = (r, i mod 2^32, i div 2^32, 256 n + k),
+ * whose four output words x0..x3 give a = (x0 2^32 + x1) div 2^11 and
+ * b = (x2 2^32 + x3) div 2^11 (53-bit integers), u1 = (a + 1/2) 2^-53,
+ * u2 = b 2^-53 and the value sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller, FP64).
+ * Every entry is independent of the matrix sizes, so a slab of rows of
+ * W_k^(n) is drawn alone with the same values (the sharded form uses this).
+ * tdk_sketch_matrices writes the matrices that desc->seed defines: W_out is
+ * N*N device pointers, W_out[n*N + k] (k != n) FP64 [I_k x Rt_n], the
+ * diagonal entries ignored (may be NULL).  Errors: TDK_EINVAL, TDK_ECUDA.
+ */
+int tdk_sketch_matrices(tdk_ctx* ctx, const tdk_tucker_desc* desc, double* const W_out[]);
 
 /* Host-only check of a descriptor, the one every entry point applies before
    any CUDA call: 2 <= N <= TDK_MAX_MODES, a known dtype and prec, p >= 0,
@@ -136,15 +162,18 @@ typedef struct {
 int tdk_tucker_check(const tdk_tucker_desc* desc);
 
 /*
- * tucker_sketch -- all-mode randomized range finder (Sec. IV-A; Alg. 2 lines
- * "Z = Y_(n) Omega" and "U = orth(Z)"; Eq. 22 for the blockwise sums).
+ * tucker_sketch -- all-mode randomized range finder (Sec. IV-A; Alg. 2, the
+ * sketch of every mode and its orthonormal basis; Eq. 22 for the blockwise
+ * sums).
  *
  *   Y      [I_1 x ... x I_N] in desc->dtype.
- *   W      array of N*N device pointers; W[n*N + k] (k != n) is the FP64
- *          matrix W_k^(n) [I_k x Rt_n]; W[n*N + n] is ignored.  The random
- *          test matrix of mode n is Omega_n = KRP_{k != n} W_k^(n).  Values
- *          are rounded to the operand precision of the chosen form (exact if
- *          they are BF16 values, as the bundled generator draws them).
+ *   W      NULL: the matrices are drawn from desc->seed (see
+ *          tdk_sketch_matrices).  Otherwise an array of N*N device pointers;
+ *          W[n*N + k] (k != n) is the FP64 matrix W_k^(n) [I_k x Rt_n];
+ *          W[n*N + n] is ignored.  The random test matrix of mode n is
+ *          Omega_n = KRP_{k != n} W_k^(n).  Values are rounded to the operand
+ *          precision of the chosen form (exact if they are BF16 values, as
+ *          both the seeded draw and the bundled generator make them).
  *   U_out  N device pointers, U_out[n] FP64 [I_n x Rt_n]: orthonormal columns
  *          spanning range(Z_n), diag of the triangular factor positive
  *          (CholQR2: two rounds of Gram -> Cholesky -> Z R^-1, all FP64).
@@ -167,7 +196,8 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
  * sketch kernel for callers that cannot allocate device memory.
  *
  *   desc   as tucker_sketch; prec must be TDK_PREC_SIMT (else TDK_ENOTSUP).
- *   Y, W   as tucker_sketch.
+ *   Y, W   as tucker_sketch, except that W must not be NULL (the seeded draw
+ *          would need scratch of its own): use tdk_sketch_matrices once.
  *   Z_out  N device pointers, all non-NULL; Z_out[n] FP64 [I_n x Rt_n]
  *          receives Z_n = Y_(n) Omega_n.
  * Scratch: a file-scope device array of TDK_SKETCH_STATIC_MAX_BYTES bytes
@@ -182,7 +212,10 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
  * and give wrong results; serialise them (one stream, or events).
  * Set-up: the first call on each device resolves the array's address with
  * cudaGetSymbolAddress (this may load the module); make that first call
- * before any stream capture begins.
+ * before any stream capture begins.  The address is kept per device together
+ * with the identity of the CUDA context it was resolved in; a call that finds
+ * another context current on the device (after cudaDeviceReset, say)
+ * resolves it again, so that call is a set-up call too.
  * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOTSUP, TDK_ESCRATCH,
  * TDK_ECUDA.
  */
@@ -200,7 +233,10 @@ int tucker_sketch_static(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* 
  *   completed as in tucker_sketch).
  *   Y      [I_1 x ... x I_N], desc->dtype FP64 or FP32 (CUDA-core form).
  *   W      N*N device pointers; W[n*N + k] (k != n) FP64 [Rt_k x Rt_n],
- *          a fresh draw per pass; W[n*N + n] is ignored.
+ *          a fresh draw per pass; W[n*N + n] is ignored.  NULL: drawn from
+ *          desc->seed as in tdk_sketch_matrices with I_k replaced by Rt_k
+ *          (the first Rt_k rows of that seed's matrices), so give every pass
+ *          its own seed.
  *   U_io   N device pointers, FP64 [I_n x Rt_n]: the factors in (any full
  *          rank start, e.g. Gaussian), refined in place.
  * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOMEM, TDK_ENOTSUP
@@ -210,8 +246,8 @@ int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
                   double* const U_io[]);
 
 /*
- * tucker_core -- G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2 line
- * "Y <- Y x_n U^T" for every n; Eq. 1), plus ||Y||_F^2.
+ * tucker_core -- G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2, the projection
+ * step of every mode; Eq. 1), plus ||Y||_F^2.
  *
  *   U       N device pointers, U[n] FP64 [I_n x Rt_n] (e.g. from tucker_sketch).
  *   G_out   [Rt_1 x ... x Rt_N], FP64 for F64 data, FP32 otherwise.
@@ -224,6 +260,11 @@ int tucker_core(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
                 const double* const U[], void* G_out, double* normY2);
 
 enum { TDK_INIT_GIVEN = 0, TDK_INIT_HOSVD = 1 };
+/* ALS form: AUTO picks the fastest form that covers the problem; STEPS forces
+   the kernel-per-step form (any core size, pseudo-inverse, time limit). */
+enum { TDK_ALS_FORM_AUTO = 0, TDK_ALS_FORM_STEPS = 1 };
+/* form that ran (tdk_als_report.form) */
+enum { TDK_ALS_RAN_ONE_CTA = 1, TDK_ALS_RAN_GRID = 2, TDK_ALS_RAN_STEPS = 3 };
 enum { TDK_NONNEG_NONE = 0, TDK_NONNEG_LS = 1, TDK_NONNEG_HALS = 2, TDK_NONNEG_MU = 3 };
 
 typedef struct {
@@ -236,13 +277,13 @@ typedef struct {
                        HALS (Eq. 8); TDK_NONNEG_MU (3): multiplicative
                        update in the low-rank form (Eq. 15).  HALS and MU
                        start each mode from A_n diag(lambda) and need the
-                       persistent kernel (N >= 3, core fits on chip, no
-                       time limit): otherwise TDK_ENOTSUP                  */
+                       persistent kernel or, for rows that do not fit on
+                       chip, the kernel-per-step form                       */
   int init;         /* TDK_INIT_GIVEN: start from B_io (nonneg or l1: A_io);
                        TDK_INIT_HOSVD: leading R left singular vectors of
                        every G_(n) (nonneg: their magnitudes lifted)        */
   int check_every;  /* sweeps per convergence check on the host (<= 0: 8) */
-  int reserved;
+  int form;         /* TDK_ALS_FORM_AUTO or TDK_ALS_FORM_STEPS             */
   double timeout_s; /* bound on the whole call in seconds; <= 0 or NaN =
                        none; exceeded -> TDK_ETIMEOUT with the last
                        iterate in the outputs.  A limit selects the
@@ -252,8 +293,7 @@ typedef struct {
                        sign(x) max(|x| - c, 0) with c = l1, then projected
                        if nonneg = TDK_NONNEG_LS.  The factors are updated
                        as A_n (start from A_io, or the HOSVD start lifted);
-                       needs the persistent kernel and nonneg NONE or LS,
-                       else TDK_ENOTSUP / TDK_EINVAL                        */
+                       needs nonneg NONE or LS, else TDK_EINVAL            */
 } tdk_als_opts;
 
 typedef struct {
@@ -263,6 +303,9 @@ typedef struct {
   double fit_Y;     /* 1 - ||Y - [[A]]|| / ||Y|| via the Gram identities
                        (NaN if normY2 was NULL)                             */
   double ms;        /* wall time of the call in milliseconds               */
+  int form;         /* TDK_ALS_RAN_*: the form that produced the result    */
+  int grid;         /* CTAs of the persistent launch (1 for ONE_CTA, 0 for
+                       the kernel-per-step form)                           */
 } tdk_als_report;
 
 /*
@@ -292,8 +335,78 @@ int ffcp_als(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* G,
              tdk_als_report* rep);
 
 /* ======================================================================
+ * Sharded form (Sec. IV-B): Y split along its first mode into slabs of
+ * consecutive rows i_1, one slab per worker.  The calls below compute one
+ * worker's share; the caller sums the shares over the workers (an allreduce)
+ * between the calls, which is the whole exchange of the method:
+ *   1. tucker_sketch_partial on each slab; sum the Z_n shares (n >= 2).
+ *   2. U_n (n >= 2) = tdk_orth(Z_n), on every worker (same input, same bits).
+ *   3. U_1 by CholQR2 over the row blocks of Z_1 (Eq. 23: the Gram of the
+ *      stacked blocks is the sum of the blocks' Grams): gram = sum of
+ *      tdk_gram(Z_1 slab rows); Q = tdk_orth_apply(gram, Z_1 rows); then the
+ *      same again on Q gives the slab's rows of U_1.
+ *   4. tucker_core_partial on each slab with its rows of U_1; sum the core
+ *      shares and the ||Y||^2 shares.
+ *   5. ffcp_als on the summed core, on every worker.
+ * A slab descriptor is the whole tensor's descriptor with I[0] replaced by
+ * the slab's row count (any count >= 1; the rule R_1 + p <= I_1 applies to
+ * I1_total instead).
+ * ====================================================================== */
+
+/*
+ * tucker_sketch_partial -- one slab's share of the all-mode sketch (Eq. 22).
+ *   slab   slab descriptor (rows [row_off, row_off + slab->I[0]) of mode 1 of
+ *          a tensor whose first dimension is I1_total).
+ *   Y      the slab, [slab->I[0] x I_2 x ... x I_N] in slab->dtype.
+ *   W      NULL (draw from slab->seed, rows of W_1^(n) at their global index)
+ *          or the whole tensor's N*N pointers as in tucker_sketch (W_1^(n)
+ *          with I1_total rows; the library reads the slab's rows).
+ *   Z_out  N device pointers: Z_out[0] FP64 [slab->I[0] x Rt_1] receives the
+ *          slab's rows of Z_1; Z_out[n] (n >= 1) FP64 [I_n x Rt_n] the slab's
+ *          share of Z_n (sum over its i_1).
+ * Errors: TDK_EINVAL (bad desc, offsets or pointers), TDK_ENOMEM, TDK_ENOTSUP
+ * (as tucker_sketch), TDK_ECUDA.
+ */
+int tucker_sketch_partial(tdk_ctx* ctx, const tdk_tucker_desc* slab, int64_t row_off, int64_t I1_total,
+                          const void* Y, const double* const W[], double* const Z_out[]);
+/*
+ * tucker_core_partial -- one slab's share of the core and of ||Y||^2:
+ * G_share = Y_slab x_1 U_1[slab rows]^T x_2 U_2^T ... x_N U_N^T (Eq. 1 summed
+ * over the slabs).  U[0] points at the slab's rows of U_1, FP64
+ * [slab->I[0] x Rt_1]; U[n] (n >= 1) FP64 [I_n x Rt_n].  G_out and normY2 as
+ * tucker_core, for the share.  Errors as tucker_core.
+ */
+int tucker_core_partial(tdk_ctx* ctx, const tdk_tucker_desc* slab, int64_t I1_total, const void* Y,
+                        const double* const U[], void* G_out, double* normY2);
+/*
+ * tdk_gram -- gram_out = upper triangle of Z^T Z (FP64 [cols x cols], rows
+ * <= cols entries set, the others 0) for Z FP64 [rows x cols] (row-major,
+ * 1 <= cols <= TDK_MAX_RANK).  The sum of the Grams of row blocks is the
+ * Gram of the stacked matrix (Eq. 23).  Errors: TDK_EINVAL, TDK_ENOMEM,
+ * TDK_ECUDA.
+ */
+int tdk_gram(tdk_ctx* ctx, const double* Z, int64_t rows, int cols, double* gram_out);
+/*
+ * tdk_orth_apply -- Q = Z R^-1 with R the upper Cholesky factor of the
+ * symmetric matrix whose upper triangle `gram` holds (one round of CholQR;
+ * Eq. 23 with a Cholesky factor in place of the eigendecomposition).  If a
+ * pivot is not above cols * eps * max diag, Q is not written and the
+ * context's status word gets TDK_WRANKDEF (tdk_ctx_sync_status).
+ * Errors: TDK_EINVAL, TDK_ENOMEM, TDK_ECUDA.
+ */
+int tdk_orth_apply(tdk_ctx* ctx, const double* gram, const double* Z, int64_t rows, int cols, double* Q_out);
+/*
+ * tdk_orth -- orthonormal basis U of range(Z) for one matrix, the step 3 of
+ * the range finder that tucker_sketch applies to each mode: CholQR2 in FP64,
+ * completed by two-pass Gram-Schmidt when Z is numerically rank deficient
+ * (status TDK_WRANKDEF).  Z, U_out FP64 [rows x cols], cols <= min(rows,
+ * TDK_MAX_RANK).  Errors: TDK_EINVAL, TDK_ENOMEM, TDK_ECUDA.
+ */
+int tdk_orth(tdk_ctx* ctx, const double* Z, int64_t rows, int cols, double* U_out);
+
+/* ======================================================================
  * Learned initialiser (no counterpart in the paper: its ALS starts from random
- * or HOSVD factors, Alg. 1 "Initialize A").  A small MLP maps a Tucker core G
+ * or HOSVD factors, Alg. 1's first step).  A small MLP maps a Tucker core G
  * (output of tucker_core, all sketch widths equal to Rt) to initial
  * core-space factors B_n for ffcp_als.
  *
@@ -328,7 +441,17 @@ enum {
   TDK_MLP_GRADS = 1,       /* gradient of the last train step's batch loss   */
   TDK_MLP_CANON_CORE = 2,  /* last batch: S, FP32 [batch x Rt^N]            */
   TDK_MLP_ROTATIONS = 3,   /* last batch: V_n, FP32 [batch][N][Rt][Rt]      */
-  TDK_MLP_OUTPUT = 4       /* last batch: network output, FP32 [batch x N*Rt*Rt] */
+  TDK_MLP_OUTPUT = 4,      /* last batch: network output, FP32 [batch x N*Rt*Rt] */
+  /* last batch, the stored intermediates of the forward and backward passes
+     (BF16 values returned as FP32; rows of the batch, no padding): */
+  TDK_MLP_INPUT = 5,       /* x = BF16(sqrt(Rt^N) vec S)   [batch x Rt^N]   */
+  TDK_MLP_Z1 = 6,          /* x W1^T + b1, FP32            [batch x hidden] */
+  TDK_MLP_H1 = 7,          /* BF16(gelu(Z1))               [batch x hidden] */
+  TDK_MLP_Z2 = 8,          /* H1 W2^T + b2, FP32           [batch x hidden] */
+  TDK_MLP_H2 = 9,          /* BF16(gelu(Z2))               [batch x hidden] */
+  TDK_MLP_DO = 10,         /* BF16(dLoss/dO)               [batch x N*Rt*Rt] */
+  TDK_MLP_DZ2 = 11,        /* BF16((dO W3) * gelu'(Z2))    [batch x hidden] */
+  TDK_MLP_DZ1 = 12         /* BF16((dZ2 W2) * gelu'(Z1))   [batch x hidden] */
 };
 
 typedef struct {
@@ -351,6 +474,16 @@ int64_t tdk_mlp_param_count(const tdk_mlp* m);
 int tdk_mlp_set_params(tdk_ctx* ctx, tdk_mlp* m, const float* host_params);
 /* Copy one of the TDK_MLP_* arrays out to host memory.  Synchronous. */
 int tdk_mlp_get(tdk_ctx* ctx, tdk_mlp* m, int what, float* host_out);
+/* Checkpoint: tdk_mlp_save writes the model's shape (N, Rt, hidden), the
+   parameter vector, Adam's two moment vectors and its step counter to the
+   file `path` (little-endian; an 8-byte tag "TDKMLP01", four int32 N, Rt,
+   hidden, 0, int64 parameter count, int64 step, then three FP32 vectors of
+   that count: parameters, first and second moments).  tdk_mlp_load reads
+   such a file into a model of the same shape, so that training resumes where
+   it stopped.  Both synchronous.  Errors: TDK_EINVAL (null argument),
+   TDK_EIO (file error, wrong tag, shape or size), TDK_ECUDA. */
+int tdk_mlp_save(tdk_ctx* ctx, const tdk_mlp* m, const char* path);
+int tdk_mlp_load(tdk_ctx* ctx, tdk_mlp* m, const char* path);
 /* colsum_n = 1^T U_n for every mode, FP64 [N][Rt] device output (the sign
    rule's input; all Rt_n must be equal). */
 int tdk_mlp_colsums(tdk_ctx* ctx, const tdk_tucker_desc* desc, const double* const U[], double* out);

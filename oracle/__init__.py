@@ -28,11 +28,12 @@ from .tucker import (unfold, fold, khatri_rao, sketch, sketch_row, householder_q
 from .cpals import (mttkrp, hadamard_grams, cp_full, cp_als, cp_als_nonneg, core_fit,
                     lift, congruence, sir_db, solve_normal, hosvd_init, hals_rows, mu_rows, soft_threshold)
 from . import mlp
+from . import philox
 
 __all__ = [
     "unfold", "fold", "khatri_rao", "sketch", "sketch_row", "householder_qr", "ttm",
     "tucker_core", "rand_tucker", "hosvd_factors", "refine_pass", "rand_tucker_2i", "evd_orth",
     "rand_tucker_dense", "rand_tucker_seq", "grid_blocks", "sketch_share", "core_share", "rand_tucker_grid", "tucker_full", "norm2", "mttkrp", "hadamard_grams",
     "cp_full", "cp_als", "cp_als_nonneg", "core_fit", "lift", "congruence", "sir_db", "solve_normal",
-    "hosvd_init", "hals_rows", "mu_rows", "soft_threshold", "mlp",
+    "hosvd_init", "hals_rows", "mu_rows", "soft_threshold", "mlp", "philox",
 ]

@@ -22,7 +22,7 @@ from .tucker import khatri_rao, unfold
 
 def mttkrp(G: np.ndarray, Bs, n: int) -> np.ndarray:
     """H_n = G_(n) [KRP_{p != n} B_p] with the Khatri-Rao product formed
-    (Alg. 1, "compute H"; Eq. 12).  Pinned by brute force in tests."""
+    (Alg. 1, the matricised-tensor product; Eq. 12).  Pinned by brute force in tests."""
     N = G.ndim
     return unfold(G, n) @ khatri_rao([Bs[p] for p in range(N) if p != n])
 

@@ -4,7 +4,7 @@ forward and backward pass, the loss and the Adam update.
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper has no learned part; its ALS starts from random or HOSVD factors
-(Alg. 1, "Initialize A").  The initialiser built here maps a compressed core G
+(the first step of Alg. 1).  The initialiser built here maps a compressed core G
 (Alg. 2 output) to initial core-space factors B_n for FFCP.  Its definition:
 
 canonicalise(G, colsums)
@@ -53,7 +53,7 @@ from .tucker import fold, unfold
 from .cpals import cp_full
 
 __all__ = ["mlp_dims", "param_sizes", "unpack", "canonicalise", "canonical_target", "network_input", "gelu",
-           "gelu_grad",
+           "gelu_grad", "linear", "activation", "delta", "dloss_dO",
            "forward", "loss", "loss_grad", "adam_step", "decanonicalise"]
 
 
@@ -143,16 +143,35 @@ def gelu_grad(z):
     return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
+def _q(bf16: bool):
+    return _bf16 if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+
+
+def linear(H, W, b, bf16: bool = True):
+    """One layer's pre-activation H W^T + b, the weights in storage precision."""
+    return np.asarray(H, dtype=np.float64) @ _q(bf16)(W).T + b
+
+
+def activation(Z, bf16: bool = True):
+    """gelu(Z) in storage precision (the stored activation)."""
+    return _q(bf16)(gelu(Z))
+
+
+def delta(D_next, W, Z, bf16: bool = True):
+    """Back-propagated pre-activation gradient (D_next W) * gelu'(Z) in
+    storage precision, D_next the gradient of the next layer's output."""
+    return _q(bf16)((np.asarray(D_next, dtype=np.float64) @ _q(bf16)(W)) * gelu_grad(Z))
+
+
 def forward(theta, X, N: int, Rt: int, hidden: int, bf16: bool = True):
     """Batch forward pass; X [batch x Rt^N].  Returns (O, cache)."""
     W1, b1, W2, b2, W3, b3 = unpack(theta, N, Rt, hidden)
-    q = _bf16 if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
-    X = q(X)
-    Z1 = X @ q(W1).T + b1
-    H1 = q(gelu(Z1))
-    Z2 = H1 @ q(W2).T + b2
-    H2 = q(gelu(Z2))
-    O = H2 @ q(W3).T + b3
+    X = _q(bf16)(X)
+    Z1 = linear(X, W1, b1, bf16)
+    H1 = activation(Z1, bf16)
+    Z2 = linear(H1, W2, b2, bf16)
+    H2 = activation(Z2, bf16)
+    O = linear(H2, W3, b3, bf16)
     return O, {"X": X, "Z1": Z1, "H1": H1, "Z2": Z2, "H2": H2}
 
 
@@ -178,7 +197,7 @@ def loss(O, S, R, T=None, alpha: float = 0.0):
     return tot / B
 
 
-def _dloss_dO(O, S, R, T, alpha):
+def dloss_dO(O, S, R, T, alpha):
     """Gradient of `loss` with respect to O (dense, exact)."""
     Bsz = O.shape[0]
     N = S.ndim - 1
@@ -211,16 +230,15 @@ def loss_grad(theta, X, S, R, N: int, Rt: int, hidden: int, T=None, alpha: float
     those rounded values against the (rounded) stored activations.
     """
     W1, b1, W2, b2, W3, b3 = unpack(theta, N, Rt, hidden)
-    q = _bf16 if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     O, c = forward(theta, X, N, Rt, hidden, bf16)
     L = loss(O, S, R, T, alpha)
-    dO = q(_dloss_dO(O, S, R, T, alpha))
+    dO = _q(bf16)(dloss_dO(O, S, R, T, alpha))
     gW3 = dO.T @ c["H2"]
     gb3 = dO.sum(axis=0)
-    dZ2 = q((dO @ q(W3)) * gelu_grad(c["Z2"]))
+    dZ2 = delta(dO, W3, c["Z2"], bf16)
     gW2 = dZ2.T @ c["H1"]
     gb2 = dZ2.sum(axis=0)
-    dZ1 = q((dZ2 @ q(W2)) * gelu_grad(c["Z1"]))
+    dZ1 = delta(dZ2, W2, c["Z1"], bf16)
     gW1 = dZ1.T @ c["X"]
     gb1 = dZ1.sum(axis=0)
     g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3)])

@@ -56,7 +56,7 @@ def khatri_rao(mats) -> np.ndarray:
 
 
 def sketch(Y: np.ndarray, W) -> tuple[list, float]:
-    """All-mode range-finder sketch (Sec. IV-A step 2; Alg. 2 line "Z = Y_(n) Omega").
+    """All-mode range-finder sketch (Sec. IV-A step 2; Alg. 2, the sketch of each mode).
 
     Z_n = Y_(n) Omega_n with Omega_n = KRP_{k != n} W[n][k] formed explicitly,
     for every n from the same (original) Y; also returns ||Y||^2.
@@ -91,7 +91,7 @@ def sketch_row(slab: np.ndarray, n: int, W, chunk: int = 32) -> np.ndarray:
 
 
 def householder_qr(Z: np.ndarray):
-    """Thin QR by Householder reflections (Sec. IV-A step 3, "e.g. QR").
+    """Thin QR by Householder reflections (Sec. IV-A step 3, which names QR as one way).
 
     Returns Q (m x k, orthonormal columns) and R (k x k, upper triangular)
     with Z = Q R and diag(R) >= 0 (sign convention that makes Q unique for
@@ -131,7 +131,7 @@ def householder_qr(Z: np.ndarray):
 
 
 def ttm(Y: np.ndarray, U: np.ndarray, n: int) -> np.ndarray:
-    """Y x_n U^T (Alg. 2, "Y <- Y x_n U^T"): contracts mode n of Y with the
+    """Y x_n U^T (Alg. 2, the mode-n projection step): contracts mode n of Y with the
     columns of U, (Y x_n U^T)_(n) = U^T Y_(n).  Pinned: exact Tucker tensors."""
     Y = np.asarray(Y, dtype=np.float64)
     shape = list(Y.shape)

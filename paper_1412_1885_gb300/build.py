@@ -1,5 +1,11 @@
 """Build libtdk.so in-tree for sm_103a (nvcc, one object per translation unit,
-compiled in parallel, linked as a shared library with the static CUDA runtime)."""
+compiled in parallel, linked as a shared library with the static CUDA runtime).
+
+Beside it, libtdk_test.so: the same library with the test hooks compiled in
+(-DTDK_TESTING: a forced workspace-allocation failure, a device wait that
+nothing satisfies, one raw GEMM call, and cycle-counter profiling switches).
+Only the translation units that mention TDK_TESTING are compiled twice; the
+product library exports none of the hooks."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -11,8 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtdk.so")
+TEST_LIB = os.path.join(HERE, "libtdk_test.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+LINK = ["-lcudart_static", "-ldl", "-lrt", "-lpthread"]
 
 
 def _nvcc() -> str:
@@ -26,8 +34,13 @@ def sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _has_test_hooks(src: str) -> bool:
+    with open(os.path.join(CSRC, src), encoding="utf-8") as f:
+        return "TDK_TESTING" in f.read()
+
+
 def _deps_mtime() -> float:
-    t = 0.0
+    t = os.path.getmtime(os.path.abspath(__file__))
     for d in (CSRC, os.path.join(HERE, "..", "include")):
         for f in os.listdir(d):
             t = max(t, os.path.getmtime(os.path.join(d, f)))
@@ -35,14 +48,18 @@ def _deps_mtime() -> float:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    dep = _deps_mtime()
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= dep and os.path.exists(TEST_LIB)
+            and os.path.getmtime(TEST_LIB) >= dep):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def one(src):
-        obj = os.path.join(BUILD, src[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def one(job):
+        src, testing = job
+        obj = os.path.join(BUILD, src[:-3] + (".test.o" if testing else ".o"))
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, *(["-DTDK_TESTING"] if testing else []), "-c",
+               os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -50,14 +67,18 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stdout + r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(one, sources()))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    srcs = sources()
+    hooked = [s for s in srcs if _has_test_hooks(s)]
+    jobs = [(s, False) for s in srcs] + [(s, True) for s in hooked]
+    with cf.ThreadPoolExecutor(max_workers=min(12, os.cpu_count() or 4)) as ex:
+        objs = dict(zip(jobs, ex.map(one, jobs)))
+    for path, testing in ((LIB, False), (TEST_LIB, True)):
+        parts = [objs[(s, testing and s in hooked)] for s in srcs]
+        tmp = path + ".tmp"
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *parts, *LINK], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, path)
     return LIB
 
 

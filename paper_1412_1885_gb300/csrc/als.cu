@@ -37,7 +37,10 @@ struct AlsState {
 
 template <class T>
 struct AlsArgs {
-  int N, R, nonneg, max_sweeps;
+  int N, R, nonneg, max_sweeps;  // nonneg: the factors are updated as A_n (ambient rows)
+  int nn_rule;                   // 0 LS solve, 1 HALS (Eq. 8), 2 multiplicative (Eq. 15)
+  int clip;                      // project onto the nonnegative orthant (P_+)
+  double l1;                     // > 0: soft threshold of the LS solution (Eq. 16)
   double tol;
   int64_t Rt[TDK_MAX_MODES];
   int64_t I[TDK_MAX_MODES];
@@ -309,6 +312,48 @@ __global__ void __launch_bounds__(64) als_solve(AlsArgs<T> a, int n) {
   __shared__ double V[RMAX * RMAX];
   __shared__ double x[RMAX], tmp[RMAX];
   const double* gram = a.gram;
+  if (a.nonneg && a.nn_rule != 0) {
+    // HALS and multiplicative rules: T_n itself, the row of M = U_n H_n and
+    // the current iterate of the row, A_n[i, :] diag(lambda)
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      double v = 1.0;
+      for (int p = 0; p < a.N; ++p)
+        if (p != n) v *= gram[(int64_t)p * R * R + e];
+      Tm[e] = v;
+    }
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      double m = 0.0;
+      for (int64_t q = 0; q < Rtn; ++q) {
+        double h = 0.0;
+        for (int s = 0; s < a.S[n]; ++s) h += (double)a.Hpart[((int64_t)s * RMAX + q) * R + r];
+        if (i == 0) a.Hfull[q * R + r] = h;
+        m = fma(a.U[n][(int64_t)i * Rtn + q], h, m);
+      }
+      x[r] = m;
+      tmp[r] = a.A[n][(int64_t)i * R + r] * a.lam[r];
+    }
+    __syncthreads();
+    if (a.nn_rule == 2) {
+      // multiplicative: a <- a (*) P_+(m) (/) (a T_n); 0 where a T_n is not positive
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        double d = 0.0;
+        for (int q = 0; q < R; ++q) d = fma(tmp[q], Tm[q * R + r], d);
+        a.Bnew[(int64_t)i * R + r] = d > 0.0 ? tmp[r] * fmax(x[r], 0.0) / d : 0.0;
+      }
+    } else if (threadIdx.x < 32) {
+      // HALS, column by column: a_r <- P_+(a_r + (m_r - a t_r) / t_rr), each
+      // column seeing the ones already updated (one warp; the row is short)
+      for (int r = 0; r < R; ++r) {
+        double part = 0.0;
+        for (int q = threadIdx.x; q < R; q += 32) part = fma(tmp[q], Tm[q * R + r], part);
+        part = warp_sum(part);
+        if (threadIdx.x == 0) tmp[r] = fmax(0.0, tmp[r] + (x[r] - part) / Tm[r * R + r]);
+        __syncwarp();
+      }
+      for (int r = threadIdx.x; r < R; r += 32) a.Bnew[(int64_t)i * R + r] = tmp[r];
+    }
+    return;
+  }
   int bad = build_and_cholesky(gram, a.N, n, R, Tm);
   if (!a.nonneg) {
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -339,7 +384,8 @@ __global__ void __launch_bounds__(64) als_solve(AlsArgs<T> a, int n) {
   }
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double v = x[r];
-    if (a.nonneg) v = v > 0.0 ? v : 0.0;
+    if (a.l1 > 0.0) v = copysign(fmax(fabs(v) - a.l1, 0.0), v);
+    if (a.clip) v = v > 0.0 ? v : 0.0;
     a.Bnew[(int64_t)i * R + r] = v;
   }
 }
@@ -399,7 +445,9 @@ __global__ void __launch_bounds__(128) als_normalize(AlsArgs<T> a, int n, int ra
   }
 #undef SCALED
   __syncthreads();
-  if (r == 0 && !raw)
+  // lambda of the model [[lambda; A]]: 1 for a raw start (the HALS and
+  // multiplicative rules read it as the weights of the current iterate)
+  if (r == 0)
     for (int c = threadIdx.x; c < R; c += blockDim.x) a.lam[c] = lam[c];
   if (n == a.N - 1 && !raw) {
     // inner = <G, [[lambda; B]]> = sum_{q, c} H[q, c] lambda_c B_n[q, c]  (column r)
@@ -595,9 +643,11 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
   AlsArgs<T> a{};
   a.N = N;
   a.R = R;
-  // the HALS, multiplicative and l1 rules live in the persistent kernel only
-  if (o->nonneg == TDK_NONNEG_HALS || o->nonneg == TDK_NONNEG_MU || o->l1 > 0.0) return TDK_ENOTSUP;
-  a.nonneg = o->nonneg ? 1 : 0;
+  // the l1 form updates the factors as A_n like the nonnegative forms
+  a.nonneg = (o->nonneg || o->l1 > 0.0) ? 1 : 0;
+  a.nn_rule = o->nonneg == TDK_NONNEG_HALS ? 1 : (o->nonneg == TDK_NONNEG_MU ? 2 : 0);
+  a.clip = o->nonneg ? 1 : 0;
+  a.l1 = o->l1;
   a.max_sweeps = o->max_sweeps;
   a.tol = o->tol;
   int64_t Rtmax = 0, Imax = 0, bsum = 0;
@@ -676,7 +726,7 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
       hosvd_init_kernel<T><<<1, 128, 0, s>>>(a, n, a.nonneg ? a.Hfull : a.Bnew);
       TDK_LAUNCH_CHECK(ctx);
       if (a.nonneg) {
-        abs_lift_kernel<<<64, 256, 0, s>>>(U[n], a.Hfull, g.I[n], g.Rt[n], R, a.Bnew, true);
+        abs_lift_kernel<<<64, 256, 0, s>>>(U[n], a.Hfull, g.I[n], g.Rt[n], R, a.Bnew, a.clip != 0);
         TDK_LAUNCH_CHECK(ctx);
       }
     }
@@ -772,6 +822,8 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
     rep->fit_core = hs.fit;
     rep->fit_Y = normY2 ? hs.fitY : nan("");
     rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    rep->form = TDK_ALS_RAN_STEPS;
+    rep->grid = 0;
   }
   return status;
 }
@@ -862,14 +914,15 @@ int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double*
   // HOSVD start is computed first and handed to either form as a given start.
   tdk_als_opts oo = *o_in;
   const tdk_als_opts* o = &oo;
-  if (oo.init == TDK_INIT_HOSVD && !ctx->als_multi_kernel && !(oo.timeout_s > 0)) {
+  const bool steps = oo.form == TDK_ALS_FORM_STEPS;
+  if (oo.init == TDK_INIT_HOSVD && !steps && !(oo.timeout_s > 0)) {
     const int rc0 = (dtype == TDK_F64) ? hosvd_into<double>(ctx, g, reinterpret_cast<const double*>(G), U, o, B_io, A_io)
                                        : hosvd_into<float>(ctx, g, reinterpret_cast<const float*>(G), U, o, B_io, A_io);
     if (rc0) return rc0;
     oo.init = TDK_INIT_GIVEN;
   }
   int rc = TDK_ENOTSUP;
-  if (!ctx->als_multi_kernel) {
+  if (!steps) {
     rc = (dtype == TDK_F64)
              ? als_persistent_t<double>(ctx, g, reinterpret_cast<const double*>(G), U, normY2, o, B_io, A_io,
                                         lambda_out, rep)

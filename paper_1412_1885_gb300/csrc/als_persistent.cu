@@ -1283,7 +1283,11 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   double* nG2 = cv.take<double>(1);
   a.rpart = cv.take<double>(grid);
   unsigned long long* prof = nullptr;
+#ifdef TDK_TESTING
   const bool want_prof = getenv("TDK_ALS_PROFILE") != nullptr;
+#else
+  const bool want_prof = false;
+#endif
   if (want_prof) {
     TDK_CUDA_TRY(cudaMallocAsync((void**)&prof, 16 * sizeof(unsigned long long), ctx->stream));
     TDK_CUDA_TRY(cudaMemsetAsync(prof, 0, 16 * sizeof(unsigned long long), ctx->stream));
@@ -1353,6 +1357,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
     rep->fit_core = hs.fit;
     rep->fit_Y = normY2 ? hs.fitY : nan("");
     rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    rep->form = small ? TDK_ALS_RAN_ONE_CTA : TDK_ALS_RAN_GRID;
+    rep->grid = small ? 1 : grid;
   }
   return status;
 }

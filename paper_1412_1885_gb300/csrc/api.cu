@@ -8,8 +8,10 @@ namespace tdk {
 
 int ws_reserve(tdk_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_size) return TDK_OK;
+#ifdef TDK_TESTING
   if (ctx->fail_alloc_after == 0) return TDK_ENOMEM;
   if (ctx->fail_alloc_after > 0) ctx->fail_alloc_after--;
+#endif
   if (ctx->ws) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->ws);
@@ -26,7 +28,10 @@ int ws_reserve(tdk_ctx* ctx, size_t bytes) {
   return TDK_OK;
 }
 
-int make_geom(const tdk_tucker_desc* d, Geom* g) {
+// geometry of a descriptor; the rule R_n + p <= I_n is checked against
+// i1_check for the first mode (a slab of a tensor whose first dimension is
+// i1_check may hold fewer rows than the sketch width)
+static int make_geom_checked(const tdk_tucker_desc* d, int64_t i1_check, Geom* g) {
   if (!d || !g) return TDK_EINVAL;
   if (d->N < 2 || d->N > TDK_MAX_MODES) return TDK_EINVAL;
   if (d->dtype != TDK_F64 && d->dtype != TDK_F32 && d->dtype != TDK_BF16) return TDK_EINVAL;
@@ -39,7 +44,7 @@ int make_geom(const tdk_tucker_desc* d, Geom* g) {
   for (int n = 0; n < d->N; ++n) {
     if (d->I[n] < 1 || d->R[n] < 1) return TDK_EINVAL;
     int64_t rt = (int64_t)d->R[n] + d->p;
-    if (rt > TDK_MAX_RANK || rt > d->I[n]) return TDK_EINVAL;
+    if (rt > TDK_MAX_RANK || rt > (n == 0 ? i1_check : d->I[n])) return TDK_EINVAL;
     g->I[n] = d->I[n];
     g->Rt[n] = (int)rt;
     if (g->numel > (((int64_t)1 << 62) / d->I[n])) return TDK_EINVAL;
@@ -49,6 +54,65 @@ int make_geom(const tdk_tucker_desc* d, Geom* g) {
   }
   g->L = d->I[d->N - 1];
   g->M = g->numel / g->L;
+  return TDK_OK;
+}
+
+int make_geom(const tdk_tucker_desc* d, Geom* g) { return make_geom_checked(d, d ? d->I[0] : 0, g); }
+
+// geometry of a slab of rows of mode 1 (the sharded form)
+static int make_geom_slab(const tdk_tucker_desc* d, int64_t row_off, int64_t I1_total, Geom* g) {
+  if (!d || row_off < 0 || I1_total < 1 || d->I[0] < 1 || d->I[0] > I1_total - row_off) return TDK_EINVAL;
+  return make_geom_checked(d, I1_total, g);
+}
+
+// W_k^(n) drawn from the seed into one stream-ordered allocation: rows
+// [row0[k], row0[k] + rows[k]) of every W_k^(n); ptrs[n*N + k] point into it
+static int seeded_w(tdk_ctx* ctx, const Geom& g, uint64_t seed, const int64_t* rows, const int64_t* row0,
+                    double** buf, const double** ptrs) {
+  size_t total = 0;
+  for (int n = 0; n < g.N; ++n)
+    for (int k = 0; k < g.N; ++k)
+      if (k != n) total += (size_t)rows[k] * g.Rt[n];
+  *buf = nullptr;
+  if (cudaMallocAsync((void**)buf, sizeof(double) * total, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TDK_ENOMEM;
+  }
+  double* mats[TDK_MAX_MODES * TDK_MAX_MODES] = {};
+  size_t off = 0;
+  for (int n = 0; n < g.N; ++n)
+    for (int k = 0; k < g.N; ++k) {
+      ptrs[n * g.N + k] = nullptr;
+      if (k == n) continue;
+      mats[n * g.N + k] = *buf + off;
+      ptrs[n * g.N + k] = *buf + off;
+      off += (size_t)rows[k] * g.Rt[n];
+    }
+  const int rc = draw_sketch_matrices(ctx, g.N, rows, row0, g.Rt, seed, mats);
+  if (rc) {
+    cudaFreeAsync(*buf, ctx->stream);
+    *buf = nullptr;
+  }
+  return rc;
+}
+
+// the sketch pass alone: Z_n of every mode, packed by zoff, into a
+// stream-ordered allocation that the caller frees (Z stays out of the
+// workspace, which the sub-steps carve)
+static int sketch_pass(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc, const void* Y,
+                       const double* const W[], double** Zout) {
+  double* Z = nullptr;
+  if (cudaMallocAsync((void**)&Z, sizeof(double) * (size_t)g.zoff[g.N], ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TDK_ENOMEM;
+  }
+  const int rc = desc->prec == TDK_PREC_TC ? sketch_tc(ctx, g, desc->dtype, Y, W, Z)
+                                           : sketch_simt(ctx, g, desc->dtype, Y, W, Z);
+  if (rc) {
+    cudaFreeAsync(Z, ctx->stream);
+    return rc;
+  }
+  *Zout = Z;
   return TDK_OK;
 }
 
@@ -72,6 +136,7 @@ const char* tdk_strerror(int code) {
     case TDK_ETIMEOUT: return "bounded wait or time limit exceeded";
     case TDK_ENOTSUP: return "not supported for this configuration";
     case TDK_ESCRATCH: return "problem exceeds the static scratch array (TDK_SKETCH_STATIC_MAX_BYTES)";
+    case TDK_EIO: return "file could not be read or written, or does not hold what the call expects";
     case TDK_WRANKDEF: return "warning: rank-deficient sketch completed";
     case TDK_WNOCONV: return "warning: ALS stopped at max_sweeps";
     case TDK_WPINV: return "warning: pseudo-inverse used in an ALS solve";
@@ -195,50 +260,41 @@ int tdk_ctx_profile_read(tdk_ctx* c, int region, double* total_ms, int64_t* laun
   return TDK_OK;
 }
 
-// selects the ALS form: 0 = persistent kernel when the core fits (default),
-// 1 = one kernel per step (test hook, not in the public header)
-int tdk_ctx_test_als_form(tdk_ctx* c, int multi) {
-  if (!c) return TDK_EINVAL;
-  c->als_multi_kernel = multi != 0;
-  return TDK_OK;
-}
+size_t tdk_ctx_workspace_bytes(const tdk_ctx* c) { return c ? c->ws_size : 0; }
 
-// test hook (not in the public header): make the n-th workspace growth fail
+#ifdef TDK_TESTING
+// test library only (not in the public header): make the n-th workspace
+// growth fail (after = 0: the next one; -1: none)
 int tdk_ctx_test_fail_alloc(tdk_ctx* c, int after) {
   if (!c) return TDK_EINVAL;
   c->fail_alloc_after = after;
   return TDK_OK;
 }
+#endif
 
 int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
                   double* const U_out[], double* const Z_out[]) {
-  if (!ctx || !desc || !Y || !W || !U_out) return TDK_EINVAL;
+  if (!ctx || !desc || !Y || !U_out) return TDK_EINVAL;
   Geom g;
   int rc = make_geom(desc, &g);
   if (rc) return rc;
   for (int n = 0; n < g.N; ++n) {
     if (!U_out[n]) return TDK_EINVAL;
     for (int k = 0; k < g.N; ++k)
-      if (k != n && !W[n * g.N + k]) return TDK_EINVAL;
+      if (W && k != n && !W[n * g.N + k]) return TDK_EINVAL;
   }
   if (desc->prec == TDK_PREC_TC && desc->dtype == TDK_F64) return TDK_ENOTSUP;
   cudaSetDevice(ctx->device);
-  // the packed sketch lives at the end of a separate workspace slice: allocate
-  // it first so the kernels' own carving does not overlap it
-  double* Z = nullptr;
-  {
-    size_t zbytes = sizeof(double) * (size_t)g.zoff[g.N];
-    // Z is kept in its own allocation to survive the sub-steps' workspace use
-    static_assert(sizeof(double) == 8, "");
-    if (cudaMallocAsync((void**)&Z, zbytes, ctx->stream) != cudaSuccess) {
-      cudaGetLastError();
-      return TDK_ENOMEM;
-    }
+  double* wbuf = nullptr;
+  const double* wp[TDK_MAX_MODES * TDK_MAX_MODES];
+  if (!W) {
+    int64_t row0[TDK_MAX_MODES] = {};
+    rc = seeded_w(ctx, g, desc->seed, g.I, row0, &wbuf, wp);
+    if (rc) return rc;
+    W = wp;
   }
-  if (desc->prec == TDK_PREC_TC)
-    rc = sketch_tc(ctx, g, desc->dtype, Y, W, Z);
-  else
-    rc = sketch_simt(ctx, g, desc->dtype, Y, W, Z);
+  double* Z = nullptr;
+  rc = sketch_pass(ctx, g, desc, Y, W, &Z);
   if (rc == TDK_OK) rc = cholqr2(ctx, g, Z, U_out);
   if (rc == TDK_OK && Z_out) {
     for (int n = 0; n < g.N; ++n)
@@ -248,24 +304,115 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
           rc = TDK_ECUDA;
       }
   }
-  cudaFreeAsync(Z, ctx->stream);
+  if (Z) cudaFreeAsync(Z, ctx->stream);
+  if (wbuf) cudaFreeAsync(wbuf, ctx->stream);
   return rc;
+}
+
+int tucker_sketch_partial(tdk_ctx* ctx, const tdk_tucker_desc* slab, int64_t row_off, int64_t I1_total,
+                          const void* Y, const double* const W[], double* const Z_out[]) {
+  if (!ctx || !slab || !Y || !Z_out) return TDK_EINVAL;
+  Geom g;
+  int rc = make_geom_slab(slab, row_off, I1_total, &g);
+  if (rc) return rc;
+  for (int n = 0; n < g.N; ++n) {
+    if (!Z_out[n]) return TDK_EINVAL;
+    for (int k = 0; k < g.N; ++k)
+      if (W && k != n && !W[n * g.N + k]) return TDK_EINVAL;
+  }
+  if (slab->prec == TDK_PREC_TC && slab->dtype == TDK_F64) return TDK_ENOTSUP;
+  cudaSetDevice(ctx->device);
+  double* wbuf = nullptr;
+  const double* wp[TDK_MAX_MODES * TDK_MAX_MODES];
+  if (!W) {
+    int64_t row0[TDK_MAX_MODES] = {};
+    row0[0] = row_off;  // the slab's rows of every W_1^(n), at their global index
+    rc = seeded_w(ctx, g, slab->seed, g.I, row0, &wbuf, wp);
+    if (rc) return rc;
+  } else {
+    // the slab's rows of W_1^(n): Z_n (n >= 2) sums Eq. 22's products over
+    // the slab's i_1 only, and Z_1's rows are the slab's own
+    for (int n = 0; n < g.N; ++n)
+      for (int k = 0; k < g.N; ++k)
+        wp[n * g.N + k] = (k == n) ? nullptr : (k == 0 ? W[n * g.N] + row_off * g.Rt[n] : W[n * g.N + k]);
+  }
+  double* Z = nullptr;
+  rc = sketch_pass(ctx, g, slab, Y, wp, &Z);
+  if (rc == TDK_OK)
+    for (int n = 0; n < g.N; ++n)
+      if (cudaMemcpyAsync(Z_out[n], Z + g.zoff[n], sizeof(double) * g.I[n] * g.Rt[n], cudaMemcpyDeviceToDevice,
+                          ctx->stream) != cudaSuccess)
+        rc = TDK_ECUDA;
+  if (Z) cudaFreeAsync(Z, ctx->stream);
+  if (wbuf) cudaFreeAsync(wbuf, ctx->stream);
+  return rc;
+}
+
+int tucker_core_partial(tdk_ctx* ctx, const tdk_tucker_desc* slab, int64_t I1_total, const void* Y,
+                        const double* const U[], void* G_out, double* normY2) {
+  if (!ctx || !slab || !Y || !U || !G_out) return TDK_EINVAL;
+  Geom g;
+  int rc = make_geom_slab(slab, 0, I1_total, &g);
+  if (rc) return rc;
+  for (int n = 0; n < g.N; ++n)
+    if (!U[n]) return TDK_EINVAL;
+  if (slab->prec == TDK_PREC_TC && slab->dtype == TDK_F64) return TDK_ENOTSUP;
+  cudaSetDevice(ctx->device);
+  if (slab->prec == TDK_PREC_TC) return core_tc(ctx, g, slab->dtype, Y, U, G_out, normY2);
+  return core_simt(ctx, g, slab->dtype, Y, U, G_out, normY2);
+}
+
+int tdk_gram(tdk_ctx* ctx, const double* Z, int64_t rows, int cols, double* gram_out) {
+  if (!ctx || !Z || !gram_out || rows < 1 || cols < 1 || cols > TDK_MAX_RANK) return TDK_EINVAL;
+  cudaSetDevice(ctx->device);
+  return gram_one(ctx, Z, rows, cols, gram_out);
+}
+
+int tdk_orth_apply(tdk_ctx* ctx, const double* gram, const double* Z, int64_t rows, int cols, double* Q_out) {
+  if (!ctx || !gram || !Z || !Q_out || rows < 1 || cols < 1 || cols > TDK_MAX_RANK) return TDK_EINVAL;
+  cudaSetDevice(ctx->device);
+  return orth_apply_one(ctx, gram, Z, rows, cols, Q_out);
+}
+
+int tdk_orth(tdk_ctx* ctx, const double* Z, int64_t rows, int cols, double* U_out) {
+  if (!ctx || !Z || !U_out || cols < 1 || cols > TDK_MAX_RANK || rows < cols) return TDK_EINVAL;
+  cudaSetDevice(ctx->device);
+  Geom g{};
+  g.N = 1;
+  g.I[0] = rows;
+  g.Rt[0] = cols;
+  g.zoff[0] = 0;
+  g.zoff[1] = rows * cols;
+  double* const dst[1] = {U_out};
+  return cholqr2(ctx, g, Z, dst);
 }
 
 int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
                   double* const U_io[]) {
-  if (!ctx || !desc || !Y || !W || !U_io) return TDK_EINVAL;
+  if (!ctx || !desc || !Y || !U_io) return TDK_EINVAL;
   Geom g;
   int rc = make_geom(desc, &g);
   if (rc) return rc;
   for (int n = 0; n < g.N; ++n) {
     if (!U_io[n]) return TDK_EINVAL;
     for (int k = 0; k < g.N; ++k)
-      if (k != n && !W[n * g.N + k]) return TDK_EINVAL;
+      if (W && k != n && !W[n * g.N + k]) return TDK_EINVAL;
   }
   if (desc->dtype != TDK_F64 && desc->dtype != TDK_F32) return TDK_ENOTSUP;
   cudaSetDevice(ctx->device);
-  return refine_pass(ctx, g, desc->dtype, Y, W, U_io);
+  double* wbuf = nullptr;
+  const double* wp[TDK_MAX_MODES * TDK_MAX_MODES];
+  if (!W) {
+    // the pass matrices are Rt_k x Rt_n: the first Rt_k rows of the seed's draw
+    int64_t rows[TDK_MAX_MODES], row0[TDK_MAX_MODES] = {};
+    for (int n = 0; n < g.N; ++n) rows[n] = g.Rt[n];
+    rc = seeded_w(ctx, g, desc->seed, rows, row0, &wbuf, wp);
+    if (rc) return rc;
+    W = wp;
+  }
+  rc = refine_pass(ctx, g, desc->dtype, Y, W, U_io);
+  if (wbuf) cudaFreeAsync(wbuf, ctx->stream);
+  return rc;
 }
 
 int tucker_core(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const U[], void* G_out,
@@ -294,6 +441,7 @@ int ffcp_als(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* G, const dou
   if (opts->nonneg < TDK_NONNEG_NONE || opts->nonneg > TDK_NONNEG_MU) return TDK_EINVAL;
   if (!(opts->l1 >= 0.0) || opts->l1 > 1e300) return TDK_EINVAL;
   if (opts->l1 > 0.0 && opts->nonneg > TDK_NONNEG_LS) return TDK_EINVAL;
+  if (opts->form != TDK_ALS_FORM_AUTO && opts->form != TDK_ALS_FORM_STEPS) return TDK_EINVAL;
   for (int n = 0; n < g.N; ++n) {
     if (opts->R > g.Rt[n]) return TDK_EINVAL;
     if (!U[n] || !B_io[n] || !A_io[n]) return TDK_EINVAL;

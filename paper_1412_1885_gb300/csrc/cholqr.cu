@@ -1,5 +1,5 @@
-// Orthonormal basis of every sketch Z_n (Sec. IV-A step 3; Alg. 2
-// "compute U as an orthonormal basis of Z").  The paper's distributed variant
+// Orthonormal basis of every sketch Z_n (Sec. IV-A, range-finder step 3;
+// Alg. 2, the basis of each mode's sketch).  The paper's distributed variant
 // (Eq. 23) forms the Gram sum_s Z_s^T Z_s from row blocks and whitens it;
 // here the same row-block Gram feeds a Cholesky factor instead of an EVD
 // (CholQR), applied twice (CholQR2) so that the result is orthonormal to
@@ -267,7 +267,65 @@ __global__ void __launch_bounds__(256) cgs2_kernel(const double* __restrict__ Z,
   if (threadIdx.x == 0) atomicOr(status, TDK_STATUS_RANKDEF);
 }
 
+// a failed Cholesky of a standalone Gram shows in the context's status word
+__global__ void fail_to_status_kernel(const int* __restrict__ fail, unsigned* __restrict__ status) {
+  if (threadIdx.x == 0 && fail[0]) atomicOr(status, TDK_STATUS_RANKDEF);
+}
+
+QRArgs one_matrix(int64_t rows, int cols) {
+  QRArgs q{};
+  q.N = 1;
+  q.I[0] = rows;
+  q.Rt[0] = cols;
+  q.zoff[0] = 0;
+  q.zoff[1] = rows * cols;
+  q.nchunk[0] = (int)((rows + GRAM_ROWS - 1) / GRAM_ROWS);
+  q.gp_off[0] = 0;
+  return q;
+}
+
 }  // namespace
+
+int gram_one(tdk_ctx* ctx, const double* Z, int64_t rows, int cols, double* gram_out) {
+  const QRArgs q = one_matrix(rows, cols);
+  Planner pl;
+  pl.take<double>((size_t)q.nchunk[0] * cols * cols);
+  pl.take<int>(TDK_MAX_MODES);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  double* gpart = cv.take<double>((size_t)q.nchunk[0] * cols * cols);
+  int* fail = cv.take<int>(TDK_MAX_MODES);
+  TDK_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int) * TDK_MAX_MODES, ctx->stream));
+  gram_partial_kernel<<<dim3((unsigned)q.nchunk[0], 1), 256, 0, ctx->stream>>>(Z, q, gpart, fail);
+  TDK_LAUNCH_CHECK(ctx);
+  gram_reduce_kernel<<<dim3((unsigned)((cols * cols + 255) / 256), 1), 256, 0, ctx->stream>>>(q, gpart, fail,
+                                                                                               gram_out);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
+int orth_apply_one(tdk_ctx* ctx, const double* gram, const double* Z, int64_t rows, int cols, double* Q_out) {
+  const QRArgs q = one_matrix(rows, cols);
+  Planner pl;
+  pl.take<double>((size_t)TDK_MAX_RANK * TDK_MAX_RANK);
+  pl.take<int>(TDK_MAX_MODES);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  double* rinv = cv.take<double>((size_t)TDK_MAX_RANK * TDK_MAX_RANK);
+  int* fail = cv.take<int>(TDK_MAX_MODES);
+  TDK_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int) * TDK_MAX_MODES, ctx->stream));
+  chol_kernel<<<1, 256, 0, ctx->stream>>>(q, gram, rinv, fail);
+  TDK_LAUNCH_CHECK(ctx);
+  Dst d{};
+  d.p[0] = Q_out;
+  apply_rinv_kernel<<<dim3((unsigned)std::max(1, 2 * ctx->num_sms), 1), 256, 0, ctx->stream>>>(Z, q, rinv, fail, d);
+  TDK_LAUNCH_CHECK(ctx);
+  fail_to_status_kernel<<<1, 32, 0, ctx->stream>>>(fail, ctx->d_status);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
 
 int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[]) {
   QRArgs q{};

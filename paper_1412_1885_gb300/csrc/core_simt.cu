@@ -1,4 +1,4 @@
-// Core G = Y x_1 U_1^T ... x_N U_N^T on CUDA cores (Alg. 2, "Y <- Y x_n U^T"
+// Core G = Y x_1 U_1^T ... x_N U_N^T on CUDA cores (Alg. 2, the mode-n projection steps
 // for every n; Eq. 1).  The contiguous mode N is contracted first:
 //   X_1[row, r] = sum_col Y[row, col] U_N[col, r]        (row = (i_1..i_{N-1}))
 // which is the only pass over the full tensor (it also accumulates ||Y||^2);

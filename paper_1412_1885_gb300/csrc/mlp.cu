@@ -1,5 +1,5 @@
 // Learned initialiser for FFCP (no counterpart in the paper, whose ALS starts
-// from random or HOSVD factors; Alg. 1 "Initialize A").  A small MLP maps a
+// from random or HOSVD factors, the first step of Alg. 1).  A small MLP maps a
 // Tucker core G (Alg. 2 output) to initial core-space factors B_n.
 //
 //   canonicalise  V_n = eigenvectors of G_(n) G_(n)^T (HOSVD of the core) by
@@ -721,15 +721,95 @@ int tdk_mlp_get(tdk_ctx* ctx, tdk_mlp* m, int what, float* host_out) {
   const float* src = nullptr;
   size_t n = 0;
   const int64_t B = m->last_batch, RR = (int64_t)m->Rt * m->Rt;
+  // stored BF16 intermediates: [batch x cols] rows of pitch ld, widened on the host
+  const __nv_bfloat16* sb = nullptr;
+  int cols = 0, ld = 0;
   switch (what) {
     case TDK_MLP_PARAMS: src = m->theta; n = m->P; break;
     case TDK_MLP_GRADS: src = m->grad; n = m->P; break;
     case TDK_MLP_CANON_CORE: src = m->Xs; n = B * m->din; break;
     case TDK_MLP_ROTATIONS: src = m->V; n = B * m->N * RR; break;
     case TDK_MLP_OUTPUT: src = m->O; n = B * m->dout; break;
+    case TDK_MLP_Z1: src = m->Z1; n = B * m->H; break;
+    case TDK_MLP_Z2: src = m->Z2; n = B * m->H; break;
+    case TDK_MLP_INPUT: sb = m->Xb; cols = m->din; ld = m->ld_din; break;
+    case TDK_MLP_H1: sb = m->H1; cols = m->H; ld = m->ld_H; break;
+    case TDK_MLP_H2: sb = m->H2; cols = m->H; ld = m->ld_H; break;
+    case TDK_MLP_DO: sb = m->dO; cols = m->dout; ld = m->ld_dout; break;
+    case TDK_MLP_DZ2: sb = m->dZ2; cols = m->H; ld = m->ld_H; break;
+    case TDK_MLP_DZ1: sb = m->dZ1; cols = m->H; ld = m->ld_H; break;
     default: return TDK_EINVAL;
   }
+  if (sb) {
+    std::vector<uint16_t> raw((size_t)B * ld);
+    if (!raw.empty())
+      TDK_CUDA_TRY(cudaMemcpyAsync(raw.data(), sb, sizeof(uint16_t) * raw.size(), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    TDK_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int64_t b = 0; b < B; ++b)
+      for (int c = 0; c < cols; ++c) {
+        // a BF16 value is the upper half of the FP32 value with the same bits
+        const uint32_t bits = (uint32_t)raw[(size_t)b * ld + c] << 16;
+        float f;
+        std::memcpy(&f, &bits, sizeof f);
+        host_out[b * cols + c] = f;
+      }
+    return TDK_OK;
+  }
   if (n) TDK_CUDA_TRY(cudaMemcpyAsync(host_out, src, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  TDK_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return TDK_OK;
+}
+
+// checkpoint file: tag, shape, parameter count, Adam step, then the
+// parameters and Adam's two moment vectors (FP32, host byte order, which is
+// little-endian on every platform this library builds for)
+static const char kMlpTag[8] = {'T', 'D', 'K', 'M', 'L', 'P', '0', '1'};
+
+int tdk_mlp_save(tdk_ctx* ctx, const tdk_mlp* m, const char* path) {
+  if (!ctx || !m || !path) return TDK_EINVAL;
+  cudaSetDevice(ctx->device);
+  std::vector<float> buf((size_t)3 * m->P);
+  const float* src[3] = {m->theta, m->m, m->v};
+  for (int i = 0; i < 3; ++i)
+    TDK_CUDA_TRY(cudaMemcpyAsync(buf.data() + (size_t)i * m->P, src[i], sizeof(float) * m->P,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  TDK_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  FILE* f = fopen(path, "wb");
+  if (!f) return TDK_EIO;
+  const int32_t shape[4] = {m->N, m->Rt, m->H, 0};
+  const int64_t counts[2] = {m->P, m->step};
+  bool ok = fwrite(kMlpTag, 1, 8, f) == 8 && fwrite(shape, sizeof(int32_t), 4, f) == 4 &&
+            fwrite(counts, sizeof(int64_t), 2, f) == 2 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? TDK_OK : TDK_EIO;
+}
+
+int tdk_mlp_load(tdk_ctx* ctx, tdk_mlp* m, const char* path) {
+  if (!ctx || !m || !path) return TDK_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return TDK_EIO;
+  char tag[8];
+  int32_t shape[4];
+  int64_t counts[2];
+  std::vector<float> buf((size_t)3 * m->P);
+  bool ok = fread(tag, 1, 8, f) == 8 && std::memcmp(tag, kMlpTag, 8) == 0 && fread(shape, sizeof(int32_t), 4, f) == 4 &&
+            shape[0] == m->N && shape[1] == m->Rt && shape[2] == m->H && fread(counts, sizeof(int64_t), 2, f) == 2 &&
+            counts[0] == m->P && counts[1] >= 0 && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  if (ok) {
+    char extra;
+    ok = fread(&extra, 1, 1, f) == 0;  // nothing after the three vectors
+  }
+  fclose(f);
+  if (!ok) return TDK_EIO;
+  cudaSetDevice(ctx->device);
+  float* dst[3] = {m->theta, m->m, m->v};
+  for (int i = 0; i < 3; ++i)
+    TDK_CUDA_TRY(cudaMemcpyAsync(dst[i], buf.data() + (size_t)i * m->P, sizeof(float) * m->P, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  refresh_kernel<<<2 * ctx->num_sms, 256, 0, ctx->stream>>>(m->theta, segs_of(m));
+  TDK_LAUNCH_CHECK(ctx);
+  m->step = counts[1];
   TDK_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return TDK_OK;
 }

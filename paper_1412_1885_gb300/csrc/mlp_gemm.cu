@@ -214,7 +214,8 @@ int gemm_bf16(tdk_ctx* ctx, const GemmOp& op) {
 
 }  // namespace tdk
 
-// test hook: one GEMM through the library (operands and outputs caller-owned)
+#ifdef TDK_TESTING
+// test library only: one GEMM through the library (operands and outputs caller-owned)
 extern "C" int tdk_test_gemm_bf16(tdk_ctx* ctx, int M, int N, int K, const void* A, int lda, int a_mn,
                                   const void* B, int ldb, int b_mn, int mode, const float* bias,
                                   const float* zin, int ldz, float* outf, int ldf, void* outb, int ldob) {
@@ -246,3 +247,4 @@ extern "C" int tdk_test_gemm_bf16(tdk_ctx* ctx, int M, int N, int K, const void*
   if (mode < 0 || mode > 3) return TDK_EINVAL;
   return gemm_bf16(ctx, op);
 }
+#endif  // TDK_TESTING

@@ -341,22 +341,60 @@ constexpr int MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_sketch_scratch[SKETCH_STATIC_BYTES];
 
 std::mutex g_scratch_mu;
-void* g_scratch_addr[MAX_DEVICES];
+struct ScratchAddr {
+  unsigned long long ctx_id;  // context the address was resolved in (0: unknown)
+  void* addr;
+};
+ScratchAddr g_scratch_addr[MAX_DEVICES];
 
-// address of the array on the current device; resolved once per device
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// unique identity of the CUDA context current on this thread, 0 if the
+// driver cannot tell (the caller then resolves the address on every call)
+unsigned long long current_context_id() {
+  static PfnCtxGetCurrent get_cur = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PfnCtxGetCurrent>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PfnCtxGetId>(p);
+    cudaGetLastError();
+  }
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// address of the array on the current device; resolved once per device and
+// context (a context created after a device reset loads the module anew)
 int static_scratch(int device, unsigned char** out) {
   if (device < 0 || device >= MAX_DEVICES) return TDK_EINVAL;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[device]) {
+  const unsigned long long id = current_context_id();
+  ScratchAddr& s = g_scratch_addr[device];
+  if (!s.addr || id == 0 || s.ctx_id != id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_sketch_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
+      s.addr = nullptr;
       return TDK_ECUDA;
     }
-    g_scratch_addr[device] = p;
+    s.addr = p;
+    s.ctx_id = id;
   }
-  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+  *out = static_cast<unsigned char*>(s.addr);
   return TDK_OK;
 }
 

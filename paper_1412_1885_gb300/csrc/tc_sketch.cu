@@ -18,7 +18,7 @@
 // range, p-range) writes its own partial block (the blockwise sums of Eq. 22);
 // a fixed-order compensated FP32 reduction produces Z.
 //
-// CORE (Alg. 2, the first "Y <- Y x_n U^T", contiguous mode): X_1 = Y_(rows) U_N
+// CORE (Alg. 2, the first projection step, contiguous mode): X_1 = Y_(rows) U_N
 // with U split hi+lo into one B operand [U_hi | U_lo]; ||Y||^2 on the side.
 //
 // FP32 data: TMA brings FP32 boxes; converter warps split every value into
@@ -799,7 +799,11 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   }
   a.ustride = (o + 63) / 64 * 64;
   a.status = ctx->d_status;
+#ifdef TDK_TESTING
   const bool want_prof = getenv("TDK_SKETCH_PROFILE") != nullptr;
+#else
+  const bool want_prof = false;
+#endif
   if (want_prof) {
     TDK_CUDA_TRY(cudaMallocAsync((void**)&a.prof, 16 * sizeof(unsigned long long), ctx->stream));
     TDK_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 16 * sizeof(unsigned long long), ctx->stream));
@@ -897,7 +901,8 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
 
 }  // namespace tdk
 
-// ---- test hook (not in the public header): a bounded wait that cannot be
+#ifdef TDK_TESTING
+// ---- test library only (not in the public header): a bounded wait that cannot be
 // satisfied.  One thread waits for the first phase of an mbarrier that nothing
 // arrives at; after limit_ns it raises the timeout bit in the context's status
 // word and returns, exactly as the waits of the passes above do.
@@ -931,3 +936,4 @@ extern "C" int tdk_test_bounded_wait(tdk_ctx* ctx, unsigned long long limit_ns) 
   TDK_LAUNCH_CHECK(ctx);
   return TDK_OK;
 }
+#endif  // TDK_TESTING

@@ -25,8 +25,7 @@ struct tdk_ctx {
   size_t ws_size = 0;
   unsigned* d_status = nullptr;  // device status word (TDK_STATUS_* bits)
   int64_t launches = 0;
-  int fail_alloc_after = -1;   // test hook: fail the n-th workspace growth
-  bool als_multi_kernel = false;  // force the kernel-per-step ALS form
+  int fail_alloc_after = -1;   // set only by the test library's hook: fail the n-th workspace growth
   // event timing of the main kernels (regions 0: sketch pass, 1: core pass)
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev[2];
@@ -129,6 +128,12 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
               double* Zdst);
 // CholQR2 of every Z_n (packed FP64) into U_out
 int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[]);
+// one matrix Z [rows x cols]: upper triangle of Z^T Z; Q = Z R^-1 from a Gram
+int gram_one(tdk_ctx* ctx, const double* Z, int64_t rows, int cols, double* gram_out);
+int orth_apply_one(tdk_ctx* ctx, const double* gram, const double* Z, int64_t rows, int cols, double* Q_out);
+// seeded test matrices: W_out[n*N + k] <- rows [row0_k, row0_k + rows_k) of W_k^(n)
+int draw_sketch_matrices(tdk_ctx* ctx, int N, const int64_t* rows, const int64_t* row0, const int* Rt,
+                         uint64_t seed, double* const W_out[]);
 // core: G (T) and ||Y||^2 (FP64 device scalar, may be null)
 int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[],
               void* G, double* normY2);

@@ -13,7 +13,7 @@ This module draws inputs only; it holds none of the decomposition arithmetic
   test matrix Omega_n of the range finder (Sec. IV-A, step 1).  They are drawn
   N(0,1) and stored rounded to the nearest BF16 value, so every precision form
   of the sketch (FP64, FP32, BF16 tensor cores) consumes the identical Omega.
-* Initial CP factors for ALS (Alg. 1, "Initialize A").
+* Initial CP factors for ALS (the first step of Alg. 1).
 
 Every draw is keyed by (seed, tag...) through numpy's SeedSequence, so a draw
 does not depend on which other draws were made before it.  Big tensors are
@@ -137,6 +137,12 @@ def tucker_dense(shape, ranks, seed: int) -> np.ndarray:
         U = r.standard_normal((I, Rn))
         out = np.moveaxis(np.tensordot(U, out, axes=([1], [n])), 0, n)
     return out
+
+
+def omega_seed(w: "Workload") -> int:
+    """Seed of a workload's test matrices when the library draws them
+    (tdk_tucker_desc.seed): the workload seed with the sketch offset."""
+    return (int(w.seed) ^ OMEGA_SEED_XOR) & ((1 << 64) - 1)
 
 
 def sketch_matrices(shape, Rt, seed: int, shared: bool = False):

@@ -43,6 +43,22 @@ def core_abs_bound(Y, U):
     return oracle.tucker_core(np.abs(Y), [np.abs(u) for u in U])
 
 
+def basis_tol(Z) -> float:
+    """Distance to expect between two FP64 orthonormal bases of the same Z
+    (CholQR2 against Householder, both with diag(R) > 0): the QR factors of Z
+    move by about cond(Z) units of rounding; 1000 units of 2^-52 per unit of
+    condition, and never below 1e-12."""
+    return max(1e-12, 1e3 * 2.220446049250313e-16 * float(np.linalg.cond(np.asarray(Z, dtype=np.float64))))
+
+
+def bf16_ulp(x) -> np.ndarray:
+    """Spacing of the BF16 values (8 significant bits) at |x|: 2^(e - 7) for
+    |x| in [2^e, 2^(e+1)), between 2^-8 and 2^-7 of |x|."""
+    x = np.abs(np.asarray(x, dtype=np.float64))
+    _, e = np.frexp(np.where(x > 0, x, 1.0))
+    return np.where(x > 0, np.ldexp(1.0, e - 8), 0.0)
+
+
 def recon_err(normY2: float, G: np.ndarray) -> float:
     """||Y - [[G; U]]|| / ||Y|| for orthonormal U (Pythagoras)."""
     return float(np.sqrt(max(0.0, normY2 - float(np.sum(np.asarray(G, dtype=np.float64) ** 2))) / normY2))

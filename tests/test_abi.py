@@ -44,6 +44,18 @@ def test_library_exports_every_declared_symbol(L):
         assert hasattr(L, name), name
 
 
+def test_test_hooks_live_only_in_the_test_build(L):
+    """The product library exports no test hook; libtdk_test.so, the same
+    sources built with -DTDK_TESTING, exports them and every public symbol."""
+    import paper_1412_1885_gb300 as t
+
+    for name in t.TEST_EXPORTS:
+        assert not hasattr(L, name), name
+    T = t.lib_test()
+    for name in t.TEST_EXPORTS + _declared_functions():
+        assert hasattr(T, name), name
+
+
 def test_python_binding_names_match_header():
     import paper_1412_1885_gb300 as t
 
@@ -65,10 +77,13 @@ def test_strerror_and_argument_checks_without_gpu(L):
 def test_struct_layouts_match_header():
     import paper_1412_1885_gb300 as t
 
-    # int N, dtype, prec, p; int64 I[8]; int R[8]
-    assert ctypes.sizeof(t.TuckerDesc) == 16 + 64 + 32
+    # int N, dtype, prec, p; int64 I[8]; int R[8]; uint64 seed
+    assert ctypes.sizeof(t.TuckerDesc) == 16 + 64 + 32 + 8
+    assert t.TuckerDesc.seed.offset == 112
+    # int R, max_sweeps; double tol; int nonneg, init, check_every, form; double timeout_s, l1
     assert ctypes.sizeof(t.AlsOpts) == 4 + 4 + 8 + 4 * 4 + 8 + 8
-    assert ctypes.sizeof(t.AlsReport) == 4 + 4 + 8 * 3
+    # int sweeps, status; double fit_core, fit_Y, ms; int form, grid
+    assert ctypes.sizeof(t.AlsReport) == 4 + 4 + 8 * 3 + 4 + 4
 
 
 def test_desc_validation_rules():

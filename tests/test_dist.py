@@ -106,3 +106,60 @@ def test_subtensor_layout_on_two_ranks_matches_one_process():
         assert p.exitcode == 0
     assert sorted(n for n, _ in out) == [12, 12]
     assert all(ok for _, ok in out)
+
+
+def test_slab_bounds_partition_the_first_mode():
+    from paper_1412_1885_gb300.sharded import slab_bounds
+
+    for I1 in (1, 7, 60, 3000, 3001):
+        for world in range(1, min(I1, 9) + 1):
+            b = [slab_bounds(I1, world, r) for r in range(world)]
+            assert b[0][0] == 0 and b[-1][1] == I1
+            assert all(b[r][1] == b[r + 1][0] for r in range(world - 1))
+            sizes = [hi - lo for lo, hi in b]
+            assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 1
+    with pytest.raises(ValueError):
+        slab_bounds(3, 4, 0)
+
+
+def _comm_worker(rank, world, port, q):
+    import torch
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1412_1885_gb300.sharded import Comm, slab_bounds
+
+    comm = Comm()
+    a = torch.full((3, 4), float(rank + 1), dtype=torch.float64)
+    b = torch.arange(5, dtype=torch.float32) * (rank + 1)
+    comm.allreduce_sum([a, b])
+    flags = (comm.any_flag(rank == 1), comm.any_flag(False))
+    lo, hi = slab_bounds(7, world, rank)
+    rows = torch.arange(lo * 3, hi * 3, dtype=torch.float64).reshape(hi - lo, 3)
+    counts = [slab_bounds(7, world, r)[1] - slab_bounds(7, world, r)[0] for r in range(world)]
+    full = comm.allgather_rows(rows, counts)
+    q.put((rank, a.tolist(), b.tolist(), flags, full.tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_exchange_layer_sums_flags_and_gathers_on_two_ranks():
+    """The sharded form's exchange (Comm) over gloo: the sums equal the
+    element-wise sums of both ranks' arrays in their own dtypes, a flag set
+    on one rank is seen on both, and uneven row blocks come back stacked in
+    rank order."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_comm_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, a, b, flags, full in out:
+        assert a == [[3.0] * 4] * 3
+        assert b == [0.0, 3.0, 6.0, 9.0, 12.0]
+        assert flags == (True, False)
+        assert full == [[float(3 * i + j) for j in range(3)] for i in range(7)]

@@ -1,7 +1,8 @@
 """Failure detection without a GPU fault: a device wait that runs out of time
 (a barrier that nothing completes) must come back as a status bit and leave
 the context usable; a workspace allocation failure and an ALS time limit must
-come back as error codes."""
+come back as error codes.  The first two use the test build of the library
+(libtdk_test.so), which alone carries the hooks that stage the failures."""
 import numpy as np
 import pytest
 
@@ -31,9 +32,9 @@ def _small_sketch(tdk, ctx):
 
 
 def test_bounded_wait_times_out_into_the_status_word(tdk):
-    ctx = tdk.Context(0)
+    ctx = tdk.Context(0, testing=True)
     assert ctx.sync_status() == 0
-    assert tdk.lib().tdk_test_bounded_wait(ctx.handle, 2_000_000) == 0  # 2 ms
+    assert ctx.L.tdk_test_bounded_wait(ctx.handle, 2_000_000) == 0  # 2 ms
     assert ctx.sync_status() & TDK_STATUS_TIMEOUT
     assert ctx.sync_status() == 0  # read and cleared
     # the context and the device stay usable
@@ -45,12 +46,12 @@ def test_bounded_wait_times_out_into_the_status_word(tdk):
 
 
 def test_workspace_allocation_failure_returns_enomem(tdk):
-    ctx = tdk.Context(0)
-    assert tdk.lib().tdk_ctx_test_fail_alloc(ctx.handle, 0) == 0  # the next growth fails
+    ctx = tdk.Context(0, testing=True)
+    assert ctx.L.tdk_ctx_test_fail_alloc(ctx.handle, 0) == 0  # the next growth fails
     with pytest.raises(tdk.TdkError) as e:
         _small_sketch(tdk, ctx)
     assert e.value.code == tdk.TDK_ENOMEM
-    assert tdk.lib().tdk_ctx_test_fail_alloc(ctx.handle, -1) == 0  # growth allowed again
+    assert ctx.L.tdk_ctx_test_fail_alloc(ctx.handle, -1) == 0  # growth allowed again
     _small_sketch(tdk, ctx)
     assert ctx.sync_status() == 0
     ctx.close()

@@ -16,7 +16,7 @@ import pytest
 import oracle
 import synth
 from oracle import mlp as omlp
-from helpers import dev_tensor, dev_W, host
+from helpers import bf16_ulp, dev_tensor, dev_W, host
 
 pytestmark = pytest.mark.gpu
 
@@ -74,11 +74,12 @@ def test_gemm_bf16_layouts_and_epilogues(tdk, ctx, shape, a_mn, b_mn):
     zind = torch.as_tensor(zin).cuda()
     D = A @ B.T
     bound = K * 2.0 ** -23 * (np.abs(A) @ np.abs(B).T) + 1e-30
-    L = tdk.lib()
+    tctx = tdk.Context(0, testing=True)  # the raw GEMM entry is in the test build only
+    L = tctx.L
     for mode in range(4):
         outf = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
         outb = torch.full((M, _ru8(N)), float("nan"), dtype=torch.bfloat16, device="cuda")
-        rc = L.tdk_test_gemm_bf16(ctx.handle, M, N, K, Ad.data_ptr(), lda, a_mn, Bd.data_ptr(), ldb, b_mn, mode,
+        rc = L.tdk_test_gemm_bf16(tctx.handle, M, N, K, Ad.data_ptr(), lda, a_mn, Bd.data_ptr(), ldb, b_mn, mode,
                                   biasd.data_ptr(), zind.data_ptr(), N, outf.data_ptr(), N, outb.data_ptr(), _ru8(N))
         assert rc == 0
         torch.cuda.synchronize()
@@ -96,7 +97,8 @@ def test_gemm_bf16_layouts_and_epilogues(tdk, ctx, shape, a_mn, b_mn):
         else:
             ref = D * omlp.gelu_grad(zin)
             assert np.all(np.abs(bo - ref) <= 2.0 ** -7 * np.abs(ref) + bound * 2 + 1e-6)
-    assert ctx.sync_status() == 0
+    assert tctx.sync_status() == 0
+    tctx.close()
 
 
 def _odeco_cores(batch, Rt, N, seed, noise=1e-3):
@@ -282,4 +284,94 @@ def test_learned_start_needs_fewer_sweeps(tdk, ctx):
     assert med["learned"] < med["random"], med
     # the same final fit: the learned start does not land in worse optima on average
     assert mean_fit["learned"] >= mean_fit["random"] - 2e-3, mean_fit
+    m.close()
+
+
+def test_layers_and_gradients_elementwise_at_full_width(tdk, ctx):
+    """The workload's network (20^3 cores: 8000 -> 1024 -> 1024 -> 1200) on a
+    batch of 64, every stored quantity and every gradient entry checked
+    against the oracle's step fed with the kernels' own inputs of that step
+    (the stored BF16 activations and deltas, exact values), so that each
+    bound is the arithmetic of one step:
+      FP32 products of BF16 values: |error| <= K 2^-23 sum |a b| (K terms);
+      a BF16 store: one unit in the last place (2^-8 to 2^-7 relative), where
+      the FP32 and FP64 values straddle a rounding boundary;
+      dL/dO from the Gram identities in FP32: one BF16 unit plus 1e-4 of the
+      sample's largest entry.
+    Biases are random so that the bias terms are exercised."""
+    import torch
+
+    N, Rt, hidden, batch, alpha = 3, 20, 1024, 64, 0.5
+    G, cs, R, Bs = _problem(batch, N, Rt, 77)
+    theta = synth.mlp_init_params(N, Rt, hidden, 5).astype(np.float64)
+    sizes = omlp.param_sizes(N, Rt, hidden)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    r = np.random.default_rng(6)
+    for k in (1, 3, 5):  # b1, b2, b3
+        theta[offs[k]:offs[k + 1]] = 0.1 * r.standard_normal(sizes[k])
+    theta = theta.astype(np.float32)
+    m = tdk.Mlp(ctx, N, Rt, hidden, max_batch=batch)
+    m.set_params(theta)
+    Gd, csd, Rd, Bd = _dev_batch(G, cs, R, Bs)
+    lam = r.uniform(0.5, 2.0, (batch, Rt))
+    m.train_step(Gd, csd, Rd, Bd, alpha=alpha, update=False, lam=torch.as_tensor(lam).cuda())
+    get = lambda what, cols: m.get(what).astype(np.float64).reshape(batch, cols)  # noqa: E731
+    din, dout = Rt ** N, N * Rt * Rt
+    X, Z1, H1 = get(tdk.MLP_INPUT, din), get(tdk.MLP_Z1, hidden), get(tdk.MLP_H1, hidden)
+    Z2, H2, O = get(tdk.MLP_Z2, hidden), get(tdk.MLP_H2, hidden), get(tdk.MLP_OUTPUT, dout)
+    dO, dZ2, dZ1 = get(tdk.MLP_DO, dout), get(tdk.MLP_DZ2, hidden), get(tdk.MLP_DZ1, hidden)
+    S = m.get(tdk.MLP_CANON_CORE).astype(np.float64).reshape((batch,) + (Rt,) * N)
+    V = m.get(tdk.MLP_ROTATIONS).astype(np.float64).reshape(batch, N, Rt, Rt)
+    g = m.get(tdk.MLP_GRADS).astype(np.float64)
+    W1, b1, W2, b2, W3, b3 = omlp.unpack(theta.astype(np.float64), N, Rt, hidden)
+    q = synth.round_bf16
+    u23 = 2.0 ** -23
+
+    # the network input is the BF16 value of sqrt(Rt^N) vec S (scaled in FP32)
+    xin = omlp.network_input(S)
+    assert np.all(np.abs(X - q(xin)) <= bf16_ulp(np.maximum(np.abs(X), np.abs(xin))))
+
+    def check_linear(Hin, Wt, b, Zout, name):
+        ref = omlp.linear(Hin, Wt, b)
+        bound = Hin.shape[1] * u23 * (np.abs(Hin) @ np.abs(q(Wt)).T + np.abs(b)) + 1e-30
+        err = np.abs(Zout - ref)
+        assert np.all(err <= bound), (name, float((err / bound).max()))
+
+    def check_store(got, ref, name, extra=0.0):
+        err = np.abs(got - ref)
+        bound = bf16_ulp(np.maximum(np.abs(ref), np.abs(got))) + extra + 1e-30
+        assert np.all(err <= bound), (name, float((err / bound).max()))
+
+    check_linear(X, W1, b1, Z1, "Z1")
+    check_store(H1, omlp.activation(Z1), "H1")
+    check_linear(H1, W2, b2, Z2, "Z2")
+    check_store(H2, omlp.activation(Z2), "H2")
+    check_linear(H2, W3, b3, O, "O")
+    # dL/dO from the kernel's O, S and target (with the kernel's rotations)
+    G32 = G.astype(np.float32).astype(np.float64)
+    Ts = []
+    for s in range(batch):
+        nrm = float(np.sqrt(np.sum(G32[s] ** 2)))
+        Bw = [Bs[s, n][:, :R[s]] * (lam[s, :R[s]] if n == N - 1 else 1.0) for n in range(N)]
+        Ts.append(omlp.canonical_target(Bw, [V[s, n] for n in range(N)], nrm))
+    dOo = omlp.dloss_dO(O, S, R, Ts, alpha)
+    check_store(dO, dOo, "dO", extra=1e-4 * np.abs(dOo).max(axis=1, keepdims=True))
+    # deltas from the kernel's own upstream delta and pre-activation
+    for got, dn, Wt, Z, K, name in ((dZ2, dO, W3, Z2, dout, "dZ2"), (dZ1, dZ2, W2, Z1, hidden, "dZ1")):
+        ref = omlp.delta(dn, Wt, Z)
+        acc = 2 * K * u23 * (np.abs(dn) @ np.abs(q(Wt))) * np.abs(omlp.gelu_grad(Z))
+        check_store(got, ref, name, extra=acc)
+    # weight and bias gradients: batch sums of exact BF16 products
+    for k, (D, Hin) in zip((4, 2, 0), ((dO, H2), (dZ2, H1), (dZ1, X))):
+        gw = g[offs[k]:offs[k + 1]].reshape(D.shape[1], Hin.shape[1])
+        bound = batch * u23 * (np.abs(D).T @ np.abs(Hin)) + 1e-30
+        assert np.all(np.abs(gw - D.T @ Hin) <= bound), k
+        gb = g[offs[k + 1]:offs[k + 2]]
+        assert np.all(np.abs(gb - D.sum(axis=0)) <= batch * u23 * np.abs(D).sum(axis=0) + 1e-30), k + 1
+    # and the whole chain against the oracle run from the kernel's input
+    Lo, go, Oo = omlp.loss_grad(theta.astype(np.float64), X, S, R, N, Rt, hidden, T=Ts, alpha=alpha, bf16=True)
+    assert np.linalg.norm(O - Oo) <= 2e-3 * np.linalg.norm(Oo)
+    for k in range(6):
+        a, b = g[offs[k]:offs[k + 1]], go[offs[k]:offs[k + 1]]
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-12, k
     m.close()

@@ -566,20 +566,39 @@ def test_nonneg_rules_match_oracle(tdk, ctx, rule, dtype):
         assert oracle.congruence(Ao, Ah) > 0.9999
 
 
-def test_nonneg_rules_need_the_persistent_form(tdk, ctx):
-    """HALS and MU have no kernel-per-step form: TDK_ENOTSUP there."""
-    shape, ranks, p, R = (24, 22, 20), (5, 5, 5), 3, 4
-    Y, W, _ = small_problem(shape, ranks, p, seed=8, dtype="f64", dist="uniform", clip0=True)
+@pytest.mark.parametrize("rule", ["hals", "mu", "l1", "l1+"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_nonneg_rules_in_the_steps_form_match_oracle(tdk, ctx, rule, dtype):
+    """HALS (Eq. 8), MU (Eq. 15) and the l1 update (Eq. 16, signed and
+    projected) in the kernel-per-step form, the form that takes factors whose
+    rows do not fit on chip, against the oracle's rules on the same core."""
+    shape, ranks, p, R = (24, 22, 20, 18), (5, 5, 5, 5), 3, 4
+    clip = rule != "l1"
+    dist = "uniform" if clip else "normal"
+    Y, W, _ = small_problem(shape, ranks, p, seed=8, dtype="f64", snr=25.0, R_cp=R, dist=dist, clip0=clip)
     ref = oracle.rand_tucker(Y, W)
-    A0 = synth.init_factors(shape, R, 6, dist="uniform")
-    ctx.set_als_form(True)
-    try:
-        with pytest.raises(tdk.TdkError):
-            tdk.ffcp_als(ctx, dev_tensor(ref["G"], "f64"), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
-                         p, 0, R, max_sweeps=5, tol=0.0, nonneg="hals", A0=[dev_tensor(a, "f64") for a in A0])
-    finally:
-        ctx.set_als_form(False)
+    A0 = synth.init_factors(shape, R, 6, dist=dist)
+    c = 0.05 if rule.startswith("l1") else 0.0
+    orule = rule if rule in ("hals", "mu") else "ls"
+    o = oracle.cp_als_nonneg(ref["G"], ref["U"], A0, max_sweeps=25, tol=0.0, rule=orule, l1=c, clip=clip)
+    nn = rule if rule in ("hals", "mu") else ("ls" if clip else False)
+    out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], dtype), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks,
+                       p, DT_CODE[dtype], R, max_sweeps=25, tol=0.0, nonneg=nn,
+                       A0=[dev_tensor(a, "f64") for a in A0], l1=c, form="steps")
+    assert out["form"] == "steps"
     assert ctx.sync_status() == 0
+    assert out["sweeps"] == 25
+    assert abs(out["fit_core"] - o["fit"]) < (1e-10 if dtype == "f64" else 1e-5)
+    Ah = [host(a) for a in out["A"]]
+    if clip:
+        assert all(np.all(a >= 0) for a in Ah)
+    Ao = [a.copy() for a in o["A"]]
+    Ao[-1] = Ao[-1] * o["lam"][None, :]
+    if dtype == "f64":
+        for n in range(4):
+            assert np.allclose(Ah[n], Ao[n], atol=1e-8)
+    else:
+        assert oracle.congruence(Ao, Ah) > 0.9999
 
 
 @pytest.mark.parametrize("clip", [False, True])

@@ -752,7 +752,7 @@ def test_mlp_backward_matches_central_differences():
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
     # columns beyond a sample's rank R are outside the model: zero gradient
     O, _ = omlp.forward(theta, X, N, Rt, hidden, bf16=False)
-    dO = omlp._dloss_dO(O, S, R, T, 0.3)
+    dO = omlp.dloss_dO(O, S, R, T, 0.3)
     for s, Rs in enumerate(R):
         for n in range(N):
             blk = dO[s, n * Rt * Rt:(n + 1) * Rt * Rt].reshape(Rt, Rt)
@@ -844,3 +844,84 @@ def test_adam_constant_gradient_closed_form():
     for t in range(1, 26):
         th, m, v = omlp.adam_step(th, m, v, g, t, lr, eps=eps)
     assert np.abs(th - (-25 * lr * g / (np.abs(g) + eps))).max() < 1e-12
+
+
+# ---------------------------------------------------------------- seeded test matrices
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the known-answer vectors that Salmon et al.
+    publish with the generator (SC'11, Random123): zero counter and key, all
+    ones, and the digits of pi."""
+    from oracle import philox as P
+
+    cases = [((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+             ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+             ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+              (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for ctr, key, want in cases:
+        got = tuple(int(x) for x in P.philox4x32_10(*ctr, *key))
+        assert got == want, [hex(x) for x in got]
+
+
+def test_bf16_rounding_is_nearest_ties_to_even():
+    """round_bf16 against its definition: the result has 8 significant bits
+    and is the nearer of the two neighbouring such values, ties to the one
+    with an even last bit."""
+    from oracle import philox as P
+
+    r = np.random.default_rng(3)
+    x = np.concatenate([r.standard_normal(20000) * 10.0 ** r.integers(-3, 4, 20000),
+                        # exact midpoints between neighbouring BF16 values
+                        (np.arange(256, 512) + 0.5) / 256.0 * 2.0 ** r.integers(-5, 5, 256)])
+    y = P.round_bf16(x)
+    m, e = np.frexp(np.abs(x))
+    lo = np.ldexp(np.floor(m * 256.0) / 256.0, e)
+    hi = lo + np.ldexp(1.0 / 256.0, e)
+    dlo, dhi = np.abs(x) - lo, hi - np.abs(x)
+    even_lo = (np.floor(m * 256.0) % 2) == 0
+    want = np.where(dlo < dhi, lo, np.where(dhi < dlo, hi, np.where(even_lo, lo, hi))) * np.sign(x)
+    assert np.array_equal(y, want)
+    assert np.array_equal(np.asarray(y, dtype=np.float32).view(np.uint32) & 0xFFFF, np.zeros(len(y), np.uint32))
+
+
+def test_seeded_test_matrices_are_standard_normal_and_independent():
+    """The seeded draw has the moments and the distribution of N(0, 1), and
+    matrices of different (n, k), neighbouring rows and columns, and seeds
+    that differ only in their high word, are uncorrelated."""
+    from scipy import stats
+
+    from oracle import philox as P
+
+    z = P.normals(2024, 1, 2, 3000, 60).ravel()
+    n = z.size
+    assert abs(z.mean()) < 5.0 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+    assert abs(np.mean(z ** 4) - 3.0) < 0.1
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    W = P.sketch_matrices(2024, (300, 280, 260), [40, 40, 40])
+    pairs = [(W[0][1], W[2][1]), (W[0][1][:, :40], W[1][0][:280, :40]), (W[1][2], W[0][2])]
+    zs = P.normals(2024, 1, 2, 300, 60)
+    pairs += [(zs[:-1], zs[1:]), (zs[:, :-1], zs[:, 1:])]
+    hi = P.normals(2024 + (1 << 32), 1, 2, 300, 60)
+    pairs.append((zs, hi))
+    for a, b in pairs:
+        c = np.corrcoef(a.ravel(), b.ravel())[0, 1]
+        assert abs(c) < 5.0 / math.sqrt(a.size), c
+
+
+def test_seeded_row_blocks_equal_rows_of_the_whole_matrix():
+    """Every entry depends on (seed, n, k, i, r) alone: a block of rows drawn
+    on its own (a worker's slab of mode 1) equals those rows of the whole."""
+    from oracle import philox as P
+
+    dims, Rt = (50, 40, 30), [8, 9, 10]
+    full = P.sketch_matrices(77, dims, Rt)
+    part = P.sketch_matrices(77, dims, Rt, row0=[13, 0, 0], rows=[11, 40, 30])
+    for n in range(3):
+        for k in range(3):
+            if k == n:
+                continue
+            want = full[n][k][13:24] if k == 0 else full[n][k]
+            assert np.array_equal(part[n][k], want)
+    # and the values are BF16 values
+    assert np.array_equal(P.round_bf16(full[0][1]), full[0][1])

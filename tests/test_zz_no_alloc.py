@@ -61,6 +61,35 @@ def test_static_sketch_matches_allocating_sketch(tdk, ctx, shape, dtype):
     assert ctx.sync_status() == 0
 
 
+def test_static_sketch_allocates_nothing(tdk):
+    """The property the entry point exists for.  On a fresh context the call
+    leaves the context's workspace at zero bytes and torch's allocator
+    untouched; and in the test build, with every workspace growth made to
+    fail, the call still succeeds (the allocating sketch is refused)."""
+    import torch
+
+    shape, ranks, p = (67, 45, 130), [4, 4, 4], 3
+    Y, W, _ = small_problem(shape, ranks, p, seed=12, dtype="f32")
+    Yd, Wd = dev_tensor(Y, "f32"), dev_W(W)
+    Z = [torch.empty((shape[n], ranks[n] + p), dtype=torch.float64, device="cuda") for n in range(3)]
+    torch.cuda.synchronize()
+    for testing in (False, True):
+        c = tdk.Context(0, testing=testing)
+        if testing:
+            assert c.L.tdk_ctx_test_fail_alloc(c.handle, 0) == 0  # any growth now fails
+            with pytest.raises(tdk.TdkError) as e:
+                tdk.tucker_sketch(c, Yd, Wd, ranks, p, "simt")
+            assert e.value.code == tdk.TDK_ENOMEM
+        before = torch.cuda.memory_allocated()
+        assert c.workspace_bytes() == 0
+        for _call in range(2):
+            tdk.tucker_sketch_static(c, Yd, Wd, ranks, p, Z_out=Z)
+        assert c.sync_status() == 0
+        assert c.workspace_bytes() == 0
+        assert torch.cuda.memory_allocated() == before
+        c.close()
+
+
 def test_static_sketch_rejects_problems_beyond_the_array(tdk, ctx):
     import torch
 

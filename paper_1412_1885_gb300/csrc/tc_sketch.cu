@@ -25,6 +25,7 @@
 // BF16 hi + lo in place, and both parts are multiplied (two MMAs per step).
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
 #include "tc_common.cuh"
 
@@ -92,7 +93,10 @@ struct SkArgs {
   int64_t PCW;
   int64_t nunits;
   int d1_cols;                     // TMEM column stride of the two D1 buffers
-  int S;                           // stages in the ring (2 or 3)
+  int S;                           // stages in the ring
+  int nd1;                         // D1^T buffers in TMEM (form with W in TMEM)
+  signed char lane_mode[128];      // form with W in TMEM: mode of channel c (-1: padding)
+  unsigned char lane_r[128];       //   and its column r within the mode
   const float* Wf[TDK_MAX_MODES][TDK_MAX_MODES];  // FP32 W_k^(n) [I_k x Rt_n]
   float* part;
   int64_t ustride;                 // floats per unit
@@ -618,6 +622,432 @@ __global__ void __launch_bounds__(320, 1)
   }
 }
 
+// =====================================================================
+//        SKETCH, BF16 data: test matrices of the modes < N in TMEM
+// =====================================================================
+// The first product is taken transposed, D1^T[c, j] = sum_k WN[c, k] Y[p, j, k]:
+// the unit's block of the W_N^(n) (channels x columns, BF16) is the A operand
+// and lives in Tensor Memory, written once per unit by the epilogue warps; the
+// staged Y tile is a K-major B operand.  Shared memory then holds only the
+// stage ring and the K_p tiles, so the ring is deeper than with a resident W
+// block; and with one channel per TMEM lane, the modes that are constant over
+// the tile reduce within the lane (a dot product with W_{N-1}^(m) over the
+// tile's rows j) instead of across lanes.
+// TMEM, 512 columns: W [0, 64 KS) | D1^T [.., + 128 nd1) | D2 [.., + 64 KS).
+constexpr int TW_SMAX = 6;
+
+struct TwLayout {  // byte offsets in the 1024-aligned dynamic shared memory
+  uint32_t kt, bars, red, coef, flag, total;
+};
+__host__ __device__ inline TwLayout tw_layout(int S) {
+  TwLayout L{};
+  L.kt = (uint32_t)S * 32u * KB;           // stage ring: S x (128 j x 128 columns) BF16
+  L.bars = L.kt + SK_KTB * 16u * KB;       // K_p tiles
+  L.red = L.bars + 256u;                   // mbarriers and the TMEM address
+  L.coef = L.red + 2u * 128u * 4u;         // [2][128] FP32: second j half of the dot products
+  L.flag = L.coef + SK_CB * 256u * 4u;     // [SK_CB][256] FP32 per-p coefficients
+  L.total = L.flag + 64u;
+  return L;
+}
+
+__global__ void __launch_bounds__(320, 1)
+    tc_sketch_tw_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ SkArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const TwLayout Lay = tw_layout(a.S);
+  unsigned char* st_base = base;
+  unsigned char* kt_base = base + Lay.kt;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + Lay.bars);
+  uint64_t* full = bars;                   // [TW_SMAX]
+  uint64_t* empty = bars + TW_SMAX;        // [TW_SMAX]
+  uint64_t* d1full = bars + 2 * TW_SMAX;   // [2]
+  uint64_t* d1empty = d1full + 2;          // [2]
+  uint64_t* ktfull = d1full + 4;           // [SK_KTB]
+  uint64_t* ktempty = ktfull + SK_KTB;     // [SK_KTB]
+  uint64_t* wfull = ktempty + SK_KTB;
+  uint64_t* wempty = wfull + 1;
+  uint64_t* d2full = wfull + 2;
+  uint64_t* d2empty = wfull + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wfull + 4);
+  float* red = reinterpret_cast<float*>(base + Lay.red);
+  float* coef = reinterpret_cast<float*>(base + Lay.coef);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(base + Lay.flag);
+  constexpr int EG = 2;          // epilogue warp groups
+  constexpr int NE = 128 * EG;   // epilogue threads
+  constexpr int CH = 32;         // K_p channels written per group (64 in all)
+  constexpr int HW = CH / 2;
+  const int S = a.S, KS = a.KS, ND1 = a.nd1;
+  const uint32_t w_col = 0, d1_col = 64u * KS, d2_col = 64u * KS + 128u * ND1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    for (int i = 0; i < ND1; ++i) {
+      mbar_init(smem_u32(&d1full[i]), 1);
+      mbar_init(smem_u32(&d1empty[i]), 4 * EG);
+    }
+    for (int i = 0; i < SK_KTB; ++i) {
+      mbar_init(smem_u32(&ktfull[i]), 4 * EG);
+      mbar_init(smem_u32(&ktempty[i]), 1);
+    }
+    mbar_init(smem_u32(wfull), 4 * EG);
+    mbar_init(smem_u32(wempty), 1);
+    mbar_init(smem_u32(d2full), 1);
+    mbar_init(smem_u32(d2empty), 4 * EG);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  unsigned* status = a.status;
+  bool ok = true;
+  // cycle accounting of CTA 0 (test build: lane 0 of each role's first warp)
+  const bool prof_on = a.prof != nullptr && blockIdx.x == 0 && lane == 0 && (warp <= 2);
+  unsigned long long pt = clock64();
+  auto pmark = [&](int slot) {
+    if (prof_on) {
+      const unsigned long long t = clock64();
+      atomicAdd(a.prof + slot, t - pt);
+      pt = t;
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmY);
+      uint32_t s = 0, sph = 0;  // ring slot and the phase of its barriers
+      for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+        const int pc = (int)(u % a.PC);
+        const int kr = (int)((u / a.PC) % a.KR);
+        const int jt = (int)(u / ((int64_t)a.PC * a.KR));
+        const int64_t p0 = (int64_t)pc * a.PCW;
+        const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+        const int k0 = kr * a.KRW, j0 = jt * 128;
+        for (int64_t p = p0; p < p1 && ok; ++p) {
+          for (int st = 0; st < KS; ++st) {
+            pmark(5);
+            if (!mbar_wait(smem_u32(&empty[s]), sph ^ 1, status)) { ok = false; break; }
+            pmark(6);  // producer waits for a free stage
+            const uint32_t dst = smem_u32(st_base) + s * 32 * KB;
+            const uint32_t fb = smem_u32(&full[s]);
+            mbar_expect_tx(fb, 32 * KB);
+            const int kc = k0 + 128 * st;
+            tma_load_3d(dst, &tmY, kc, j0, (int)p, fb);
+            tma_load_3d(dst + BOX_BYTES, &tmY, kc + 64, j0, (int)p, fb);
+            if (++s == (uint32_t)S) {
+              s = 0;
+              sph ^= 1;
+            }
+          }
+        }
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(128, 128, 0, 0);  // D1^T: M = channels (A in TMEM), N = rows j
+      const uint32_t id2 = idesc_bf16(128, 64, 1, 1);   // D2: M = columns k, N = K_p channels
+      // descriptor bases: the start-address field is addr >> 4 in the low 14
+      // bits and every operand lies below 256 KB of shared memory, so the
+      // descriptor of base + off is the base's plus off >> 4 (the issue loop
+      // then spends one add per operand)
+      const uint64_t dB1 = smem_desc(smem_u32(st_base), 16, 1024, SW128);         // Y tile, K-major
+      const uint64_t dA2 = smem_desc(smem_u32(st_base), BOX_BYTES, 1024, SW128);  // Y tile, MN-major
+      const uint64_t dK = smem_desc(smem_u32(kt_base), 16, 1024, SW128);          // K_p tiles
+      uint32_t s = 0, sph = 0;    // ring slot and its phase
+      uint32_t kb = 0, kph = 0;   // K tile and its phase
+      uint32_t pi = 0, un = 0;
+      for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
+        const int pc = (int)(u % a.PC);
+        const int64_t p0 = (int64_t)pc * a.PCW;
+        const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+        if (!mbar_wait(smem_u32(wfull), un & 1, status)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(d2empty), (un & 1) ^ 1, status)) { ok = false; break; }
+        tc_fence_after();
+        bool first_p = true;
+        for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
+          const int db = ND1 == 2 ? (int)(pi & 1) : 0;
+          const uint32_t use = ND1 == 2 ? (pi >> 1) : pi;
+          pmark(0);
+          if (!mbar_wait(smem_u32(&ktfull[kb]), kph, status)) { ok = false; break; }
+          pmark(2);  // MMA waits for the K_p tile
+          tc_fence_after();
+          const uint64_t kdesc = dK + ((kb * 16 * KB) >> 4);
+          const uint32_t d1 = tmem + d1_col + 128u * db;
+          for (int st = 0; st < KS; ++st) {
+            pmark(0);
+            if (!mbar_wait(smem_u32(&full[s]), sph, status)) { ok = false; break; }
+            pmark(3);  // MMA waits for data
+            tc_fence_after();
+            const uint32_t so = (s * 32 * KB) >> 4;
+            // G2 first: it does not touch D1^T, so it overlaps the epilogue's
+            // read of the previous p's D1^T.  8 K-steps of 16 rows (2048 B)
+            const uint32_t d2 = tmem + d2_col + 64u * st;
+            mma_bf16(d2, dA2 + so, kdesc, id2, first_p ? 0u : 1u);
+#pragma unroll
+            for (int kk = 1; kk < 8; ++kk) mma_bf16(d2, dA2 + so + 128 * kk, kdesc + 128 * kk, id2, 1u);
+            if (st == 0) {
+              pmark(4);
+              if (!mbar_wait(smem_u32(&d1empty[db]), (use & 1) ^ 1, status)) { ok = false; break; }
+              pmark(1);  // MMA waits for the epilogue to free D1^T
+              tc_fence_after();
+            }
+            // G1^T: 8 K-steps of 16 columns (two 64-column boxes); A = the W
+            // columns of this stage in TMEM, 8 TMEM columns per K-step
+            const uint32_t wa = tmem + w_col + 64u * st;
+            mma_bf16_ts(d1, wa, dB1 + so, id1, st != 0 ? 1u : 0u);
+#pragma unroll
+            for (int kk = 1; kk < 8; ++kk)
+              mma_bf16_ts(d1, wa + 8u * kk, dB1 + so + (uint32_t)((kk >> 2) * (BOX_BYTES >> 4) + (kk & 3) * 2), id1,
+                          1u);
+            umma_commit(smem_u32(&empty[s]));
+            if (++s == (uint32_t)S) {
+              s = 0;
+              sph ^= 1;
+            }
+            pmark(4);  // MMA issue
+          }
+          if (!ok) break;
+          umma_commit(smem_u32(&d1full[db]));
+          umma_commit(smem_u32(&ktempty[kb]));
+          if (++kb == (uint32_t)SK_KTB) {
+            kb = 0;
+            kph ^= 1;
+          }
+          first_p = false;
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(d2full));
+        umma_commit(smem_u32(wempty));
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else if (warp < 2 + 4 * EG) {
+    // ------------------------------------------------------------ epilogue (2 groups of 4 warps)
+    // Two roles per thread.  As TMEM lane c = 32 q + lane it owns channel c
+    // of D1^T and the rows j of its group's half of the tile: the row mode
+    // accumulates D1^T[c, j] over p (weighted by the outer coefficients), a
+    // mode constant over the tile takes the dot product with its W row.  As
+    // tile row jl = 32 q + lane it writes its group's 32 channels of K_p.
+    const int q = warp & 3;
+    const int grp = (warp - 2) >> 2;
+    const int cg = grp * CH;
+    const int jl = 32 * q + lane;
+    const int c = jl;
+    const int jh = 64 * grp;
+    const int et = grp * 128 + jl;
+    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    const int Nm = a.N;
+    const int nj = Nm - 2;
+    const int nl = Nm - 1;
+    const int Rj = a.Rt[nj];
+    const int lm = a.lane_mode[c];
+    const int lr = a.lane_r[c];
+    const bool rowrole = lm == nj;
+    const bool dotrole = lm >= 0 && lm < nj;
+    auto coef_load = [&](int64_t pp, float* cr) {
+      // outer indices of p (N = 3: i_1 = p; N = 4: p = i_1 I_2 + i_2)
+      const int i1 = Nm == 4 ? (int)(pp / a.I[1]) : (int)pp;
+      const int i2 = Nm == 4 ? (int)(pp - (int64_t)i1 * a.I[1]) : 0;
+      const int vec = et >> 6, r = et & 63;
+      const int n = vec == 0 ? nl : (vec == 1 ? nj : vec - 2);
+      const bool live = (vec < 2 || vec - 2 < nj) && r < a.Rt[n];
+      cr[0] = live ? 1.f : 0.f;
+      cr[1] = 1.f;
+      if (live && !(vec >= 2 && n == 0)) cr[0] *= __ldg(a.Wf[n][0] + (int64_t)i1 * a.Rt[n] + r);
+      if (live && Nm == 4 && !(vec >= 2 && n == 1)) cr[1] = __ldg(a.Wf[n][1] + (int64_t)i2 * a.Rt[n] + r);
+    };
+    auto coef_store = [&](uint32_t pidx, const float* cr) { coef[(pidx % SK_CB) * 256 + et] = cr[0] * cr[1]; };
+    auto unpack = [](uint32_t w, int e) -> float {
+      return e ? __uint_as_float(w & 0xFFFF0000u) : __uint_as_float(w << 16);
+    };
+    uint32_t pi = 0, un = 0;
+    for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x, ++un) {
+      const int pc = (int)(u % a.PC);
+      const int kr = (int)((u / a.PC) % a.KR);
+      const int jt = (int)(u / ((int64_t)a.PC * a.KR));
+      const int64_t p0 = (int64_t)pc * a.PCW;
+      const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+      const int j0 = jt * 128;
+      const int k0 = kr * a.KRW;
+      float* up = a.part + u * a.ustride;
+      // ---- this unit's W block into TMEM (lane c = channel c; group g writes
+      //      the columns [32 KS g, 32 KS (g + 1)), two W values per column)
+      if (!mbar_wait(smem_u32(wempty), (un & 1) ^ 1, status)) { ok = false; break; }
+      tc_fence_after();
+      for (int cc = 0; cc < 2 * KS; ++cc) {
+        const int col0 = 32 * KS * grp + 16 * cc;
+        uint32_t r16[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int k = k0 + 2 * (col0 + e);
+          float v0 = 0.f, v1 = 0.f;
+          if (lm >= 0) {
+            const float* wr = a.Wf[lm][nl];
+            if (k < a.L) v0 = __ldg(wr + (int64_t)k * a.Rt[lm] + lr);
+            if (k + 1 < a.L) v1 = __ldg(wr + (int64_t)(k + 1) * a.Rt[lm] + lr);
+          }
+          r16[e] = pack_bf16x2(v0, v1);
+        }
+        tmem_st16(tmem + lane_addr + w_col + col0, r16);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(wfull));
+      pmark(13);  // epilogue: W block into TMEM (incl. waiting for the previous unit)
+      // ---- per-thread constants of the unit
+      // dot role: W_{N-1}^(m)[j0 + jh + jj, r]; row role: the accumulators
+      float aw[64];
+#pragma unroll
+      for (int jj = 0; jj < 64; ++jj) {
+        const int j = j0 + jh + jj;
+        aw[jj] = (dotrole && j < a.J) ? __ldg(a.Wf[lm][nj] + (int64_t)j * a.Rt[lm] + lr) : 0.f;
+      }
+      // K_p role: this row's W_{N-1}^(N) over the group's channels, packed BF16
+      uint32_t wk[HW];
+      {
+        const int jj = j0 + jl;
+#pragma unroll
+        for (int i = 0; i < HW; ++i) {
+          float k0v = 0.f, k1v = 0.f;
+          const int r = cg + 2 * i;
+          if (jj < a.J) {
+            const float* wkr = a.Wf[nl][nj] + (int64_t)jj * a.RtL;
+            if (r < a.RtL) k0v = __ldg(wkr + r);
+            if (r + 1 < a.RtL) k1v = __ldg(wkr + r + 1);
+          }
+          wk[i] = pack_bf16x2(k0v, k1v);
+        }
+      }
+      // K_p rows for G2 (row jl of the tile), MN-major [j][r], 128-byte swizzle
+      auto gen_k = [&](uint32_t pidx) -> bool {
+        const int kb = pidx % SK_KTB;
+        if (!mbar_wait(smem_u32(&ktempty[kb]), ((pidx / SK_KTB) & 1) ^ 1, status)) return false;
+        const float* cK = coef + (pidx % SK_CB) * 256;
+        unsigned char* row = kt_base + kb * 16 * KB + jl * 128;
+        const int ph = jl & 7;
+#pragma unroll
+        for (int cc = 0; cc < CH / 8; ++cc) {
+          uint32_t w4[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int rl = 8 * cc + 2 * e;
+            w4[e] = pack_bf16x2(unpack(wk[rl / 2], 0) * cK[cg + rl], unpack(wk[rl / 2], 1) * cK[cg + rl + 1]);
+          }
+          const int chunk = cg / 8 + cc;
+          *reinterpret_cast<uint4*>(row + ((chunk ^ ph) << 4)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&ktfull[kb]));
+        return true;
+      };
+      {
+        float cr[2];
+        for (int d = 0; d < 3; ++d)
+          if (p0 + d < p1) {
+            coef_load(p0 + d, cr);
+            coef_store(pi + d, cr);
+          }
+      }
+      named_bar(1, NE);
+      if (!gen_k(pi)) { ok = false; break; }
+      if (p0 + 1 < p1 && !gen_k(pi + 1)) { ok = false; break; }
+      for (int64_t p = p0; p < p1 && ok; ++p, ++pi) {
+        const int db = ND1 == 2 ? (int)(pi & 1) : 0;
+        const uint32_t use = ND1 == 2 ? (pi >> 1) : pi;
+        float cr2[2] = {0.f, 0.f};
+        const bool have3 = p + 3 < p1;
+        if (have3) coef_load(p + 3, cr2);
+        const float* cb = coef + (pi % SK_CB) * 256;
+        pmark(8);
+        // D1^T first: its single buffer holds back the next p's first product
+        if (!mbar_wait(smem_u32(&d1full[db]), use & 1, status)) { ok = false; break; }
+        pmark(10);  // epilogue waits for D1^T
+        tc_fence_after();
+        const uint32_t d1 = tmem + lane_addr + d1_col + 128u * db + jh;
+        const float rowc = rowrole ? cb[64 + lr] : 0.f;
+        float dot = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld16(d1 + 32 * h, v);
+          tmem_ld16(d1 + 32 * h + 16, v + 16);
+          tmem_wait_ld();
+          if (h == 1) {
+            // D1^T is read: the next p's first product may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&d1empty[db]));
+          }
+          if (rowrole) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) aw[32 * h + e] = fmaf(v[e], rowc, aw[32 * h + e]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) dot = fmaf(v[e], aw[32 * h + e], dot);
+          }
+        }
+        pmark(11);  // D1^T read and the row / dot products
+        if (p + 2 < p1 && !gen_k(pi + 2)) { ok = false; break; }
+        pmark(9);  // epilogue: K tile (incl. waiting for the MMA to free it)
+        // modes constant over the tile: the two j halves meet in shared memory
+        float* rb = red + (pi & 1) * 128;
+        if (dotrole && grp == 1) rb[c] = dot;
+        if (have3) coef_store(pi + 3, cr2);
+        named_bar(1, NE);
+        if (dotrole && grp == 0)
+          up[a.poff_p[lm] + (p - p0) * a.Rt[lm] + lr] = (dot + rb[c]) * cb[128 + 64 * lm + lr];
+        pmark(12);  // tail barrier and the partial store
+      }
+      if (!ok) break;
+      // ---- unit end: row-mode partial and the contiguous mode from D2
+      if (rowrole) {
+#pragma unroll
+        for (int jj = 0; jj < 64; ++jj)
+          if (j0 + jh + jj < a.J) up[a.poff_j + (int64_t)(jh + jj) * Rj + lr] = aw[jj];
+      }
+      if (!mbar_wait(smem_u32(d2full), un & 1, status)) { ok = false; break; }
+      tc_fence_after();
+      for (int st = grp; st < KS; st += EG) {
+        float v[64];
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16) tmem_ld16(tmem + d2_col + st * 64 + c16 * 16 + lane_addr, v + c16 * 16);
+        tmem_wait_ld();
+        const int kloc = 128 * st + jl;
+        if (k0 + kloc < a.L) {
+          float* dst = up + a.poff_last + (int64_t)kloc * a.RtL;
+#pragma unroll
+          for (int r = 0; r < 64; ++r)
+            if (r < a.RtL) dst[r] = v[r];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(d2empty));
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 // fixed-order reduction of the unit partials into Z (packed by zoff): a
 // compensated (Kahan) FP32 sum, since FP64 arithmetic would bound this pass
 struct RedArgs {
@@ -749,13 +1179,65 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   a.RtL = g.Rt[nl];
   a.hilo = (f32 && a.RtL <= 32) ? 1 : 0;
   if (!f32 && a.RtL > 64) return TDK_ENOTSUP;
-  a.d1_cols = (N1 + 31) / 32 * 32;
+  // the form with the test matrices in TMEM takes BF16 data whose channels of
+  // the modes < N fit one 128-lane accumulator (each mode's own block; a shared
+  // family is not folded there); the form with a resident W block takes the rest
+  int N1tw = 0;
+  for (int n = 0; n <= nj; ++n) N1tw += a.Rtp[n];
+  // (a shared family has half the G1 channels in the resident block, which
+  // the resident form exploits)
+  bool tw = !f32 && !shared && N1tw <= 128;
+#ifdef TDK_TESTING
+  if (const char* e = getenv("TDK_SKETCH_FORM")) tw = tw && strcmp(e, "resident") != 0;
+#endif
+  if (tw) {
+    int off = 0;
+    for (int c = 0; c < 128; ++c) {
+      a.lane_mode[c] = -1;
+      a.lane_r[c] = 0;
+    }
+    for (int n = 0; n <= nj; ++n) {
+      a.off[n] = off;
+      for (int r = 0; r < a.Rtp[n]; ++r) {
+        a.lane_mode[off + r] = (signed char)(r < a.Rt[n] ? n : -1);
+        a.lane_r[off + r] = (unsigned char)r;
+      }
+      off += a.Rtp[n];
+    }
+    a.N1 = N1 = off;
+    a.d1_cols = 128;
+    // columns per unit: KS = 3 leaves TMEM room for one D1^T buffer, KS <= 2
+    // for two (W 64 KS + D1^T 128 nd1 + D2 64 KS <= 512 columns); least
+    // padding of the contiguous mode, ties to the widest; deepest ring
+    a.KS = 0;
+    int64_t best_cols = 0;
+    int fit_st = 0;
+    for (int st = TW_SMAX; st >= 2 && !fit_st; --st)
+      if (1024 + (size_t)tw_layout(st).total <= (size_t)ctx->max_smem_optin) fit_st = st;
+    if (!fit_st) return TDK_ENOTSUP;
+    for (int ks = 3; ks >= 1; --ks) {
+      if (ks > (a.L + 127) / 128 && ks > 1) continue;
+      const int64_t w = 128LL * ks;
+      const int64_t cols = (a.L + w - 1) / w * w;
+      if (!a.KS || cols < best_cols) {
+        a.KS = ks;
+        best_cols = cols;
+      }
+    }
+    a.S = fit_st;
+#ifdef TDK_TESTING
+    if (const char* e = getenv("TDK_SKETCH_KS")) a.KS = std::max(1, std::min(3, atoi(e)));
+    if (const char* e = getenv("TDK_SKETCH_S")) a.S = std::max(2, std::min(fit_st, atoi(e)));
+#endif
+    a.nd1 = a.KS == 3 ? 1 : 2;
+  }
+  a.d1_cols = tw ? 128 : (N1 + 31) / 32 * 32;
   // columns per unit (KS blocks of 128): among the widths that TMEM (two D1
   // buffers + KS D2 blocks) and shared memory (ring of at least two stages +
   // resident W block) allow, the one that pads the contiguous mode least (a
   // padded column costs a full column of work), ties to the widest (the per-p
   // epilogue is amortised over more bytes); then the deepest ring that fits
-  {
+  if (!tw) {
     const uint32_t stage_b = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
     a.KS = 0;
     int64_t best_cols = 0;
@@ -778,6 +1260,22 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
       }
     }
     if (!a.KS) return TDK_ENOTSUP;
+#ifdef TDK_TESTING
+    // test build: the column blocks per unit and the ring depth can be forced
+    // (for sweeps of the launch shape); a shape that does not fit is refused
+    if (const char* e = getenv("TDK_SKETCH_KS")) {
+      const int ks = atoi(e);
+      const char* es = getenv("TDK_SKETCH_S");
+      const int st = es ? atoi(es) : 2;
+      const size_t need = 1024 + (size_t)st * stage_b + ((2 * ks * N1 * 128 + 1023) & ~1023) + SK_KTB * 16 * KB +
+                          256 + 2 * 4 * 64 * 4 + SK_CB * 256 * 4 + 64;
+      if (ks < 1 || ks > 4 || st < 2 || st > SK_SMAX || 2 * a.d1_cols + ks * 64 > 512 ||
+          need > (size_t)ctx->max_smem_optin)
+        return TDK_ENOTSUP;
+      a.KS = ks;
+      a.S = st;
+    }
+#endif
   }
   a.KRW = 128 * a.KS;
   a.JT = (a.J + 127) / 128;
@@ -815,8 +1313,10 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   for (int n = 0; n < N; ++n)
     for (int k = 0; k < N; ++k)
       if (k != n) pl.take<float>((size_t)g.I[k] * g.Rt[n]);
-  pl.take<__nv_bfloat16>((size_t)N1 * ldw);
-  pl.take<const double*>(TDK_MAX_MODES);
+  if (!tw) {
+    pl.take<__nv_bfloat16>((size_t)N1 * ldw);
+    pl.take<const double*>(TDK_MAX_MODES);
+  }
   pl.take<float>((size_t)a.nunits * a.ustride);
   int rc = ws_reserve(ctx, pl.off);
   if (rc) return rc;
@@ -830,15 +1330,16 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
       TDK_LAUNCH_CHECK(ctx);
       a.Wf[n][k] = d;
     }
-  __nv_bfloat16* wn = cv.take<__nv_bfloat16>((size_t)N1 * ldw);
-  const double** wl = cv.take<const double*>(TDK_MAX_MODES);
-  {
+  __nv_bfloat16* wn = nullptr;
+  if (!tw) {
+    wn = cv.take<__nv_bfloat16>((size_t)N1 * ldw);
+    const double** wl = cv.take<const double*>(TDK_MAX_MODES);
     const double* hw[TDK_MAX_MODES] = {};
     for (int n = 0; n <= nj; ++n) hw[n] = W[n * N + nl];
     TDK_CUDA_TRY(cudaMemcpyAsync(wl, hw, sizeof(hw), cudaMemcpyHostToDevice, ctx->stream));
+    build_wn<<<128, 256, 0, ctx->stream>>>(wl, a, ldw, wn);
+    TDK_LAUNCH_CHECK(ctx);
   }
-  build_wn<<<128, 256, 0, ctx->stream>>>(wl, a, ldw, wn);
-  TDK_LAUNCH_CHECK(ctx);
   a.part = cv.take<float>((size_t)a.nunits * a.ustride);
 
   CUtensorMap tmY, tmW;
@@ -850,18 +1351,28 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     rc = encode_tmap(&tmY, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims,
                      str, box, true);
     if (rc) return rc;
-    uint64_t wd[3] = {(uint64_t)a.L, (uint64_t)N1, 1};
-    uint64_t ws_[2] = {(uint64_t)ldw * 2, (uint64_t)ldw * 2 * N1};
-    uint32_t wb[3] = {64u, (uint32_t)N1, 1u};
-    rc = encode_tmap(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wn, wd, ws_, wb, true);
-    if (rc) return rc;
+    if (!tw) {
+      uint64_t wd[3] = {(uint64_t)a.L, (uint64_t)N1, 1};
+      uint64_t ws_[2] = {(uint64_t)ldw * 2, (uint64_t)ldw * 2 * N1};
+      uint32_t wb[3] = {64u, (uint32_t)N1, 1u};
+      rc = encode_tmap(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wn, wd, ws_, wb, true);
+      if (rc) return rc;
+    }
   }
-  const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
-  size_t smem = 1024 + (size_t)a.S * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + SK_KTB * 16 * KB + 256 +
-                2 * 4 * 64 * 4 + SK_CB * 256 * 4 + 64;
-  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
-  {
+  if (tw) {
+    const size_t smem = 1024 + (size_t)tw_layout(a.S).total;
+    if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
+    ProfScope ps(ctx, 0);
+    auto k = tc_sketch_tw_kernel;
+    TDK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<grid, 320, smem, ctx->stream>>>(tmY, a);
+    TDK_LAUNCH_CHECK(ctx);
+  } else {
+    const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
+    const size_t smem = 1024 + (size_t)a.S * stage + ((2 * a.KS * N1 * 128 + 1023) & ~1023) + SK_KTB * 16 * KB +
+                        256 + 2 * 4 * 64 * 4 + SK_CB * 256 * 4 + 64;
+    if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
     ProfScope ps(ctx, 0);
     int rw = 0;
     for (int n = 0; n < N; ++n) rw = std::max(rw, a.Rtp[n]);
@@ -888,10 +1399,15 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     TDK_CUDA_TRY(cudaMemcpyAsync(hp, a.prof, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));
     TDK_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     cudaFree(a.prof);
-    const char* nm[14] = {"mma:other", "mma:wait_d1empty", "mma:wait_ktile", "mma:wait_data", "mma:issue",
-                          "tma:other", "tma:wait_empty", "-", "epi:other", "epi:ktile", "epi:wait_d1",
-                          "epi:rowmode", "epi:reduce", "epi:tailbar"};
-    fprintf(stderr, "tdk sketch profile (CTA 0, Mcycles, units %lld):", (long long)a.nunits);
+    const char* nm_res[14] = {"mma:other", "mma:wait_d1empty", "mma:wait_ktile", "mma:wait_data", "mma:issue",
+                              "tma:other", "tma:wait_empty", "-", "epi:other", "epi:ktile", "epi:wait_d1",
+                              "epi:rowmode", "epi:reduce", "epi:tailbar"};
+    const char* nm_tw[14] = {"mma:other", "mma:wait_d1empty", "mma:wait_ktile", "mma:wait_data", "mma:issue",
+                             "tma:other", "tma:wait_empty", "-", "epi:other", "epi:ktile", "epi:wait_d1",
+                             "epi:read+fma", "epi:bar+store", "epi:unit_setup"};
+    const char* const* nm = tw ? nm_tw : nm_res;
+    fprintf(stderr, "tdk sketch profile (%s form, KS %d, S %d, CTA 0, Mcycles, units %lld):",
+            tw ? "TMEM-W" : "resident-W", a.KS, a.S, (long long)a.nunits);
     for (int i = 0; i < 14; ++i)
       if (i != 7) fprintf(stderr, " %s=%.2f", nm[i], hp[i] / 1e6);
     fprintf(stderr, "\n");

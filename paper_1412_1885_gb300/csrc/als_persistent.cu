@@ -60,6 +60,7 @@ struct PArgs {
   int64_t Qmax, Amax;           // shared buffers (entries)
   const T* G;
   const T* Uf[TDK_MAX_MODES];   // U_n in the working precision [I_n x Rt_n]
+  const T* Ulo[TDK_MAX_MODES];  // FP32 cores, nonneg: U_n - Uf_n, so that Uf + Ulo carries U to ~2^-48
   const double* init[TDK_MAX_MODES];  // B0 (Rt_n x R) or, nonneg, A0 (I_n x R)
   T* Bnew;                      // [max(Rt,I) x R] update rows (unnormalised)
   T* H;                         // [Rtmax x R]
@@ -109,6 +110,30 @@ __device__ bool grid_sync(unsigned* bar, unsigned* status) {
 
 // block-wide FP64 sum, the same value (same order) in every thread; the warp
 // partials are added by one thread (FP64 arithmetic is scarce on this GPU)
+// Gram entries of FP32 factors with compensated accumulation: each product is
+// split exactly (FMA) and the running sum carries its rounding error (TwoSum),
+// so an entry is accurate to a few FP32 units squared.  The fit of the
+// nonnegative form subtracts two sums of Gram products of nearly equal size;
+// with plain FP32 sums their rounding noise (about 1e-7 of ||G||^2) exceeded
+// the stopping tolerance and made the sweep count a matter of summation order.
+template <class T>
+struct GramAcc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x, T y) {
+    if (sizeof(T) == 8) {
+      s = fma(x, y, s);
+    } else {
+      const T p = x * y;
+      const T e = fma(x, y, -p);
+      const T t = s + p;
+      const T z = t - s;
+      c += ((s - (t - z)) + (p - z)) + e;
+      s = t;
+    }
+  }
+  __device__ __forceinline__ T value() const { return s + c; }
+};
+
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -142,8 +167,8 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 template <class T>
 struct PLayout {
   size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_invf, o_yf,
-      o_lamt, o_ilamt, o_slice, o_work, total;
-  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax) {
+      o_lamt, o_ilamt, o_slice, o_work, o_egram, total;
+  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
       const size_t o = (off + 15) & ~size_t(15);
@@ -168,6 +193,7 @@ struct PLayout {
     o_ilamt = take(sizeof(T) * RMAXP);
     o_slice = take(sizeof(T) * (size_t)Qmax);
     o_work = take(sizeof(T) * (size_t)(Amax * R));
+    o_egram = take(egram ? sizeof(T) * N * R * R : 0);  // Grams of A_p - U_p B_p
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -229,8 +255,10 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
     btot += a.Rt[p] * R;
   }
   PLayout<T> L;
-  L.plan(N, R, btot, a.Qmax, a.Amax);
+  const bool leak32 = sizeof(T) == 4 && a.nonneg;  // FP32 nonneg: the out-of-subspace term from E_p
+  L.plan(N, R, btot, a.Qmax, a.Amax, leak32);
   T* Bs = reinterpret_cast<T*>(sm + L.o_bs);         // factors, packed
+  T* egram = reinterpret_cast<T*>(sm + L.o_egram);   // [N][R*R] Grams of D_p = A_p - U_p B_p
   T* gram = reinterpret_cast<T*>(sm + L.o_gram);     // [N][R*R]
   T* bgram = reinterpret_cast<T*>(sm + L.o_bgram);   // [N][R*R] (nonneg: Grams of B_p)
   double* Tm = reinterpret_cast<double*>(sm + L.o_tm);  // [R*R] T_n (FP64)
@@ -273,13 +301,13 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
     }
     for (int e = tid; e < R * R; e += NTP) {
       const int r = e / R, s2 = e % R;
-      T acc = T(0);
+      GramAcc<T> acc;
       if (!a.nonneg) {
-        for (int q = 0; q < a.Rt[n]; ++q) acc = fma((T)a.init[n][q * R + r], (T)a.init[n][q * R + s2], acc);
+        for (int q = 0; q < a.Rt[n]; ++q) acc.add((T)a.init[n][q * R + r], (T)a.init[n][q * R + s2]);
       } else {
-        for (int64_t i = 0; i < a.I[n]; ++i) acc = fma((T)a.init[n][i * R + r], (T)a.init[n][i * R + s2], acc);
+        for (int64_t i = 0; i < a.I[n]; ++i) acc.add((T)a.init[n][i * R + r], (T)a.init[n][i * R + s2]);
       }
-      gram[n * R * R + e] = acc;
+      gram[n * R * R + e] = acc.value();
     }
   }
   for (int r = tid; r < R; r += NTP) {
@@ -290,9 +318,32 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   for (int n = 0; n < N; ++n)
     for (int e = tid; e < R * R; e += NTP) {
       const int r = e / R, s2 = e % R;
-      T acc = T(0);
-      for (int q = 0; q < a.Rt[n]; ++q) acc = fma(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2], acc);
-      bgram[n * R * R + e] = acc;
+      GramAcc<T> acc;
+      for (int q = 0; q < a.Rt[n]; ++q) acc.add(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2]);
+      bgram[n * R * R + e] = acc.value();
+    }
+  __syncthreads();
+  // FP32 nonneg: D_p = A_p - U_p B_p of the start, its Gram E_p (see below)
+  if (leak32)
+    for (int n = 0; n < N; ++n) {
+      for (int e = tid; e < R * R; e += NTP) {
+        const int r = e / R, s2 = e % R;
+        GramAcc<T> acc;
+        for (int64_t i = 0; i < a.I[n]; ++i) {
+          GramAcc<T> dr, ds;
+          dr.s = (T)a.init[n][i * R + r];
+          ds.s = (T)a.init[n][i * R + s2];
+          for (int q = 0; q < a.Rt[n]; ++q) {
+            const T uh = a.Uf[n][i * a.Rt[n] + q], ul = a.Ulo[n][i * a.Rt[n] + q];
+            dr.add(-uh, Bs[boff[n] + q * R + r]);
+            dr.add(-ul, Bs[boff[n] + q * R + r]);
+            ds.add(-uh, Bs[boff[n] + q * R + s2]);
+            ds.add(-ul, Bs[boff[n] + q * R + s2]);
+          }
+          acc.add(dr.value(), ds.value());
+        }
+        egram[n * R * R + e] = acc.value();
+      }
     }
   __syncthreads();
   const double nG2 = *a.nG2;
@@ -582,9 +633,9 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       __syncthreads();
       for (int e = tid; e < R * R; e += NTP) {
         const int r = e / R, s2 = e % R;
-        T acc = T(0);
-        for (int64_t i = 0; i < rows; ++i) acc = fma(nb[i * R + r], nb[i * R + s2], acc);
-        gram[n * R * R + e] = acc;
+        GramAcc<T> acc;
+        for (int64_t i = 0; i < rows; ++i) acc.add(nb[i * R + r], nb[i * R + s2]);
+        gram[n * R * R + e] = acc.value();
       }
       if (!a.nonneg) {
         for (int e = tid; e < Rn * R; e += NTP) Bs[boff[n] + e] = nb[e];
@@ -600,9 +651,35 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         __syncthreads();
         for (int e = tid; e < R * R; e += NTP) {
           const int r = e / R, s2 = e % R;
-          T acc = T(0);
-          for (int q = 0; q < Rn; ++q) acc = fma(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2], acc);
-          bgram[n * R * R + e] = acc;
+          GramAcc<T> acc;
+          for (int q = 0; q < Rn; ++q) acc.add(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2]);
+          bgram[n * R * R + e] = acc.value();
+        }
+        if (leak32) {
+          // the part of the normalised A_n outside the Tucker subspace,
+          // D_n = A_n - U_n B_n (U_n = Uf + Ulo), in place of the staged rows,
+          // and its Gram E_n.  The out-of-subspace term of the fit is then a
+          // sum of products that contain E (no difference of near-equal
+          // norms), so its error stays far below the stopping tolerance
+          __syncthreads();
+          for (int64_t e = tid; e < rows * R; e += NTP) {
+            const int64_t i = e / R;
+            const int r = (int)(e % R);
+            GramAcc<T> d;
+            d.s = nb[e];
+            for (int q = 0; q < Rn; ++q) {
+              d.add(-work[i * Rn + q], Bs[boff[n] + q * R + r]);
+              d.add(-a.Ulo[n][i * Rn + q], Bs[boff[n] + q * R + r]);
+            }
+            nb[e] = d.value();
+          }
+          __syncthreads();
+          for (int e = tid; e < R * R; e += NTP) {
+            const int r = e / R, s2 = e % R;
+            GramAcc<T> acc;
+            for (int64_t i = 0; i < rows; ++i) acc.add(nb[i * R + r], nb[i * R + s2]);
+            egram[n * R * R + e] = acc.value();
+          }
         }
       }
       __syncthreads();
@@ -698,21 +775,27 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
     }
     if (!ok) break;
     // ---- fit (identical in every CTA)
-    T m2 = T(0), mb2 = T(0);
+    // ||[[lambda; A]]||^2 from the Grams, in FP64; FP32 nonneg: the term
+    // ||[[lambda; A]]||^2 - ||[[lambda; U B]]||^2 = sum lambda lambda (prod (BtB + E)
+    // - prod BtB), the products in FP64 from the FP32 Grams
+    double m2 = 0.0, lk = 0.0;
     for (int e = tid; e < R * R; e += NTP) {
-      T v = lamT[e / R] * lamT[e % R];
-      T vb = v;
+      double v = (double)lamT[e / R] * (double)lamT[e % R];
+      double va = v, vb = v;
       for (int p = 0; p < N; ++p) {
-        v *= gram[p * R * R + e];
-        vb *= bgram[p * R * R + e];
+        v *= (double)gram[p * R * R + e];
+        if (leak32) {
+          va *= (double)bgram[p * R * R + e] + (double)egram[p * R * R + e];
+          vb *= (double)bgram[p * R * R + e];
+        }
       }
       m2 += v;
-      mb2 += vb;
+      lk += va - vb;
     }
-    const double model2 = block_sum_d((double)m2, red);
+    const double model2 = block_sum_d(m2, red);
     // [[A]] leaves the Tucker subspace (nonneg): add ||[[A]]||^2 - ||P [[A]]||^2,
     // P [[A]] = [[U B]] with B_p = U_p^T A_p
-    const double mb = (sizeof(T) != 8 && a.nonneg) ? block_sum_d((double)mb2, red) : 0.0;
+    const double leak = leak32 ? block_sum_d(lk, red) : 0.0;
     PROF_MARK(6);
     // the scalar tail by one thread, shared through `red` (same value in every CTA)
     if (tid == 0) {
@@ -722,7 +805,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       } else {
         res2 = 0.0;
         for (int q = 0; q < G; ++q) res2 += __ldcg(a.rpart + q);
-        if (a.nonneg) res2 += fmax(0.0, model2 - mb);
+        if (a.nonneg) res2 += fmax(0.0, leak);
       }
       const double f = 1.0 - sqrt(res2) / sqrt(nG2);
       red[0] = f;
@@ -1183,6 +1266,11 @@ __global__ void u_to_t(const double* __restrict__ s, T* __restrict__ d, int64_t 
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     d[e] = (T)s[e];
 }
+// the FP32 remainder U - (float)U
+__global__ void u_lo_f32(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (float)(s[e] - (double)(float)s[e]);
+}
 
 }  // namespace
 
@@ -1234,7 +1322,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   if (a.nonneg)
     for (int n = 0; n < N; ++n) a.Amax = std::max<int64_t>(a.Amax, (g.I[n] * g.Rt[n] + R - 1) / R);
   PLayout<T> lay;
-  lay.plan(N, R, (int)btot, a.Qmax, a.Amax);
+  lay.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg);
   const size_t smem = lay.total + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   auto kern = als_persistent_kernel<T>;
@@ -1255,6 +1343,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   pl.take<T>((size_t)grid * R);
   for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.Rt[n] * R);
   for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.I[n] * g.Rt[n]);
+  const bool leak32 = sizeof(T) == 4 && a.nonneg;
+  if (leak32)
+    for (int n = 0; n < N; ++n) pl.take<T>((size_t)g.I[n] * g.Rt[n]);
   if (a.nonneg)
     for (int n = 0; n < N; ++n) pl.take<double>((size_t)g.I[n] * R);
   pl.take<double>(R);
@@ -1272,6 +1363,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   for (int n = 0; n < N; ++n) a.Bout[n] = cv.take<T>((size_t)g.Rt[n] * R);
   T* uf[TDK_MAX_MODES];
   for (int n = 0; n < N; ++n) uf[n] = cv.take<T>((size_t)g.I[n] * g.Rt[n]);
+  T* ulo[TDK_MAX_MODES] = {};
+  if (leak32)
+    for (int n = 0; n < N; ++n) ulo[n] = cv.take<T>((size_t)g.I[n] * g.Rt[n]);
   double* aw[TDK_MAX_MODES] = {};
   if (a.nonneg)
     for (int n = 0; n < N; ++n) aw[n] = cv.take<double>((size_t)g.I[n] * R);
@@ -1302,6 +1396,11 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
     u_to_t<T><<<64, 256, 0, s>>>(U[n], uf[n], g.I[n] * g.Rt[n]);
     TDK_LAUNCH_CHECK(ctx);
     a.Uf[n] = uf[n];
+    if (leak32) {
+      u_lo_f32<<<64, 256, 0, s>>>(U[n], reinterpret_cast<float*>(ulo[n]), g.I[n] * g.Rt[n]);
+      TDK_LAUNCH_CHECK(ctx);
+      a.Ulo[n] = ulo[n];
+    }
     a.init[n] = a.nonneg ? A_io[n] : B_io[n];
     a.Aout[n] = aw[n];  // running A_n; the caller's A_io stays the init until the end
   }

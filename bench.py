@@ -226,6 +226,26 @@ def cpu_oracle_sample(w, seconds_target=10.0, max_block=200_000_000, rule="ls"):
     return nbytes / total / 1e9, desc, total
 
 
+ONE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                  "NUMEXPR_NUM_THREADS": "1", "VECLIB_MAXIMUM_THREADS": "1"}
+
+
+def cpu_oracle_one_thread(config: str, shape: str, rule: str, seconds: float = 6.0):
+    """The same oracle sample on one host thread: a child process with the
+    BLAS and OpenMP thread counts pinned to 1 (they are fixed when numpy
+    loads).  Returns (GB/s, description) or (None, reason)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-one-thread", "--config", config,
+           "--nonneg-rule", rule, "--oracle-seconds", str(seconds)]
+    if shape:
+        cmd += ["--shape", shape]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=dict(os.environ, **ONE_THREAD_ENV))
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return d["value"], d["sample"]
+    except Exception as e:  # the all-core figure stands alone then
+        return None, f"not measured: {type(e).__name__}"
+
+
 def _fit_run(fn):
     """(device ms, result) of one call, CUDA events on the current stream."""
     import torch
@@ -259,17 +279,15 @@ def learned_setup(t, ctx, w, prec, n_train, n_eval, dev):
     def tensor(k, split):
         wk = synth.learned_init_workload(k, split, w.shape, Rt)
         Y, _ = synth.device_tensor(wk, device=dev)
-        W = synth.sketch_matrices(wk.shape, wk.Rt, wk.seed)
-        Wd = [[None if x is None else torch.as_tensor(x, device=dev) for x in row] for row in W]
         B0 = [torch.as_tensor(b, device=dev) for b in synth.init_factors(wk.Rt, wk.als_R, wk.seed)]
-        return wk, Y, Wd, B0
+        return wk, Y, None, B0  # test matrices drawn inside the library from the workload's seed
 
     t0 = time.perf_counter()
     items = []
     for k in range(n_train):
         wk, Y, Wd, B0 = tensor(k, 1)
         it = li.method_sample(ctx, m, Y, Wd, list(wk.ranks), 0, wk.als_R, B0, prec=prec, init="hosvd",
-                              max_sweeps=300)
+                              max_sweeps=300, seed=synth.omega_seed(wk))
         items.append({kk: v for kk, v in it.items() if kk not in ("U", "Gc")})
         del Y
     data = li.stack(items)
@@ -281,8 +299,9 @@ def learned_setup(t, ctx, w, prec, n_train, n_eval, dev):
     res = {k: {"sweeps": [], "fit": [], "ms": []} for k in ("random", "hosvd", "learned")}
     for k in range(n_eval):
         wk, Y, Wd, B0 = tensor(k, 2)
-        U, _ = t.tucker_sketch(ctx, Y, Wd, list(wk.ranks), 0, prec)
-        G, nrm = t.tucker_core(ctx, Y, U, list(wk.ranks), 0, prec)
+        nrm = torch.empty((), dtype=torch.float64, device=dev)
+        U, _ = t.tucker_sketch(ctx, Y, Wd, list(wk.ranks), 0, prec, seed=synth.omega_seed(wk), normY2=nrm)
+        G, _ = t.tucker_core(ctx, Y, U, list(wk.ranks), 0, prec, want_norm=False)
         args = (ctx, G, U, wk.shape, list(wk.ranks), 0, t._dtype_code(Y), wk.als_R, wk.als_max_sweeps, wk.als_tol)
         runs = {"random": lambda: t.ffcp_als(*args, B0=B0, normY2=nrm),
                 "hosvd": lambda: t.ffcp_als(*args, init="hosvd", normY2=nrm),
@@ -348,6 +367,8 @@ def main():
                     help="update rule of the nonnegative workloads: projected LS, HALS (Eq. 8), MU (Eq. 15)")
     ap.add_argument("--sketch", default=DEFAULT_SKETCH, choices=["shared", "independent"],
                     help="sketch family: Khatri-Rao factors shared between the modes, or drawn per mode")
+    ap.add_argument("--oracle-one-thread", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-seconds", type=float, default=10.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -358,6 +379,10 @@ def main():
     if args.shape:
         # same data model, ranks and dtype at another size (small ncu captures)
         w = synth.scaled(w, [int(x) for x in args.shape.split(",")])
+    if args.oracle_one_thread:
+        v, desc, _ = cpu_oracle_sample(w, seconds_target=args.oracle_seconds, rule=args.nonneg_rule)
+        print(json.dumps({"value": v, "sample": desc}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -489,7 +514,9 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cv, cdesc, _ = cpu_oracle_sample(w, rule=args.nonneg_rule)
-        cpu = {"value": cv, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle", "sample": cdesc}
+        v1, d1 = cpu_oracle_one_thread(args.config, args.shape, args.nonneg_rule)
+        cpu = {"value": cv, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle", "sample": cdesc,
+               "one_thread": {"value": v1, "unit": "GB/s", "cores": 1, "sample": d1}}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

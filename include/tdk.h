@@ -183,11 +183,17 @@ int tdk_tucker_check(const tdk_tucker_desc* desc);
  *          orthogonal, and TDK_WRANKDEF is raised in the status word.
  *   Z_out  NULL or N device pointers (entries may be NULL); Z_out[n] FP64
  *          [I_n x Rt_n] receives the raw sketch Z_n.
+ *   normY2 NULL or one FP64 device scalar receiving ||Y||_F^2 (the fit needs
+ *          it).  The tensor-core forms sum it while the pass stages the
+ *          tiles of Y; the CUDA-core form and the shared-family tensor-core
+ *          form of BF16 data take one more streaming pass over Y.  Asking for
+ *          it here lets tucker_core skip its own sum (pass it NULL there).
  * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOMEM, TDK_ENOTSUP
  * (TDK_PREC_TC with F64 data), TDK_ECUDA.
  */
 int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y,
-                  const double* const W[], double* const U_out[], double* const Z_out[]);
+                  const double* const W[], double* const U_out[], double* const Z_out[],
+                  double* normY2);
 
 /*
  * tucker_sketch_static -- the sketch pass of tucker_sketch alone (Z_n for
@@ -251,7 +257,9 @@ int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
  *
  *   U       N device pointers, U[n] FP64 [I_n x Rt_n] (e.g. from tucker_sketch).
  *   G_out   [Rt_1 x ... x Rt_N], FP64 for F64 data, FP32 otherwise.
- *   normY2  NULL or one FP64 device scalar receiving ||Y||_F^2.
+ *   normY2  NULL or one FP64 device scalar receiving ||Y||_F^2.  NULL makes
+ *           the BF16 tensor-core pass faster: its stage ring is then released
+ *           by the MMAs alone (take the norm from tucker_sketch instead).
  * The first, tensor-sized contraction is over the contiguous mode N; in the
  * TC form it runs on tcgen05 tensor cores (BF16 operands, U split hi+lo, Y
  * split hi+lo when stored as FP32).  Errors as tucker_sketch.

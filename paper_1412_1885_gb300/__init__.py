@@ -125,7 +125,7 @@ def _load(path):
         L.tdk_tucker_check.argtypes = [ctypes.POINTER(TuckerDesc)]
         L.tdk_copy_in.argtypes = [vp, vp, vp, ctypes.c_size_t]
         L.tdk_copy_out.argtypes = [vp, vp, vp, ctypes.c_size_t]
-        L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp]
+        L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp, vp]
         L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
         L.tucker_refine.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
         L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
@@ -294,10 +294,11 @@ def sketch_matrices(ctx: Context, shape, ranks, p, seed):
     return W
 
 
-def tucker_sketch(ctx: Context, Y, W, ranks, p, prec="simt", want_Z=False, seed=0):
+def tucker_sketch(ctx: Context, Y, W, ranks, p, prec="simt", want_Z=False, seed=0, normY2=None):
     """All-mode sketch + CholQR2 (see include/tdk.h).  W[n][k] are FP64 device
     tensors [I_k x (R_n + p)] (W[n][n] unused), or None to let the library
-    draw them from `seed`.  Returns (U list, Z list|None)."""
+    draw them from `seed`.  normY2: optional FP64 device scalar tensor that
+    receives ||Y||^2.  Returns (U list, Z list|None)."""
     import torch
 
     N = Y.dim()
@@ -308,7 +309,8 @@ def tucker_sketch(ctx: Context, Y, W, ranks, p, prec="simt", want_Z=False, seed=
     Z = [torch.empty((Y.shape[n], Rt[n]), dtype=torch.float64, device=dev) for n in range(N)] if want_Z else None
     ctx._bind_stream()
     _check(ctx.L.tucker_sketch(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _w_array(W, N),
-                               _ptrs(U), _ptrs(Z) if Z is not None else None), "tucker_sketch")
+                               _ptrs(U), _ptrs(Z) if Z is not None else None,
+                               ctypes.c_void_p(normY2.data_ptr() if normY2 is not None else None)), "tucker_sketch")
     return U, Z
 
 
@@ -357,19 +359,20 @@ def rand_tucker_2i(ctx: Context, Y, U0, W_passes, ranks, p, prec="simt"):
     return U, G, nrm
 
 
-def tucker_core(ctx: Context, Y, U, ranks, p, prec="simt"):
-    """G = Y x_1 U_1^T ... x_N U_N^T and ||Y||^2 (device FP64 scalar)."""
+def tucker_core(ctx: Context, Y, U, ranks, p, prec="simt", want_norm=True):
+    """G = Y x_1 U_1^T ... x_N U_N^T and ||Y||^2 (device FP64 scalar, None
+    when want_norm is False)."""
     import torch
 
     desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, prec)
     Rt = [int(r) + int(p) for r in ranks]
     gdt = torch.float64 if Y.dtype == torch.float64 else torch.float32
     G = torch.empty(Rt, dtype=gdt, device=Y.device)
-    nrm = torch.empty((), dtype=torch.float64, device=Y.device)
+    nrm = torch.empty((), dtype=torch.float64, device=Y.device) if want_norm else None
     ctx._bind_stream()
     _check(ctx.L.tucker_core(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()),
                              _ptrs([u.contiguous() for u in U]), ctypes.c_void_p(G.data_ptr()),
-                             ctypes.c_void_p(nrm.data_ptr())), "tucker_core")
+                             ctypes.c_void_p(nrm.data_ptr() if want_norm else None)), "tucker_core")
     return G, nrm
 
 
@@ -632,8 +635,11 @@ def decompose(ctx: Context, Y, W, ranks, p, R, prec="simt", nonneg=False, max_sw
     ambient = bool(NONNEG[nonneg]) or l1 > 0.0
     if init == "given" and model is None and (A0 is None if ambient else B0 is None):
         init = "hosvd"  # no start given: the HOSVD start of the core
-    U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec, seed=seed)
-    G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
+    import torch
+
+    nrm = torch.empty((), dtype=torch.float64, device=Y.device)
+    U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec, seed=seed, normY2=nrm)  # ||Y||^2 from the sketch pass
+    G, _ = tucker_core(ctx, Y, U, ranks, p, prec, want_norm=False)
     if model is not None and not ambient:
         B0 = model.predict_init(G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R)
         init = "given"

@@ -100,14 +100,15 @@ static int seeded_w(tdk_ctx* ctx, const Geom& g, uint64_t seed, const int64_t* r
 // stream-ordered allocation that the caller frees (Z stays out of the
 // workspace, which the sub-steps carve)
 static int sketch_pass(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc, const void* Y,
-                       const double* const W[], double** Zout) {
+                       const double* const W[], double** Zout, double* normY2) {
   double* Z = nullptr;
   if (cudaMallocAsync((void**)&Z, sizeof(double) * (size_t)g.zoff[g.N], ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     return TDK_ENOMEM;
   }
-  const int rc = desc->prec == TDK_PREC_TC ? sketch_tc(ctx, g, desc->dtype, Y, W, Z)
-                                           : sketch_simt(ctx, g, desc->dtype, Y, W, Z);
+  int rc = desc->prec == TDK_PREC_TC ? sketch_tc(ctx, g, desc->dtype, Y, W, Z, normY2)
+                                     : sketch_simt(ctx, g, desc->dtype, Y, W, Z);
+  if (rc == TDK_OK && normY2 && desc->prec != TDK_PREC_TC) rc = norm2_pass(ctx, g, desc->dtype, Y, normY2);
   if (rc) {
     cudaFreeAsync(Z, ctx->stream);
     return rc;
@@ -273,7 +274,7 @@ int tdk_ctx_test_fail_alloc(tdk_ctx* c, int after) {
 #endif
 
 int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
-                  double* const U_out[], double* const Z_out[]) {
+                  double* const U_out[], double* const Z_out[], double* normY2) {
   if (!ctx || !desc || !Y || !U_out) return TDK_EINVAL;
   Geom g;
   int rc = make_geom(desc, &g);
@@ -294,7 +295,7 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
     W = wp;
   }
   double* Z = nullptr;
-  rc = sketch_pass(ctx, g, desc, Y, W, &Z);
+  rc = sketch_pass(ctx, g, desc, Y, W, &Z, normY2);
   if (rc == TDK_OK) rc = cholqr2(ctx, g, Z, U_out);
   if (rc == TDK_OK && Z_out) {
     for (int n = 0; n < g.N; ++n)
@@ -337,7 +338,7 @@ int tucker_sketch_partial(tdk_ctx* ctx, const tdk_tucker_desc* slab, int64_t row
         wp[n * g.N + k] = (k == n) ? nullptr : (k == 0 ? W[n * g.N] + row_off * g.Rt[n] : W[n * g.N + k]);
   }
   double* Z = nullptr;
-  rc = sketch_pass(ctx, g, slab, Y, wp, &Z);
+  rc = sketch_pass(ctx, g, slab, Y, wp, &Z, nullptr);
   if (rc == TDK_OK)
     for (int n = 0; n < g.N; ++n)
       if (cudaMemcpyAsync(Z_out[n], Z + g.zoff[n], sizeof(double) * g.I[n] * g.Rt[n], cudaMemcpyDeviceToDevice,

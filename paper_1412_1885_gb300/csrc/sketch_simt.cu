@@ -323,6 +323,68 @@ int sketch_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const dou
   return TDK_EINVAL;
 }
 
+namespace {
+// ||Y||^2 over a grid-stride range per thread: FP64 sums of FP32 (Kahan) or
+// FP64 chunk sums, then one FP64 partial per block in a fixed order
+template <class TY>
+__global__ void __launch_bounds__(256) norm2_pass_kernel(const TY* __restrict__ Y, int64_t n,
+                                                         double* __restrict__ parts) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  while (e < n) {
+    // 64 elements at a time in the storage's natural precision
+    double chunk = 0.0;
+    float f = 0.f;
+    for (int k = 0; k < 64 && e < n; ++k, e += stride) {
+      if (sizeof(TY) == 8) {
+        const double v = (double)to_f(Y[e]);
+        chunk = fma(v, v, chunk);
+      } else {
+        const float v = to_f(Y[e]);
+        f = fmaf(v, v, f);
+      }
+    }
+    acc += sizeof(TY) == 8 ? chunk : (double)f;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    parts[blockIdx.x] = s;
+  }
+}
+__global__ void norm2_sum_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += parts[i];
+    *out = s;
+  }
+}
+}  // namespace
+
+int norm2_pass(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, double* normY2) {
+  const int blocks = 4 * ctx->num_sms;
+  int rc = ws_reserve(ctx, sizeof(double) * blocks + 256);
+  if (rc) return rc;
+  double* parts = reinterpret_cast<double*>(ctx->ws);
+  switch (dtype) {
+    case TDK_F64: norm2_pass_kernel<double><<<blocks, 256, 0, ctx->stream>>>((const double*)Y, g.numel, parts); break;
+    case TDK_F32: norm2_pass_kernel<float><<<blocks, 256, 0, ctx->stream>>>((const float*)Y, g.numel, parts); break;
+    case TDK_BF16:
+      norm2_pass_kernel<__nv_bfloat16><<<blocks, 256, 0, ctx->stream>>>((const __nv_bfloat16*)Y, g.numel, parts);
+      break;
+    default: return TDK_EINVAL;
+  }
+  TDK_LAUNCH_CHECK(ctx);
+  norm2_sum_kernel<<<1, 32, 0, ctx->stream>>>(parts, blocks, normY2);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
 }  // namespace tdk
 
 // ---- allocation-free variant of the sketch pass --------------------------------

@@ -289,6 +289,7 @@ struct FuArgs {
   float* X2;               // [P][Rt2][Rt]
   double* nrm_part;
   unsigned* status;
+  int want_norm;           // 0: no ||Y||^2, the MMA commit alone frees a stage
 };
 
 constexpr int FU_S = 4;                 // stage ring
@@ -333,7 +334,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
-      mbar_init(smem_u32(&empty[i]), 5);  // the MMA commit and the four epilogue warps (||Y||^2)
+      // the MMA commit, and the four epilogue warps when they sum ||Y||^2
+      mbar_init(smem_u32(&empty[i]), a.want_norm ? 5 : 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&dfull[i]), 1);
@@ -515,7 +517,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     for (int p = blockIdx.x; p < a.P && ok; p += gridDim.x, ++ui) {
       for (int jt = 0; jt < a.JT; ++jt, ++tl) {
         // ||Y||^2 from the staged tiles
-        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+        if (!a.want_norm) it += a.KC;
+        for (int kc = 0; kc < a.KC && a.want_norm; ++kc, ++it) {
           const int s = it % S;
           const uint32_t n = it / S;
           if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
@@ -752,6 +755,7 @@ static int core_tc_fused(tdk_ctx* ctx, const Geom& g, const void* Y, const doubl
   a.X2 = cv.take<float>((size_t)P * a.Rt2 * a.Rt);
   float* tmp0 = cv.take<float>((size_t)tmpsz);
   float* tmp1 = cv.take<float>((size_t)tmpsz);
+  a.want_norm = normY2 != nullptr;
   a.nrm_part = cv.take<double>((size_t)grid);
   float* spl = cv.take<float>((size_t)pcap);
 

@@ -95,6 +95,7 @@ struct SkArgs {
   int d1_cols;                     // TMEM column stride of the two D1 buffers
   int S;                           // stages in the ring
   int nd1;                         // D1^T buffers in TMEM (form with W in TMEM)
+  double* nrm_part;                // null, or [grid][4]: sums of squares of the staged Y (per warp)
   signed char lane_mode[128];      // form with W in TMEM: mode of channel c (-1: padding)
   unsigned char lane_r[128];       //   and its column r within the mode
   const float* Wf[TDK_MAX_MODES][TDK_MAX_MODES];  // FP32 W_k^(n) [I_k x Rt_n]
@@ -594,6 +595,7 @@ __global__ void __launch_bounds__(320, 1)
     const int q = warp - 6;
     const int r = 32 * q + lane;
     uint32_t it = 0;
+    double sq = 0.0;  // ||Y||^2 of the rows this thread splits (the split sums the squares)
     for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
       const int pc = (int)(u % a.PC);
       const int64_t p0 = (int64_t)pc * a.PCW;
@@ -605,13 +607,15 @@ __global__ void __launch_bounds__(320, 1)
           if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
           unsigned char* sb = st_base + s * SkLayout<true>::STAGE_BYTES;
           for (int h = 0; h < 2; ++h)
-            split_row64(sb + h * 2 * BOX_BYTES + r * 128, sb + (h * 2 + 1) * BOX_BYTES + r * 128, r);
+            sq += (double)split_row64(sb + h * 2 * BOX_BYTES + r * 128, sb + (h * 2 + 1) * BOX_BYTES + r * 128, r);
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&cfull[s]));
         }
       }
     }
+    sq = warp_sum(sq);
+    if (a.nrm_part && lane == 0) a.nrm_part[4 * blockIdx.x + q] = sq;
     if (!ok) *abort_flag = 1;
   }
   tc_fence_before();
@@ -650,7 +654,7 @@ __host__ __device__ inline TwLayout tw_layout(int S) {
   return L;
 }
 
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(384, 1)
     tc_sketch_tw_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ SkArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -669,6 +673,7 @@ __global__ void __launch_bounds__(320, 1)
   uint64_t* d2full = wfull + 2;
   uint64_t* d2empty = wfull + 3;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wfull + 4);
+  double* nred = reinterpret_cast<double*>(wfull + 5);  // [2] sums of squares of the norm warps
   float* red = reinterpret_cast<float*>(base + Lay.red);
   float* coef = reinterpret_cast<float*>(base + Lay.coef);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(base + Lay.flag);
@@ -680,11 +685,14 @@ __global__ void __launch_bounds__(320, 1)
   const uint32_t w_col = 0, d1_col = 64u * KS, d2_col = 64u * KS + 128u * ND1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool want_norm = a.nrm_part != nullptr;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
-      mbar_init(smem_u32(&empty[i]), 1);
+      // the MMA commit, and the two norm warps when they sum ||Y||^2
+      mbar_init(smem_u32(&empty[i]), want_norm ? 3 : 1);
     }
+    nred[0] = nred[1] = 0.0;
     for (int i = 0; i < ND1; ++i) {
       mbar_init(smem_u32(&d1full[i]), 1);
       mbar_init(smem_u32(&d1empty[i]), 4 * EG);
@@ -1039,9 +1047,66 @@ __global__ void __launch_bounds__(320, 1)
       if (lane == 0) mbar_arrive(smem_u32(d2empty));
     }
     if (!ok) *abort_flag = 1;
+  } else if (want_norm) {
+    // ------------------------------------------------------------ ||Y||^2 (warps 10, 11)
+    // Each staged tile waits in the ring for its MMAs; meanwhile warp 10 + h
+    // sums the squares of box h (64 columns x 128 rows, a 128-byte row per lane
+    // and step), so the slot is released no later than the MMAs release it.
+    const int h = warp - 2 - 4 * EG;
+    uint32_t s = 0, sph = 0;
+    double acc = 0.0;
+    for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const int pc = (int)(u % a.PC);
+      const int64_t p0 = (int64_t)pc * a.PCW;
+      const int64_t p1 = std::min<int64_t>(a.P, p0 + a.PCW);
+      for (int64_t p = p0; p < p1 && ok; ++p) {
+        for (int st = 0; st < KS; ++st) {
+          if (!mbar_wait(smem_u32(&full[s]), sph, status)) { ok = false; break; }
+          const unsigned char* box = st_base + s * 32 * KB + h * BOX_BYTES;
+          float part = 0.f, comp = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const int row = lane + 32 * rr;
+            const unsigned char* rp = box + row * 128;
+            float q = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const uint4 w = *reinterpret_cast<const uint4*>(rp + ((c ^ (row & 7)) << 4));
+              const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
+                q = fmaf(lo, lo, q);
+                q = fmaf(hi, hi, q);
+              }
+            }
+            const float y = q - comp;  // Kahan over the rows
+            const float t = part + y;
+            comp = (t - part) - y;
+            part = t;
+          }
+          acc += (double)part - (double)comp;
+          // the slot is refilled by TMA (async proxy): order these reads first
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+          if (++s == (uint32_t)S) {
+            s = 0;
+            sph ^= 1;
+          }
+        }
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) nred[h] = acc;
+    if (!ok) *abort_flag = 1;
   }
   tc_fence_before();
   __syncthreads();
+  if (want_norm && threadIdx.x == 0) {
+    a.nrm_part[4 * blockIdx.x] = nred[0];
+    a.nrm_part[4 * blockIdx.x + 1] = nred[1];
+  }
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
@@ -1112,6 +1177,20 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
   }
 }
 
+// fixed-order sum of per-warp partials (one block)
+__global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+    *out = t;
+  }
+}
+
 __global__ void w_to_f32(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     d[e] = (float)s[e];
@@ -1147,7 +1226,8 @@ static int launch_sketch(tdk_ctx* ctx, const CUtensorMap& tmY, const CUtensorMap
   return TDK_OK;
 }
 
-int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[], double* Zdst) {
+int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[], double* Zdst,
+              double* normY2) {
   if (g.N < 3 || g.N > 4 || !tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
   const bool f32 = dtype == TDK_F32;
   const int N = g.N, nj = N - 2, nl = N - 1;
@@ -1318,6 +1398,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     pl.take<const double*>(TDK_MAX_MODES);
   }
   pl.take<float>((size_t)a.nunits * a.ustride);
+  pl.take<double>((size_t)4 * ctx->num_sms);
   int rc = ws_reserve(ctx, pl.off);
   if (rc) return rc;
   Carver cv(ctx->ws);
@@ -1341,6 +1422,11 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     TDK_LAUNCH_CHECK(ctx);
   }
   a.part = cv.take<float>((size_t)a.nunits * a.ustride);
+  // ||Y||^2 on the side of the pass: the norm warps of the TMEM-W form, the
+  // converter warps of FP32 data; per warp and CTA, summed in a fixed order
+  double* nrmp = cv.take<double>((size_t)4 * ctx->num_sms);
+  a.nrm_part = (normY2 && (tw || f32)) ? nrmp : nullptr;
+  if (a.nrm_part) TDK_CUDA_TRY(cudaMemsetAsync(nrmp, 0, sizeof(double) * 4 * ctx->num_sms, ctx->stream));
 
   CUtensorMap tmY, tmW;
   {
@@ -1366,7 +1452,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     ProfScope ps(ctx, 0);
     auto k = tc_sketch_tw_kernel;
     TDK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, 320, smem, ctx->stream>>>(tmY, a);
+    k<<<grid, 384, smem, ctx->stream>>>(tmY, a);
     TDK_LAUNCH_CHECK(ctx);
   } else {
     const uint32_t stage = f32 ? SkLayout<true>::STAGE_BYTES : SkLayout<false>::STAGE_BYTES;
@@ -1394,6 +1480,15 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   }
   sketch_tc_reduce<<<(unsigned)std::min<int64_t>((g.zoff[N] + 255) / 256, 65535), 256, 0, ctx->stream>>>(ra, Zdst);
   TDK_LAUNCH_CHECK(ctx);
+  if (normY2) {
+    if (a.nrm_part) {
+      sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(nrmp, 4 * grid, normY2);
+      TDK_LAUNCH_CHECK(ctx);
+    } else {
+      rc = norm2_pass(ctx, g, dtype, Y, normY2);
+      if (rc) return rc;
+    }
+  }
   if (want_prof) {
     unsigned long long hp[16];
     TDK_CUDA_TRY(cudaMemcpyAsync(hp, a.prof, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));

@@ -123,9 +123,13 @@ inline int64_t chain_split_cap(const Geom& g) { return 8 * g.core_numel; }
 // sketch (SIMT): writes FP64 Z_n for all modes into Zdst (packed by zoff)
 int sketch_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],
                 double* Zdst);
-// tensor-core sketch; returns TDK_ENOTSUP when the form does not apply
+// tensor-core sketch; returns TDK_ENOTSUP when the form does not apply.
+// normY2 (null or an FP64 device scalar) receives ||Y||^2, summed while the
+// tiles are staged where the form allows it, else by norm2_pass
 int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],
-              double* Zdst);
+              double* Zdst, double* normY2);
+// ||Y||^2 by one streaming pass over Y (fixed-order sums)
+int norm2_pass(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, double* normY2);
 // CholQR2 of every Z_n (packed FP64) into U_out
 int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[]);
 // one matrix Z [rows x cols]: upper triangle of Z^T Z; Q = Z R^-1 from a Gram

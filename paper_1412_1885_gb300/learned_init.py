@@ -29,16 +29,18 @@ class Samples:
 
 
 def method_sample(ctx: Context, model: Mlp, Y, W, ranks, p, R, B0, prec="tc", max_sweeps=1000, tol=1e-7,
-                  init="given"):
-    """Compress Y, run FFCP from B0 on its core; returns a dict with the flat
-    FP32 core G, colsums [N, Rt], Bstar [N, Rt, Rt], R, sweeps, fit, U and
-    the core in its own type (Gc) with ||Y||^2."""
+                  init="given", seed=0):
+    """Compress Y (W = None: test matrices drawn from `seed`), run FFCP from
+    B0 on its core; returns a dict with the flat FP32 core G, colsums
+    [N, Rt], Bstar [N, Rt, Rt], R, sweeps, fit, U and the core in its own
+    type (Gc) with ||Y||^2."""
     import torch
 
     N = Y.dim()
     Rt = int(ranks[0]) + int(p)
-    U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec)
-    G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
+    nrm = torch.empty((), dtype=torch.float64, device=Y.device)
+    U, _ = tucker_sketch(ctx, Y, W, ranks, p, prec, seed=seed, normY2=nrm)
+    G, _ = tucker_core(ctx, Y, U, ranks, p, prec, want_norm=False)
     init = "given" if init in ("given", "rand") else init
     out = ffcp_als(ctx, G, U, tuple(Y.shape), ranks, p, _dtype_code(Y), R, max_sweeps, tol, init=init, B0=B0,
                    normY2=nrm)

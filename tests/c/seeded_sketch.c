@@ -70,7 +70,7 @@ int main(int argc, char** argv) {
     CHECK_CUDA(cudaMalloc((void**)&Z[n], bytes[n]));
     CHECK_CUDA(cudaMalloc((void**)&U[n], bytes[n]));
   }
-  if (!rc) rc = tucker_sketch(ctx, &d, Y, NULL, U, Z);
+  if (!rc) rc = tucker_sketch(ctx, &d, Y, NULL, U, Z, NULL);
   int flags = 0;
   if (!rc) rc = tdk_ctx_sync_status(ctx, &flags);
   if (rc || flags) {

@@ -68,7 +68,7 @@ def test_strerror_and_argument_checks_without_gpu(L):
     assert t.strerror(t.TDK_EINVAL).startswith("invalid")
     assert t.strerror(t.TDK_WRANKDEF).startswith("warning")
     # null context / descriptor are rejected before any CUDA call
-    assert L.tucker_sketch(None, None, None, None, None, None) == t.TDK_EINVAL
+    assert L.tucker_sketch(None, None, None, None, None, None, None) == t.TDK_EINVAL
     assert L.tucker_core(None, None, None, None, None, None) == t.TDK_EINVAL
     assert L.ffcp_als(None, None, None, None, None, None, None, None, None, None) == t.TDK_EINVAL
     assert L.tdk_ctx_create(None, 0, None) == t.TDK_EINVAL

@@ -339,3 +339,30 @@ def test_ffcp_hals_on_the_sec5_tucker_format_case_reaches_200_db(tdk, ctx):
     Ao[-1] = Ao[-1] * o["lam"][None, :]
     for n in range(N):
         assert np.allclose(Ah[n], Ao[n], rtol=0, atol=1e-8 * np.abs(Ao[n]).max()), n
+
+
+@pytest.mark.parametrize("dtype,prec,shared", [("bf16", "tc", False), ("bf16", "tc", True), ("f32", "tc", False),
+                                               ("f64", "simt", False), ("f32", "simt", False)])
+def test_sketch_pass_returns_the_norm_of_y(tdk, ctx, dtype, prec, shared):
+    """||Y||^2 from tucker_sketch: summed by the norm warps while the
+    TMEM-W form stages the tiles, by the converter warps for FP32 data, or
+    by a streaming pass (CUDA-core form, shared family); equal to the exact
+    sum of squares of the stored values up to FP32 accumulation (1e-6
+    relative; FP64 data 1e-12), and to the core pass's own sum."""
+    import torch
+
+    shape, ranks, p = (67, 45, 136), (5, 6, 7), 3
+    Y, W, _ = small_problem(shape, ranks, p, seed=41, dtype=dtype, shared=shared)
+    Yd = dev_tensor(Y, dtype)
+    nrm = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+    U, _ = tdk.tucker_sketch(ctx, Yd, dev_W(W), ranks, p, prec, normY2=nrm)
+    _, nrm_core = tdk.tucker_core(ctx, Yd, U, ranks, p, prec)
+    assert ctx.sync_status() == 0
+    ref = oracle.norm2(Y)
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    assert abs(float(nrm.item()) - ref) <= tol * ref, (float(nrm.item()), ref)
+    assert abs(float(nrm.item()) - float(nrm_core.item())) <= tol * ref
+    # the core pass without its own sum gives the same core
+    G1, _ = tdk.tucker_core(ctx, Yd, U, ranks, p, prec)
+    G2, none = tdk.tucker_core(ctx, Yd, U, ranks, p, prec, want_norm=False)
+    assert none is None and torch.equal(G1, G2)

@@ -23,7 +23,8 @@ marks a function with no pin independent of itself.
 """
 from .tucker import (unfold, fold, khatri_rao, sketch, sketch_row, householder_qr,
                      ttm, tucker_core, rand_tucker, tucker_full, norm2, hosvd_factors, refine_pass,
-                     rand_tucker_2i, evd_orth, rand_tucker_dense, rand_tucker_seq, grid_blocks,
+                     rand_tucker_2i, evd_orth, rand_tucker_dense, rand_tucker_seq, seq_test_matrices,
+                     rand_tucker_seq_krp, grid_blocks,
                      sketch_share, core_share, rand_tucker_grid)
 from .cpals import (mttkrp, hadamard_grams, cp_full, cp_als, cp_als_nonneg, core_fit,
                     lift, congruence, sir_db, solve_normal, hosvd_init, hals_rows, mu_rows, soft_threshold)
@@ -33,7 +34,7 @@ from . import philox
 __all__ = [
     "unfold", "fold", "khatri_rao", "sketch", "sketch_row", "householder_qr", "ttm",
     "tucker_core", "rand_tucker", "hosvd_factors", "refine_pass", "rand_tucker_2i", "evd_orth",
-    "rand_tucker_dense", "rand_tucker_seq", "grid_blocks", "sketch_share", "core_share", "rand_tucker_grid", "tucker_full", "norm2", "mttkrp", "hadamard_grams",
+    "rand_tucker_dense", "rand_tucker_seq", "seq_test_matrices", "rand_tucker_seq_krp", "grid_blocks", "sketch_share", "core_share", "rand_tucker_grid", "tucker_full", "norm2", "mttkrp", "hadamard_grams",
     "cp_full", "cp_als", "cp_als_nonneg", "core_fit", "lift", "congruence", "sir_db", "solve_normal",
     "hosvd_init", "hals_rows", "mu_rows", "soft_threshold", "mlp", "philox",
 ]

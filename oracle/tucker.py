@@ -243,6 +243,33 @@ def rand_tucker_seq(Y: np.ndarray, Omegas, orth: str = "qr") -> dict:
     return {"U": U, "G": X}
 
 
+def seq_test_matrices(shape, W) -> list:
+    """Khatri-Rao test matrices for Alg. 2's sequential sketch, drawn like
+    the one-pass sketch's: Omega_n = KRP_{k != n} W[n][k][:d_k], with d_k the
+    size of mode k at the time mode n is sketched (Rt_k for k < n, the modes
+    already shrunk; I_k for k > n).  W[n][k] has at least d_k rows; only its
+    first d_k rows enter.  Pinned: the mixed-product identity of the
+    sequential sketch (tests)."""
+    N = len(shape)
+    Rt = [np.asarray(W[n][(n + 1) % N]).shape[1] for n in range(N)]
+    out = []
+    for n in range(N):
+        rows = [Rt[k] if k < n else shape[k] for k in range(N)]
+        out.append(khatri_rao([np.asarray(W[n][k], dtype=np.float64)[:rows[k]] for k in range(N) if k != n]))
+    return out
+
+
+def rand_tucker_seq_krp(Y: np.ndarray, W, orth: str = "qr") -> dict:
+    """Alg. 2 (`rand_tucker_seq`) with the Khatri-Rao test matrices of
+    `seq_test_matrices` in place of dense Gaussian ones; also returns
+    ||Y||^2.  Pinned: exact recovery, and each Z_n equals the sketch of the
+    original Y with the factors U_k W[n][k] for the shrunk modes (tests)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    out = rand_tucker_seq(Y, seq_test_matrices(Y.shape, W), orth)
+    out["normY2"] = norm2(Y)
+    return out
+
+
 def grid_blocks(shape, grid):
     """Index ranges of the sub-tensor grid of Sec. IV-B (Eq. 19): mode n is
     cut into grid[n] contiguous, near-equal blocks.  Returns one list of index

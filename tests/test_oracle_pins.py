@@ -231,20 +231,64 @@ def test_sequential_and_dense_forms_recover_exact_tucker_tensors(orth, p):
     assert rel(den["G"], den["U"]) < 1e-10
 
 
+def _sketch_einsum(Y, n, facs):
+    """Z[i, r] = sum over the other indices of Y times prod_k facs_k[j_k, r],
+    written as one einsum (independent of unfold and khatri_rao)."""
+    N = Y.ndim
+    idx = "abcdefgh"[:N]
+    ops, subs = [Y], [idx]
+    it = iter(facs)
+    for k in range(N):
+        if k != n:
+            ops.append(next(it))
+            subs.append(idx[k] + "z")
+    return np.einsum(",".join(subs) + "->" + idx[n] + "z", *ops)
+
+
+@pytest.mark.parametrize("shape,ranks,p", [((14, 12, 10), (3, 4, 2), 2), ((7, 6, 5, 4), (2, 3, 2, 2), 1)])
+def test_krp_sequential_sketch_mixed_product_identity_and_recovery(shape, ranks, p):
+    """Alg. 2 with Khatri-Rao test matrices sketches mode n on the shrunk
+    X = Y x_{k<n} U_k^T.  By the mixed product (U_a (x) U_b)(W_a (.) W_b) =
+    (U_a W_a) (.) (U_b W_b), that sketch equals the sketch of the ORIGINAL Y
+    with the factors U_k W[n][k][:Rt_k] (k < n) and W[n][k] (k > n), so U_n
+    spans the range of the latter.  On an exact multilinear-rank tensor the
+    result reproduces Y."""
+    Rt = [r + p for r in ranks]
+    N = len(shape)
+    W = synth.sketch_matrices(shape, Rt, 6)
+    Y = synth.tucker_dense(shape, ranks, 4) + 0.05 * _rand(shape, 9)
+    out = oracle.rand_tucker_seq_krp(Y, W)
+    assert math.isclose(out["normY2"], float(np.sum(Y * Y)), rel_tol=1e-13)
+    for n in range(N):
+        facs = [out["U"][k] @ np.asarray(W[n][k])[:Rt[k]] if k < n else np.asarray(W[n][k])
+                for k in range(N) if k != n]
+        Q, _ = np.linalg.qr(_sketch_einsum(Y, n, facs))
+        U = out["U"][n]
+        assert np.allclose(U.T @ U, np.eye(Rt[n]), atol=1e-12)
+        assert np.linalg.norm(U @ U.T - Q @ Q.T) < 1e-9
+    # the last shrunk tensor is the core of Y with the same factors
+    assert np.allclose(out["G"], tucker_core(Y, out["U"]), atol=1e-12 * np.abs(out["G"]).max())
+    Ye = synth.tucker_dense(shape, ranks, 4)
+    ex = oracle.rand_tucker_seq_krp(Ye, W)
+    assert np.linalg.norm(tucker_full(ex["G"], ex["U"]) - Ye) < 1e-10 * np.linalg.norm(Ye)
+
+
 def test_accuracy_cost_of_the_one_pass_khatri_rao_sketch():
     """What the method's sketch gives up against the range finder and Alg. 2
     as printed, at equal widths: 60x56x52 tensors of multilinear rank 6 at
     SNR 10 dB, p = 6, error of [[G; U]] against the noise-free tensor, mean
     over 6 seeds.  Measured: Khatri-Rao Omega 0.49 (shared family 0.49),
-    dense Omega 0.43, Alg. 2 sequential 0.32, RandTucker2i 0.12, HOSVD 0.04.
-    Asserted with margins for the seed noise:
+    dense Omega 0.43, Alg. 2 sequential 0.32 (with Khatri-Rao test matrices
+    0.33), RandTucker2i 0.12, HOSVD 0.04.  Asserted with margins for the seed
+    noise:
       * the Khatri-Rao Omega costs at most 25 % over a dense Gaussian Omega;
       * the shared family costs at most 10 % over independent draws;
-      * the sequential form beats both one-pass forms by at least 15 %;
+      * the sequential form beats both one-pass forms by at least 15 %, and
+        its Khatri-Rao test matrices cost it at most 10 %;
       * RandTucker2i beats all of them, and HOSVD beats RandTucker2i."""
     shape, r, p, S = (60, 56, 52), 6, 6, 6
     Rt = [r + p] * 3
-    e = {k: [] for k in ("krp", "shared", "dense", "seq", "2i", "hosvd")}
+    e = {k: [] for k in ("krp", "shared", "dense", "seq", "seqkrp", "2i", "hosvd")}
     for seed in range(S):
         Ys = synth.tucker_dense(shape, (r,) * 3, seed)
         Y = synth.add_noise(Ys, 10.0, seed)
@@ -253,6 +297,7 @@ def test_accuracy_cost_of_the_one_pass_khatri_rao_sketch():
         e["shared"].append(err(oracle.rand_tucker(Y, synth.sketch_matrices(shape, Rt, seed, shared=True))))
         e["dense"].append(err(oracle.rand_tucker_dense(Y, synth.dense_test_matrices(shape, Rt, seed))))
         e["seq"].append(err(oracle.rand_tucker_seq(Y, synth.dense_test_matrices(shape, Rt, seed, sequential=True))))
+        e["seqkrp"].append(err(oracle.rand_tucker_seq_krp(Y, synth.sketch_matrices(shape, Rt, seed))))
         e["2i"].append(err(oracle.rand_tucker_2i(Y, synth.random_factors(shape, Rt, seed),
                                                  [synth.refine_matrices(Rt, seed, it) for it in range(2)])))
         U = oracle.hosvd_factors(Y, Rt)
@@ -261,6 +306,7 @@ def test_accuracy_cost_of_the_one_pass_khatri_rao_sketch():
     assert m["krp"] <= 1.25 * m["dense"], m
     assert m["shared"] <= 1.10 * m["krp"], m
     assert m["seq"] <= 0.85 * min(m["krp"], m["dense"]), m
+    assert m["seqkrp"] <= 1.10 * m["seq"] and m["seqkrp"] <= 0.85 * m["krp"], m
     assert m["2i"] < m["seq"] and m["hosvd"] < m["2i"], m
 
 

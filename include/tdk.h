@@ -237,19 +237,54 @@ int tucker_sketch_static(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* 
  *   Z_n = X_(n) Omega_n with Omega_n = KRP_{k != n} W[n*N + k],
  *   U_n <- orthonormal basis of Z_n (CholQR2, FP64; rank-deficient Z_n
  *   completed as in tucker_sketch).
- *   Y      [I_1 x ... x I_N], desc->dtype FP64 or FP32 (CUDA-core form).
+ *   Y      [I_1 x ... x I_N] in desc->dtype.  The pass reads Y twice: the
+ *          core pass with mode 1 left open (X of n = 1), and Y x_1 U_1^T with
+ *          the U_1 just refined, from which every n >= 2 shrinks its X.  For
+ *          BF16 data with desc->prec TDK_PREC_TC both run on the tensor cores
+ *          (U split hi + lo in BF16, FP32 accumulation); the shrunk tensors
+ *          are FP32 (FP64 for FP64 data).  TDK_PREC_SIMT: CUDA cores only.
  *   W      N*N device pointers; W[n*N + k] (k != n) FP64 [Rt_k x Rt_n],
  *          a fresh draw per pass; W[n*N + n] is ignored.  NULL: drawn from
  *          desc->seed as in tdk_sketch_matrices with I_k replaced by Rt_k
  *          (the first Rt_k rows of that seed's matrices), so give every pass
- *          its own seed.
+ *          its own seed.  The tensor-core sketch of a shrunk tensor rounds W
+ *          to BF16 as tucker_sketch does.
  *   U_io   N device pointers, FP64 [I_n x Rt_n]: the factors in (any full
  *          rank start, e.g. Gaussian), refined in place.
+ * Workspace: the context's, plus stream-ordered allocations for the shrunk
+ * tensors (the largest is Y x_1 U_1^T: numel / I_1 * Rt_1 elements).
  * Errors: TDK_EINVAL (bad desc, null pointers), TDK_ENOMEM, TDK_ENOTSUP
- * (BF16 data).
+ * (TDK_PREC_TC with FP64 data).
  */
 int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
                   double* const U_io[]);
+
+/*
+ * tucker_seq -- the sequential randomized Tucker compression of Alg. 2 as
+ * printed, with Khatri-Rao test matrices: for n = 1..N in order, starting
+ * from X = Y,
+ *   Z_n = X_(n) Omega_n,  Omega_n = KRP_{k != n} (first d_k rows of W[n*N + k]),
+ *   U_n = orthonormal basis of Z_n (CholQR2, FP64),
+ *   X  <- X x_n U_n^T  (mode n shrinks to Rt_n),
+ * with d_k the size of mode k when mode n is sketched (Rt_k for k < n, I_k
+ * for k > n).  The last X is the core.  It reads Y twice (the sketch of mode
+ * 1 and Y x_1 U_1^T); later modes work on the shrunk tensor.
+ *   desc   as tucker_sketch (dtype, prec, seed).
+ *   Y      [I_1 x ... x I_N] in desc->dtype.  BF16 data with TDK_PREC_TC:
+ *          the sketch of Y and Y x_1 U_1^T on the tensor cores (as in
+ *          tucker_sketch and tucker_core), the shrunk tensors in FP32.
+ *   W      NULL or N*N device pointers as for tucker_sketch (FP64
+ *          [I_k x Rt_n]); only the first d_k rows are read.  NULL: the
+ *          matrices tdk_sketch_matrices draws for desc->seed.
+ *   U_out  N device pointers, FP64 [I_n x Rt_n].
+ *   G_out  the core [Rt_1 x ... x Rt_N], FP64 for FP64 data, FP32 otherwise.
+ *   normY2 NULL or an FP64 device scalar receiving ||Y||_F^2.
+ * Workspace: as tucker_refine.
+ * Errors: TDK_EINVAL, TDK_ENOMEM, TDK_ENOTSUP (TDK_PREC_TC with FP64 data),
+ * TDK_ECUDA, TDK_ETIMEOUT (status word).
+ */
+int tucker_seq(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
+               double* const U_out[], void* G_out, double* normY2);
 
 /*
  * tucker_core -- G = Y x_1 U_1^T x_2 ... x_N U_N^T (Alg. 2, the projection

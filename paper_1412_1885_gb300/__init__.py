@@ -36,7 +36,7 @@ EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_s
            "tdk_mlp_param_count", "tdk_mlp_set_params", "tdk_mlp_get", "tdk_mlp_colsums", "tdk_mlp_train_step",
            "ffcp_predict_init", "tdk_tucker_check", "tdk_copy_in", "tdk_copy_out", "tucker_refine",
            "tdk_ctx_workspace_bytes", "tdk_sketch_matrices", "tucker_sketch_partial", "tucker_core_partial",
-           "tdk_gram", "tdk_orth_apply", "tdk_orth", "tdk_mlp_save", "tdk_mlp_load"]
+           "tdk_gram", "tdk_orth_apply", "tdk_orth", "tdk_mlp_save", "tdk_mlp_load", "tucker_seq"]
 # symbols only the test library exports
 TEST_EXPORTS = ["tdk_ctx_test_fail_alloc", "tdk_test_bounded_wait", "tdk_test_gemm_bf16"]
 MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
@@ -128,6 +128,7 @@ def _load(path):
         L.tucker_sketch.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, pp, vp]
         L.tucker_core.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, vp]
         L.tucker_refine.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
+        L.tucker_seq.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp, vp, vp]
         L.tucker_sketch_static.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, pp]
         L.ffcp_als.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, pp, vp, ctypes.POINTER(AlsOpts), pp, pp, vp,
                                ctypes.POINTER(AlsReport)]
@@ -332,13 +333,14 @@ def tucker_sketch_static(ctx: Context, Y, W, ranks, p, Z_out=None):
     return Z_out
 
 
-def tucker_refine(ctx: Context, Y, W, U, ranks, p, seed=0):
+def tucker_refine(ctx: Context, Y, W, U, ranks, p, seed=0, prec="simt"):
     """One RandTucker2i refinement pass (see include/tdk.h): U (FP64 device
     tensors [I_n x Rt_n]) refined in place with the pass matrices W[n][k]
     (FP64 device [Rt_k x Rt_n]), or with matrices drawn from `seed` when W is
-    None.  Returns U."""
+    None.  prec "tc" runs the two passes over BF16 data on the tensor cores.
+    Returns U."""
     N = Y.dim()
-    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, "simt", seed)
+    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, prec, seed)
     ctx._bind_stream()
     _check(ctx.L.tucker_refine(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _w_array(W, N),
                                _ptrs(U)), "tucker_refine")
@@ -352,10 +354,30 @@ def rand_tucker_2i(ctx: Context, Y, U0, W_passes, ranks, p, prec="simt"):
     U = [u.clone() for u in U0]
     for W in W_passes:
         if isinstance(W, int):
-            tucker_refine(ctx, Y, None, U, ranks, p, seed=W)
+            tucker_refine(ctx, Y, None, U, ranks, p, seed=W, prec=prec)
         else:
-            tucker_refine(ctx, Y, W, U, ranks, p)
+            tucker_refine(ctx, Y, W, U, ranks, p, prec=prec)
     G, nrm = tucker_core(ctx, Y, U, ranks, p, prec)
+    return U, G, nrm
+
+
+def tucker_seq(ctx: Context, Y, W, ranks, p, prec="simt", seed=0):
+    """Alg. 2 as printed, with Khatri-Rao test matrices (tucker_seq): W as
+    for tucker_sketch (None: drawn from `seed`).  Returns (U, G, ||Y||^2)
+    with U FP64 device [I_n x Rt_n], G the core (FP64 for FP64 data, else
+    FP32) and the norm an FP64 device scalar."""
+    import torch
+
+    N = Y.dim()
+    desc = make_desc(Y.shape, _dtype_code(Y), ranks, p, prec, seed)
+    Rt = [int(r) + int(p) for r in ranks]
+    U = [torch.empty((Y.shape[n], Rt[n]), dtype=torch.float64, device=Y.device) for n in range(N)]
+    gdt = torch.float64 if Y.dtype == torch.float64 else torch.float32
+    G = torch.empty(Rt, dtype=gdt, device=Y.device)
+    nrm = torch.empty((), dtype=torch.float64, device=Y.device)
+    ctx._bind_stream()
+    _check(ctx.L.tucker_seq(ctx.handle, ctypes.byref(desc), ctypes.c_void_p(Y.data_ptr()), _w_array(W, N), _ptrs(U),
+                            ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(nrm.data_ptr())), "tucker_seq")
     return U, G, nrm
 
 

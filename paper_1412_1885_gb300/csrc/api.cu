@@ -399,7 +399,7 @@ int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
     for (int k = 0; k < g.N; ++k)
       if (W && k != n && !W[n * g.N + k]) return TDK_EINVAL;
   }
-  if (desc->dtype != TDK_F64 && desc->dtype != TDK_F32) return TDK_ENOTSUP;
+  if (desc->prec == TDK_PREC_TC && desc->dtype == TDK_F64) return TDK_ENOTSUP;
   cudaSetDevice(ctx->device);
   double* wbuf = nullptr;
   const double* wp[TDK_MAX_MODES * TDK_MAX_MODES];
@@ -411,7 +411,34 @@ int tucker_refine(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
     if (rc) return rc;
     W = wp;
   }
-  rc = refine_pass(ctx, g, desc->dtype, Y, W, U_io);
+  rc = refine_pass(ctx, g, desc->dtype, desc->prec, Y, W, U_io);
+  if (wbuf) cudaFreeAsync(wbuf, ctx->stream);
+  return rc;
+}
+
+int tucker_seq(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
+               double* const U_out[], void* G_out, double* normY2) {
+  if (!ctx || !desc || !Y || !U_out || !G_out) return TDK_EINVAL;
+  Geom g;
+  int rc = make_geom(desc, &g);
+  if (rc) return rc;
+  for (int n = 0; n < g.N; ++n) {
+    if (!U_out[n]) return TDK_EINVAL;
+    for (int k = 0; k < g.N; ++k)
+      if (W && k != n && !W[n * g.N + k]) return TDK_EINVAL;
+  }
+  if (desc->prec == TDK_PREC_TC && desc->dtype == TDK_F64) return TDK_ENOTSUP;
+  cudaSetDevice(ctx->device);
+  double* wbuf = nullptr;
+  const double* wp[TDK_MAX_MODES * TDK_MAX_MODES];
+  if (!W) {
+    // the one-pass sketch's draw; a shrunk mode k reads the first Rt_k rows
+    int64_t row0[TDK_MAX_MODES] = {};
+    rc = seeded_w(ctx, g, desc->seed, g.I, row0, &wbuf, wp);
+    if (rc) return rc;
+    W = wp;
+  }
+  rc = seq_tucker(ctx, g, desc, Y, W, U_out, G_out, normY2);
   if (wbuf) cudaFreeAsync(wbuf, ctx->stream);
   return rc;
 }

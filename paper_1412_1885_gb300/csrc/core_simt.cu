@@ -90,21 +90,25 @@ __global__ void __launch_bounds__(NT) ttm_last_kernel(const TY* __restrict__ Y, 
   }
 }
 
-// Xo[a, r, b] = sum_i U[i, r] X[a, i, b];  grid (A, ceil(Bd/64), KS), Rt <= 64.
+// Xo[a, r, b] = sum_i U[i, r] X[a, i, b];  grid (A, min(ceil(Bd/64), 65535), KS),
+// Rt <= 64; a CTA strides over the 64-column tiles of b.
 // Split over the contracted index: CTA z sums i in [z kch, (z+1) kch) into
 // the z-th copy of the output (KS = 1: the output itself).
-template <class T>
-__global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, int64_t Ic, int64_t Bd,
+// X may be stored in a narrower type TX (BF16 data), converted on load.
+template <class T, class TX = T>
+__global__ void __launch_bounds__(NT) ttm_mid_kernel(const TX* __restrict__ X, int64_t Ic, int64_t Bd,
                                                      const T* __restrict__ U, int Rt, T* __restrict__ Xo,
                                                      int64_t kch) {
   __shared__ T Xs[32 * 64];
   __shared__ T Us[32 * 64];
   const int t = threadIdx.x, tb = t & 15, tr = t >> 4;
   const int64_t a = blockIdx.x;
-  const int64_t b0 = (int64_t)blockIdx.y * 64;
   const int64_t k0 = (int64_t)blockIdx.z * kch, k1 = k0 + kch < Ic ? k0 + kch : Ic;
-  const T* Xa = X + a * Ic * Bd;
+  const TX* Xa = X + a * Ic * Bd;
   Xo += (int64_t)blockIdx.z * gridDim.x * (int64_t)Rt * Bd;
+  const int64_t nbt = (Bd + 63) / 64;
+  for (int64_t bt = blockIdx.y; bt < nbt; bt += gridDim.y) {
+  const int64_t b0 = bt * 64;
   T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, in
     for (int e = t; e < 32 * 64; e += NT) {
       int ii = e / 64, c = e % 64;
       int64_t i = i0 + ii;
-      Xs[e] = (i < k1 && b0 + c < Bd) ? Xa[i * Bd + b0 + c] : T(0);
+      Xs[e] = (i < k1 && b0 + c < Bd) ? CvtIn<T>::cvt(Xa[i * Bd + b0 + c]) : T(0);
       Us[e] = (i < k1 && c < Rt) ? U[i * Rt + c] : T(0);
     }
     __syncthreads();
@@ -144,13 +148,14 @@ __global__ void __launch_bounds__(NT) ttm_mid_kernel(const T* __restrict__ X, in
       if (b < Bd) Xoa[(int64_t)r * Bd + b] = acc[p][q];
     }
   }
+  }
 }
 
 // Same contraction for wide FP32 slabs (Rt and Bd above 32): a 64 x 64 output
 // tile per CTA, 64 threads with 8 x 8 outputs each (two 4-wide groups 32 apart
 // in each direction), K staged 32 deep through
 // double-buffered shared memory with the next slice prefetched in registers.
-// grid (A, ceil(Bd / 64))
+// grid (A, min(ceil(Bd / 64), 65535), KS); a CTA strides over the column tiles
 __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__ X, int64_t Ic, int64_t Bd,
                                                        const float* __restrict__ U, int Rt, float* __restrict__ Xo,
                                                        int64_t kch) {
@@ -159,10 +164,12 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
   __shared__ __align__(16) float Us[2][KC][64];
   const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
   const int64_t a = blockIdx.x;
-  const int64_t b0 = (int64_t)blockIdx.y * 64;
   const int64_t k0 = (int64_t)blockIdx.z * kch, k1 = k0 + kch < Ic ? k0 + kch : Ic;
   const float* Xa = X + a * Ic * Bd;
   Xo += (int64_t)blockIdx.z * gridDim.x * (int64_t)Rt * Bd;
+  const int64_t nbt = (Bd + 63) / 64;
+  for (int64_t bt = blockIdx.y; bt < nbt; bt += gridDim.y) {
+  const int64_t b0 = bt * 64;
   const bool bok = b0 + t < Bd, rok = t < Rt;
   float rx[KC], ru[KC];
   // thread t loads column t of the slice: 32 rows of X (coalesced along b) and of U
@@ -222,6 +229,8 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
       const int64_t b = b0 + ((q < 4) ? tx * 4 + q : 32 + tx * 4 + (q - 4));
       if (b < Bd) Xoa[(int64_t)r * Bd + b] = acc[p][q];
     }
+  }
+  __syncthreads();  // the next tile refills the shared buffers
   }
 }
 
@@ -322,7 +331,7 @@ int launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, 
   const int64_t nb = (Bd + 63) / 64, out_n = A * Rt * Bd;
   const int ks = split_count(ctx, A * nb, 2, Ic, out_n, part_cap);
   const int64_t kch = (Ic + ks - 1) / ks;
-  dim3 grid((unsigned)A, (unsigned)nb, (unsigned)ks);
+  dim3 grid((unsigned)A, (unsigned)std::min<int64_t>(nb, 65535), (unsigned)ks);
   ttm_mid_kernel<T><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, ks > 1 ? part : Xo, kch);
   TDK_LAUNCH_CHECK(ctx);
   if (ks > 1) {
@@ -341,13 +350,13 @@ int launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, i
                       : split_count(ctx, narrow ? A : A * nb, 2, Ic, out_n, part_cap);
   const int64_t kch = (Ic + ks - 1) / ks;
   float* dst = ks > 1 ? part : Xo;
+  const unsigned gy = (unsigned)std::min<int64_t>(nb, 65535);
   if (wide)
-    ttm_mid64_kernel<<<dim3((unsigned)A, (unsigned)nb, (unsigned)ks), 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, dst, kch);
+    ttm_mid64_kernel<<<dim3((unsigned)A, gy, (unsigned)ks), 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, dst, kch);
   else if (narrow)
     ttm_mid32_kernel<<<dim3((unsigned)A, 1, (unsigned)ks), 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
   else
-    ttm_mid_kernel<float><<<dim3((unsigned)A, (unsigned)nb, (unsigned)ks), NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt,
-                                                                                                 dst, kch);
+    ttm_mid_kernel<float><<<dim3((unsigned)A, gy, (unsigned)ks), NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, dst, kch);
   TDK_LAUNCH_CHECK(ctx);
   if (ks > 1) {
     sum_split_kernel<float><<<(unsigned)std::min<int64_t>((out_n + 255) / 256, 1024), 256, 0, ctx->stream>>>(
@@ -360,19 +369,50 @@ int launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, i
 template int launch_ttm_mid<double>(tdk_ctx*, const double*, int64_t, int64_t, int64_t, const double*, int, double*,
                                     double*, int64_t);
 
+int launch_ttm_mid_bf16(tdk_ctx* ctx, const __nv_bfloat16* X, int64_t A, int64_t Ic, int64_t Bd, const float* U,
+                        int Rt, float* Xo) {
+  const int64_t nb = (Bd + 63) / 64;
+  dim3 grid((unsigned)A, (unsigned)std::min<int64_t>(nb, 65535), 1);
+  ttm_mid_kernel<float, __nv_bfloat16><<<grid, NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, Xo, Ic);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
+}
+
+template <class T>
+int launch_ttm_last(tdk_ctx* ctx, const T* X, int64_t M, int64_t L, const T* U, int Rt, T* Xo, double* parts,
+                    int grid) {
+  switch ((Rt + 15) / 16) {
+    case 1: return launch_last<T, T, 1>(ctx, X, M, L, U, Rt, Xo, parts, grid);
+    case 2: return launch_last<T, T, 2>(ctx, X, M, L, U, Rt, Xo, parts, grid);
+    case 3: return launch_last<T, T, 3>(ctx, X, M, L, U, Rt, Xo, parts, grid);
+    case 4: return launch_last<T, T, 4>(ctx, X, M, L, U, Rt, Xo, parts, grid);
+  }
+  return TDK_EINVAL;
+}
+template int launch_ttm_last<float>(tdk_ctx*, const float*, int64_t, int64_t, const float*, int, float*, double*, int);
+template int launch_ttm_last<double>(tdk_ctx*, const double*, int64_t, int64_t, const double*, int, double*, double*,
+                                     int);
+
 // core chain from a partly contracted tensor X with dims I_0..I_{m0},
-// Rt_{m0+1}..Rt_{N-1} (modes m0 .. 0 remain); X is neither tmp0 nor tmp1
+// Rt_{m0+1}..Rt_{N-1}: modes m0 down to m_stop are contracted (m_stop = 0:
+// the core; m_stop = 1: mode 0 stays open); X is neither tmp0 nor tmp1
 template <class T>
 int core_chain_from(tdk_ctx* ctx, const Geom& g, const T* X, int m0, T* const Ut[], T* G, T* tmp0, T* tmp1,
-                    T* part, int64_t part_cap) {
+                    T* part, int64_t part_cap, int m_stop) {
   const int N = g.N;
   const T* cur = X;
   int64_t Bd = 1;
   for (int k = m0 + 1; k < N; ++k) Bd *= g.Rt[k];
-  for (int m = m0; m >= 0; --m) {
+  if (m0 < m_stop) {  // nothing left to contract
+    int64_t n = Bd;
+    for (int k = 0; k <= m0; ++k) n *= g.I[k];
+    TDK_CUDA_TRY(cudaMemcpyAsync(G, X, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return TDK_OK;
+  }
+  for (int m = m0; m >= m_stop; --m) {
     int64_t A = 1;
     for (int k = 0; k < m; ++k) A *= g.I[k];
-    T* out = (m == 0) ? G : ((m % 2) ? tmp0 : tmp1);
+    T* out = (m == m_stop) ? G : ((m % 2) ? tmp0 : tmp1);
     const int rc = launch_ttm_mid<T>(ctx, cur, A, g.I[m], Bd, Ut[m], g.Rt[m], out, part, part_cap);
     if (rc) return rc;
     cur = out;
@@ -381,22 +421,22 @@ int core_chain_from(tdk_ctx* ctx, const Geom& g, const T* X, int m0, T* const Ut
   return TDK_OK;
 }
 template int core_chain_from<float>(tdk_ctx*, const Geom&, const float*, int, float* const[], float*, float*,
-                                    float*, float*, int64_t);
+                                    float*, float*, int64_t, int);
 
-// core chain shared by both forms once X_1 exists (modes N-2 .. 0)
+// core chain shared by both forms once X_1 exists (modes N-2 .. m_stop)
 template <class T>
 int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1, T* part,
-                    int64_t part_cap) {
-  return core_chain_from<T>(ctx, g, X1, g.N - 2, Ut, G, tmp0, tmp1, part, part_cap);
+                    int64_t part_cap, int m_stop) {
+  return core_chain_from<T>(ctx, g, X1, g.N - 2, Ut, G, tmp0, tmp1, part, part_cap, m_stop);
 }
 template int core_chain_rest<float>(tdk_ctx*, const Geom&, const float*, float* const[], float*, float*, float*,
-                                    float*, int64_t);
+                                    float*, int64_t, int);
 template int core_chain_rest<double>(tdk_ctx*, const Geom&, const double*, double* const[], double*, double*,
-                                     double*, double*, int64_t);
+                                     double*, double*, int64_t, int);
 
 template <class TY, class T>
 static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double* const U[], void* Gv,
-                       double* normY2) {
+                       double* normY2, int open0) {
   const int N = g.N;
   const int RtL = g.Rt[N - 1];
   const int TC = (RtL + 15) / 16;
@@ -428,6 +468,7 @@ static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double*
   T* Ut[TDK_MAX_MODES];
   for (int n = 0; n < N; ++n) {
     Ut[n] = cv.take<T>((size_t)g.I[n] * g.Rt[n]);
+    if (open0 && n == 0) continue;  // mode 0 stays open: U_1 is not read
     cvt_f64_kernel<T><<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
     TDK_LAUNCH_CHECK(ctx);
   }
@@ -448,15 +489,15 @@ static int core_simt_t(tdk_ctx* ctx, const Geom& g, const void* Y, const double*
     sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(parts, grid, normY2);
     TDK_LAUNCH_CHECK(ctx);
   }
-  return core_chain_rest<T>(ctx, g, X1, Ut, reinterpret_cast<T*>(Gv), tmp0, tmp1, spl, pcap);
+  return core_chain_rest<T>(ctx, g, X1, Ut, reinterpret_cast<T*>(Gv), tmp0, tmp1, spl, pcap, open0 ? 1 : 0);
 }
 
 int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* G,
-              double* normY2) {
+              double* normY2, int open0) {
   switch (dtype) {
-    case TDK_F64: return core_simt_t<double, double>(ctx, g, Y, U, G, normY2);
-    case TDK_F32: return core_simt_t<float, float>(ctx, g, Y, U, G, normY2);
-    case TDK_BF16: return core_simt_t<__nv_bfloat16, float>(ctx, g, Y, U, G, normY2);
+    case TDK_F64: return core_simt_t<double, double>(ctx, g, Y, U, G, normY2, open0);
+    case TDK_F32: return core_simt_t<float, float>(ctx, g, Y, U, G, normY2, open0);
+    case TDK_BF16: return core_simt_t<__nv_bfloat16, float>(ctx, g, Y, U, G, normY2, open0);
   }
   return TDK_EINVAL;
 }

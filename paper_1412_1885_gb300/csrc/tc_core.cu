@@ -17,10 +17,10 @@ namespace tdk {
 
 template <class T>
 int core_chain_rest(tdk_ctx* ctx, const Geom& g, const T* X1, T* const Ut[], T* G, T* tmp0, T* tmp1, T* part,
-                    int64_t part_cap);
+                    int64_t part_cap, int m_stop);
 template <class T>
 int core_chain_from(tdk_ctx* ctx, const Geom& g, const T* X, int m0, T* const Ut[], T* G, T* tmp0, T* tmp1,
-                    T* part, int64_t part_cap);
+                    T* part, int64_t part_cap, int m_stop);
 
 namespace {
 
@@ -262,6 +262,180 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += nred[w];
     a.nrm_part[blockIdx.x] = s;
   }
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Contraction of the leading mode (BF16 data): Alg. 2's first
+// "Y <- Y x_1 U_1^T", and the projection shared by the later modes of a
+// RandTucker2i pass (Alg. 3).  Y is read as [I_1][B] (B = the product of the
+// other dimensions, contiguous) and
+//   X[r, b] = sum_i U_1[i, r] Y[i, b].
+// A CTA tile is LD_MT sub-tiles of 128 columns b.  The MMA reads the Y tile as
+// its A operand MN-major (M = 128 columns b in two 64-column boxes, K = 16
+// rows i per step) and [U_hi | U_lo]^T as the K-major B operand (N = 2 Rtp),
+// so D[b, c] holds the hi products in columns c < Rtp and the lo ones at
+// Rtp + c; the epilogue adds the two and writes X[r, b], coalesced over b.
+// Rows i past I_1 and columns b past B arrive as zeros from TMA.
+struct LdArgs {
+  int64_t B;     // columns
+  int KC;        // 64-row chunks of I_1
+  int NB, Rt, Rtp;
+  int tmem_cols;
+  int64_t ntiles;
+  float* X;      // [Rt][B]
+  unsigned* status;
+};
+
+constexpr int LD_S = 4;                  // stage ring
+constexpr int LD_MT = 2;                 // 128-column sub-tiles per CTA tile
+constexpr uint32_t LD_BOX = 8 * KB;      // 64 rows i x 64 columns b
+constexpr uint32_t LD_SUB = 2 * LD_BOX;  // one 128-column sub-tile
+constexpr int LD_THREADS = 192;
+
+__host__ __device__ inline uint32_t ld_stage_bytes(int NB) { return LD_MT * LD_SUB + (((uint32_t)NB * 128u + 1023u) & ~1023u); }
+inline size_t ld_smem_bytes(int NB) { return 1024 + (size_t)LD_S * ld_stage_bytes(NB) + 8 * (2 * LD_S + 4) + 16; }
+
+__global__ void __launch_bounds__(LD_THREADS, 1)
+    tc_ttm_lead_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmU,
+                       const LdArgs a) {
+  constexpr int S = LD_S;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t b_bytes = (uint32_t)a.NB * 128u;
+  const uint32_t stage_bytes = ld_stage_bytes(a.NB);
+  const uint32_t dcols = (uint32_t)LD_MT * a.NB;  // TMEM columns per accumulator buffer
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * stage_bytes);
+  uint64_t* full = bars;            // [S]
+  uint64_t* empty = bars + S;       // [S]
+  uint64_t* dfull = bars + 2 * S;   // [2]
+  uint64_t* dempty = dfull + 2;     // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&dfull[i]), 1);
+      mbar_init(smem_u32(&dempty[i]), 4);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  unsigned* status = a.status;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmY);
+      prefetch_tmap(&tmU);
+      uint32_t it = 0;
+      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t n = it / S;
+          if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, status)) { ok = false; break; }
+          unsigned char* dst = base + s * stage_bytes;
+          mbar_expect_tx(smem_u32(&full[s]), LD_MT * LD_SUB + b_bytes);
+#pragma unroll
+          for (int m = 0; m < LD_MT; ++m)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              // x = a multiple of 64 columns (128 bytes)
+              const int col = (int)(t * 128 * LD_MT + 128 * m + 64 * h);
+              tma_load_2d(smem_u32(dst + m * LD_SUB + h * LD_BOX), &tmY, col, kc * 64, smem_u32(&full[s]));
+            }
+          tma_load_2d(smem_u32(dst + LD_MT * LD_SUB), &tmU, kc * 64, 0, smem_u32(&full[s]));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id = idesc_bf16(128, a.NB, 1, 0);  // A MN-major (Y tile), B K-major (U^T)
+      uint32_t it = 0, tl = 0;
+      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tl) {
+        const int db = tl & 1;
+        if (!mbar_wait(smem_u32(&dempty[db]), ((tl >> 1) & 1) ^ 1, status)) { ok = false; break; }
+        tc_fence_after();
+        for (int kc = 0; kc < a.KC; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t n = it / S;
+          if (!mbar_wait(smem_u32(&full[s]), n & 1, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sb = smem_u32(base + s * stage_bytes);
+          const uint32_t bb = sb + LD_MT * LD_SUB;
+#pragma unroll
+          for (int m = 0; m < LD_MT; ++m) {
+            const uint32_t d = tmem + db * dcols + m * a.NB;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              // A: 16 rows i (2048 bytes) per step, the two 64-column boxes LD_BOX apart
+              const uint64_t ad = smem_desc(sb + m * LD_SUB + kk * 2048, LD_BOX, 1024, SW128);
+              const uint64_t bd = smem_desc(bb + kk * 32, 16, 1024, SW128);
+              mma_bf16(d, ad, bd, id, (kc | kk) != 0);
+            }
+          }
+          umma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&dfull[db]));
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..5)
+    const int q = warp & 3;
+    const int bl = 32 * q + lane;
+    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    uint32_t tl = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tl) {
+      const int db = tl & 1;
+      if (!mbar_wait(smem_u32(&dfull[db]), (tl >> 1) & 1, status)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll 1
+      for (int m = 0; m < LD_MT; ++m) {
+        float v[128];
+#pragma unroll
+        for (int c16 = 0; c16 < 8; ++c16)
+          if (c16 * 16 < a.NB) tmem_ld16(tmem + db * dcols + m * a.NB + c16 * 16 + lane_addr, v + c16 * 16);
+        tmem_wait_ld();
+        if (m == LD_MT - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&dempty[db]));
+        }
+        const int64_t b = (t * LD_MT + m) * 128 + bl;
+        if (b < a.B) {
+#pragma unroll
+          for (int r = 0; r < 64; ++r) {
+            if (r < a.Rt) {
+              float x = v[r];
+#pragma unroll
+              for (int h = 16; h <= 64; h += 16)
+                if (a.Rtp == h) x += v[h + r];
+              a.X[(int64_t)r * a.B + b] = x;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, a.tmem_cols);
@@ -695,7 +869,7 @@ int launch_core(tdk_ctx* ctx, const CUtensorMap& tmY, const CUtensorMap& tmU, co
 // BF16 data, N >= 3: the fused first two contractions, then the rest of the
 // chain from X_2 on CUDA cores
 static int core_tc_fused(tdk_ctx* ctx, const Geom& g, const void* Y, const double* const U[], void* Gv,
-                         double* normY2) {
+                         double* normY2, int open0) {
   const int N = g.N;
   FuArgs a{};
   a.L = (int)g.L;
@@ -747,12 +921,13 @@ static int core_tc_fused(tdk_ctx* ctx, const Geom& g, const void* Y, const doubl
   float* Ut[TDK_MAX_MODES];
   for (int n = 0; n < N; ++n) {
     Ut[n] = cv.take<float>((size_t)g.I[n] * g.Rt[n]);
-    if (n < N - 2) {
+    if (n < N - 2 && !(open0 && n == 0)) {
       cvt_u<<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
       TDK_LAUNCH_CHECK(ctx);
     }
   }
-  a.X2 = cv.take<float>((size_t)P * a.Rt2 * a.Rt);
+  // with mode 0 open and N = 3, X_2 is the result itself
+  a.X2 = (open0 && N == 3) ? reinterpret_cast<float*>(Gv) : cv.take<float>((size_t)P * a.Rt2 * a.Rt);
   float* tmp0 = cv.take<float>((size_t)tmpsz);
   float* tmp1 = cv.take<float>((size_t)tmpsz);
   a.want_norm = normY2 != nullptr;
@@ -787,14 +962,16 @@ static int core_tc_fused(tdk_ctx* ctx, const Geom& g, const void* Y, const doubl
     sum_doubles<<<1, 256, 0, ctx->stream>>>(a.nrm_part, grid, normY2);
     TDK_LAUNCH_CHECK(ctx);
   }
-  return core_chain_from<float>(ctx, g, a.X2, N - 3, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1, spl, pcap);
+  if (open0 && N == 3) return TDK_OK;
+  return core_chain_from<float>(ctx, g, a.X2, N - 3, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1, spl, pcap,
+                                open0 ? 1 : 0);
 }
 
 int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[], void* Gv,
-            double* normY2) {
+            double* normY2, int open0) {
   if (!tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
   if (dtype == TDK_BF16 && g.N >= 3) {
-    const int rc = core_tc_fused(ctx, g, Y, U, Gv, normY2);
+    const int rc = core_tc_fused(ctx, g, Y, U, Gv, normY2, open0);
     if (rc != TDK_ENOTSUP) return rc;
   }
   const bool f32 = dtype == TDK_F32;
@@ -847,6 +1024,7 @@ int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double*
   float* Ut[TDK_MAX_MODES];
   for (int n = 0; n < N; ++n) {
     Ut[n] = cv.take<float>((size_t)g.I[n] * g.Rt[n]);
+    if (open0 && n == 0) continue;
     cvt_u<<<64, 256, 0, ctx->stream>>>(U[n], Ut[n], g.I[n] * g.Rt[n]);
     TDK_LAUNCH_CHECK(ctx);
   }
@@ -877,7 +1055,57 @@ int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double*
     sum_doubles<<<1, 256, 0, ctx->stream>>>(a.nrm_part, grid, normY2);
     TDK_LAUNCH_CHECK(ctx);
   }
-  return core_chain_rest<float>(ctx, g, a.X, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1, spl, pcap);
+  return core_chain_rest<float>(ctx, g, a.X, Ut, reinterpret_cast<float*>(Gv), tmp0, tmp1, spl, pcap,
+                               open0 ? 1 : 0);
+}
+
+int ttm_lead_tc(tdk_ctx* ctx, const Geom& g, const void* Y, const double* U1, float* X) {
+  const int64_t I0 = g.I[0];
+  const int64_t B = g.numel / I0;
+  LdArgs a{};
+  a.B = B;
+  a.Rt = g.Rt[0];
+  a.Rtp = (a.Rt + 15) / 16 * 16;
+  a.NB = 2 * a.Rtp;  // U_1 split hi + lo
+  // TMA: 16-byte row stride of Y; 32-bit coordinates of the last tile
+  if (a.Rt > 64 || B % 8 != 0 || B + 128 * LD_MT > (int64_t)0x7fffffff || I0 > (int64_t)0x7fffffff)
+    return TDK_ENOTSUP;
+  a.KC = (int)((I0 + 63) / 64);
+  a.tmem_cols = 32;
+  while (a.tmem_cols < 2 * LD_MT * a.NB) a.tmem_cols *= 2;
+  if (a.tmem_cols > 512) return TDK_ENOTSUP;
+  const size_t smem = ld_smem_bytes(a.NB);
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
+  a.ntiles = (B + 128 * LD_MT - 1) / (128 * LD_MT);
+  a.X = X;
+  a.status = ctx->d_status;
+  const int grid = (int)std::min<int64_t>(a.ntiles, ctx->num_sms);
+  const int64_t ldu = (I0 + 7) / 8 * 8;
+  Planner pl;
+  pl.take<__nv_bfloat16>((size_t)a.NB * ldu);
+  int rc = ws_reserve(ctx, pl.off);
+  if (rc) return rc;
+  Carver cv(ctx->ws);
+  __nv_bfloat16* ub = cv.take<__nv_bfloat16>((size_t)a.NB * ldu);
+  build_u_bf16<<<128, 256, 0, ctx->stream>>>(U1, (int)I0, a.Rt, a.Rtp, 1, (int)ldu, ub);
+  TDK_LAUNCH_CHECK(ctx);
+  CUtensorMap tmY, tmU;
+  {
+    uint64_t dims[2] = {(uint64_t)B, (uint64_t)I0};
+    uint64_t str[1] = {(uint64_t)B * 2};
+    uint32_t box[2] = {64u, 64u};
+    rc = encode_tmap(&tmY, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Y, dims, str, box, true);
+    if (rc) return rc;
+    uint64_t ud[2] = {(uint64_t)I0, (uint64_t)a.NB};
+    uint64_t us[1] = {(uint64_t)ldu * 2};
+    uint32_t ubx[2] = {64u, (uint32_t)a.NB};
+    rc = encode_tmap(&tmU, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ub, ud, us, ubx, true);
+    if (rc) return rc;
+  }
+  TDK_CUDA_TRY(cudaFuncSetAttribute(tc_ttm_lead_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc_ttm_lead_kernel<<<grid, LD_THREADS, smem, ctx->stream>>>(tmY, tmU, a);
+  TDK_LAUNCH_CHECK(ctx);
+  return TDK_OK;
 }
 
 }  // namespace tdk

@@ -138,19 +138,39 @@ int orth_apply_one(tdk_ctx* ctx, const double* gram, const double* Z, int64_t ro
 // seeded test matrices: W_out[n*N + k] <- rows [row0_k, row0_k + rows_k) of W_k^(n)
 int draw_sketch_matrices(tdk_ctx* ctx, int N, const int64_t* rows, const int64_t* row0, const int* Rt,
                          uint64_t seed, double* const W_out[]);
-// core: G (T) and ||Y||^2 (FP64 device scalar, may be null)
+// core: G (T) and ||Y||^2 (FP64 device scalar, may be null).  open0 = 1
+// leaves mode 0 uncontracted: G receives Y x_2 U_2^T ... x_N U_N^T with dims
+// (I_1, Rt_2, ..., Rt_N), and U[0] is not read
 int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[],
-              void* G, double* normY2);
+              void* G, double* normY2, int open0 = 0);
 int core_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const U[],
-            void* G, double* normY2);
-// one refinement pass of RandTucker2i on CUDA cores (FP64/FP32 data)
-int refine_pass(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[],
+            void* G, double* normY2, int open0 = 0);
+// the leading mode contracted: X[r, b] = sum_i U_1[i, r] Y[i, b], Y read as
+// [I_1][B] with B = numel / I_1, X in the compute type (FP64 for FP64 data,
+// FP32 otherwise); the tensor-core form for BF16 data when prec is TC and
+// the shape allows it, else CUDA cores
+int ttm_lead(tdk_ctx* ctx, const Geom& g, int dtype, int prec, const void* Y, const double* U1, void* X);
+// tensor-core form of ttm_lead (BF16 data); TDK_ENOTSUP when it does not apply
+int ttm_lead_tc(tdk_ctx* ctx, const Geom& g, const void* Y, const double* U1, float* X);
+// one refinement pass of RandTucker2i
+int refine_pass(tdk_ctx* ctx, const Geom& g, int dtype, int prec, const void* Y, const double* const W[],
                 double* const U_io[]);
+// Alg. 2 in its printed order (the sequential sketch)
+int seq_tucker(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
+               double* const U_out[], void* G_out, double* normY2);
 // X_out[a, r, b] = sum_i U[i, r] X[a, i, b] (T = float or double), with an
 // optional buffer for split partial outputs (nullptr = no split)
 template <class T>
 int launch_ttm_mid(tdk_ctx* ctx, const T* X, int64_t A, int64_t Ic, int64_t Bd, const T* U, int Rt, T* Xo,
                    T* part, int64_t part_cap);
+// the same with BF16 X and FP32 U and output (no split)
+int launch_ttm_mid_bf16(tdk_ctx* ctx, const __nv_bfloat16* X, int64_t A, int64_t Ic, int64_t Bd, const float* U,
+                        int Rt, float* Xo);
+// Xo[row, r] = sum_col X[row, col] U[col, r] (the contiguous mode); parts
+// receives grid FP64 partial sums of X's squares
+template <class T>
+int launch_ttm_last(tdk_ctx* ctx, const T* X, int64_t M, int64_t L, const T* U, int Rt, T* Xo, double* parts,
+                    int grid);
 int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double* const U[],
             const double* normY2, const tdk_als_opts* o, double* const B_io[],
             double* const A_io[], double* lambda_out, tdk_als_report* rep);

@@ -38,7 +38,7 @@ EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_s
            "tdk_ctx_workspace_bytes", "tdk_sketch_matrices", "tucker_sketch_partial", "tucker_core_partial",
            "tdk_gram", "tdk_orth_apply", "tdk_orth", "tdk_mlp_save", "tdk_mlp_load", "tucker_seq"]
 # symbols only the test library exports
-TEST_EXPORTS = ["tdk_ctx_test_fail_alloc", "tdk_test_bounded_wait", "tdk_test_gemm_bf16"]
+TEST_EXPORTS = ["tdk_ctx_test_fail_alloc", "tdk_test_bounded_wait", "tdk_test_gemm_bf16", "tdk_test_ttm_lead"]
 MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
 MLP_INPUT, MLP_Z1, MLP_H1, MLP_Z2, MLP_H2, MLP_DO, MLP_DZ2, MLP_DZ1 = 5, 6, 7, 8, 9, 10, 11, 12
 
@@ -153,6 +153,8 @@ def _load(path):
             L.tdk_ctx_test_fail_alloc.argtypes = [vp, ctypes.c_int]
         if hasattr(L, "tdk_test_bounded_wait"):
             L.tdk_test_bounded_wait.argtypes = [vp, ctypes.c_ulonglong]
+        if hasattr(L, "tdk_test_ttm_lead"):
+            L.tdk_test_ttm_lead.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, vp, vp]
         return L
 
 

@@ -308,6 +308,20 @@ int refine_pass(tdk_ctx* ctx, const Geom& g, int dtype, int prec, const void* Y,
   return refine_pass_t<float>(ctx, g, dtype, prec, Y, W, U_io);
 }
 
+#ifdef TDK_TESTING
+// test library only: the leading-mode contraction alone, X = Y x_1 U_1^T in
+// the compute type (FP64 for FP64 data, else FP32), X [Rt_1 x numel / I_1]
+extern "C" int tdk_test_ttm_lead(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, const double* U1,
+                                 void* X) {
+  if (!ctx || !desc || !Y || !U1 || !X) return TDK_EINVAL;
+  Geom g;
+  const int rc = make_geom(desc, &g);
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  return ttm_lead(ctx, g, desc->dtype, desc->prec, Y, U1, X);
+}
+#endif
+
 int seq_tucker(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc, const void* Y, const double* const W[],
                double* const U_out[], void* G_out, double* normY2) {
   if (desc->dtype == TDK_F64)

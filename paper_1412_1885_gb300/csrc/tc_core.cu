@@ -296,7 +296,9 @@ constexpr uint32_t LD_BOX = 8 * KB;      // 64 rows i x 64 columns b
 constexpr uint32_t LD_SUB = 2 * LD_BOX;  // one 128-column sub-tile
 constexpr int LD_THREADS = 192;
 
-__host__ __device__ inline uint32_t ld_stage_bytes(int NB) { return LD_MT * LD_SUB + (((uint32_t)NB * 128u + 1023u) & ~1023u); }
+__host__ __device__ inline uint32_t ld_stage_bytes(int NB) {
+  return LD_MT * LD_SUB + (((uint32_t)NB * 128u + 1023u) & ~1023u);
+}
 inline size_t ld_smem_bytes(int NB) { return 1024 + (size_t)LD_S * ld_stage_bytes(NB) + 8 * (2 * LD_S + 4) + 16; }
 
 __global__ void __launch_bounds__(LD_THREADS, 1)

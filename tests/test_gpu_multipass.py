@@ -166,3 +166,41 @@ def test_refine_pass_matches_the_oracle_step_by_step(tdk, ctx, dtype, prec, shap
             _basis_check(U_out[n], Z, dtype, ("pass", it, "mode", n))
     G, nrm = tdk.tucker_core(ctx, Yd, U, ranks, p, prec)
     _core_check(Y, [host(u) for u in U], host(G), dtype)
+
+
+@pytest.mark.parametrize("dtype,prec,shape", [
+    ("bf16", "tc", (300, 260, 136)),    # 4 full 64-row chunks + 44 rows; 138.1 column tiles of 256
+    ("bf16", "tc", (130, 8, 9, 16)),    # B = 1152: 4.5 tiles
+    ("bf16", "simt", (67, 45, 130)),
+    ("f32", "tc", (67, 45, 128)),       # FP32 data: CUDA cores
+    ("f64", "simt", (31, 17, 11)),
+])
+def test_leading_mode_contraction_matches_oracle_elementwise(tdk, dtype, prec, shape):
+    """X = Y x_1 U_1^T alone (the test library's hook), every entry against
+    the oracle's TTM, relative to the bound |Y| x_1 |U_1|^T: FP32 sums plus
+    the hi + lo split of U (below 2^-17) on the tensor cores."""
+    import ctypes
+
+    import torch
+
+    c = tdk.Context(0, testing=True)
+    try:
+        Rt0 = 60 if shape[0] >= 60 else 7
+        ranks, p = [Rt0 - 4] + [3] * (len(shape) - 1), 4
+        Y, _, _ = small_problem(shape, ranks, p, seed=71, dtype=dtype)
+        U1 = np.linalg.qr(np.random.default_rng(71).standard_normal((shape[0], Rt0)))[0]
+        Yd, Ud = dev_tensor(Y, dtype), dev_tensor(U1, "f64")
+        B = int(np.prod(shape[1:]))
+        X = torch.empty((Rt0, B), dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")
+        desc = tdk.make_desc(shape, tdk._dtype_code(Yd), ranks, p, prec)
+        c._bind_stream()
+        rc = c.L.tdk_test_ttm_lead(c.handle, ctypes.byref(desc), ctypes.c_void_p(Yd.data_ptr()),
+                                   ctypes.c_void_p(Ud.data_ptr()), ctypes.c_void_p(X.data_ptr()))
+        assert rc == 0 and c.sync_status() == 0
+        ref = oracle.ttm(Y, U1, 0).reshape(Rt0, B)
+        bnd = oracle.ttm(np.abs(Y), np.abs(U1), 0).reshape(Rt0, B)
+        tol = 1e-13 if dtype == "f64" else 2e-5 + 2.0 ** -17
+        err = np.abs(host(X) - ref)
+        assert np.all(err <= tol * bnd), float((err / bnd).max())
+    finally:
+        c.close()

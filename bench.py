@@ -260,6 +260,55 @@ def _fit_run(fn):
     return e0.elapsed_time(e1), out
 
 
+def compress_forms(t, ctx, w, Y, Wd, prec, dev, reps=2):
+    """One-pass sketch + core, Alg. 2 (tucker_seq) and RandTucker2i (two
+    tucker_refine passes from Gaussian factors, then the core) on the timed
+    tensor: device ms per run (CUDA events, after a warm run), the passes
+    over Y each makes, GB/s of Y read, and the relative reconstruction error
+    sqrt(1 - ||G||^2 / ||Y||^2) (orthonormal factors)."""
+    import math
+
+    import torch
+
+    import synth
+
+    U0 = [torch.as_tensor(u, device=dev) for u in synth.random_factors(w.shape, w.Rt, w.seed)]
+
+    def one_pass():
+        nrm = torch.empty((), dtype=torch.float64, device=dev)
+        U, _ = t.tucker_sketch(ctx, Y, Wd, w.ranks, w.p, prec, normY2=nrm)
+        G, _ = t.tucker_core(ctx, Y, U, w.ranks, w.p, prec, want_norm=False)
+        return G, nrm
+
+    def seq():
+        _, G, nrm = t.tucker_seq(ctx, Y, Wd, w.ranks, w.p, prec)
+        return G, nrm
+
+    def two_i():
+        _, G, nrm = t.rand_tucker_2i(ctx, Y, U0, [w.seed + 101, w.seed + 102], w.ranks, w.p, prec)
+        return G, nrm
+
+    y_bytes = w.itemsize * w.numel
+    out = {}
+    for name, fn, passes in (("one_pass", one_pass, 2), ("alg2_sequential", seq, 2), ("randtucker2i", two_i, 5)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            G, nrm = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        n2 = float(nrm.item())
+        err = math.sqrt(max(0.0, n2 - float((G.double() ** 2).sum().item())) / n2)
+        out[name] = {"ms": ms, "passes_over_Y": passes, "GBps_of_Y": passes * y_bytes / (ms * 1e-3) / 1e9,
+                     "rel_error": err}
+    out["note"] = ("device ms per run with Y resident; rel_error = ||Y - [[G; U]]|| / ||Y|| on the bench tensor "
+                   "(CP model plus noise); RandTucker2i: two refinement passes from Gaussian factors, then the core")
+    return out
+
+
 def learned_setup(t, ctx, w, prec, n_train, n_eval, dev):
     """Learned-initialiser workload: build a training set with the method
     (compress, FFCP from the HOSVD start to convergence), train the MLP, then
@@ -361,6 +410,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-ttf", action="store_true", help="skip the time-to-fit comparison of the forms")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the comparison of the one-pass, sequential (Alg. 2) and RandTucker2i compressions")
     ap.add_argument("--train", type=int, default=2048, help="learned-init workload: training tensors")
     ap.add_argument("--eval", type=int, default=64, help="learned-init workload: held-out tensors")
     ap.add_argument("--nonneg-rule", default="ls", choices=["ls", "hals", "mu"],
@@ -499,6 +550,12 @@ def main():
             ttf["speedup_vs_simt"] = forms["simt"]["ms"] / forms[args.prec]["ms"]
             ttf["fit_Y_diff"] = abs(forms["simt"]["fit_Y"] - forms[args.prec]["fit_Y"])
 
+    # ---- the three compressions of Sec. IV-A on the same tensor: passes over
+    # Y, device time and reconstruction error ||Y - [[G; U]]|| / ||Y||
+    forms = None
+    if not args.no_forms and rank == 0:
+        forms = compress_forms(t, ctx, w, Y, Wd, args.prec, dev)
+
     peak, peak_kind = _peaks()
     sk_avg = sk_ms / max(sk_n, 1)
     achieved = y_bytes / (sk_avg * 1e-3) / 1e9 if sk_n else None
@@ -531,7 +588,8 @@ def main():
                 "gpu_launches": launches,
                 "als": {"sweeps": sweeps, "fit_core": out["fit_core"], "fit_Y": out["fit_Y"],
                         "ms_last": out["ms"]},
-                "sketch_ms": sk_avg, "core_ms": co_ms / max(co_n, 1), "time_to_fit": ttf}
+                "sketch_ms": sk_avg, "core_ms": co_ms / max(co_n, 1), "time_to_fit": ttf,
+                "compress_forms": forms}
         if li_info is not None:
             line["learned_init"] = li_info
             line["config"]["train_tensors"] = li_info["train_tensors"]

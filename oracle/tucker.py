@@ -10,10 +10,11 @@ The method computes, for every mode n from the ORIGINAL tensor Y,
 i.e. the range-finder sketch of every mode taken in one pass over Y with a
 Khatri-Rao structured Gaussian test matrix, then the Tucker core (Eq. 1).
 
-The forms the paper prints are here too, for comparison: the range finder
-with a dense Gaussian Omega (`rand_tucker_dense`), Alg. 2's sequential sketch
-on the shrinking tensor (`rand_tucker_seq`), the Gram-based basis of Eq. 23
-(`evd_orth`), and RandTucker2i (Alg. 3).
+The forms the paper prints are here too: the range finder with a dense
+Gaussian Omega (`rand_tucker_dense`), Alg. 2's sequential sketch on the
+shrinking tensor (`rand_tucker_seq`, and `rand_tucker_seq_krp` with
+Khatri-Rao test matrices), the Gram-based basis of Eq. 23 (`evd_orth`), the
+sub-tensor grid of Sec. IV-B (`rand_tucker_grid`) and RandTucker2i (Alg. 3).
 """
 from __future__ import annotations
 
@@ -230,7 +231,7 @@ def rand_tucker_seq(Y: np.ndarray, Omegas, orth: str = "qr") -> dict:
     dense Gaussian Omega_n, U_n an orthonormal basis of Z_n, then Y <- Y x_n
     U_n^T (mode n shrinks to Rt_n before mode n + 1 is sketched); the last Y
     is the core.  Omega_n therefore has prod_{k<n} Rt_k prod_{k>n} I_k rows.
-    orth "qr" takes the Householder basis (step 3's "e.g. QR"), "evd" the Gram
+    orth "qr" takes the Householder basis (step 3 names QR as one choice), "evd" the Gram
     route of Eq. 23.  Pinned: exact recovery, and the core equals the TTM
     chain of the original Y with the same factors."""
     X = np.asarray(Y, dtype=np.float64)

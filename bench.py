@@ -361,12 +361,17 @@ def learned_setup(t, ctx, w, prec, n_train, n_eval, dev):
             res[name]["sweeps"].append(o["sweeps"])
             res[name]["fit"].append(o["fit_Y"])
             res[name]["ms"].append(ms)
+        ms_p, _ = _fit_run(lambda: m.predict_init(G, U, wk.shape, list(wk.ranks), 0, t._dtype_code(Y), wk.als_R))
+        res["learned"].setdefault("ms_predict", []).append(ms_p)
         del Y
     ev = {k: {"sweeps_median": float(np.median(v["sweeps"])), "sweeps_mean": float(np.mean(v["sweeps"])),
               "sweeps_p90": float(np.percentile(v["sweeps"], 90)), "ms_median": float(np.median(v["ms"])),
-              "ms_mean": float(np.mean(v["ms"])), "fit_Y_mean": float(np.mean(v["fit"]))} for k, v in res.items()}
+              "ms_mean": float(np.mean(v["ms"])), "fit_Y_mean": float(np.mean(v["fit"])),
+              **({"ms_predict_median": float(np.median(v["ms_predict"]))} if "ms_predict" in v else {})}
+          for k, v in res.items()}
     info = {"train_tensors": int(data.G.shape[0]), "generated": n_train, "epochs": 40, "hidden": hidden,
-            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "gen_s": gen_s, "train_s": train_s,
+            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "loss_best_epoch": min(hist),
+            "loss_per_epoch": hist, "grad_clip": 1.0, "gen_s": gen_s, "train_s": train_s,
             "eval_tensors": n_eval, "eval": ev}
     return m, info
 

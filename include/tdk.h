@@ -91,7 +91,9 @@ int tdk_ctx_destroy(tdk_ctx* ctx);
 int tdk_ctx_set_stream(tdk_ctx* ctx, void* cuda_stream);
 /* Wait for the stream, then return (and clear) the OR of the device-side
    status flags raised since the last call (TDK_WRANKDEF, TDK_ETIMEOUT as
-   bit 8).  Returns TDK_ECUDA if the stream reported a CUDA error. */
+   bit 8; in the test library, built with bounds checks, bit 9 when an index
+   fell outside its range and the access was skipped).  Returns TDK_ECUDA if
+   the stream reported a CUDA error. */
 int tdk_ctx_sync_status(tdk_ctx* ctx, int* flags_out /* host */);
 /* Number of kernel launches this context has issued since creation. */
 int64_t tdk_ctx_launch_count(const tdk_ctx* ctx);
@@ -503,6 +505,10 @@ typedef struct {
   double beta1, beta2, eps;  /* Adam moments and denominator guard        */
   int update;     /* 0: loss and gradients only; 1: also one Adam step      */
   int reserved;
+  double clip;    /* > 0: before the Adam step the gradient is scaled by
+                     min(1, clip / ||g||_2), the norm over all parameters
+                     (gradient-norm clipping); 0: no clipping.  The stored
+                     gradient (TDK_MLP_GRADS) stays unscaled.              */
 } tdk_mlp_train_opts;
 
 /* Create a model (weights zero until tdk_mlp_set_params) with device

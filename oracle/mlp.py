@@ -54,7 +54,7 @@ from .cpals import cp_full
 
 __all__ = ["mlp_dims", "param_sizes", "unpack", "canonicalise", "canonical_target", "network_input", "gelu",
            "gelu_grad", "linear", "activation", "delta", "dloss_dO",
-           "forward", "loss", "loss_grad", "adam_step", "decanonicalise"]
+           "forward", "loss", "loss_grad", "clip_grad", "adam_step", "decanonicalise"]
 
 
 def _bf16(x):
@@ -243,6 +243,17 @@ def loss_grad(theta, X, S, R, N: int, Rt: int, hidden: int, T=None, alpha: float
     gb1 = dZ1.sum(axis=0)
     g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3)])
     return L, g, O
+
+
+def clip_grad(g, clip: float):
+    """Gradient-norm clipping (Pascanu, Mikolov and Bengio, ICML 2013): g
+    scaled by min(1, clip / ||g||_2), the norm taken over all parameters;
+    clip <= 0 leaves g as it is."""
+    g = np.asarray(g, dtype=np.float64)
+    if clip <= 0.0:
+        return g
+    n = float(np.sqrt(np.sum(g * g)))
+    return g * (clip / n) if n > clip else g
 
 
 def adam_step(theta, m, v, g, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):

@@ -38,7 +38,8 @@ EXPORTS = ["tdk_ctx_create", "tdk_ctx_destroy", "tdk_ctx_set_stream", "tdk_ctx_s
            "tdk_ctx_workspace_bytes", "tdk_sketch_matrices", "tucker_sketch_partial", "tucker_core_partial",
            "tdk_gram", "tdk_orth_apply", "tdk_orth", "tdk_mlp_save", "tdk_mlp_load", "tucker_seq"]
 # symbols only the test library exports
-TEST_EXPORTS = ["tdk_ctx_test_fail_alloc", "tdk_test_bounded_wait", "tdk_test_gemm_bf16", "tdk_test_ttm_lead"]
+TEST_EXPORTS = ["tdk_ctx_test_fail_alloc", "tdk_test_bounded_wait", "tdk_test_gemm_bf16", "tdk_test_ttm_lead",
+                "tdk_test_checked_store"]
 MLP_PARAMS, MLP_GRADS, MLP_CANON_CORE, MLP_ROTATIONS, MLP_OUTPUT = 0, 1, 2, 3, 4
 MLP_INPUT, MLP_Z1, MLP_H1, MLP_Z2, MLP_H2, MLP_DO, MLP_DZ2, MLP_DZ1 = 5, 6, 7, 8, 9, 10, 11, 12
 
@@ -66,7 +67,7 @@ class MlpDesc(ctypes.Structure):
 class MlpTrainOpts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("update", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("reserved", ctypes.c_int), ("clip", ctypes.c_double)]
 
 
 class TdkError(RuntimeError):
@@ -153,6 +154,8 @@ def _load(path):
             L.tdk_ctx_test_fail_alloc.argtypes = [vp, ctypes.c_int]
         if hasattr(L, "tdk_test_bounded_wait"):
             L.tdk_test_bounded_wait.argtypes = [vp, ctypes.c_ulonglong]
+        if hasattr(L, "tdk_test_checked_store"):
+            L.tdk_test_checked_store.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong]
         if hasattr(L, "tdk_test_ttm_lead"):
             L.tdk_test_ttm_lead.argtypes = [vp, ctypes.POINTER(TuckerDesc), vp, vp, vp]
         return L
@@ -561,12 +564,13 @@ class Mlp:
         _check(self.ctx.L.tdk_mlp_load(self.ctx.handle, self._h, os.fsencode(path)), "tdk_mlp_load")
 
     def train_step(self, G, colsums, R, Bstar=None, alpha=0.0, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-                   update=True, lam=None):
+                   update=True, lam=None, clip=0.0):
         """One step on a device batch: G FP32 [B, Rt^N], colsums FP64 [B, N, Rt],
         R int32 [B], Bstar FP64 [B, N, Rt, Rt] or None, lam FP64 [B, Rt] or None
-        (weights of Bstar's columns).  Returns the batch loss."""
+        (weights of Bstar's columns); clip > 0 caps the gradient's global norm
+        before the Adam step.  Returns the batch loss."""
         o = MlpTrainOpts(alpha=float(alpha), lr=float(lr), beta1=float(beta1), beta2=float(beta2), eps=float(eps),
-                         update=int(bool(update)), reserved=0)
+                         update=int(bool(update)), reserved=0, clip=float(clip))
         loss = ctypes.c_double(0.0)
         B = int(G.shape[0])
         self.ctx._bind_stream()

@@ -1,11 +1,12 @@
 """Build libtdk.so in-tree for sm_103a (nvcc, one object per translation unit,
 compiled in parallel, linked as a shared library with the static CUDA runtime).
 
-Beside it, libtdk_test.so: the same library with the test hooks compiled in
-(-DTDK_TESTING: a forced workspace-allocation failure, a device wait that
-nothing satisfies, one raw GEMM call, and cycle-counter profiling switches).
-Only the translation units that mention TDK_TESTING are compiled twice; the
-product library exports none of the hooks."""
+Beside it, libtdk_test.so: the same sources compiled with -DTDK_TESTING (the
+test hooks: a forced workspace-allocation failure, a device wait that nothing
+satisfies, raw kernel calls, cycle-counter profiling switches) and
+-DTDK_CHECKED (bounds checks on the kernels' index computations that report
+through the status word instead of faulting).  The product library exports
+none of the hooks and carries none of the checks."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -34,11 +35,6 @@ def sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _has_test_hooks(src: str) -> bool:
-    with open(os.path.join(CSRC, src), encoding="utf-8") as f:
-        return "TDK_TESTING" in f.read()
-
-
 def _deps_mtime() -> float:
     t = os.path.getmtime(os.path.abspath(__file__))
     for d in (CSRC, os.path.join(HERE, "..", "include")):
@@ -58,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     def one(job):
         src, testing = job
         obj = os.path.join(BUILD, src[:-3] + (".test.o" if testing else ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, *(["-DTDK_TESTING"] if testing else []), "-c",
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, *(["-DTDK_TESTING", "-DTDK_CHECKED"] if testing else []), "-c",
                os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,12 +64,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return obj
 
     srcs = sources()
-    hooked = [s for s in srcs if _has_test_hooks(s)]
-    jobs = [(s, False) for s in srcs] + [(s, True) for s in hooked]
-    with cf.ThreadPoolExecutor(max_workers=min(12, os.cpu_count() or 4)) as ex:
+    jobs = [(s, False) for s in srcs] + [(s, True) for s in srcs]
+    with cf.ThreadPoolExecutor(max_workers=min(24, os.cpu_count() or 4)) as ex:
         objs = dict(zip(jobs, ex.map(one, jobs)))
     for path, testing in ((LIB, False), (TEST_LIB, True)):
-        parts = [objs[(s, testing and s in hooked)] for s in srcs]
+        parts = [objs[(s, testing)] for s in srcs]
         tmp = path + ".tmp"
         r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *parts, *LINK], capture_output=True, text=True)
         if r.returncode != 0:

@@ -936,3 +936,7 @@ int als_run(tdk_ctx* ctx, const Geom& g, int dtype, const void* G, const double*
 }
 
 }  // namespace tdk
+
+namespace tdk {
+TDK_CHECKED_UNIT(als)
+}  // namespace tdk

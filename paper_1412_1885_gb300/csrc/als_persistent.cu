@@ -453,7 +453,8 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             rem /= a.Rt[p];
           }
           const T* src = Gi + off;
-          for (int l = tid & 31; l < Rl; l += 32) slice[a1 * Rl + l] = src[l * sl];
+          for (int l = tid & 31; l < Rl; l += 32)
+            slice[a1 * Rl + l] = TDK_IN((int64_t)i * a.stride[n] + off + l * sl, a.gnumel) ? src[l * sl] : T(0);
         }
         __syncthreads();
         // work[a1, r] = sum_l S[a1, l] B_last[l, r] in 4 x 4 register tiles
@@ -513,17 +514,20 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         }
         if (Pn == 1) {
           for (int r = tid; r < R; r += NTP) {
-            a.H[(int64_t)i * R + r] = in[r];
+            if (TDK_IN((int64_t)i * R + r, (int64_t)Rn * R)) a.H[(int64_t)i * R + r] = in[r];
             xrow[r] = (double)in[r];
           }
           __syncthreads();
           if (!a.nonneg) {
             solve_row();
             __syncthreads();
-            for (int r = tid; r < R; r += NTP) a.Bnew[(int64_t)i * R + r] = (T)xrow[r];
+            for (int r = tid; r < R; r += NTP)
+              if (TDK_IN((int64_t)i * R + r, (int64_t)Rn * R)) a.Bnew[(int64_t)i * R + r] = (T)xrow[r];
           }
         } else {
-          for (int r = tid; r < R; r += NTP) a.Hpart[((int64_t)part * Rn + i) * R + r] = in[r];
+          for (int r = tid; r < R; r += NTP)
+            if (TDK_IN(((int64_t)part * Rn + i) * R + r, (int64_t)gridDim.x * R))
+              a.Hpart[((int64_t)part * Rn + i) * R + r] = in[r];
         }
         __syncthreads();
       }
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             for (int r = tid; r < R; r += NTP) {
               double x = xrow[r];
               if (a.l1 > 0.0) x = copysign(fmax(fabs(x) - a.l1, 0.0), x);
-              a.Bnew[i * R + r] = (T)(a.clip ? fmax(x, 0.0) : x);
+              if (TDK_IN(i * R + r, a.I[n] * R)) a.Bnew[i * R + r] = (T)(a.clip ? fmax(x, 0.0) : x);
             }
           } else {
             // from the current iterate of the row, A_n[i, :] diag(lambda) (FP64)
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
               for (int r = tid; r < R; r += NTP) {
                 double d = 0.0;
                 for (int q = 0; q < R; ++q) d = fma(hrow[q], Tm[q * R + r], d);
-                a.Bnew[i * R + r] = (T)(d > 0.0 ? hrow[r] * fmax(xrow[r], 0.0) / d : 0.0);
+                if (TDK_IN(i * R + r, a.I[n] * R)) a.Bnew[i * R + r] = (T)(d > 0.0 ? hrow[r] * fmax(xrow[r], 0.0) / d : 0.0);
               }
             } else {
               // HALS, column by column: a_r <- P_+(a_r + (m_r - a t_r) / t_rr), one warp
@@ -591,7 +595,8 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
                 }
               }
               __syncthreads();
-              for (int r = tid; r < R; r += NTP) a.Bnew[i * R + r] = (T)hrow[r];
+              for (int r = tid; r < R; r += NTP)
+                if (TDK_IN(i * R + r, a.I[n] * R)) a.Bnew[i * R + r] = (T)hrow[r];
             }
           }
           __syncthreads();
@@ -1468,4 +1473,8 @@ template int als_persistent_t<double>(tdk_ctx*, const Geom&, const double*, cons
                                       const tdk_als_opts*, double* const[], double* const[], double*,
                                       tdk_als_report*);
 
+}  // namespace tdk
+
+namespace tdk {
+TDK_CHECKED_UNIT(als_persistent)
 }  // namespace tdk

@@ -119,6 +119,67 @@ static int sketch_pass(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc,
 
 }  // namespace tdk
 
+#ifdef TDK_CHECKED
+namespace tdk {
+// the check words of every translation unit (checked build)
+int tdk_chk_take_als(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_als_persistent(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_api(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_cholqr(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_core_simt(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_mlp(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_mlp_gemm(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_refine(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_rng(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_sketch_simt(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_tc_core(cudaStream_t, unsigned*, unsigned*);
+int tdk_chk_take_tc_sketch(cudaStream_t, unsigned*, unsigned*);
+
+// OR of every unit's bounds-check word; the first failure of each unit is
+// reported on stderr with its source line
+static unsigned checked_take_all(cudaStream_t s) {
+  struct Unit {
+    const char* name;
+    int (*take)(cudaStream_t, unsigned*, unsigned*);
+  };
+  static const Unit units[] = {{"als.cu", tdk_chk_take_als},
+                               {"als_persistent.cu", tdk_chk_take_als_persistent},
+                               {"api.cu", tdk_chk_take_api},
+                               {"cholqr.cu", tdk_chk_take_cholqr},
+                               {"core_simt.cu", tdk_chk_take_core_simt},
+                               {"mlp.cu", tdk_chk_take_mlp},
+                               {"mlp_gemm.cu", tdk_chk_take_mlp_gemm},
+                               {"refine.cu", tdk_chk_take_refine},
+                               {"rng.cu", tdk_chk_take_rng},
+                               {"sketch_simt.cu", tdk_chk_take_sketch_simt},
+                               {"tc_core.cu", tdk_chk_take_tc_core},
+                               {"tc_sketch.cu", tdk_chk_take_tc_sketch}};
+  unsigned any = 0;
+  for (const Unit& u : units) {
+    unsigned w = 0, l = 0;
+    if (u.take(s, &w, &l) != 0) continue;
+    if (w) {
+      fprintf(stderr, "tdk: bounds check failed in %s, line %u\n", u.name, l);
+      any = TDK_STATUS_OOB;
+    }
+  }
+  return any;
+}
+}  // namespace tdk
+#endif
+
+#ifdef TDK_TESTING
+namespace tdk {
+namespace {
+// one store guarded by the checked build's bounds check: index outside
+// [0, n) is reported and skipped, never performed
+__global__ void checked_store_kernel(int* buf, long long index, long long n) {
+  if (TDK_IN(index, n)) buf[index] = 1;
+}
+}  // namespace
+}  // namespace tdk
+#endif
+
 using namespace tdk;
 
 extern "C" {
@@ -205,6 +266,9 @@ int tdk_ctx_sync_status(tdk_ctx* c, int* flags_out) {
   TDK_CUDA_TRY(cudaStreamSynchronize(c->stream));
   TDK_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
   TDK_CUDA_TRY(cudaStreamSynchronize(c->stream));
+#ifdef TDK_CHECKED
+  h |= checked_take_all(c->stream);
+#endif
   if (flags_out) *flags_out = (int)h;
   return TDK_OK;
 }
@@ -264,6 +328,23 @@ int tdk_ctx_profile_read(tdk_ctx* c, int region, double* total_ms, int64_t* laun
 size_t tdk_ctx_workspace_bytes(const tdk_ctx* c) { return c ? c->ws_size : 0; }
 
 #ifdef TDK_TESTING
+// test library only: exercise the bounds-check reporting with one guarded
+// store into a fresh n-element buffer (index outside it sets the OOB bit)
+int tdk_test_checked_store(tdk_ctx* c, long long index, long long n) {
+  if (!c || n < 1 || n > (1 << 20)) return TDK_EINVAL;
+  cudaSetDevice(c->device);
+  int* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, sizeof(int) * (size_t)n, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TDK_ENOMEM;
+  }
+  tdk::checked_store_kernel<<<1, 1, 0, c->stream>>>(buf, index, n);
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(buf, c->stream);
+  c->launches++;
+  return e == cudaSuccess ? TDK_OK : TDK_ECUDA;
+}
+
 // test library only (not in the public header): make the n-th workspace
 // growth fail (after = 0: the next one; -1: none)
 int tdk_ctx_test_fail_alloc(tdk_ctx* c, int after) {
@@ -479,3 +560,7 @@ int ffcp_als(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* G, const dou
 }
 
 }  // extern "C"
+
+namespace tdk {
+TDK_CHECKED_UNIT(api)
+}  // namespace tdk

@@ -41,7 +41,8 @@ __global__ void gram_partial_kernel(const double* __restrict__ Z, QRArgs q, doub
   const int rows = (int)((I - r0) < GRAM_ROWS ? (I - r0) : GRAM_ROWS);
   __shared__ double Zs[GRAM_ROWS * TDK_MAX_RANK];  // 32 KB
   const double* Zn = Z + q.zoff[n];
-  for (int e = threadIdx.x; e < rows * Rt; e += blockDim.x) Zs[e] = Zn[r0 * Rt + e];
+  for (int e = threadIdx.x; e < rows * Rt; e += blockDim.x)
+    Zs[e] = TDK_IN(r0 * Rt + e, I * Rt) ? Zn[r0 * Rt + e] : 0.0;
   __syncthreads();
   double* out = gp + q.gp_off[n] + (int64_t)blockIdx.x * Rt * Rt;
   for (int e = threadIdx.x; e < Rt * Rt; e += blockDim.x) {
@@ -184,7 +185,7 @@ __global__ void apply_rinv_kernel(const double* __restrict__ Z, QRArgs q, const 
     }
     double s = 0.0;
     for (int a = 0; a <= b; ++a) s = fma(Zn[i * Rt + a], Ri[a * Rt + b], s);
-    Qn[e] = s;
+    if (TDK_IN(i * Rt + b, I * Rt)) Qn[e] = s;
   }
 }
 
@@ -395,4 +396,8 @@ int cholqr2(tdk_ctx* ctx, const Geom& g, const double* Z, double* const U_out[])
   return TDK_OK;
 }
 
+}  // namespace tdk
+
+namespace tdk {
+TDK_CHECKED_UNIT(cholqr)
 }  // namespace tdk

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(NT) ttm_mid_kernel(const TX* __restrict__ X, i
     for (int e = t; e < 32 * 64; e += NT) {
       int ii = e / 64, c = e % 64;
       int64_t i = i0 + ii;
-      Xs[e] = (i < k1 && b0 + c < Bd) ? CvtIn<T>::cvt(Xa[i * Bd + b0 + c]) : T(0);
+      Xs[e] = (i < k1 && b0 + c < Bd && TDK_IN(a * Ic * Bd + i * Bd + b0 + c, (int64_t)gridDim.x * Ic * Bd))
+                  ? CvtIn<T>::cvt(Xa[i * Bd + b0 + c])
+                  : T(0);
       Us[e] = (i < k1 && c < Rt) ? U[i * Rt + c] : T(0);
     }
     __syncthreads();
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(NT) ttm_mid_kernel(const TX* __restrict__ X, i
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int64_t b = b0 + tb + 16 * q;
-      if (b < Bd) Xoa[(int64_t)r * Bd + b] = acc[p][q];
+      if (b < Bd && TDK_IN((a * Rt + r) * Bd + b, (int64_t)gridDim.x * Rt * Bd)) Xoa[(int64_t)r * Bd + b] = acc[p][q];
     }
   }
   }
@@ -177,7 +179,9 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
       const int64_t i = i0 + j;
-      rx[j] = (i < k1 && bok) ? __ldg(Xa + i * Bd + b0 + t) : 0.f;
+      rx[j] = (i < k1 && bok && TDK_IN(a * Ic * Bd + i * Bd + b0 + t, (int64_t)gridDim.x * Ic * Bd))
+                  ? __ldg(Xa + i * Bd + b0 + t)
+                  : 0.f;
       ru[j] = (i < k1 && rok) ? __ldg(U + i * Rt + t) : 0.f;
     }
   };
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int64_t b = b0 + ((q < 4) ? tx * 4 + q : 32 + tx * 4 + (q - 4));
-      if (b < Bd) Xoa[(int64_t)r * Bd + b] = acc[p][q];
+      if (b < Bd && TDK_IN((a * Rt + r) * Bd + b, (int64_t)gridDim.x * Rt * Bd)) Xoa[(int64_t)r * Bd + b] = acc[p][q];
     }
   }
   __syncthreads();  // the next tile refills the shared buffers
@@ -267,7 +271,8 @@ __global__ void __launch_bounds__(256) ttm_mid32_kernel(const float* __restrict_
   if (b < Bd)
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (r0 + u < Rt) Xoa[(int64_t)(r0 + u) * Bd + b] = acc[u];
+      if (r0 + u < Rt && TDK_IN((a * Rt + r0 + u) * Bd + b, (int64_t)gridDim.x * Rt * Bd))
+        Xoa[(int64_t)(r0 + u) * Bd + b] = acc[u];
 }
 
 // fixed-order sum of the KS partial outputs of a split contraction
@@ -502,4 +507,8 @@ int core_simt(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   return TDK_EINVAL;
 }
 
+}  // namespace tdk
+
+namespace tdk {
+TDK_CHECKED_UNIT(core_simt)
 }  // namespace tdk

@@ -36,6 +36,8 @@ struct tdk_mlp {
   __nv_bfloat16 *Xb, *H1, *H2, *dO, *dZ2, *dZ1;
   float *Xs, *Z1, *Z2, *O, *V, *T;
   double *nrm, *lpart, *cs;
+  double* gsq;    // per-block partial sums of the squared gradient
+  float* gscale;  // the clipping factor of the last step
   int* Rdev;
   int last_batch;
 };
@@ -394,12 +396,37 @@ __global__ void refresh_kernel(const float* __restrict__ theta, Segs sg) {
 }
 
 // Adam (Kingma and Ba, Algorithm 1) on the FP32 master parameters
+constexpr int GN_BLOCKS = 256;  // blocks of the gradient-norm reduction
+
+// squared gradient norm: one FP64 partial per block, summed in a fixed order
+__global__ void gradsq_kernel(const float* __restrict__ g, int64_t n, double* __restrict__ parts) {
+  __shared__ double red[CT / 32];
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = g[e];
+    s = fma(x, x, s);
+  }
+  s = blk_sum_d(s, red);
+  if (threadIdx.x == 0) parts[blockIdx.x] = s;
+}
+
+// clipping factor min(1, clip / ||g||)
+__global__ void clip_scale_kernel(const double* __restrict__ parts, int nparts, double clip, float* __restrict__ scale) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < nparts; ++i) s += parts[i];
+  const double nrm = sqrt(s);
+  *scale = (float)(nrm > clip ? clip / nrm : 1.0);
+}
+
+// gscale: null, or the clipping factor applied to the gradient first
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, Segs sg, float lr, float b1, float b2, float eps,
-                            float bc1, float bc2) {
+                            float bc1, float bc2, const float* __restrict__ gscale) {
+  const float sc = gscale ? *gscale : 1.f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.off[6];
        e += (int64_t)gridDim.x * blockDim.x) {
-    const float ge = g[e];
+    const float ge = g[e] * sc;
     const float me = b1 * m[e] + (1.f - b1) * ge;
     const float ve = b2 * v[e] + (1.f - b2) * ge * ge;
     m[e] = me;
@@ -651,6 +678,8 @@ int tdk_mlp_create(tdk_ctx* ctx, const tdk_mlp_desc* d, tdk_mlp** out) {
   for (int i = 0; i < 2; ++i) pl.take<double>((size_t)Bt);
   pl.take<double>((size_t)m->N * m->Rt);
   pl.take<int>((size_t)Bt);
+  pl.take<double>((size_t)GN_BLOCKS);
+  pl.take<float>(1);
   if (cudaMalloc(&m->block, pl.off) != cudaSuccess) {
     cudaGetLastError();
     delete m;
@@ -680,6 +709,8 @@ int tdk_mlp_create(tdk_ctx* ctx, const tdk_mlp_desc* d, tdk_mlp** out) {
   m->lpart = cv.take<double>((size_t)Bt);
   m->cs = cv.take<double>((size_t)m->N * m->Rt);
   m->Rdev = cv.take<int>((size_t)Bt);
+  m->gsq = cv.take<double>((size_t)GN_BLOCKS);
+  m->gscale = cv.take<float>(1);
   if (cudaMemsetAsync(m->block, 0, pl.off, ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -836,7 +867,7 @@ int tdk_mlp_train_step(tdk_ctx* ctx, tdk_mlp* m, int batch, const float* G, cons
   if (!ctx || !m || !G || !colsums || !R || !o) return TDK_EINVAL;
   if (batch < 1 || batch > m->max_batch) return TDK_EINVAL;
   if (!(o->lr >= 0.0) || !(o->beta1 >= 0.0 && o->beta1 < 1.0) || !(o->beta2 >= 0.0 && o->beta2 < 1.0) ||
-      !(o->eps > 0.0))
+      !(o->eps > 0.0) || !(o->clip >= 0.0))
     return TDK_EINVAL;
   cudaSetDevice(ctx->device);
   int rc = run_canon(ctx, m, batch, G, 0, colsums, Bstar, lambda, R);
@@ -857,9 +888,17 @@ int tdk_mlp_train_step(tdk_ctx* ctx, tdk_mlp* m, int batch, const float* G, cons
   if (o->update) {
     m->step++;
     const double bc1 = 1.0 - std::pow(o->beta1, (double)m->step), bc2 = 1.0 - std::pow(o->beta2, (double)m->step);
+    const float* gsc = nullptr;
+    if (o->clip > 0.0) {
+      gradsq_kernel<<<GN_BLOCKS, CT, 0, ctx->stream>>>(m->grad, m->P, m->gsq);
+      TDK_LAUNCH_CHECK(ctx);
+      clip_scale_kernel<<<1, 32, 0, ctx->stream>>>(m->gsq, GN_BLOCKS, o->clip, m->gscale);
+      TDK_LAUNCH_CHECK(ctx);
+      gsc = m->gscale;
+    }
     adam_kernel<<<4 * ctx->num_sms, 256, 0, ctx->stream>>>(m->theta, m->m, m->v, m->grad, segs_of(m), (float)o->lr,
                                                            (float)o->beta1, (float)o->beta2, (float)o->eps,
-                                                           (float)bc1, (float)bc2);
+                                                           (float)bc1, (float)bc2, gsc);
     TDK_LAUNCH_CHECK(ctx);
   }
   if (loss_out) {
@@ -897,3 +936,7 @@ int ffcp_predict_init(tdk_ctx* ctx, tdk_mlp* m, const tdk_tucker_desc* desc, con
 }
 
 }  // extern "C"
+
+namespace tdk {
+TDK_CHECKED_UNIT(mlp)
+}  // namespace tdk

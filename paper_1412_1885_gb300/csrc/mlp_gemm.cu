@@ -141,6 +141,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int j = 0; j < 16; ++j) {
           const int col = nb + j;
           if (col >= a.N) break;
+          // a column past a leading dimension would land in the next row
+          if (!TDK_IN(col, (a.mode == GEMM_GELU_GRAD) ? a.ldb : a.ldf)) break;
+          if (a.mode == GEMM_BIAS_GELU && !TDK_IN(col, a.ldb)) break;
           float x = v[j];
           switch (a.mode) {
             case GEMM_STORE_F32:
@@ -248,3 +251,7 @@ extern "C" int tdk_test_gemm_bf16(tdk_ctx* ctx, int M, int N, int K, const void*
   return gemm_bf16(ctx, op);
 }
 #endif  // TDK_TESTING
+
+namespace tdk {
+TDK_CHECKED_UNIT(mlp_gemm)
+}  // namespace tdk

@@ -331,3 +331,7 @@ int seq_tucker(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc, const v
 }
 
 }  // namespace tdk
+
+namespace tdk {
+TDK_CHECKED_UNIT(refine)
+}  // namespace tdk

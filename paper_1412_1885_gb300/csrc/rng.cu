@@ -124,3 +124,7 @@ extern "C" int tdk_sketch_matrices(tdk_ctx* ctx, const tdk_tucker_desc* desc, do
   for (int n = 0; n < g.N; ++n) rows[n] = g.I[n];
   return draw_sketch_matrices(ctx, g.N, rows, row0, g.Rt, desc->seed, W_out);
 }
+
+namespace tdk {
+TDK_CHECKED_UNIT(rng)
+}  // namespace tdk

@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(NT) sketch_simt_kernel(const TY* __restrict__ 
         decode_row<T>(row, a, idx);
         v = T(1);
         for (int k = 0; k < N - 1; ++k)
-          v *= reinterpret_cast<const T*>(a.Wk[last][k])[(int64_t)idx[k] * a.RtL + r];
+          v *= TDK_IN(idx[k], a.I[k]) ? reinterpret_cast<const T*>(a.Wk[last][k])[(int64_t)idx[k] * a.RtL + r]
+                                      : T(0);
       }
       Ks[e] = v;
     }
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(NT) sketch_simt_kernel(const TY* __restrict__ 
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             int r = rg + 8 * j;
-            if (r < a.RtL) zlast[col * a.RtL + r] += accL[j];
+            if (r < a.RtL && TDK_IN(col * a.RtL + r, a.L * a.RtL)) zlast[col * a.RtL + r] += accL[j];
           }
         }
       }
@@ -163,13 +164,15 @@ __global__ void __launch_bounds__(NT) sketch_simt_kernel(const TY* __restrict__ 
       for (int rr = 0; rr < rows; ++rr) {
         T coef = T(1);
         for (int k = 0; k < N - 1; ++k)
-          if (k != n) coef *= reinterpret_cast<const T*>(a.Wk[n][k])[(int64_t)idx[k] * Rn + r];
+          if (k != n)
+            coef *= TDK_IN(idx[k], a.I[k]) ? reinterpret_cast<const T*>(a.Wk[n][k])[(int64_t)idx[k] * Rn + r] : T(0);
         T v = Pst[rr * a.C1p + c] * coef;
         if (n == N - 2) {
-          zn[(int64_t)idx[n] * Rn + r] += v;  // changes every row: update in place
+          // changes every row: update in place
+          if (TDK_IN((int64_t)idx[n] * Rn + r, a.zoff[n + 1] - a.zoff[n])) zn[(int64_t)idx[n] * Rn + r] += v;
         } else {
           if (idx[n] != cur) {
-            zn[(int64_t)cur * Rn + r] += run;
+            if (TDK_IN((int64_t)cur * Rn + r, a.zoff[n + 1] - a.zoff[n])) zn[(int64_t)cur * Rn + r] += run;
             run = T(0);
             cur = idx[n];
           }
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(NT) sketch_simt_kernel(const TY* __restrict__ 
           idx[k] = 0;
         }
       }
-      if (n != N - 2) zn[(int64_t)cur * Rn + r] += run;
+      if (n != N - 2 && TDK_IN((int64_t)cur * Rn + r, a.zoff[n + 1] - a.zoff[n])) zn[(int64_t)cur * Rn + r] += run;
     }
     __syncthreads();
   }
@@ -598,3 +601,7 @@ extern "C" int tucker_sketch_static(tdk_ctx* ctx, const tdk_tucker_desc* desc, c
   }
   return TDK_EINVAL;
 }
+
+namespace tdk {
+TDK_CHECKED_UNIT(sketch_simt)
+}  // namespace tdk

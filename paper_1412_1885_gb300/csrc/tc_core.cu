@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
           float* xr = a.X + row * a.Rt;
 #pragma unroll
           for (int r = 0; r < 64; ++r) {
-            if (r < a.Rt) {
+            if (r < a.Rt && TDK_IN(row * a.Rt + r, a.M * a.Rt)) {
               float x = v[r];
               if (a.hilo) {
 #pragma unroll
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(LD_THREADS, 1)
 #pragma unroll
               for (int h = 16; h <= 64; h += 16)
                 if (a.Rtp == h) x += v[h + r];
-              a.X[(int64_t)r * a.B + b] = x;
+              if (TDK_IN((int64_t)r * a.B + b, (int64_t)a.Rt * a.B)) a.X[(int64_t)r * a.B + b] = x;
             }
           }
         }
@@ -676,10 +676,11 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         if (!mbar_wait(smem_u32(sfull), fu & 1, status)) return false;
         const float* sr = scr + rl * FU_SCR_LD;
         if (rl < a.Rt2) {
-          float* out = a.X2 + ((int64_t)fp * a.Rt2 + rl) * a.Rt;
+          const int64_t o = ((int64_t)fp * a.Rt2 + rl) * a.Rt;
+          float* out = a.X2 + o;
 #pragma unroll
           for (int r = 0; r < 64; ++r)
-            if (r < a.Rt) out[r] = y[r] + sr[r];
+            if (r < a.Rt && TDK_IN(o + r, (int64_t)a.P * a.Rt2 * a.Rt)) out[r] = y[r] + sr[r];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(sempty));
@@ -1110,4 +1111,8 @@ int ttm_lead_tc(tdk_ctx* ctx, const Geom& g, const void* Y, const double* U1, fl
   return TDK_OK;
 }
 
+}  // namespace tdk
+
+namespace tdk {
+TDK_CHECKED_UNIT(tc_core)
 }  // namespace tdk

@@ -546,7 +546,8 @@ __global__ void __launch_bounds__(320, 1)
           const int Rm = a.Rt[m];
           if (jl < CH && cg + jl < Rm) {
             const float s = rg[jl] + rg[64 + jl] + rg[128 + jl] + rg[192 + jl];
-            up[a.poff_p[m] + (p - p0) * Rm + cg + jl] = s * cb[128 + 64 * m + cg + jl];
+            const int64_t o = a.poff_p[m] + (p - p0) * Rm + cg + jl;
+            if (TDK_IN(o, a.ustride)) up[o] = s * cb[128 + 64 * m + cg + jl];
           }
           named_bar(1, NE);
         }
@@ -563,7 +564,8 @@ __global__ void __launch_bounds__(320, 1)
       if (vj) {
 #pragma unroll
         for (int r = 0; r < CH; ++r)
-          if (cg + r < Rj) up[a.poff_j + (int64_t)jl * Rj + cg + r] = accj[r];
+          if (cg + r < Rj && TDK_IN(a.poff_j + (int64_t)jl * Rj + cg + r, a.ustride))
+            up[a.poff_j + (int64_t)jl * Rj + cg + r] = accj[r];
       }
       if (!mbar_wait(smem_u32(d2full), un & 1, status)) { ok = false; break; }
       tc_fence_after();
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(320, 1)
           float* dst = up + a.poff_last + (int64_t)kloc * a.RtL;
 #pragma unroll
           for (int r = 0; r < 64; ++r) {
-            if (r < a.RtL) {
+            if (r < a.RtL && TDK_IN(a.poff_last + (int64_t)kloc * a.RtL + r, a.ustride)) {
               float z = v[r];
               if (a.hilo && r < 32) z += v[32 + (r & 31)];
               dst[r] = z;
@@ -1017,7 +1019,8 @@ __global__ void __launch_bounds__(384, 1)
         if (have3) coef_store(pi + 3, cr2);
         named_bar(1, NE);
         if (dotrole && grp == 0)
-          up[a.poff_p[lm] + (p - p0) * a.Rt[lm] + lr] = (dot + rb[c]) * cb[128 + 64 * lm + lr];
+          if (TDK_IN(a.poff_p[lm] + (p - p0) * a.Rt[lm] + lr, a.ustride))
+            up[a.poff_p[lm] + (p - p0) * a.Rt[lm] + lr] = (dot + rb[c]) * cb[128 + 64 * lm + lr];
         pmark(12);  // tail barrier and the partial store
       }
       if (!ok) break;
@@ -1025,7 +1028,8 @@ __global__ void __launch_bounds__(384, 1)
       if (rowrole) {
 #pragma unroll
         for (int jj = 0; jj < 64; ++jj)
-          if (j0 + jh + jj < a.J) up[a.poff_j + (int64_t)(jh + jj) * Rj + lr] = aw[jj];
+          if (j0 + jh + jj < a.J && TDK_IN(a.poff_j + (int64_t)(jh + jj) * Rj + lr, a.ustride))
+            up[a.poff_j + (int64_t)(jh + jj) * Rj + lr] = aw[jj];
       }
       if (!mbar_wait(smem_u32(d2full), un & 1, status)) { ok = false; break; }
       tc_fence_after();
@@ -1039,7 +1043,7 @@ __global__ void __launch_bounds__(384, 1)
           float* dst = up + a.poff_last + (int64_t)kloc * a.RtL;
 #pragma unroll
           for (int r = 0; r < 64; ++r)
-            if (r < a.RtL) dst[r] = v[r];
+            if (r < a.RtL && TDK_IN(a.poff_last + (int64_t)kloc * a.RtL + r, a.ustride)) dst[r] = v[r];
         }
       }
       tc_fence_before();
@@ -1138,13 +1142,17 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
       cmp = (t - s) - y;
       s = t;
     };
+    // one unit's partial entry (the checked build tests the unit and the offset)
+    auto part_at = [&](int64_t u, int64_t off) -> float {
+      return (TDK_IN(u, a.nunits) && TDK_IN(off, a.ustride)) ? a.part[u * a.ustride + off] : 0.f;
+    };
     if (n == nl) {
       const int kr = (int)(i / a.KRW);
       const int64_t kl = i - (int64_t)kr * a.KRW;
       for (int jt = 0; jt < a.JT; ++jt)
         for (int pc = 0; pc < a.PC; ++pc) {
           const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
-          add(a.part[u * a.ustride + a.poff_last + kl * Rn + r]);
+          add(part_at(u, a.poff_last + kl * Rn + r));
         }
     } else if (n == nj) {
       const int jt = (int)(i / 128);
@@ -1152,7 +1160,7 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
       for (int kr = 0; kr < a.KR; ++kr)
         for (int pc = 0; pc < a.PC; ++pc) {
           const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
-          add(a.part[u * a.ustride + a.poff_j + jl * Rn + r]);
+          add(part_at(u, a.poff_j + jl * Rn + r));
         }
     } else {
       // every p with i_n(p) = i: enumerate the other outer indices
@@ -1169,7 +1177,7 @@ __global__ void sketch_tc_reduce(RedArgs ra, double* __restrict__ Z) {
         for (int jt = 0; jt < a.JT; ++jt)
           for (int kr = 0; kr < a.KR; ++kr) {
             const int64_t u = ((int64_t)jt * a.KR + kr) * a.PC + pc;
-            add(a.part[u * a.ustride + a.poff_p[n] + pl * Rn + r]);
+            add(part_at(u, a.poff_p[n] + pl * Rn + r));
           }
       }
     }
@@ -1548,3 +1556,7 @@ extern "C" int tdk_test_bounded_wait(tdk_ctx* ctx, unsigned long long limit_ns) 
   return TDK_OK;
 }
 #endif  // TDK_TESTING
+
+namespace tdk {
+TDK_CHECKED_UNIT(tc_sketch)
+}  // namespace tdk

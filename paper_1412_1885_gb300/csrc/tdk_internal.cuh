@@ -13,6 +13,48 @@
 
 #define TDK_STATUS_RANKDEF 1u
 #define TDK_STATUS_TIMEOUT 256u
+#define TDK_STATUS_OOB 512u  // checked build: a bounds check failed
+
+// ---- bounds checks of the checked build ----------------------------------
+// The test library is compiled with -DTDK_CHECKED.  TDK_IN(i, n) tests
+// 0 <= i < n; a failure sets this translation unit's check word (and keeps
+// the first failing source line) instead of faulting, and the caller skips
+// the access.  tdk_ctx_sync_status collects the words of every unit into
+// TDK_STATUS_OOB.  The product build compiles every check to `true`.
+#ifdef TDK_CHECKED
+namespace tdk_chk {
+namespace {
+__device__ unsigned word_;
+__device__ unsigned line_;
+__device__ __forceinline__ bool in_range(long long i, long long n, unsigned ln) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&word_, 1u);
+  atomicCAS(&line_, 0u, ln);
+  return false;
+}
+// host: this unit's word and first failing line, read and cleared on a stream
+inline int take(cudaStream_t s, unsigned* w, unsigned* l) {
+  unsigned v[2] = {0u, 0u};
+  const unsigned z = 0u;
+  if (cudaMemcpyFromSymbolAsync(&v[0], word_, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyFromSymbolAsync(&v[1], line_, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(word_, &z, sizeof(unsigned), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(line_, &z, sizeof(unsigned), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  *w = v[0];
+  *l = v[1];
+  return 0;
+}
+}  // namespace
+}  // namespace tdk_chk
+#define TDK_IN(i, n) tdk_chk::in_range((long long)(i), (long long)(n), (unsigned)__LINE__)
+#define TDK_CHECKED_UNIT(name) \
+  int tdk_chk_take_##name(cudaStream_t s, unsigned* w, unsigned* l) { return tdk_chk::take(s, w, l); }
+#else
+#define TDK_IN(i, n) true
+#define TDK_CHECKED_UNIT(name)
+#endif
 
 struct tdk_ctx {
   int device = 0;

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import F64, Context, Mlp, _dtype_code, ffcp_als, tucker_core, tucker_sketch
+from . import F64, MLP_PARAMS, Context, Mlp, _dtype_code, ffcp_als, tucker_core, tucker_sketch
 
 
 @dataclass
@@ -77,10 +77,12 @@ def stack(items) -> Samples:
 
 
 def train(model: Mlp, data: Samples, epochs: int, batch: int, lr: float = 1e-3, alpha: float = 0.5,
-          seed: int = 0, lr_final: float | None = None, warmup: float = 0.05):
+          seed: int = 0, lr_final: float | None = None, warmup: float = 0.05, clip: float = 1.0):
     """Adam over shuffled mini-batches; the step size rises linearly over the
     first `warmup` fraction of the steps, then decays linearly to lr_final
-    (default lr / 10).  Returns the mean loss of every epoch."""
+    (default lr / 10); every step's gradient is clipped to a global norm of
+    `clip` (0: no clipping).  The parameters of the epoch with the lowest
+    mean loss are kept.  Returns the mean loss of every epoch."""
     import torch
 
     n = int(data.G.shape[0])
@@ -88,6 +90,7 @@ def train(model: Mlp, data: Samples, epochs: int, batch: int, lr: float = 1e-3, 
     steps = epochs * max(1, n // batch)
     lr_final = lr / 10 if lr_final is None else lr_final
     hist, k = [], 0
+    best, best_params = None, None
     for _ in range(epochs):
         perm = torch.as_tensor(rng.permutation(n), device=data.G.device)
         tot, cnt = 0.0, 0
@@ -100,8 +103,12 @@ def train(model: Mlp, data: Samples, epochs: int, batch: int, lr: float = 1e-3, 
                 step_lr = lr + (lr_final - lr) * (k - nw) / max(1, steps - nw - 1)
             tot += model.train_step(data.G[idx].contiguous(), data.colsums[idx].contiguous(), data.R[idx].contiguous(),
                                     data.Bstar[idx].contiguous(), alpha=alpha, lr=step_lr,
-                                    lam=data.lam[idx].contiguous())
+                                    lam=data.lam[idx].contiguous(), clip=clip)
             cnt += 1
             k += 1
         hist.append(tot / max(cnt, 1))
+        if np.isfinite(hist[-1]) and (best is None or hist[-1] < best):
+            best, best_params = hist[-1], model.get(MLP_PARAMS)
+    if best_params is not None:
+        model.set_params(best_params)
     return hist

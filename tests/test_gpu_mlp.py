@@ -202,6 +202,34 @@ def test_adam_step_matches_oracle(tdk, ctx):
     m.close()
 
 
+def test_adam_step_with_gradient_clipping_matches_oracle(tdk, ctx):
+    """clip > 0: the Adam step takes the gradient scaled to the cap
+    (oracle.mlp.clip_grad); the stored gradient stays unscaled.  Two steps,
+    since the first Adam step is nearly invariant to the gradient's scale."""
+    N, Rt, hidden, batch = 3, 6, 32, 20
+    G, cs, R, Bs = _problem(batch, N, Rt, 33)
+    theta = synth.mlp_init_params(N, Rt, hidden, 5)
+    m = tdk.Mlp(ctx, N, Rt, hidden, max_batch=32)
+    m.set_params(theta)
+    Gd, csd, Rd, Bd = _dev_batch(G, cs, R, Bs)
+    m.train_step(Gd, csd, Rd, None, lr=1e-3, update=True)          # step 1, unclipped
+    g1 = m.get(tdk.MLP_GRADS).astype(np.float64)
+    m.train_step(Gd, csd, Rd, None, lr=1e-3, update=False)         # the gradient at the new point
+    g2 = m.get(tdk.MLP_GRADS).astype(np.float64)
+    cap = 0.25 * float(np.linalg.norm(g2))
+    m.train_step(Gd, csd, Rd, None, lr=1e-3, update=True, clip=cap)  # step 2, clipped
+    assert np.array_equal(m.get(tdk.MLP_GRADS).astype(np.float64), g2)
+    th = m.get(tdk.MLP_PARAMS).astype(np.float64)
+    z = np.zeros_like(g1)
+    t1, m1, v1 = omlp.adam_step(theta.astype(np.float64), z, z, g1, 1, 1e-3)
+    ref, _, _ = omlp.adam_step(t1, m1, v1, omlp.clip_grad(g2, cap), 2, 1e-3)
+    unclipped, _, _ = omlp.adam_step(t1, m1, v1, g2, 2, 1e-3)
+    err = np.abs(th - ref).max()
+    assert err <= 1e-6 * max(1.0, np.abs(ref).max())
+    assert np.abs(unclipped - ref).max() > 100 * err   # the clipping is visible at this tolerance
+    m.close()
+
+
 def test_predict_init_matches_oracle(tdk, ctx):
     import torch
 

@@ -892,6 +892,15 @@ def test_adam_constant_gradient_closed_form():
     assert np.abs(th - (-25 * lr * g / (np.abs(g) + eps))).max() < 1e-12
 
 
+def test_gradient_clipping_caps_the_norm_and_keeps_the_direction():
+    g = np.array([3.0, -4.0, 0.0, 12.0])          # norm 13
+    c = omlp.clip_grad(g, 6.5)
+    assert math.isclose(float(np.linalg.norm(c)), 6.5, rel_tol=1e-14)
+    assert np.allclose(c, g / 2.0, rtol=0, atol=1e-15)     # same direction, half the length
+    assert np.array_equal(omlp.clip_grad(g, 13.5), g)      # under the cap: unchanged
+    assert np.array_equal(omlp.clip_grad(g, 0.0), g)       # off
+
+
 # ---------------------------------------------------------------- seeded test matrices
 
 def test_philox_known_answer_vectors():

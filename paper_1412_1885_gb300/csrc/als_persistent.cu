@@ -202,13 +202,99 @@ struct PLayout {
 // by Gauss-Jordan elimination without pivoting, spread over a group of nt
 // threads (named barrier bar_id).  A pivot is the Schur complement a Cholesky
 // factorisation would meet, so the breakdown test (pivot not above
-// R * eps * max diag) is the same.  One barrier per pivot: the threads that
-// update row k+1 and column k+1 also copy them into the other half of `buf`
-// (4 R entries), from which pivot k+1 reads.  Returns the same value in
-// every thread of the group.
-template <class F>
-__device__ int group_gj_inverse(F* A, F* buf, int R, F eps, int t, int nt, int bar_id) {
+// R * eps * max diag) is the same.  Each thread keeps its entries
+// e = t + q nt (at most EPT of them) in registers for the whole elimination,
+// with their row and column decoded once.  Per pivot k it loads the pivot row
+// and column entries it needs from `buf` (4 R entries, two halves) before
+// any store, updates its entries, and the threads that hold row k+1 and
+// column k+1 copy them into the other half: one barrier per pivot, and the
+// loads of a step in flight together.  Returns the same value in every
+// thread of the group.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
+template <class F, int EPT>
+__device__ int gj_inverse_regs(F* A, F* buf, int R, F eps, int t, int nt, int bar_id) {
   tc::named_bar(bar_id, nt);  // `buf` may still be read by a previous call
+  F mx = F(0);
+  for (int j = 0; j < R; ++j) mx = A[j * R + j] > mx ? A[j * R + j] : mx;
+  const F tiny = (F)R * eps * mx;
+  const int RR = R * R;
+  F a[EPT];
+  int ri[EPT], ci[EPT];  // row and column of each entry; -1: none
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = t + q * nt;
+    ri[q] = e < RR ? e / R : -1;
+    ci[q] = e < RR ? e - ri[q] * R : 0;
+    a[q] = e < RR ? A[e] : F(0);
+  }
+  if (t < R) {
+    buf[t] = A[t];
+    buf[R + t] = A[t * R];
+  }
+  tc::named_bar(bar_id, nt);
+  int ok = 1;
+  for (int k = 0; k < R; ++k) {
+    const F* rowk = buf + (k & 1) * 2 * R;
+    const F* colk = rowk + R;
+    F* rown = buf + ((k + 1) & 1) * 2 * R;
+    F* coln = rown + R;
+    const F p = rowk[k];
+    if (!(p > tiny)) {
+      ok = 0;
+      break;
+    }
+    const F ip = rcp_rn(p);
+    F rv[EPT], cv[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      rv[q] = ri[q] >= 0 ? rowk[ci[q]] : F(0);
+      cv[q] = ri[q] >= 0 ? colk[ri[q]] : F(0);
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const bool rk = ri[q] == k, ck = ci[q] == k;
+      a[q] = rk ? (ck ? ip : rv[q] * ip) : (ck ? -cv[q] * ip : fma(-cv[q], rv[q] * ip, a[q]));
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (ri[q] == k + 1) rown[ci[q]] = a[q];
+      if (ri[q] >= 0 && ci[q] == k + 1) coln[ri[q]] = a[q];
+    }
+    tc::named_bar(bar_id, nt);
+  }
+  if (!ok) return 0;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (ri[q] >= 0) A[t + q * nt] = a[q];
+  tc::named_bar(bar_id, nt);
+  return 1;
+}
+
+template <class F>
+__device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, int bar_id);
+
+// entries per thread chosen by the size (R <= 64 and nt >= 256); MAXEPT caps
+// the register arrays (a kernel short of registers takes the shared-memory
+// form above it)
+template <class F, int MAXEPT = 16>
+__device__ int group_gj_inverse(F* A, F* buf, int R, F eps, int t, int nt, int bar_id) {
+  const int per = (R * R + nt - 1) / nt;
+  if (per <= 4) return gj_inverse_regs<F, 4>(A, buf, R, eps, t, nt, bar_id);
+  if (MAXEPT >= 8 && per <= 8) return gj_inverse_regs<F, (MAXEPT >= 8 ? 8 : 4)>(A, buf, R, eps, t, nt, bar_id);
+  if (MAXEPT >= 16) return gj_inverse_regs<F, (MAXEPT >= 16 ? 16 : 4)>(A, buf, R, eps, t, nt, bar_id);
+  return group_gj_inverse_smem<F>(A, buf, R, eps, t, nt, bar_id);
+}
+
+// the same elimination with the matrix kept in shared memory (every entry
+// read and written per pivot): the single-CTA kernel's form, whose small
+// matrices leave most of the register form's slots idle (51.9 against
+// 53.8 us per sweep on a 20^3 core, R = 10); the register form takes the
+// 60^3 core, R = 40, from 59k to 42k cycles per inverse
+template <class F>
+__device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, int bar_id) {
+  tc::named_bar(bar_id, nt);
   F mx = F(0);
   for (int j = 0; j < R; ++j) mx = A[j * R + j] > mx ? A[j * R + j] : mx;
   const F tiny = (F)R * eps * mx;
@@ -370,12 +456,14 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         Tid[e] = v;
       }
       __syncthreads();
+      PROF_MARK(7);
       // ---- 1b. inverse of T_n: FP32 by default (the solves are refined against
       //          T_n in FP64), FP64 if an FP32 pivot breaks down
       // (the HALS and multiplicative rules use T_n itself, not its inverse)
       bool use32 = true;
       if (!(a.nonneg && a.nn_rule != 0)) {
         use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
+        if (a.prof && !use32 && blockIdx.x == 0 && tid == 0) a.prof[9] += 1;  // FP64 inverses
         if (!use32 && !group_gj_inverse<double>(Tid, gjs, R, 2.220446049250313e-16, tid, NTP, 1)) {
           needpinv = 1;
           ok = false;  // identical in every CTA: all leave here
@@ -972,9 +1060,9 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
         // ---- invert T_n (FP32 for FP32 cores, FP64 otherwise / as fallback), warps 0-7
         const unsigned long long pt0 = clock64();
         int mode = 0;
-        if (!F64 && group_gj_inverse<float>(Lf, Lif, R, 1.1920929e-7f, tid, 256, 2)) {
+        if (!F64 && group_gj_inverse_smem<float>(Lf, Lif, R, 1.1920929e-7f, tid, 256, 2)) {
           mode = 1;
-        } else if (group_gj_inverse<double>(Ld, Lid, R, 2.220446049250313e-16, tid, 256, 2)) {
+        } else if (group_gj_inverse_smem<double>(Ld, Lid, R, 2.220446049250313e-16, tid, 256, 2)) {
           mode = 2;
         }
         if (tid == 0) {
@@ -1440,7 +1528,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
       fprintf(stderr, "tdk ALS profile (single CTA, Mcycles over %d sweeps):", hs.sweeps);
       for (int i = 0; i < 10; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
     } else {
-      const char* names[7] = {"chol", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
+      fprintf(stderr, "tdk ALS profile: T_n build=%.3f Mcycles, FP64 inverses=%llu\n", hp[7] / 1e6, hp[9]);
+      const char* names[7] = {"inverse", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
                               "barrier3", "fit"};
       fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);
       for (int i = 0; i < 7; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);

@@ -10,6 +10,13 @@
 // 64-deep K slices (128-byte swizzle, 4-stage ring), warp 1 issues the MMAs
 // into a TMEM accumulator, warps 2-5 run the fused epilogue (bias, GELU,
 // GELU derivative, BF16 / FP32 stores).  Every wait is bounded.
+// A product with few output tiles and a long K (the forward layers and the
+// input gradients at batch <= 128: 8-10 tiles) is split over K: CTA z of the
+// grid's third dimension sums its range of K slices into an FP32 partial
+// tile, and a finishing kernel adds the partials in a fixed order and applies
+// the same epilogue, so the weight stream is spread over the whole GPU.
+#include <algorithm>
+
 #include "mlp_internal.cuh"
 #include "tc_common.cuh"
 
@@ -27,6 +34,8 @@ struct GemmArgs {
   int M, N, K;
   int a_mn, b_mn;
   int mode;
+  int kper;      // K slices per CTA along the grid's third dimension
+  float* part;   // split over K: FP32 partial tiles [gridDim.z][M][N]; null: the epilogue itself
   const float* bias;
   const float* zin;
   int ldz;
@@ -62,7 +71,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-  const int KC = (a.K + TK - 1) / TK;
+  const int KCT = (a.K + TK - 1) / TK;
+  const int kc_lo = blockIdx.z * a.kper;
+  const int KC = KCT - kc_lo < a.kper ? KCT - kc_lo : a.kper;  // this CTA's slices
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
@@ -91,7 +102,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t dst = smem_u32(base + s * STAGE_BYTES);
         const uint32_t bar = smem_u32(&full[s]);
         mbar_expect_tx(bar, STAGE_BYTES);
-        const int k0 = kc * TK;
+        const int k0 = (kc_lo + kc) * TK;
         if (a.a_mn) {
           tma_load_2d(dst, &tmA, m0, k0, bar);
           tma_load_2d(dst + 8192, &tmA, m0 + 64, k0, bar);
@@ -137,6 +148,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_wait_ld();
         if (row >= a.M) continue;
         const int nb = n0 + c16 * 16;
+        if (a.part) {  // split over K: the raw partial tile
+          float* pr = a.part + ((int64_t)blockIdx.z * a.M + row) * a.N;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (nb + j < a.N) pr[nb + j] = v[j];
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = nb + j;
@@ -171,6 +189,34 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, TN);
+  }
+}
+
+// sum of the K-split partials in a fixed order, then the epilogue of the mode
+__global__ void splitk_finish_kernel(const float* __restrict__ part, int ks, GemmArgs a) {
+  const int64_t MN = (int64_t)a.M * a.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / a.N), col = (int)(e % a.N);
+    float x = 0.f;
+    for (int z = 0; z < ks; ++z) x += part[z * MN + e];
+    if (!TDK_IN(col, (a.mode == GEMM_GELU_GRAD) ? a.ldb : a.ldf)) continue;
+    if (a.mode == GEMM_BIAS_GELU && !TDK_IN(col, a.ldb)) continue;
+    switch (a.mode) {
+      case GEMM_STORE_F32:
+        a.outf[(int64_t)row * a.ldf + col] = x;
+        break;
+      case GEMM_BIAS_GELU:
+        x += a.bias[col];
+        a.outf[(int64_t)row * a.ldf + col] = x;
+        a.outb[(int64_t)row * a.ldb + col] = __float2bfloat16_rn(gelu_f(x));
+        break;
+      case GEMM_BIAS_F32:
+        a.outf[(int64_t)row * a.ldf + col] = x + a.bias[col];
+        break;
+      case GEMM_GELU_GRAD:
+        a.outb[(int64_t)row * a.ldb + col] = __float2bfloat16_rn(x * gelu_grad_f(a.zin[(int64_t)row * a.ldz + col]));
+        break;
+    }
   }
 }
 
@@ -209,9 +255,28 @@ int gemm_bf16(tdk_ctx* ctx, const GemmOp& op) {
   a.status = ctx->d_status;
   const size_t smem = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2);
   TDK_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const dim3 grid((op.M + TM - 1) / TM, (op.N + TN - 1) / TN);
-  gemm_bf16_kernel<<<grid, THREADS, smem, ctx->stream>>>(tmA, tmB, a);
+  const int gx = (op.M + TM - 1) / TM, gy = (op.N + TN - 1) / TN;
+  const int KC = (op.K + TK - 1) / TK;
+  // split over K when the tiles leave most SMs idle: at least 4 slices per
+  // CTA, about one CTA per SM in all
+  const int tiles = gx * gy;
+  int ks = 1;
+  if (2 * tiles <= ctx->num_sms && KC >= 8) ks = std::min((ctx->num_sms + tiles - 1) / tiles, KC / 4);
+  a.kper = (KC + ks - 1) / ks;
+  ks = (KC + a.kper - 1) / a.kper;
+  if (ks > 1) {
+    const size_t pbytes = sizeof(float) * (size_t)ks * op.M * op.N;
+    const int rc2 = ws_reserve(ctx, pbytes);
+    if (rc2) return rc2;
+    a.part = reinterpret_cast<float*>(ctx->ws);
+  }
+  gemm_bf16_kernel<<<dim3(gx, gy, ks), THREADS, smem, ctx->stream>>>(tmA, tmB, a);
   TDK_LAUNCH_CHECK(ctx);
+  if (ks > 1) {
+    const int64_t MN = (int64_t)op.M * op.N;
+    splitk_finish_kernel<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 2048), 256, 0, ctx->stream>>>(a.part, ks, a);
+    TDK_LAUNCH_CHECK(ctx);
+  }
   return TDK_OK;
 }
 

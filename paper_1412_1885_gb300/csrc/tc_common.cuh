@@ -184,17 +184,6 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                : "memory");
 }
 
-// acc + lo^2 + hi^2 for the two BF16 values packed in w (low half first), by
-// two mixed-precision FMAs: a BF16 operand is exact in FP32, so this is the
-// FP32 fmaf chain without the unpacking shifts
-__device__ __forceinline__ float sq2_bf16(uint32_t w, float acc) {
-  asm("{\n .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %1;\n fma.rn.f32.bf16 %0, lo, lo, %0;\n"
-      " fma.rn.f32.bf16 %0, hi, hi, %0;\n}\n"
-      : "+f"(acc)
-      : "r"(w));
-  return acc;
-}
-
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);

@@ -175,7 +175,11 @@ __global__ void __launch_bounds__(CoLayout<F32, MT>::THREADS, 1)
               const uint4 w = *reinterpret_cast<const uint4*>(row + ((c ^ (rl & 7)) << 4));
               const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-              for (int e = 0; e < 4; ++e) part = sq2_bf16(ws[e], part);
+              for (int e = 0; e < 4; ++e) {
+                const float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
+                part = fmaf(lo, lo, part);
+                part = fmaf(hi, hi, part);
+              }
             }
           }
           const float y = part - nrm_c;
@@ -702,7 +706,11 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             const uint4 w = *reinterpret_cast<const uint4*>(row + ((c ^ (rl & 7)) << 4));
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) part = sq2_bf16(ws[e], part);
+            for (int e = 0; e < 4; ++e) {
+              const float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
+              part = fmaf(lo, lo, part);
+              part = fmaf(hi, hi, part);
+            }
           }
           const float y = part - nrm_c;
           const float tt = nrm + y;

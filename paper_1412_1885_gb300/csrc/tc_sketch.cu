@@ -1078,7 +1078,11 @@ __global__ void __launch_bounds__(384, 1)
               const uint4 w = *reinterpret_cast<const uint4*>(rp + ((c ^ (row & 7)) << 4));
               const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-              for (int e = 0; e < 4; ++e) q = sq2_bf16(ws[e], q);
+              for (int e = 0; e < 4; ++e) {
+                const float lo = __uint_as_float(ws[e] << 16), hi = __uint_as_float(ws[e] & 0xFFFF0000u);
+                q = fmaf(lo, lo, q);
+                q = fmaf(hi, hi, q);
+              }
             }
             const float y = q - comp;  // Kahan over the rows
             const float t = part + y;

@@ -111,10 +111,14 @@ int tdk_ctx_profile_read(tdk_ctx* ctx, int region, double* total_ms /* host */,
                          int64_t* launches /* host */);
 /* Host <-> device copies on the context's stream, for callers whose data
    live in host memory (pinned memory for full link speed).  tdk_copy_in is
-   asynchronous: later calls on the stream see the data.  tdk_copy_out waits
-   for the stream, so *dst_host is valid on return.  Both buffers are
-   caller-owned; bytes = 0 is a no-op.  Errors: TDK_EINVAL (null context or
-   buffer), TDK_ECUDA. */
+   asynchronous: later calls on the stream see the data.  A page-locked
+   source of 64 MiB or more, with both addresses 16-byte aligned, is read by
+   a copy kernel on the SMs through its mapped device address (on GB300
+   about 210 GB/s against 140-180 GB/s for the copy engine); any other
+   source, and the last bytes past a multiple of 16, go through
+   cudaMemcpyAsync.  tdk_copy_out waits for the stream, so *dst_host is valid
+   on return.  Both buffers are caller-owned; bytes = 0 is a no-op.  Errors:
+   TDK_EINVAL (null context or buffer), TDK_ECUDA. */
 int tdk_copy_in(tdk_ctx* ctx, void* dst /* device */, const void* src_host, size_t bytes);
 int tdk_copy_out(tdk_ctx* ctx, void* dst_host, const void* src /* device */, size_t bytes);
 /* Human-readable text for a return code. */

@@ -168,6 +168,27 @@ static unsigned checked_take_all(cudaStream_t s) {
 }  // namespace tdk
 #endif
 
+namespace tdk {
+namespace {
+constexpr size_t PULL_MIN_BYTES = (size_t)1 << 26;  // 64 MiB
+// dst[i] = src[i] for 16-byte words, src in page-locked host memory seen
+// through its device mapping; four loads in flight per thread
+__global__ void __launch_bounds__(512) pull_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                   int64_t n16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += 4 * stride) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i + u * stride < n16) v[u] = __ldg(src + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i + u * stride < n16 && TDK_IN(i + u * stride, n16)) dst[i + u * stride] = v[u];
+  }
+}
+}  // namespace
+}  // namespace tdk
+
 #ifdef TDK_TESTING
 namespace tdk {
 namespace {
@@ -279,7 +300,25 @@ int tdk_copy_in(tdk_ctx* c, void* dst, const void* src_host, size_t bytes) {
   if (!c || (bytes && (!dst || !src_host))) return TDK_EINVAL;
   if (!bytes) return TDK_OK;
   cudaSetDevice(c->device);
-  TDK_CUDA_TRY(cudaMemcpyAsync(dst, src_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  // page-locked source: the SMs pull it through its mapped device address
+  // (GB300: about 210 GB/s against 140-180 for the copy engine); the rest
+  // and pageable sources go through the copy engine
+  cudaPointerAttributes at{};
+  const bool pinned = cudaPointerGetAttributes(&at, src_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                      at.devicePointer != nullptr;
+  cudaGetLastError();
+  size_t done = 0;
+  if (pinned && bytes >= PULL_MIN_BYTES && ((reinterpret_cast<uintptr_t>(at.devicePointer) |
+                                             reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    const int64_t n16 = (int64_t)(bytes / 16);
+    pull_kernel<<<2 * c->num_sms, 512, 0, c->stream>>>(static_cast<const uint4*>(at.devicePointer),
+                                                       static_cast<uint4*>(dst), n16);
+    TDK_LAUNCH_CHECK(c);
+    done = (size_t)n16 * 16;
+  }
+  if (done < bytes)
+    TDK_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(dst) + done, static_cast<const char*>(src_host) + done,
+                                 bytes - done, cudaMemcpyHostToDevice, c->stream));
   return TDK_OK;
 }
 

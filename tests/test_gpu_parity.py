@@ -539,6 +539,26 @@ def test_host_data_through_the_abi_copies(tdk, ctx):
     assert ctx.sync_status() == 0
 
 
+@pytest.mark.parametrize("pinned,offset,extra", [(True, 0, 5), (True, 8, 0), (False, 0, 3), (True, 0, -(1 << 25))])
+def test_copy_in_every_path_is_exact(tdk, ctx, pinned, offset, extra):
+    """tdk_copy_in: a page-locked 16-byte-aligned source of 64 MiB or more
+    goes through the SM copy kernel (with its tail bytes by the copy engine);
+    an unaligned, a pageable or a smaller source goes through the copy
+    engine.  Every path delivers the bytes exactly."""
+    import torch
+
+    n = (1 << 26) + extra
+    src = torch.randint(0, 256, (n + offset,), dtype=torch.uint8)
+    if pinned:
+        src = src.pin_memory()
+    view = src[offset:]
+    dst = torch.empty(n, dtype=torch.uint8, device="cuda")
+    tdk.copy_in(ctx, dst, view)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert torch.equal(dst.cpu(), view)
+
+
 @pytest.mark.parametrize("rule", ["hals", "mu"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_nonneg_rules_match_oracle(tdk, ctx, rule, dtype):

@@ -68,6 +68,7 @@ namespace {
 
 using namespace tc;
 
+
 constexpr int KB = 1024;
 constexpr uint32_t BOX_BYTES = 16 * KB;  // one 128-row x 128-byte box
 constexpr int SK_SMAX = 4;               // deepest stage ring of the sketch
@@ -105,7 +106,19 @@ struct SkArgs {
   int64_t poff_p[TDK_MAX_MODES];
   unsigned* status;
   unsigned long long* prof;        // optional cycle counters of CTA 0 (null = off)
+  int yhint;                       // L2 policy of Y's boxes: 1 evict-first, 0 normal
 };
+
+// Y is read once: its boxes go first out of L2, so that the test-matrix rows
+// the epilogue re-reads stay there.  At 3000^3 BF16 this takes the pass from
+// 12.36 to 12.14 ms, although DRAM reads grow from 57.1 to 61.0 GB.
+__device__ __forceinline__ void load_y_box(const SkArgs& a, uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                           int c2, uint32_t bar) {
+  if (a.yhint)
+    tma_load_3d_evict_first(dst, map, c0, c1, c2, bar);
+  else
+    tma_load_3d(dst, map, c0, c1, c2, bar);
+}
 
 template <bool F32>
 struct SkLayout {
@@ -223,10 +236,10 @@ __global__ void __launch_bounds__(320, 1)
             const int kc = k0 + 128 * st;
             if (F32) {
               for (int q = 0; q < 4; ++q)
-                tma_load_3d(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 32 * q, j0, (int)p, smem_u32(&full[s]));
+                load_y_box(a, smem_u32(dst + q * BOX_BYTES), &tmY, kc + 32 * q, j0, (int)p, smem_u32(&full[s]));
             } else {
               for (int q = 0; q < 2; ++q)
-                tma_load_3d(smem_u32(dst + q * BOX_BYTES), &tmY, kc + 64 * q, j0, (int)p, smem_u32(&full[s]));
+                load_y_box(a, smem_u32(dst + q * BOX_BYTES), &tmY, kc + 64 * q, j0, (int)p, smem_u32(&full[s]));
             }
           }
         }
@@ -752,8 +765,8 @@ __global__ void __launch_bounds__(384, 1)
             const uint32_t fb = smem_u32(&full[s]);
             mbar_expect_tx(fb, 32 * KB);
             const int kc = k0 + 128 * st;
-            tma_load_3d(dst, &tmY, kc, j0, (int)p, fb);
-            tma_load_3d(dst + BOX_BYTES, &tmY, kc + 64, j0, (int)p, fb);
+            load_y_box(a, dst, &tmY, kc, j0, (int)p, fb);
+            load_y_box(a, dst + BOX_BYTES, &tmY, kc + 64, j0, (int)p, fb);
             if (++s == (uint32_t)S) {
               s = 0;
               sph ^= 1;
@@ -1385,6 +1398,10 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   }
   a.ustride = (o + 63) / 64 * 64;
   a.status = ctx->d_status;
+  a.yhint = 1;
+#ifdef TDK_TESTING
+  if (const char* e = getenv("TDK_SKETCH_YHINT")) a.yhint = atoi(e) != 0;
+#endif
 #ifdef TDK_TESTING
   const bool want_prof = getenv("TDK_SKETCH_PROFILE") != nullptr;
 #else

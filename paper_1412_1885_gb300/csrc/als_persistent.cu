@@ -77,6 +77,7 @@ struct PArgs {
   const double* nY2;            // may be null
   double* rpart;                // [grid] per-CTA residual partials
   unsigned long long* prof;     // optional: cycles per phase, CTA 0 (null = off)
+  float* xprev;                 // grid kernel: [grid][N][R*R] each CTA's last FP32 inverse of T_n
 };
 
 __device__ bool grid_sync(unsigned* bar, unsigned* status) {
@@ -134,6 +135,47 @@ struct GramAcc {
   __device__ __forceinline__ T value() const { return s + c; }
 };
 
+// Float-float arithmetic (value = hi + lo) for the explicit residual of the
+// FP32 fit.  Products are split exactly by an FMA and every sum keeps its
+// rounding error (TwoSum), the compensated scheme of Ogita, Rump and Oishi
+// (SIAM J. Sci. Comput. 26, 2005).  The residual norm then comes out accurate
+// to about 2^-44 whatever the order of the sums, so the stopping test sees the
+// change of the fit between sweeps rather than FP32 rounding noise, which near
+// convergence is as large as a relative change of 1e-7 and made the sweep
+// count differ between two kernels that sum in different orders.
+struct FFAcc {
+  float s = 0.f, c = 0.f;
+  // s + c += ph + pl
+  __device__ __forceinline__ void add(float ph, float pl) {
+    const float t = s + ph;
+    const float z = t - s;
+    c += ((s - (t - z)) + (ph - z)) + pl;
+    s = t;
+  }
+  // s + c += (xh + xl) y
+  __device__ __forceinline__ void fma2(float xh, float xl, float y) {
+    const float p = xh * y;
+    add(p, fmaf(xl, y, fmaf(xh, y, -p)));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+// (xh + xl) y as a float-float pair
+__device__ __forceinline__ void ff_mul(float xh, float xl, float y, float& ph, float& pl) {
+  ph = xh * y;
+  pl = fmaf(xl, y, fmaf(xh, y, -ph));
+}
+// acc += (g - (xh + xl))^2, the difference and its square in float-float
+__device__ __forceinline__ void ff_add_sq_diff(FFAcc& acc, float g, float xh, float xl) {
+  const float d0 = g - xh;  // TwoSum: d0 + e0 = g - xh exactly
+  const float z = d0 - g;
+  const float e0 = (g - (d0 - z)) + (-xh - z);
+  const float e1 = e0 - xl;
+  const float dh = d0 + e1;  // renormalised: dh + dl = d0 + e1
+  const float dl = e1 - (dh - d0);
+  const float q = dh * dh;
+  acc.add(q, fmaf(2.f * dh, dl, fmaf(dh, dh, -q)));
+}
+
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -167,7 +209,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 template <class T>
 struct PLayout {
   size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_invf, o_yf,
-      o_lamt, o_ilamt, o_slice, o_work, o_egram, total;
+      o_lamt, o_ilamt, o_slice, o_work, o_egram, o_ns, total;
   __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -194,6 +236,7 @@ struct PLayout {
     o_slice = take(sizeof(T) * (size_t)Qmax);
     o_work = take(sizeof(T) * (size_t)(Amax * R));
     o_egram = take(egram ? sizeof(T) * N * R * R : 0);  // Grams of A_p - U_p B_p
+    o_ns = take(sizeof(float) * R * R);                 // Newton-Schulz iterate
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -328,6 +371,84 @@ __device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, 
   return 1;
 }
 
+// Newton-Schulz refinement of an approximate inverse X of T (Schulz 1933;
+// Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., 14.5):
+//   E = I - T X,   X <- X + X E,
+// which squares the residual E at every step.  Started from the inverse of
+// the previous sweep's T_n, which moved only as far as the factors did, it
+// reaches the FP32 floor in a few steps: two R x R products per step instead
+// of the R barrier-separated pivot steps of Gauss-Jordan elimination.
+// T, X0, X1, E: R x R row-major FP32 (shared memory), X0 holding the start;
+// computed by the nt threads of a group (named barrier bar_id) in 2 x 4
+// register tiles; red: nt / 32 floats.  Returns the buffer that holds the
+// inverse once max |E| <= tol (at most max_it updates), with that max |E| in
+// *dev, or null when the residual does not fall below 1/2 or stops shrinking
+// quadratically; the same outcome in every thread.
+__device__ const float* ns_inverse(const float* T, float* X0, float* X1, float* E, float* red, int R, float tol,
+                                   int max_it, float* dev, int t, int nt, int bar_id) {
+  const int tr = (R + 1) / 2, tcn = (R + 3) / 4;
+  // C = I - A B (sub = true) or C = Xc + A B, and max |C - I| over the tiles
+  auto prod = [&](const float* A, const float* B, const float* Xc, float* C, bool sub) -> float {
+    float mx = 0.f;
+    for (int tile = t; tile < tr * tcn; tile += nt) {
+      const int i0 = (tile / tcn) * 2, j0 = (tile % tcn) * 4;
+      float acc[2][4] = {};
+      for (int k = 0; k < R; ++k) {
+        float a2[2], b4[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) a2[u] = (i0 + u < R) ? A[(i0 + u) * R + k] : 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) b4[v] = (j0 + v < R) ? B[k * R + j0 + v] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a2[u], b4[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (i0 + u < R && j0 + v < R) {
+            const int e = (i0 + u) * R + j0 + v;
+            const float id = (i0 + u == j0 + v) ? 1.f : 0.f;
+            const float cv = sub ? id - acc[u][v] : Xc[e] + acc[u][v];
+            C[e] = cv;
+            mx = fmaxf(mx, fabsf(sub ? cv : cv - id));
+          }
+    }
+    return mx;
+  };
+  auto group_max = [&](float v) -> float {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((t & 31) == 0) red[t >> 5] = v;
+    tc::named_bar(bar_id, nt);
+    float m = 0.f;
+    for (int w = 0; w < (nt >> 5); ++w) m = fmaxf(m, red[w]);
+    tc::named_bar(bar_id, nt);  // red is rewritten by the next call
+    return m;
+  };
+  tc::named_bar(bar_id, nt);  // T and X0 written by the group
+  float* X = X0;
+  float* Xn = X1;
+  float d = group_max(prod(T, X, nullptr, E, true));
+  for (int it = 0;; ++it) {
+    if (d <= tol) {
+      *dev = d;
+      return X;
+    }
+    if (!(d < 0.5f) || it == max_it) return nullptr;
+    prod(X, E, X, Xn, false);
+    tc::named_bar(bar_id, nt);
+    float* tmp = X;
+    X = Xn;
+    Xn = tmp;
+    const float dn = group_max(prod(T, X, nullptr, E, true));
+    if (!(dn <= tol) && !(dn < 0.5f * d)) return nullptr;  // stalled above tol
+    d = dn;
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   unsigned long long prof_t = clock64();
@@ -354,7 +475,8 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   double* hrow = reinterpret_cast<double*>(sm + L.o_hrow);  // right-hand side
   double* red = reinterpret_cast<double*>(sm + L.o_red);    // [32]
   float* Lf = reinterpret_cast<float*>(sm + L.o_lf);        // [R*R] FP32 inverse of T_n
-  double* Tid = reinterpret_cast<double*>(sm + L.o_tid);   // [R*R] FP64 inverse (fallback)
+  double* Tid = reinterpret_cast<double*>(sm + L.o_tid);   // [R*R] FP64 inverse (fallback); Newton-Schulz X, E
+  float* nsX1 = reinterpret_cast<float*>(sm + L.o_ns);       // [R*R] Newton-Schulz iterate
   double* gjs = reinterpret_cast<double*>(sm + L.o_gjs);   // Gauss-Jordan pivot rows / columns (two pairs)
   float* invf = reinterpret_cast<float*>(sm + L.o_invf);
   float* yf = reinterpret_cast<float*>(sm + L.o_yf);
@@ -437,6 +559,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
 
   double fit = 0.0, fitY = nan("");
   int sweep = 0, converged = 0, needpinv = 0;
+  unsigned have_prev = 0;  // modes whose last FP32 inverse is in this CTA's xprev slot
   for (sweep = 1; sweep <= a.max_sweeps && ok; ++sweep) {
     double inner = 0.0;
     for (int n = 0; n < N && ok; ++n) {
@@ -453,26 +576,58 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         for (int p = 0; p < N; ++p)
           if (p != n) v *= (double)gram[p * R * R + e];
         Tm[e] = v;
-        Tid[e] = v;
       }
       __syncthreads();
       PROF_MARK(7);
       // ---- 1b. inverse of T_n: FP32 by default (the solves are refined against
-      //          T_n in FP64), FP64 if an FP32 pivot breaks down
+      //          T_n in FP64), FP64 if an FP32 pivot breaks down.  From the
+      //          second sweep on, Newton-Schulz steps from the previous sweep's
+      //          inverse, Gauss-Jordan when they do not converge.  FP32 cores
+      //          take one refinement step after an inverse with residual below
+      //          2^-13 (solve error below 2^-26), FP64 cores two.
       // (the HALS and multiplicative rules use T_n itself, not its inverse)
       bool use32 = true;
+      int nref = 2;
       if (!(a.nonneg && a.nn_rule != 0)) {
-        use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
-        if (a.prof && !use32 && blockIdx.x == 0 && tid == 0) a.prof[9] += 1;  // FP64 inverses
-        if (!use32 && !group_gj_inverse<double>(Tid, gjs, R, 2.220446049250313e-16, tid, NTP, 1)) {
-          needpinv = 1;
-          ok = false;  // identical in every CTA: all leave here
-          break;
+        float* xp = a.xprev + ((int64_t)c * N + n) * R * R;
+        const float* Xi = nullptr;
+        if (have_prev & (1u << n)) {
+          float* X0 = reinterpret_cast<float*>(Tid);
+          for (int e = tid; e < R * R; e += NTP) X0[e] = xp[e];
+          float dev = 1.f;
+          Xi = ns_inverse(Lf, X0, nsX1, X0 + R * R, reinterpret_cast<float*>(gjs), R,
+                          sizeof(T) == 4 ? 0x1p-13f : 0x1p-17f, 4, &dev, tid, NTP, 1);
+          if (Xi) {
+            for (int e = tid; e < R * R; e += NTP) Lf[e] = Xi[e];
+            if (sizeof(T) == 4) nref = 1;
+          }
+        }
+        if (!Xi) {
+          use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
+          if (a.prof && !use32 && blockIdx.x == 0 && tid == 0) a.prof[9] += 1;  // FP64 inverses
+          if (!use32) {
+            for (int e = tid; e < R * R; e += NTP) Tid[e] = Tm[e];
+            __syncthreads();
+            if (!group_gj_inverse<double>(Tid, gjs, R, 2.220446049250313e-16, tid, NTP, 1)) {
+              needpinv = 1;
+              ok = false;  // identical in every CTA: all leave here
+              break;
+            }
+          }
+        } else if (a.prof && blockIdx.x == 0 && tid == 0) {
+          a.prof[10] += 1;  // Newton-Schulz inverses
+        }
+        __syncthreads();
+        if (use32) {
+          for (int e = tid; e < R * R; e += NTP) xp[e] = Lf[e];
+          have_prev |= 1u << n;
+        } else {
+          have_prev &= ~(1u << n);
         }
       }
       __syncthreads();
       // x <- x T_n^{-1} for the row in xrow, block-parallel: one product with the
-      // inverse, then two refinement steps against T_n in FP64 (invd: residual)
+      // inverse, then nref refinement steps against T_n in FP64 (invd: residual)
       auto solve_row = [&]() {
         for (int r = tid; r < R; r += NTP) hrow[r] = xrow[r];
         __syncthreads();
@@ -488,7 +643,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           xrow[r] = acc;
         }
         __syncthreads();
-        for (int it = 0; it < 2; ++it) {
+        for (int it = 0; it < nref; ++it) {
           for (int q = tid; q < R; q += NTP) {
             double rr = hrow[q];
             for (int r = 0; r < R; ++r) rr = fma(-xrow[r], Tm[r * R + q], rr);
@@ -787,51 +942,41 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           // FP32 forms: ||G - [[lambda; B]]||^2 summed explicitly over this CTA's
           // share of the core (the Gram identity cancels to rounding noise near
           // convergence in FP32)
-          T sacc = T(0), scmp = T(0);
+          FFAcc racc;
           if (N == 3) {
             // slab i of mode 1: P[j, r] = lambda_r B_1[i, r] B_2[j, r], then the
-            // model slab P B_3^T in 4 x 4 register tiles against G[i, :, :]
-            const int R0 = a.Rt[0], R1 = a.Rt[1], R2 = a.Rt[2];
+            // model slab P B_3^T in 4 x 4 register tiles against G[i, :, :],
+            // P and the sums in float-float
+            const int R1 = a.Rt[1], R2 = a.Rt[2];
             const T* B0 = Bs + boff[0];
             const T* B1 = Bs + boff[1];
             const T* B2 = Bs + boff[2];
-            for (int i = c; i < R0; i += G) {
-              __syncthreads();
-              for (int e = tid; e < R1 * R; e += NTP) {
-                const int j = e / R, r = e % R;
-                work[e] = lamT[r] * B0[i * R + r] * B1[j * R + r];
-              }
-              __syncthreads();
-              const int tj = (R1 + 3) / 4, tk = (R2 + 3) / 4;
+            const int tj = (R1 + 3) / 4, tk = (R2 + 3) / 4;
+            for (int i = c; i < a.Rt[0]; i += G) {
               for (int tile = tid; tile < tj * tk; tile += NTP) {
                 const int j0 = (tile / tk) * 4, k0 = (tile % tk) * 4;
-                T acc[4][4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                  for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+                FFAcc acc[4][4];
                 for (int r = 0; r < R; ++r) {
-                  T p4[4], b4[4];
+                  float lh, ll;  // lambda_r B_1[i, r]
+                  ff_mul((float)lamT[r], 0.f, (float)B0[i * R + r], lh, ll);
+                  float ph[4], pl[4], b4[4];
 #pragma unroll
-                  for (int u = 0; u < 4; ++u) p4[u] = (j0 + u < R1) ? work[(j0 + u) * R + r] : T(0);
+                  for (int u = 0; u < 4; ++u) ff_mul(lh, ll, (j0 + u < R1) ? (float)B1[(j0 + u) * R + r] : 0.f, ph[u], pl[u]);
 #pragma unroll
-                  for (int v = 0; v < 4; ++v) b4[v] = (k0 + v < R2) ? B2[(k0 + v) * R + r] : T(0);
+                  for (int v = 0; v < 4; ++v) b4[v] = (k0 + v < R2) ? (float)B2[(k0 + v) * R + r] : 0.f;
 #pragma unroll
                   for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(p4[u], b4[v], acc[u][v]);
+                    for (int v = 0; v < 4; ++v) acc[u][v].fma2(ph[u], pl[u], b4[v]);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
                   for (int v = 0; v < 4; ++v)
-                    if (j0 + u < R1 && k0 + v < R2) {
-                      const T d = a.G[(int64_t)i * a.stride[0] + (int64_t)(j0 + u) * a.stride[1] + k0 + v] - acc[u][v];
-                      const T y = d * d - scmp;  // Kahan
-                      const T tt = sacc + y;
-                      scmp = (tt - sacc) - y;
-                      sacc = tt;
-                    }
+                    if (j0 + u < R1 && k0 + v < R2)
+                      ff_add_sq_diff(racc,
+                                     (float)a.G[(int64_t)i * a.stride[0] + (int64_t)(j0 + u) * a.stride[1] + k0 + v],
+                                     acc[u][v].s, acc[u][v].c);
               }
             }
           } else {
@@ -844,20 +989,16 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
               ix[p] = rem % a.Rt[p];
               rem /= a.Rt[p];
             }
-            T x = T(0);
+            FFAcc x;
             for (int r = 0; r < R; ++r) {
-              T v = lamT[r];
-              for (int p = 0; p < N; ++p) v *= Bs[boff[p] + ix[p] * R + r];
-              x += v;
+              float vh = (float)lamT[r], vl = 0.f;
+              for (int p = 0; p < N; ++p) ff_mul(vh, vl, (float)Bs[boff[p] + ix[p] * R + r], vh, vl);
+              x.add(vh, vl);
             }
-            const T d = a.G[e] - x;
-            const T y = d * d - scmp;  // Kahan
-            const T t = sacc + y;
-            scmp = (t - sacc) - y;
-            sacc = t;
+            ff_add_sq_diff(racc, (float)a.G[e], x.s, x.c);
           }
           }
-          double s2 = block_sum_d((double)sacc - (double)scmp, red);
+          double s2 = block_sum_d(racc.value(), red);
           if (tid == 0) a.rpart[c] = s2;
         }
       }
@@ -945,7 +1086,7 @@ constexpr int NTS = 512;
 template <class T>
 struct SLayout {
   size_t o_g, o_b0, o_b1, o_b2, o_gram, o_w, o_h, o_x, o_res, o_tm, o_ld, o_lid, o_lf, o_lif, o_lam, o_lamt, o_red,
-      total;
+      o_xp, o_ns, total;
   __host__ __device__ void plan(int R0, int R1, int R2, int R) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -972,6 +1113,8 @@ struct SLayout {
     o_lam = take(sizeof(double) * 64);
     o_lamt = take(sizeof(T) * 64);
     o_red = take(sizeof(double) * 32);
+    o_xp = take(sizeof(float) * 3 * RR);  // last FP32 inverse of each T_n
+    o_ns = take(sizeof(float) * RR);      // Newton-Schulz iterate
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -997,10 +1140,13 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   double* Lid = reinterpret_cast<double*>(sm + L.o_lid);
   float* Lf = reinterpret_cast<float*>(sm + L.o_lf);
   float* Lif = reinterpret_cast<float*>(sm + L.o_lif);
+  float* Xp = reinterpret_cast<float*>(sm + L.o_xp);
+  float* Xns = reinterpret_cast<float*>(sm + L.o_ns);
   double* lam = reinterpret_cast<double*>(sm + L.o_lam);
   T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
   double* red = reinterpret_cast<double*>(sm + L.o_red);
   __shared__ int s_mode;  // 1: FP32 factor, 2: FP64 factor, 0: singular
+  __shared__ int s_nref;  // refinement steps of the solve
   __shared__ T s_irows[3];  // 1 / sqrt(Rt_n): the column a zero column is replaced by
   __shared__ unsigned long long s_prof[10];
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -1041,6 +1187,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   const double nY2 = a.nY2 ? *a.nY2 : 0.0;
   double fit = 0.0, fitY = nan("");
   int sweep = 0, converged = 0, singular = 0;
+  unsigned have_prev = 0;  // warps 0-7: modes whose last FP32 inverse is in Xp
   for (sweep = 1; sweep <= a.max_sweeps; ++sweep) {
     for (int n = 0; n < 3; ++n) {
       const int Rn = Rt[n];
@@ -1051,22 +1198,45 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
         for (int p = 0; p < 3; ++p)
           if (p != n) v *= (double)gram[p * RR + e];
         Tm[e] = v;
-        Ld[e] = v;
+        if (F64) Ld[e] = v;
         Lf[e] = (float)v;
       }
       __syncthreads();
       pms(0);
       if (warp < 8) {
-        // ---- invert T_n (FP32 for FP32 cores, FP64 otherwise / as fallback), warps 0-7
+        // ---- invert T_n, warps 0-7: FP32 cores by Newton-Schulz steps from the
+        //      previous sweep's inverse (one refinement step of the solve
+        //      after it), else by FP32 Gauss-Jordan; FP64 cores and the
+        //      fallback by FP64 Gauss-Jordan
         const unsigned long long pt0 = clock64();
-        int mode = 0;
-        if (!F64 && group_gj_inverse_smem<float>(Lf, Lif, R, 1.1920929e-7f, tid, 256, 2)) {
-          mode = 1;
-        } else if (group_gj_inverse_smem<double>(Ld, Lid, R, 2.220446049250313e-16, tid, 256, 2)) {
-          mode = 2;
+        int mode = 0, nref = 2;
+        if (!F64) {
+          const float* Xi = nullptr;
+          if (have_prev & (1u << n)) {
+            float* X0 = reinterpret_cast<float*>(Ld);
+            for (int e = tid; e < RR; e += 256) X0[e] = Xp[n * RR + e];
+            float dev = 1.f;
+            Xi = ns_inverse(Lf, X0, Xns, X0 + RR, Lif, R, 0x1p-13f, 4, &dev, tid, 256, 2);
+            if (Xi) {
+              for (int e = tid; e < RR; e += 256) Lf[e] = Xi[e];
+              mode = 1;
+              nref = 1;
+            }
+          }
+          if (!Xi && group_gj_inverse_smem<float>(Lf, Lif, R, 1.1920929e-7f, tid, 256, 2)) mode = 1;
+          if (mode == 1) {
+            for (int e = tid; e < RR; e += 256) Xp[n * RR + e] = Lf[e];
+            have_prev |= 1u << n;
+          } else {
+            have_prev &= ~(1u << n);
+            for (int e = tid; e < RR; e += 256) Ld[e] = Tm[e];
+            tc::named_bar(2, 256);
+          }
         }
+        if (mode == 0 && group_gj_inverse_smem<double>(Ld, Lid, R, 2.220446049250313e-16, tid, 256, 2)) mode = 2;
         if (tid == 0) {
           s_mode = mode;
+          s_nref = nref;
           if (prof_on) s_prof[8] += clock64() - pt0;
         }
       } else {
@@ -1160,8 +1330,9 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
         singular = 1;
         break;
       }
-      // ---- B_n = H_n T_n^-1, refined twice against T_n in FP64
+      // ---- B_n = H_n T_n^-1, refined against T_n in FP64 (s_nref steps)
       const bool f32 = s_mode == 1;
+      const int nref = s_nref;
       for (int e = tid; e < Rn * R; e += NTS) {
         const int i = e / R, c = e % R;
         double acc = 0.0;
@@ -1176,7 +1347,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       }
       __syncthreads();
       pms(2);
-      for (int it = 0; it < 2; ++it) {
+      for (int it = 0; it < nref; ++it) {
         for (int e = tid; e < Rn * R; e += NTS) {
           const int i = e / R, c = e % R;
           double rr = (double)H[e];
@@ -1243,16 +1414,13 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       const double inner = block_sum_d(in, red);
       res2 = fmax(0.0, nG2 - 2.0 * inner + model2);
     } else {
-      // explicit ||G - [[lambda; B]]||^2: model (B_1 (.) B_2) diag(lambda) B_3^T, tile by tile
-      T sacc = T(0), scmp = T(0);
+      // explicit ||G - [[lambda; B]]||^2: model (B_1 (.) B_2) diag(lambda) B_3^T,
+      // tile by tile, in float-float
+      FFAcc racc;
       const int tm = (M01 + 3) / 4, tk = (Rt[2] + 3) / 4;
       for (int tile = tid; tile < tm * tk; tile += NTS) {
         const int m0 = (tile / tk) * 4, k0 = (tile % tk) * 4;
-        T acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        FFAcc acc[4][4];
         int ia[4], ib[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -1261,29 +1429,28 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
           ib[u] = (m % Rt[1]) * R;
         }
         for (int r = 0; r < R; ++r) {
-          T w4[4], b4[4];
+          float wh[4], wl[4], b4[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) w4[u] = (m0 + u < M01) ? B[0][ia[u] + r] * B[1][ib[u] + r] * lamT[r] : T(0);
+          for (int u = 0; u < 4; ++u) {
+            float h, l;  // B_1[i, r] B_2[j, r] lambda_r
+            ff_mul((float)B[0][ia[u] + r], 0.f, (float)B[1][ib[u] + r], h, l);
+            ff_mul(h, l, (m0 + u < M01) ? (float)lamT[r] : 0.f, wh[u], wl[u]);
+          }
 #pragma unroll
-          for (int v = 0; v < 4; ++v) b4[v] = (k0 + v < Rt[2]) ? B[2][(k0 + v) * R + r] : T(0);
+          for (int v = 0; v < 4; ++v) b4[v] = (k0 + v < Rt[2]) ? (float)B[2][(k0 + v) * R + r] : 0.f;
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(w4[u], b4[v], acc[u][v]);
+            for (int v = 0; v < 4; ++v) acc[u][v].fma2(wh[u], wl[u], b4[v]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            if (m0 + u < M01 && k0 + v < Rt[2]) {
-              const T d = Gc[(m0 + u) * Rt[2] + k0 + v] - acc[u][v];
-              const T y = d * d - scmp;  // Kahan
-              const T tt = sacc + y;
-              scmp = (tt - sacc) - y;
-              sacc = tt;
-            }
+            if (m0 + u < M01 && k0 + v < Rt[2])
+              ff_add_sq_diff(racc, (float)Gc[(m0 + u) * Rt[2] + k0 + v], acc[u][v].s, acc[u][v].c);
       }
-      res2 = block_sum_d((double)sacc - (double)scmp, red);
+      res2 = block_sum_d(racc.value(), red);
     }
     pms(5);
     // the scalar tail by one thread, shared through `red`
@@ -1429,6 +1596,13 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   const int grid_all = per_sm * ctx->num_sms;
   const int64_t rows_cap = a.nonneg ? std::max(Rtmax, Imax) : Rtmax;
   int grid = (grid_all >= 4 * Rtmax) ? grid_all : (int)std::min<int64_t>(grid_all, rows_cap);
+#ifdef TDK_TESTING
+  // test hook: TDK_ALS_GRID=1 takes the grid kernel on a core the one-CTA
+  // kernel would take; a larger value also caps the grid (another split of
+  // the rows over the CTAs, so other orders of the sums)
+  const int grid_cap = getenv("TDK_ALS_GRID") ? atoi(getenv("TDK_ALS_GRID")) : 0;
+  if (grid_cap > 1) grid = std::min(grid, grid_cap);
+#endif
 
   Planner pl;
   pl.take<T>((size_t)(a.nonneg ? std::max(Rtmax, Imax) : Rtmax) * R);
@@ -1447,6 +1621,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   pl.take<unsigned>(2);
   pl.take<double>(1);
   pl.take<double>(grid);
+  pl.take<float>((size_t)grid * N * R * R);
   int rc = ws_reserve(ctx, pl.off);
   if (rc) return rc;
   Carver cv(ctx->ws);
@@ -1469,6 +1644,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   a.bar = cv.take<unsigned>(2);
   double* nG2 = cv.take<double>(1);
   a.rpart = cv.take<double>(grid);
+  a.xprev = cv.take<float>((size_t)grid * N * R * R);
   unsigned long long* prof = nullptr;
 #ifdef TDK_TESTING
   const bool want_prof = getenv("TDK_ALS_PROFILE") != nullptr;
@@ -1503,7 +1679,10 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   // 3-way unconstrained cores that fit in one SM: the single-CTA kernel
   SLayout<T> sl;
   sl.plan(g.Rt[0], g.Rt[N > 1 ? 1 : 0], g.Rt[N > 2 ? 2 : 0], R);
-  const bool small = N == 3 && !a.nonneg && sl.total + 64 <= (size_t)ctx->max_smem_optin;
+  bool small = N == 3 && !a.nonneg && sl.total + 64 <= (size_t)ctx->max_smem_optin;
+#ifdef TDK_TESTING
+  if (grid_cap > 0) small = false;
+#endif
   if (small) {
     auto ks = als_small_kernel<T>;
     TDK_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sl.total + 64)));
@@ -1528,7 +1707,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
       fprintf(stderr, "tdk ALS profile (single CTA, Mcycles over %d sweeps):", hs.sweeps);
       for (int i = 0; i < 10; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
     } else {
-      fprintf(stderr, "tdk ALS profile: T_n build=%.3f Mcycles, FP64 inverses=%llu\n", hp[7] / 1e6, hp[9]);
+      fprintf(stderr, "tdk ALS profile: T_n build=%.3f Mcycles, FP64 inverses=%llu, Newton-Schulz inverses=%llu\n",
+              hp[7] / 1e6, hp[9], hp[10]);
       const char* names[7] = {"inverse", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
                               "barrier3", "fit"};
       fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);

@@ -88,6 +88,80 @@ def test_als_grid_form_stopping_rule_matches_oracle_fp64(tdk, ctx):
     assert abs(out["fit_core"] - o["fit"]) < 1e-10
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_fp32_stopping_rule_does_not_depend_on_the_kernel(tdk, seed, monkeypatch):
+    """A 20^3 FP32 core with R = 10 (the 1000^3 workload's core geometry),
+    built from correlated factors so that ALS creeps, run to a relative fit
+    change below 1e-7 by the one-CTA kernel and by the grid kernel, which sum
+    the model and the residual in different orders.  The fit is evaluated in
+    float-float, so both stop at the same sweep with fits that agree far
+    inside the tolerance; and that fit stays within FP32 rounding of the FP64
+    oracle's from the same start."""
+    shape, R = (20, 20, 20), 10
+    A = synth.cp_factors(shape, R, 60 + seed, rho=0.85)
+    G = synth.add_noise(synth.cp_dense(A), 30.0, 60 + seed)
+    U = [np.eye(20) for _ in range(3)]
+    B0 = synth.init_factors(shape, R, 70 + seed)
+    ctx_t = tdk.Context(0, testing=True)
+    try:
+        runs = {}
+        for form in ["one-CTA", "grid"]:
+            if form == "grid":
+                monkeypatch.setenv("TDK_ALS_GRID", "1")
+            out = tdk.ffcp_als(ctx_t, dev_tensor(G, "f32"), [dev_tensor(u, "f64") for u in U], shape, (18, 18, 18),
+                               2, DT_CODE["f32"], R, max_sweeps=3000, tol=1e-7,
+                               B0=[dev_tensor(b, "f64") for b in B0], check_every=16)
+            monkeypatch.delenv("TDK_ALS_GRID", raising=False)
+            assert ctx_t.sync_status() == 0
+            runs[form] = out
+        assert runs["one-CTA"]["grid"] == 1 and runs["grid"]["grid"] > 1
+        s1, s2 = runs["one-CTA"]["sweeps"], runs["grid"]["sweeps"]
+        assert 30 <= s1 < 3000, s1  # a slow run, and one that stopped on the rule
+        assert s1 == s2, (s1, s2)
+        # the two kernels' FP32 iterates differ by rounding: their fits agree to
+        # a tenth of the stopping tolerance (1.1e-9 measured on seed 1)
+        assert abs(runs["one-CTA"]["fit_core"] - runs["grid"]["fit_core"]) < 1e-8
+        o = oracle.cp_als(G, B0, max_sweeps=s1, tol=0.0)
+        assert abs(runs["grid"]["fit_core"] - o["fit"]) < 1e-5
+    finally:
+        ctx_t.close()
+
+
+def test_fp32_nonneg_stopping_sweep_is_within_two_of_the_oracle(tdk, monkeypatch):
+    """The 200^4 workload's data model at 40 x 36 x 34 x 32, compressed to a
+    30^4 FP32 core; projected LS FFCP with R = 20 to a relative fit change
+    below 1e-7, by the grid kernel on the whole GPU (rows of H_n split over
+    CTAs) and on 24 CTAs (one CTA per row), against the FP64 oracle.  Here
+    the iterates themselves carry FP32 error: T_n of nonnegative factors is
+    ill-conditioned, and the rounding of H_n moves A_n by about 1e-5 (5.8e-5
+    between the two grids after 2 sweeps), so the fits of the two grids
+    differ by up to 1.3e-8 near the end and the stopping sweep by up to two.
+    Checked: each stops within two sweeps of the oracle, at a fit within
+    1e-6 of the oracle's (2.1e-7 measured: the fit still grows by about 1e-7
+    a sweep there)."""
+    shape, ranks, p, R = (40, 36, 34, 32), (20, 20, 20, 20), 10, 20
+    Y, W, _ = small_problem(shape, ranks, p, seed=3, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
+    ref = oracle.rand_tucker(Y, W)
+    A0 = synth.init_factors(shape, R, 33, dist="uniform")
+    o = oracle.cp_als_nonneg(ref["G"], ref["U"], A0, max_sweeps=2000, tol=1e-7)
+    ctx_t = tdk.Context(0, testing=True)
+    try:
+        for cap in [None, "24"]:
+            if cap:
+                monkeypatch.setenv("TDK_ALS_GRID", cap)
+            out = tdk.ffcp_als(ctx_t, dev_tensor(ref["G"], "f32"), [dev_tensor(u, "f64") for u in ref["U"]], shape,
+                               ranks, p, DT_CODE["f32"], R, max_sweeps=2000, tol=1e-7, nonneg=True,
+                               A0=[dev_tensor(a, "f64") for a in A0])
+            monkeypatch.delenv("TDK_ALS_GRID", raising=False)
+            assert ctx_t.sync_status() == 0
+            assert out["form"] == "grid"
+            assert (out["grid"] == 24) == (cap is not None), out["grid"]
+            assert abs(out["sweeps"] - o["sweeps"]) <= 2, (cap, out["sweeps"], o["sweeps"])
+            assert abs(out["fit_core"] - o["fit"]) < 1e-6, (cap, out["fit_core"], o["fit"])
+    finally:
+        ctx_t.close()
+
+
 @pytest.mark.parametrize("form", ["auto", "steps"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_nonneg_ffcp_on_the_4way_core_matches_oracle(tdk, ctx, dtype, form):

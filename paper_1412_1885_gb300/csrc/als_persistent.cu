@@ -78,6 +78,8 @@ struct PArgs {
   double* rpart;                // [grid] per-CTA residual partials
   unsigned long long* prof;     // optional: cycles per phase, CTA 0 (null = off)
   float* xprev;                 // grid kernel: [grid][N][R*R] each CTA's last FP32 inverse of T_n
+  int64_t cache_elems;          // > 0: each CTA keeps its core slice of every mode in shared memory
+  int64_t coff[TDK_MAX_MODES];  //   at these offsets of the cache (entries)
 };
 
 __device__ bool grid_sync(unsigned* bar, unsigned* status) {
@@ -134,6 +136,63 @@ struct GramAcc {
   }
   __device__ __forceinline__ T value() const { return s + c; }
 };
+
+// dst[e] = src[e] for e < n by the threads t < nt, eight loads in flight per
+// thread before their stores (a plain loop waits out the L2 latency once per
+// element: the loads cannot pass the shared-memory stores).  L2-coherent
+// loads: src may have been written by other CTAs before a grid barrier.
+template <class D, class S>
+__device__ __forceinline__ void stage_cg(D* dst, const S* src, int64_t n, int t, int nt) {
+  constexpr int U = 8;
+  for (int64_t b = t; b < n; b += (int64_t)U * nt) {
+    S v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = b + (int64_t)u * nt;
+      v[u] = e < n ? __ldcg(src + e) : S(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = b + (int64_t)u * nt;
+      if (e < n) dst[e] = (D)v[u];
+    }
+  }
+}
+
+// Gram matrix out = X^T X of X [rows x R] (row stride ldx) with compensated
+// sums, by the threads t < nt of the block: the entries r <= s only, two per
+// thread in flight, each written to (r, s) and (s, r).  A product and its
+// FMA error are the same with the operands swapped, so the result is the one
+// the full R x R loop gives, for half the work.
+template <class T>
+__device__ void gram_sym(const T* X, int64_t rows, int ldx, int R, T* out, int t, int nt) {
+  const int np = R * (R + 1) / 2;
+  auto decode = [](int q, int& r, int& s) {  // q = s (s + 1) / 2 + r, r <= s
+    s = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+    while (s * (s + 1) / 2 > q) --s;
+    while ((s + 1) * (s + 2) / 2 <= q) ++s;
+    r = q - s * (s + 1) / 2;
+  };
+  for (int q0 = t; q0 < np; q0 += 2 * nt) {
+    const int q1 = q0 + nt < np ? q0 + nt : q0;
+    int r0, s0, r1, s1;
+    decode(q0, r0, s0);
+    decode(q1, r1, s1);
+    GramAcc<T> a0, a1;
+    for (int64_t i = 0; i < rows; ++i) {
+      const T* x = X + i * ldx;
+      a0.add(x[r0], x[s0]);
+      a1.add(x[r1], x[s1]);
+    }
+    const T v0 = a0.value(), v1 = a1.value();
+    out[r0 * R + s0] = v0;
+    out[s0 * R + r0] = v0;
+    if (q0 + nt < np) {
+      out[r1 * R + s1] = v1;
+      out[s1 * R + r1] = v1;
+    }
+  }
+}
 
 // Float-float arithmetic (value = hi + lo) for the explicit residual of the
 // FP32 fit.  Products are split exactly by an FMA and every sum keeps its
@@ -199,7 +258,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
       __syncthreads();                                                           \
       if (threadIdx.x == 0) {                                                    \
         const unsigned long long t_ = clock64();                                 \
-        a.prof[(ph)] += t_ - prof_t;                                             \
+        s_pf[(ph)] += t_ - prof_t; /* shared: no global round trip per mark */   \
         prof_t = t_;                                                             \
       }                                                                          \
     }                                                                            \
@@ -208,9 +267,9 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 // shared-memory plan of the persistent kernel, every region 16-byte aligned
 template <class T>
 struct PLayout {
-  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_invf, o_yf,
-      o_lamt, o_ilamt, o_slice, o_work, o_egram, o_ns, total;
-  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram) {
+  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_yf,
+      o_lamt, o_ilamt, o_slice, o_work, o_egram, o_ns, o_cache, total;
+  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram, int64_t cache) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
       const size_t o = (off + 15) & ~size_t(15);
@@ -229,7 +288,6 @@ struct PLayout {
     o_lf = take(sizeof(float) * R * R);
     o_tid = take(sizeof(double) * R * R);
     o_gjs = take(sizeof(double) * 4 * RMAXP);
-    o_invf = take(sizeof(float) * RMAXP);
     o_yf = take(sizeof(float) * RMAXP);
     o_lamt = take(sizeof(T) * RMAXP);
     o_ilamt = take(sizeof(T) * RMAXP);
@@ -237,6 +295,7 @@ struct PLayout {
     o_work = take(sizeof(T) * (size_t)(Amax * R));
     o_egram = take(egram ? sizeof(T) * N * R * R : 0);  // Grams of A_p - U_p B_p
     o_ns = take(sizeof(float) * R * R);                 // Newton-Schulz iterate
+    o_cache = take(sizeof(T) * (size_t)cache);          // core slices kept across sweeps
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -374,22 +433,22 @@ __device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, 
 // Newton-Schulz refinement of an approximate inverse X of T (Schulz 1933;
 // Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., 14.5):
 //   E = I - T X,   X <- X + X E,
-// which squares the residual E at every step.  Started from the inverse of
-// the previous sweep's T_n, which moved only as far as the factors did, it
+// after which I - T X = E^2, so the Frobenius norm f of the residual at
+// least squares at every step once it is below 1.  Started from the inverse
+// of the previous sweep's T_n, which moved only as far as the factors did, it
 // reaches the FP32 floor in a few steps: two R x R products per step instead
 // of the R barrier-separated pivot steps of Gauss-Jordan elimination.
 // T, X0, X1, E: R x R row-major FP32 (shared memory), X0 holding the start;
 // computed by the nt threads of a group (named barrier bar_id) in 2 x 4
 // register tiles; red: nt / 32 floats.  Returns the buffer that holds the
-// inverse once max |E| <= tol (at most max_it updates), with that max |E| in
-// *dev, or null when the residual does not fall below 1/2 or stops shrinking
-// quadratically; the same outcome in every thread.
+// inverse once f <= tol (at most max_it updates), with f in *dev, or null
+// when f is not below 1 or stops falling; the same outcome in every thread.
 __device__ const float* ns_inverse(const float* T, float* X0, float* X1, float* E, float* red, int R, float tol,
                                    int max_it, float* dev, int t, int nt, int bar_id) {
   const int tr = (R + 1) / 2, tcn = (R + 3) / 4;
-  // C = I - A B (sub = true) or C = Xc + A B, and max |C - I| over the tiles
+  // C = I - A B (sub = true: returns the sum of squares of C) or C = Xc + A B
   auto prod = [&](const float* A, const float* B, const float* Xc, float* C, bool sub) -> float {
-    float mx = 0.f;
+    float sq = 0.f;
     for (int tile = t; tile < tr * tcn; tile += nt) {
       const int i0 = (tile / tcn) * 2, j0 = (tile % tcn) * 4;
       float acc[2][4] = {};
@@ -410,48 +469,53 @@ __device__ const float* ns_inverse(const float* T, float* X0, float* X1, float* 
         for (int v = 0; v < 4; ++v)
           if (i0 + u < R && j0 + v < R) {
             const int e = (i0 + u) * R + j0 + v;
-            const float id = (i0 + u == j0 + v) ? 1.f : 0.f;
-            const float cv = sub ? id - acc[u][v] : Xc[e] + acc[u][v];
-            C[e] = cv;
-            mx = fmaxf(mx, fabsf(sub ? cv : cv - id));
+            if (sub) {
+              const float cv = ((i0 + u == j0 + v) ? 1.f : 0.f) - acc[u][v];
+              C[e] = cv;
+              sq = fmaf(cv, cv, sq);
+            } else {
+              C[e] = Xc[e] + acc[u][v];
+            }
           }
     }
-    return mx;
+    return sq;
   };
-  auto group_max = [&](float v) -> float {
+  auto group_sum = [&](float v) -> float {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((t & 31) == 0) red[t >> 5] = v;
     tc::named_bar(bar_id, nt);
     float m = 0.f;
-    for (int w = 0; w < (nt >> 5); ++w) m = fmaxf(m, red[w]);
+    for (int w = 0; w < (nt >> 5); ++w) m += red[w];
     tc::named_bar(bar_id, nt);  // red is rewritten by the next call
     return m;
   };
   tc::named_bar(bar_id, nt);  // T and X0 written by the group
   float* X = X0;
   float* Xn = X1;
-  float d = group_max(prod(T, X, nullptr, E, true));
+  float f = sqrtf(group_sum(prod(T, X, nullptr, E, true)));
   for (int it = 0;; ++it) {
-    if (d <= tol) {
-      *dev = d;
+    if (f <= tol) {
+      *dev = f;
       return X;
     }
-    if (!(d < 0.5f) || it == max_it) return nullptr;
+    if (!(f < 1.f) || it == max_it) return nullptr;
     prod(X, E, X, Xn, false);
     tc::named_bar(bar_id, nt);
     float* tmp = X;
     X = Xn;
     Xn = tmp;
-    const float dn = group_max(prod(T, X, nullptr, E, true));
-    if (!(dn <= tol) && !(dn < 0.5f * d)) return nullptr;  // stalled above tol
-    d = dn;
+    const float fn = sqrtf(group_sum(prod(T, X, nullptr, E, true)));
+    if (!(fn <= tol) && !(fn < 0.5f * f)) return nullptr;  // stalled at the FP32 floor above tol
+    f = fn;
   }
 }
 
 template <class T>
 __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   unsigned long long prof_t = clock64();
+  __shared__ unsigned long long s_pf[16];  // cycles per phase (CTA 0, profiled runs)
+  if (threadIdx.x < 16) s_pf[threadIdx.x] = 0;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double s_irows[TDK_MAX_MODES];  // 1 / sqrt(rows of the updated factor of mode n)
   const int N = a.N, R = a.R;
@@ -463,7 +527,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   }
   PLayout<T> L;
   const bool leak32 = sizeof(T) == 4 && a.nonneg;  // FP32 nonneg: the out-of-subspace term from E_p
-  L.plan(N, R, btot, a.Qmax, a.Amax, leak32);
+  L.plan(N, R, btot, a.Qmax, a.Amax, leak32, a.cache_elems);
   T* Bs = reinterpret_cast<T*>(sm + L.o_bs);         // factors, packed
   T* egram = reinterpret_cast<T*>(sm + L.o_egram);   // [N][R*R] Grams of D_p = A_p - U_p B_p
   T* gram = reinterpret_cast<T*>(sm + L.o_gram);     // [N][R*R]
@@ -478,12 +542,12 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   double* Tid = reinterpret_cast<double*>(sm + L.o_tid);   // [R*R] FP64 inverse (fallback); Newton-Schulz X, E
   float* nsX1 = reinterpret_cast<float*>(sm + L.o_ns);       // [R*R] Newton-Schulz iterate
   double* gjs = reinterpret_cast<double*>(sm + L.o_gjs);   // Gauss-Jordan pivot rows / columns (two pairs)
-  float* invf = reinterpret_cast<float*>(sm + L.o_invf);
-  float* yf = reinterpret_cast<float*>(sm + L.o_yf);
+  float* yf = reinterpret_cast<float*>(sm + L.o_yf);       // [R] FP32 right-hand side of a solve step
   T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
   T* ilamT = reinterpret_cast<T*>(sm + L.o_ilamt);
   T* slice = reinterpret_cast<T*>(sm + L.o_slice);   // [Qmax]
   T* work = reinterpret_cast<T*>(sm + L.o_work);     // [Amax * R]
+  T* cache = reinterpret_cast<T*>(sm + L.o_cache);   // [cache_elems]
 
   const int tid = threadIdx.x;
   const int G = gridDim.x, c = blockIdx.x;
@@ -582,9 +646,11 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       // ---- 1b. inverse of T_n: FP32 by default (the solves are refined against
       //          T_n in FP64), FP64 if an FP32 pivot breaks down.  From the
       //          second sweep on, Newton-Schulz steps from the previous sweep's
-      //          inverse, Gauss-Jordan when they do not converge.  FP32 cores
-      //          take one refinement step after an inverse with residual below
-      //          2^-13 (solve error below 2^-26), FP64 cores two.
+      //          inverse, Gauss-Jordan when they do not converge.  The solve
+      //          error after k refinement steps is f^(k+1), f = ||I - T X||_F:
+      //          FP32 cores accept f <= 2^-9 and take one step when f <= 2^-13
+      //          (error below 2^-26), else two; FP64 cores accept f <= 2^-17
+      //          and take two.
       // (the HALS and multiplicative rules use T_n itself, not its inverse)
       bool use32 = true;
       int nref = 2;
@@ -596,15 +662,15 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           for (int e = tid; e < R * R; e += NTP) X0[e] = xp[e];
           float dev = 1.f;
           Xi = ns_inverse(Lf, X0, nsX1, X0 + R * R, reinterpret_cast<float*>(gjs), R,
-                          sizeof(T) == 4 ? 0x1p-13f : 0x1p-17f, 4, &dev, tid, NTP, 1);
+                          sizeof(T) == 4 ? 0x1p-9f : 0x1p-17f, 6, &dev, tid, NTP, 1);
           if (Xi) {
             for (int e = tid; e < R * R; e += NTP) Lf[e] = Xi[e];
-            if (sizeof(T) == 4) nref = 1;
+            if (sizeof(T) == 4 && dev <= 0x1p-13f) nref = 1;
           }
         }
         if (!Xi) {
           use32 = group_gj_inverse<float>(Lf, reinterpret_cast<float*>(gjs), R, 1.1920929e-7f, tid, NTP, 1) != 0;
-          if (a.prof && !use32 && blockIdx.x == 0 && tid == 0) a.prof[9] += 1;  // FP64 inverses
+          if (a.prof && !use32 && blockIdx.x == 0 && tid == 0) s_pf[9] += 1;  // FP64 inverses
           if (!use32) {
             for (int e = tid; e < R * R; e += NTP) Tid[e] = Tm[e];
             __syncthreads();
@@ -615,7 +681,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             }
           }
         } else if (a.prof && blockIdx.x == 0 && tid == 0) {
-          a.prof[10] += 1;  // Newton-Schulz inverses
+          s_pf[10] += 1;  // Newton-Schulz inverses
         }
         __syncthreads();
         if (use32) {
@@ -628,14 +694,20 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       __syncthreads();
       // x <- x T_n^{-1} for the row in xrow, block-parallel: one product with the
       // inverse, then nref refinement steps against T_n in FP64 (invd: residual)
+      // (the FP32 products read FP32 copies of the right-hand side and the
+      // residual: one conversion per entry instead of one per term, FP64
+      // conversions running at the FP64 rate)
       auto solve_row = [&]() {
-        for (int r = tid; r < R; r += NTP) hrow[r] = xrow[r];
+        for (int r = tid; r < R; r += NTP) {
+          hrow[r] = xrow[r];
+          yf[r] = (float)xrow[r];
+        }
         __syncthreads();
         for (int r = tid; r < R; r += NTP) {
           double acc = 0.0;
           if (use32) {
             float af = 0.f;
-            for (int q = 0; q < R; ++q) af = fmaf((float)hrow[q], Lf[q * R + r], af);
+            for (int q = 0; q < R; ++q) af = fmaf(yf[q], Lf[q * R + r], af);
             acc = af;
           } else {
             for (int q = 0; q < R; ++q) acc = fma(hrow[q], Tid[q * R + r], acc);
@@ -648,13 +720,14 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             double rr = hrow[q];
             for (int r = 0; r < R; ++r) rr = fma(-xrow[r], Tm[r * R + q], rr);
             invd[q] = rr;
+            yf[q] = (float)rr;
           }
           __syncthreads();
           for (int r = tid; r < R; r += NTP) {
             double acc = 0.0;
             if (use32) {
               float af = 0.f;
-              for (int q = 0; q < R; ++q) af = fmaf((float)invd[q], Lf[q * R + r], af);
+              for (int q = 0; q < R; ++q) af = fmaf(yf[q], Lf[q * R + r], af);
               acc = af;
             } else {
               for (int q = 0; q < R; ++q) acc = fma(invd[q], Tid[q * R + r], acc);
@@ -686,20 +759,45 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         const int lo = (int)((int64_t)part * R0o / Pn), hi = (int)((int64_t)(part + 1) * R0o / Pn);
         const int64_t rows0 = (int64_t)(hi - lo) * per0;
         // slice S[a1, l] of this part, one index decode per slice row
+        // slice S[a1, l] of this part, eight loads in flight per thread; with
+        // the cache on, this CTA's part is the same in every sweep and the
+        // slice is read from the core once
         const T* Gi = a.G + (int64_t)i * a.stride[n];
-        for (int64_t a1 = tid >> 5; a1 < rows0; a1 += NTP / 32) {
-          int64_t rem = a1 + (int64_t)lo * per0;
-          int64_t off = 0;
-          for (int k = no - 2; k >= 0; --k) {
-            const int p = oth[k];
-            off += (rem % a.Rt[p]) * a.stride[p];
-            rem /= a.Rt[p];
+        T* S = a.cache_elems > 0 ? cache + a.coff[n] : slice;
+        if (a.cache_elems == 0 || sweep == 1) {
+          // (32-bit index arithmetic: a slice of the core holds far fewer
+          // than 2^31 entries, and 64-bit division is a long subroutine)
+          constexpr int U = 8;
+          const int ns = (int)(rows0 * Rl);
+          for (int b = tid; b < ns; b += U * NTP) {
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int e = b + u * NTP;
+              v[u] = T(0);
+              if (e < ns) {
+                const int a1 = e / Rl;
+                const int l = e - a1 * Rl;
+                int rem = a1 + lo * (int)per0;
+                int off = 0;
+                for (int k = no - 2; k >= 0; --k) {
+                  const int p = oth[k];
+                  off += (rem % a.Rt[p]) * (int)a.stride[p];
+                  rem /= a.Rt[p];
+                }
+                off += l * (int)sl;
+                if (TDK_IN((int64_t)i * a.stride[n] + off, a.gnumel)) v[u] = Gi[off];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int e = b + u * NTP;
+              if (e < ns) S[e] = v[u];
+            }
           }
-          const T* src = Gi + off;
-          for (int l = tid & 31; l < Rl; l += 32)
-            slice[a1 * Rl + l] = TDK_IN((int64_t)i * a.stride[n] + off + l * sl, a.gnumel) ? src[l * sl] : T(0);
         }
         __syncthreads();
+        PROF_MARK(11);
         // work[a1, r] = sum_l S[a1, l] B_last[l, r] in 4 x 4 register tiles
         {
           const T* Bq = Bs + boff[last];
@@ -716,7 +814,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             for (int l = 0; l < Rl; ++l) {
               T s4[4], b4[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) s4[u] = (a0 + u < rows0) ? slice[(a0 + u) * Rl + l] : T(0);
+              for (int u = 0; u < 4; ++u) s4[u] = (a0 + u < rows0) ? S[(a0 + u) * Rl + l] : T(0);
 #pragma unroll
               for (int v = 0; v < 4; ++v) b4[v] = (r0 + v < R) ? Bq[l * R + r0 + v] : T(0);
 #pragma unroll
@@ -732,6 +830,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           }
         }
         __syncthreads();
+        PROF_MARK(12);
         // remaining other modes, last to first: out[b, r] = sum_m in[b*Rp + m, r] B_p[m, r];
         // the slowest one only over this part's range
         T* in = work;
@@ -755,6 +854,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           out = tt;
           rows = nrows;
         }
+        PROF_MARK(13);
         if (Pn == 1) {
           for (int r = tid; r < R; r += NTP) {
             if (TDK_IN((int64_t)i * R + r, (int64_t)Rn * R)) a.H[(int64_t)i * R + r] = in[r];
@@ -798,7 +898,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
 
       if (a.nonneg) {
         // rows of A_n = max(0, (U_n H_n) T_n^{-1}); H_n staged in shared memory
-        for (int e = tid; e < Rn * R; e += NTP) work[e] = __ldcg(a.H + e);
+        stage_cg(work, a.H, (int64_t)Rn * R, tid, NTP);
         __syncthreads();
         for (int64_t i = c; i < a.I[n]; i += G) {
           for (int r = tid; r < R; r += NTP) {
@@ -851,7 +951,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       // ---- 3. lambda, normalised factor and its Gram (every CTA, same order)
       const int64_t rows = a.nonneg ? a.I[n] : Rn;
       T* nb = slice;  // [rows x R] the update rows, then normalised (the slice is free here)
-      for (int64_t e = tid; e < rows * R; e += NTP) nb[e] = __ldcg(a.Bnew + e);
+      stage_cg(nb, a.Bnew, rows * R, tid, NTP);
       __syncthreads();
       {
         const int w = tid >> 5, lane = tid & 31;
@@ -877,14 +977,11 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         nb[e] = lamT[r] > T(0) ? nb[e] * ilamT[r] : inv_rows;
       }
       if (a.nonneg)  // U_n staged in the work buffer for B_n = U_n^T A_n
-        for (int64_t e = tid; e < rows * Rn; e += NTP) work[e] = a.Uf[n][e];
+        stage_cg(work, a.Uf[n], rows * Rn, tid, NTP);
       __syncthreads();
-      for (int e = tid; e < R * R; e += NTP) {
-        const int r = e / R, s2 = e % R;
-        GramAcc<T> acc;
-        for (int64_t i = 0; i < rows; ++i) acc.add(nb[i * R + r], nb[i * R + s2]);
-        gram[n * R * R + e] = acc.value();
-      }
+      PROF_MARK(14);
+      gram_sym<T>(nb, rows, R, R, gram + n * R * R, tid, NTP);
+      PROF_MARK(15);
       if (!a.nonneg) {
         for (int e = tid; e < Rn * R; e += NTP) Bs[boff[n] + e] = nb[e];
       } else {
@@ -897,12 +994,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
         if (c == 0)
           for (int64_t e = tid; e < rows * R; e += NTP) a.Aout[n][e] = (double)nb[e];
         __syncthreads();
-        for (int e = tid; e < R * R; e += NTP) {
-          const int r = e / R, s2 = e % R;
-          GramAcc<T> acc;
-          for (int q = 0; q < Rn; ++q) acc.add(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2]);
-          bgram[n * R * R + e] = acc.value();
-        }
+        gram_sym<T>(Bs + boff[n], Rn, R, R, bgram + n * R * R, tid, NTP);
         if (leak32) {
           // the part of the normalised A_n outside the Tucker subspace,
           // D_n = A_n - U_n B_n (U_n = Uf + Ulo), in place of the staged rows,
@@ -922,12 +1014,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             nb[e] = d.value();
           }
           __syncthreads();
-          for (int e = tid; e < R * R; e += NTP) {
-            const int r = e / R, s2 = e % R;
-            GramAcc<T> acc;
-            for (int64_t i = 0; i < rows; ++i) acc.add(nb[i * R + r], nb[i * R + s2]);
-            egram[n * R * R + e] = acc.value();
-          }
+          gram_sym<T>(nb, rows, R, R, egram + n * R * R, tid, NTP);
         }
       }
       __syncthreads();
@@ -1012,8 +1099,10 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
     // ||[[lambda; A]]||^2 from the Grams, in FP64; FP32 nonneg: the term
     // ||[[lambda; A]]||^2 - ||[[lambda; U B]]||^2 = sum lambda lambda (prod (BtB + E)
     // - prod BtB), the products in FP64 from the FP32 Grams
+    // (an FP32 unconstrained core needs neither: its fit is the explicit
+    // residual; FP64 arithmetic runs at a small fraction of the FP32 rate)
     double m2 = 0.0, lk = 0.0;
-    for (int e = tid; e < R * R; e += NTP) {
+    for (int e = tid; e < ((sizeof(T) == 8 || leak32) ? R * R : 0); e += NTP) {
       double v = (double)lamT[e / R] * (double)lamT[e % R];
       double va = v, vb = v;
       for (int p = 0; p < N; ++p) {
@@ -1030,6 +1119,12 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
     // [[A]] leaves the Tucker subspace (nonneg): add ||[[A]]||^2 - ||P [[A]]||^2,
     // P [[A]] = [[U B]] with B_p = U_p^T A_p
     const double leak = leak32 ? block_sum_d(lk, red) : 0.0;
+    // FP32 cores: the CTAs' residual partials, summed in a fixed order
+    double rsum = 0.0;
+    if (sizeof(T) == 4) {
+      for (int q = tid; q < G; q += NTP) rsum += __ldcg(a.rpart + q);
+      rsum = block_sum_d(rsum, red);
+    }
     PROF_MARK(6);
     // the scalar tail by one thread, shared through `red` (same value in every CTA)
     if (tid == 0) {
@@ -1037,8 +1132,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       if (sizeof(T) == 8) {
         res2 = fmax(0.0, nG2 - 2.0 * inner + model2);
       } else {
-        res2 = 0.0;
-        for (int q = 0; q < G; ++q) res2 += __ldcg(a.rpart + q);
+        res2 = rsum;
         if (a.nonneg) res2 += fmax(0.0, leak);
       }
       const double f = 1.0 - sqrt(res2) / sqrt(nG2);
@@ -1056,6 +1150,10 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       converged = 1;
       break;
     }
+  }
+  if (a.prof && blockIdx.x == 0) {
+    __syncthreads();
+    if (threadIdx.x < 16) a.prof[threadIdx.x] = s_pf[threadIdx.x];
   }
   if (sweep > a.max_sweeps) sweep = a.max_sweeps;
   if (c == 0) {
@@ -1086,7 +1184,7 @@ constexpr int NTS = 512;
 template <class T>
 struct SLayout {
   size_t o_g, o_b0, o_b1, o_b2, o_gram, o_w, o_h, o_x, o_res, o_tm, o_ld, o_lid, o_lf, o_lif, o_lam, o_lamt, o_red,
-      o_xp, o_ns, total;
+      o_xp, o_ns, o_resf, total;
   __host__ __device__ void plan(int R0, int R1, int R2, int R) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -1115,6 +1213,7 @@ struct SLayout {
     o_red = take(sizeof(double) * 32);
     o_xp = take(sizeof(float) * 3 * RR);  // last FP32 inverse of each T_n
     o_ns = take(sizeof(float) * RR);      // Newton-Schulz iterate
+    o_resf = take(sizeof(float) * (size_t)Rtm * R);  // FP32 copy of the refinement residual
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -1142,6 +1241,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   float* Lif = reinterpret_cast<float*>(sm + L.o_lif);
   float* Xp = reinterpret_cast<float*>(sm + L.o_xp);
   float* Xns = reinterpret_cast<float*>(sm + L.o_ns);
+  float* Resf = reinterpret_cast<float*>(sm + L.o_resf);
   double* lam = reinterpret_cast<double*>(sm + L.o_lam);
   T* lamT = reinterpret_cast<T*>(sm + L.o_lamt);
   double* red = reinterpret_cast<double*>(sm + L.o_red);
@@ -1205,9 +1305,10 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       pms(0);
       if (warp < 8) {
         // ---- invert T_n, warps 0-7: FP32 cores by Newton-Schulz steps from the
-        //      previous sweep's inverse (one refinement step of the solve
-        //      after it), else by FP32 Gauss-Jordan; FP64 cores and the
-        //      fallback by FP64 Gauss-Jordan
+        //      previous sweep's inverse (accepted at f <= 2^-9, one refinement
+        //      step of the solve when f <= 2^-13, as in the grid kernel), else
+        //      by FP32 Gauss-Jordan; FP64 cores and the fallback by FP64
+        //      Gauss-Jordan
         const unsigned long long pt0 = clock64();
         int mode = 0, nref = 2;
         if (!F64) {
@@ -1216,11 +1317,11 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
             float* X0 = reinterpret_cast<float*>(Ld);
             for (int e = tid; e < RR; e += 256) X0[e] = Xp[n * RR + e];
             float dev = 1.f;
-            Xi = ns_inverse(Lf, X0, Xns, X0 + RR, Lif, R, 0x1p-13f, 4, &dev, tid, 256, 2);
+            Xi = ns_inverse(Lf, X0, Xns, X0 + RR, Lif, R, 0x1p-9f, 6, &dev, tid, 256, 2);
             if (Xi) {
               for (int e = tid; e < RR; e += 256) Lf[e] = Xi[e];
               mode = 1;
-              nref = 1;
+              nref = dev <= 0x1p-13f ? 1 : 2;
             }
           }
           if (!Xi && group_gj_inverse_smem<float>(Lf, Lif, R, 1.1920929e-7f, tid, 256, 2)) mode = 1;
@@ -1353,6 +1454,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
           double rr = (double)H[e];
           for (int r = 0; r < R; ++r) rr = fma(-X[i * R + r], Tm[r * R + c], rr);
           Res[e] = rr;
+          Resf[e] = (float)rr;  // one conversion per entry, not per term
         }
         __syncthreads();
         for (int e = tid; e < Rn * R; e += NTS) {
@@ -1360,7 +1462,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
           double acc = 0.0;
           if (f32) {
             float af = 0.f;
-            for (int r = 0; r < R; ++r) af = fmaf((float)Res[i * R + r], Lf[r * R + c], af);
+            for (int r = 0; r < R; ++r) af = fmaf(Resf[i * R + r], Lf[r * R + c], af);
             acc = af;
           } else {
             for (int r = 0; r < R; ++r) acc = fma(Res[i * R + r], Ld[r * R + c], acc);
@@ -1398,9 +1500,10 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       pms(4);
     }
     if (singular) break;
-    // ---- fit
+    // ---- fit (||[[lambda; B]]||^2 for FP64 cores only: FP32 cores take the
+    //      explicit residual)
     double m2 = 0.0;
-    for (int e = tid; e < RR; e += NTS) {
+    for (int e = tid; e < (F64 ? RR : 0); e += NTS) {
       double v = lam[e / R] * lam[e % R];
       for (int p = 0; p < 3; ++p) v *= (double)gram[p * RR + e];
       m2 += v;
@@ -1497,19 +1600,17 @@ __global__ void norm2_core(const T* __restrict__ G, int64_t n, double* __restric
     }
   } else {
     // FP32 core: each square is split exactly into hi + lo (an FMA gives the
-    // rounding error of the product) and both are summed with compensation in
-    // FP32, since FP64 arithmetic is scarce on this GPU; FP64 only across threads
-    float hs = 0.f, c = 0.f;
+    // rounding error of the product) and summed in float-float, since FP64
+    // arithmetic is scarce on this GPU; FP64 only across threads.  (A Kahan
+    // sum that feeds its correction back into the next addend loses up to
+    // half an FP32 unit of every square: 7.8e-10 of ||G||^2 on a 20^3 core.)
+    FFAcc acc;
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       const float v = (float)G[e];
       const float sq = v * v;
-      const float sq_lo = fmaf(v, v, -sq);
-      const float y = sq - c;
-      const float t = hs + y;
-      c = ((t - hs) - y) - sq_lo;
-      hs = t;
+      acc.add(sq, fmaf(v, v, -sq));
     }
-    s = (double)hs - (double)c;
+    s = acc.value();
   }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -1545,6 +1646,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   // the row slices of H_n are indexed by the other modes but the last one:
   // with two modes there are none, and the multi-kernel form takes over
   if (N < 3) return TDK_ENOTSUP;
+  if (g.core_numel >= ((int64_t)1 << 31)) return TDK_ENOTSUP;  // the kernel indexes the core in 32 bits
   PArgs<T> a{};
   a.N = N;
   a.R = R;
@@ -1582,8 +1684,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   if (a.nonneg)
     for (int n = 0; n < N; ++n) a.Amax = std::max<int64_t>(a.Amax, (g.I[n] * g.Rt[n] + R - 1) / R);
   PLayout<T> lay;
-  lay.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg);
-  const size_t smem = lay.total + 64;
+  lay.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg, 0);
+  size_t smem = lay.total + 64;
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   auto kern = als_persistent_kernel<T>;
   TDK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1603,6 +1705,41 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   const int grid_cap = getenv("TDK_ALS_GRID") ? atoi(getenv("TDK_ALS_GRID")) : 0;
   if (grid_cap > 1) grid = std::min(grid, grid_cap);
 #endif
+  // Core slices kept in shared memory across sweeps, when every CTA has at
+  // most one part of H_n per mode (the same part every sweep, as the kernel
+  // splits the rows) and the slices fit beside the rest without lowering
+  // the CTAs per SM.
+  {
+    int64_t cache = 0;
+    bool one_part = true;
+    for (int n = 0; n < N; ++n) {
+      int oth[TDK_MAX_MODES], no = 0;
+      for (int p = 0; p < N; ++p)
+        if (p != n) oth[no++] = p;
+      const int Rn = g.Rt[n], Rl = g.Rt[oth[no - 1]], R0o = g.Rt[oth[0]];
+      const int64_t per0 = g.core_numel / Rn / Rl / R0o;
+      const int Pn = std::max(1, std::min(grid / Rn, R0o));
+      if ((int64_t)Rn * Pn > grid) one_part = false;
+      a.coff[n] = cache;
+      cache += ((int64_t)(R0o + Pn - 1) / Pn * per0 * Rl + 3) / 4 * 4;
+    }
+    if (one_part && cache > 0) {
+      PLayout<T> lc;
+      lc.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg, cache);
+      int per_sm_c = 0;
+      if (lc.total + 64 <= (size_t)ctx->max_smem_optin &&
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(lc.total + 64)) ==
+              cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kern, NTP, lc.total + 64) == cudaSuccess &&
+          per_sm_c >= per_sm) {
+        a.cache_elems = cache;
+        smem = lc.total + 64;
+      } else {
+        cudaGetLastError();
+        TDK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      }
+    }
+  }
 
   Planner pl;
   pl.take<T>((size_t)(a.nonneg ? std::max(Rtmax, Imax) : Rtmax) * R);
@@ -1713,6 +1850,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
                               "barrier3", "fit"};
       fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);
       for (int i = 0; i < 7; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
+      fprintf(stderr, "\n  inside H_rows: slice=%.3f first_product=%.3f other_products=%.3f (H_rows above: the"
+              " solve and stores); inside normalise: norms+scale=%.3f gram=%.3f", hp[11] / 1e6, hp[12] / 1e6,
+              hp[13] / 1e6, hp[14] / 1e6, hp[15] / 1e6);
     }
     fprintf(stderr, "\n");
   }

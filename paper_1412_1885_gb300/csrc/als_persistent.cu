@@ -86,29 +86,39 @@ __device__ bool grid_sync(unsigned* bar, unsigned* status) {
   __syncthreads();
   __shared__ int fail;
   if (threadIdx.x == 0) {
+    // the arrival counter only grows (zeroed before the launch): barrier k
+    // completes when it reaches (k + 1) * gridDim.x, so the last CTA to
+    // arrive releases the others with its own increment and no reset
     fail = 0;
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = tc::globaltimer();
-      while (*gen == g) {
-        if (tc::globaltimer() - t0 > tc::WAIT_LIMIT_NS) {
-          atomicOr(status, TDK_STATUS_TIMEOUT);
-          fail = 1;
-          break;
-        }
+    const unsigned target = (arrived / gridDim.x + 1u) * gridDim.x;
+    volatile unsigned* cnt = bar;
+    const unsigned long long t0 = tc::globaltimer();
+    while ((int)(*cnt - target) < 0) {
+      if (tc::globaltimer() - t0 > tc::WAIT_LIMIT_NS) {
+        atomicOr(status, TDK_STATUS_TIMEOUT);
+        fail = 1;
+        break;
       }
     }
     __threadfence();
   }
   __syncthreads();
   return fail == 0;
+}
+
+// FP32 -> FP64 by integer operations, which run on the integer pipes (FP64
+// instructions, conversions included, issue at a small fraction of the FP32
+// rate on this GPU): exact for zeros, normal numbers, infinities and NaNs;
+// subnormal inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_int(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (ex == 0u) return (u & 0x7fffffu) ? (double)x : __longlong_as_double((long long)sign);
+  const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
 
 // block-wide FP64 sum, the same value (same order) in every thread; the warp
@@ -637,8 +647,28 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           if (p != n) vt *= gram[p * R * R + e];
         Lf[e] = (float)vt;
         double v = 1.0;
-        for (int p = 0; p < N; ++p)
-          if (p != n) v *= (double)gram[p * R * R + e];
+        if (sizeof(T) == 4) {
+          // the product of the FP32 entries in float-float (exact for two
+          // factors, 2^-48 for more), one FP64 addition to join the halves
+          float h = 0.f, l = 0.f;
+          bool first = true;
+          for (int p = 0; p < N; ++p) {
+            if (p == n) continue;
+            const float y = (float)gram[p * R * R + e];
+            if (first) {
+              h = y;
+              first = false;
+            } else {
+              const float ph = h * y;
+              l = fmaf(l, y, fmaf(h, y, -ph));
+              h = ph;
+            }
+          }
+          v = f2d_int(h) + f2d_int(l);
+        } else {
+          for (int p = 0; p < N; ++p)
+            if (p != n) v *= (double)gram[p * R * R + e];
+        }
         Tm[e] = v;
       }
       __syncthreads();

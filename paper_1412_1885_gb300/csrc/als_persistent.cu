@@ -245,6 +245,33 @@ __device__ __forceinline__ void ff_add_sq_diff(FFAcc& acc, float g, float xh, fl
   acc.add(q, fmaf(2.f * dh, dl, fmaf(dh, dh, -q)));
 }
 
+// block-wide sum of float-float accumulators, the same value in every
+// thread: a butterfly over each warp in float-float, the warps' pairs added
+// in order by one thread, one conversion to FP64 at the end (the FP64 form
+// of the same sum spends most of its time in FP64 shuffles and additions)
+__device__ __forceinline__ double block_sum_ff(FFAcc a, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+    a.add(s2, c2);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* rf = reinterpret_cast<float2*>(red);
+  __syncthreads();
+  if (lane == 0) rf[w] = make_float2(a.s, a.c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    FFAcc t;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t.add(rf[i].x, rf[i].y);
+    red[0] = t.value();
+  }
+  __syncthreads();
+  const double v = red[0];
+  __syncthreads();
+  return v;
+}
+
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1115,7 +1142,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             ff_add_sq_diff(racc, (float)a.G[e], x.s, x.c);
           }
           }
-          double s2 = block_sum_d(racc.value(), red);
+          double s2 = block_sum_ff(racc, red);
           if (tid == 0) a.rpart[c] = s2;
         }
       }
@@ -1145,15 +1172,23 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       m2 += v;
       lk += va - vb;
     }
-    const double model2 = block_sum_d(m2, red);
+    const double model2 = sizeof(T) == 8 ? block_sum_d(m2, red) : 0.0;
     // [[A]] leaves the Tucker subspace (nonneg): add ||[[A]]||^2 - ||P [[A]]||^2,
     // P [[A]] = [[U B]] with B_p = U_p^T A_p
     const double leak = leak32 ? block_sum_d(lk, red) : 0.0;
-    // FP32 cores: the CTAs' residual partials, summed in a fixed order
+    // FP32 cores: the CTAs' residual partials, summed in a fixed order by
+    // the first warp
     double rsum = 0.0;
     if (sizeof(T) == 4) {
-      for (int q = tid; q < G; q += NTP) rsum += __ldcg(a.rpart + q);
-      rsum = block_sum_d(rsum, red);
+      if (tid < 32) {
+        double v = 0.0;
+        for (int q = tid; q < G; q += 32) v += __ldcg(a.rpart + q);
+        v = warp_sum(v);
+        if (tid == 0) red[0] = v;
+      }
+      __syncthreads();
+      rsum = red[0];
+      __syncthreads();
     }
     PROF_MARK(6);
     // the scalar tail by one thread, shared through `red` (same value in every CTA)
@@ -1243,7 +1278,7 @@ struct SLayout {
     o_red = take(sizeof(double) * 32);
     o_xp = take(sizeof(float) * 3 * RR);  // last FP32 inverse of each T_n
     o_ns = take(sizeof(float) * RR);      // Newton-Schulz iterate
-    o_resf = take(sizeof(float) * (size_t)Rtm * R);  // FP32 copy of the refinement residual
+    o_resf = take(sizeof(float) * (size_t)(Rtm + 1) * R);  // FP32 residual / solution, reciprocal norms
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -1255,6 +1290,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   const int Rt[3] = {a.Rt[0], a.Rt[1], a.Rt[2]};
   const int M01 = Rt[0] * Rt[1];
   const int nel = M01 * Rt[2];
+  const int Rtm = Rt[0] > Rt[1] ? (Rt[0] > Rt[2] ? Rt[0] : Rt[2]) : (Rt[1] > Rt[2] ? Rt[1] : Rt[2]);
   SLayout<T> L;
   L.plan(Rt[0], Rt[1], Rt[2], R);
   T* Gc = reinterpret_cast<T*>(sm + L.o_g);
@@ -1324,12 +1360,19 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       pms(7);
       // ---- T_n (FP64 and FP32 copies)
       for (int e = tid; e < RR; e += NTS) {
-        double v = 1.0;
-        for (int p = 0; p < 3; ++p)
-          if (p != n) v *= (double)gram[p * RR + e];
-        Tm[e] = v;
-        if (F64) Ld[e] = v;
-        Lf[e] = (float)v;
+        const int p0 = n == 0 ? 1 : 0, p1 = n == 2 ? 1 : 2;
+        if (F64) {
+          const double v = (double)gram[p0 * RR + e] * (double)gram[p1 * RR + e];
+          Tm[e] = v;
+          Ld[e] = v;
+          Lf[e] = (float)v;
+        } else {
+          // the exact product of two FP32 entries as hi + lo, joined in FP64
+          const float ga = (float)gram[p0 * RR + e], gb = (float)gram[p1 * RR + e];
+          const float ph = ga * gb;
+          Tm[e] = f2d_int(ph) + f2d_int(fmaf(ga, gb, -ph));
+          Lf[e] = ph;
+        }
       }
       __syncthreads();
       pms(0);
@@ -1502,22 +1545,42 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
         __syncthreads();
       }
       pms(3);
-      // ---- lambda (column norms), normalised B_n and its Gram
-      for (int r = warp; r < R; r += NTS / 32) {
-        double s2 = 0.0;
-        for (int i = tid & 31; i < Rn; i += 32) s2 = fma(X[i * R + r], X[i * R + r], s2);
-        s2 = warp_sum(s2);
-        if ((tid & 31) == 0) {
-          lam[r] = sqrt(s2);
-          lamT[r] = (T)lam[r];
-          Res[r] = lam[r] > 0.0 ? 1.0 / lam[r] : 0.0;  // reciprocal (Res is free here)
+      // ---- lambda (column norms), normalised B_n and its Gram (FP32 cores:
+      //      in FP32 from the solution rounded once, as B_n is stored)
+      if (F64) {
+        for (int r = warp; r < R; r += NTS / 32) {
+          double s2 = 0.0;
+          for (int i = tid & 31; i < Rn; i += 32) s2 = fma(X[i * R + r], X[i * R + r], s2);
+          s2 = warp_sum(s2);
+          if ((tid & 31) == 0) {
+            lam[r] = sqrt(s2);
+            lamT[r] = (T)lam[r];
+            Res[r] = lam[r] > 0.0 ? 1.0 / lam[r] : 0.0;  // reciprocal (Res is free here)
+          }
+        }
+      } else {
+        for (int e = tid; e < Rn * R; e += NTS) Resf[e] = (float)X[e];
+        __syncthreads();
+        for (int r = warp; r < R; r += NTS / 32) {
+          float s2 = 0.f;
+          for (int i = tid & 31; i < Rn; i += 32) s2 = fmaf(Resf[i * R + r], Resf[i * R + r], s2);
+          s2 = warp_sum(s2);
+          if ((tid & 31) == 0) {
+            const float l = sqrtf(s2);
+            lam[r] = f2d_int(l);
+            lamT[r] = (T)l;
+            Resf[Rtm * R + r] = l > 0.f ? 1.f / l : 0.f;
+          }
         }
       }
       __syncthreads();
       const T inv_rows = s_irows[n];
       for (int e = tid; e < Rn * R; e += NTS) {
         const int r = e % R;
-        B[n][e] = lam[r] > 0.0 ? (T)(X[e] * Res[r]) : inv_rows;
+        if (F64)
+          B[n][e] = lam[r] > 0.0 ? (T)(X[e] * Res[r]) : inv_rows;
+        else
+          B[n][e] = lamT[r] > T(0) ? (T)(Resf[e] * Resf[Rtm * R + r]) : inv_rows;
       }
       __syncthreads();
       for (int e = tid; e < RR; e += NTS) {
@@ -1538,7 +1601,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
       for (int p = 0; p < 3; ++p) v *= (double)gram[p * RR + e];
       m2 += v;
     }
-    const double model2 = block_sum_d(m2, red);
+    const double model2 = F64 ? block_sum_d(m2, red) : 0.0;
     double res2;
     if (F64) {
       // <G, [[lambda; B]]> from H_3 (Gram identity, as the FP64 oracle)
@@ -1583,7 +1646,7 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
             if (m0 + u < M01 && k0 + v < Rt[2])
               ff_add_sq_diff(racc, (float)Gc[(m0 + u) * Rt[2] + k0 + v], acc[u][v].s, acc[u][v].c);
       }
-      res2 = block_sum_d(racc.value(), red);
+      res2 = block_sum_ff(racc, red);
     }
     pms(5);
     // the scalar tail by one thread, shared through `red`

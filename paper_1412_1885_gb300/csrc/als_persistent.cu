@@ -304,7 +304,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 // shared-memory plan of the persistent kernel, every region 16-byte aligned
 template <class T>
 struct PLayout {
-  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_yf,
+  size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_part, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_yf,
       o_lamt, o_ilamt, o_slice, o_work, o_egram, o_ns, o_cache, total;
   __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram, int64_t cache) {
     size_t off = 0;
@@ -318,6 +318,7 @@ struct PLayout {
     o_bgram = take(sizeof(T) * N * R * R);
     o_tm = take(sizeof(double) * R * R);
     o_invd = take(sizeof(double) * RMAXP);
+    o_part = take(sizeof(double) * 8 * RMAXP);  // partial sums of the solve's products
     o_lam = take(sizeof(double) * RMAXP);
     o_xrow = take(sizeof(double) * RMAXP);
     o_hrow = take(sizeof(double) * RMAXP);
@@ -571,6 +572,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   T* bgram = reinterpret_cast<T*>(sm + L.o_bgram);   // [N][R*R] (nonneg: Grams of B_p)
   double* Tm = reinterpret_cast<double*>(sm + L.o_tm);  // [R*R] T_n (FP64)
   double* invd = reinterpret_cast<double*>(sm + L.o_invd);
+  double* spart = reinterpret_cast<double*>(sm + L.o_part);  // [8][RMAXP]
   double* lam = reinterpret_cast<double*>(sm + L.o_lam);
   double* xrow = reinterpret_cast<double*>(sm + L.o_xrow);
   double* hrow = reinterpret_cast<double*>(sm + L.o_hrow);  // right-hand side
@@ -664,6 +666,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   for (sweep = 1; sweep <= a.max_sweeps && ok; ++sweep) {
     double inner = 0.0;
     for (int n = 0; n < N && ok; ++n) {
+      PROF_MARK(8);
       const int Rn = a.Rt[n];
       // ---- 1. T_n (FP64) and a Cholesky factor: FP32 by default, the solves
       //         then refined against T_n in FP64; FP64 factor in place if an
@@ -754,43 +757,61 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       // (the FP32 products read FP32 copies of the right-hand side and the
       // residual: one conversion per entry instead of one per term, FP64
       // conversions running at the FP64 rate)
+      // Each product of the solve (R outputs, R terms) runs on SP * R threads:
+      // part p of output o sums its range of terms, and the parts are added
+      // in order, which keeps the dependent FMA chains (FP64 ones above all)
+      // short.
+      const int SP = R >= NTP ? 1 : (NTP / R > 8 ? 8 : NTP / R);
+      float* partf = reinterpret_cast<float*>(spart);
+      auto prod32 = [&](const float* v, const float* M) {  // partf[o] <- sum_q v[q] M[q, o] (FP32)
+        if (tid < SP * R) {
+          const int o = tid % R, pp = tid / R;
+          float acc = 0.f;
+          for (int q = pp * R / SP; q < (pp + 1) * R / SP; ++q) acc = fmaf(v[q], M[q * R + o], acc);
+          partf[pp * RMAXP + o] = acc;
+        }
+        __syncthreads();
+      };
+      auto prod64 = [&](const double* v, const double* M) {  // spart[o] <- sum_q v[q] M[q, o] (FP64)
+        if (tid < SP * R) {
+          const int o = tid % R, pp = tid / R;
+          double acc = 0.0;
+          for (int q = pp * R / SP; q < (pp + 1) * R / SP; ++q) acc = fma(v[q], M[q * R + o], acc);
+          spart[pp * RMAXP + o] = acc;
+        }
+        __syncthreads();
+      };
+      auto sum32 = [&](int o) {
+        float s2 = 0.f;
+        for (int pp = 0; pp < SP; ++pp) s2 += partf[pp * RMAXP + o];
+        return s2;
+      };
+      auto sum64 = [&](int o) {
+        double s2 = 0.0;
+        for (int pp = 0; pp < SP; ++pp) s2 += spart[pp * RMAXP + o];
+        return s2;
+      };
       auto solve_row = [&]() {
         for (int r = tid; r < R; r += NTP) {
           hrow[r] = xrow[r];
           yf[r] = (float)xrow[r];
         }
         __syncthreads();
-        for (int r = tid; r < R; r += NTP) {
-          double acc = 0.0;
-          if (use32) {
-            float af = 0.f;
-            for (int q = 0; q < R; ++q) af = fmaf(yf[q], Lf[q * R + r], af);
-            acc = af;
-          } else {
-            for (int q = 0; q < R; ++q) acc = fma(hrow[q], Tid[q * R + r], acc);
-          }
-          xrow[r] = acc;
-        }
+        if (use32) prod32(yf, Lf);
+        else prod64(hrow, Tid);
+        for (int r = tid; r < R; r += NTP) xrow[r] = use32 ? (double)sum32(r) : sum64(r);
         __syncthreads();
         for (int it = 0; it < nref; ++it) {
+          prod64(xrow, Tm);  // (x T_n)[q]
           for (int q = tid; q < R; q += NTP) {
-            double rr = hrow[q];
-            for (int r = 0; r < R; ++r) rr = fma(-xrow[r], Tm[r * R + q], rr);
+            const double rr = hrow[q] - sum64(q);
             invd[q] = rr;
             yf[q] = (float)rr;
           }
           __syncthreads();
-          for (int r = tid; r < R; r += NTP) {
-            double acc = 0.0;
-            if (use32) {
-              float af = 0.f;
-              for (int q = 0; q < R; ++q) af = fmaf(yf[q], Lf[q * R + r], af);
-              acc = af;
-            } else {
-              for (int q = 0; q < R; ++q) acc = fma(invd[q], Tid[q * R + r], acc);
-            }
-            xrow[r] += acc;
-          }
+          if (use32) prod32(yf, Lf);
+          else prod64(invd, Tid);
+          for (int r = tid; r < R; r += NTP) xrow[r] += use32 ? (double)sum32(r) : sum64(r);
           __syncthreads();
         }
       };
@@ -1944,8 +1965,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
       fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);
       for (int i = 0; i < 7; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
       fprintf(stderr, "\n  inside H_rows: slice=%.3f first_product=%.3f other_products=%.3f (H_rows above: the"
-              " solve and stores); inside normalise: norms+scale=%.3f gram=%.3f", hp[11] / 1e6, hp[12] / 1e6,
-              hp[13] / 1e6, hp[14] / 1e6, hp[15] / 1e6);
+              " solve and stores); inside normalise: norms+scale=%.3f gram=%.3f; sweep loop and fit tail=%.3f",
+              hp[11] / 1e6, hp[12] / 1e6, hp[13] / 1e6, hp[14] / 1e6, hp[15] / 1e6, hp[8] / 1e6);
     }
     fprintf(stderr, "\n");
   }

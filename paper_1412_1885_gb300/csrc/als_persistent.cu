@@ -36,6 +36,7 @@ namespace {
 constexpr int RMAXP = TDK_MAX_RANK;
 constexpr int NTP = 256;
 constexpr int ST_TIMEOUT = 0x100, ST_NEEDPINV = 0x200;
+constexpr int NS_MAX_IT = 8;  // Newton-Schulz updates before Gauss-Jordan takes over
 
 struct PState {
   int sweeps;
@@ -78,6 +79,7 @@ struct PArgs {
   double* rpart;                // [grid] per-CTA residual partials
   unsigned long long* prof;     // optional: cycles per phase, CTA 0 (null = off)
   float* xprev;                 // grid kernel: [grid][N][R*R] each CTA's last FP32 inverse of T_n
+  float ns_gate;                // Newton-Schulz start accepted while ||I - T X||_F < ns_gate
   int64_t cache_elems;          // > 0: each CTA keeps its core slice of every mode in shared memory
   int64_t coff[TDK_MAX_MODES];  //   at these offsets of the cache (entries)
 };
@@ -479,10 +481,11 @@ __device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, 
 // T, X0, X1, E: R x R row-major FP32 (shared memory), X0 holding the start;
 // computed by the nt threads of a group (named barrier bar_id) in 2 x 4
 // register tiles; red: nt / 32 floats.  Returns the buffer that holds the
-// inverse once f <= tol (at most max_it updates), with f in *dev, or null
-// when f is not below 1 or stops falling; the same outcome in every thread.
+// inverse once f <= tol (at most max_it updates), with f in *dev and the
+// updates in *nit, or null when the start's f is not below `gate` or f stops
+// falling; the same outcome in every thread.
 __device__ const float* ns_inverse(const float* T, float* X0, float* X1, float* E, float* red, int R, float tol,
-                                   int max_it, float* dev, int t, int nt, int bar_id) {
+                                   int max_it, float gate, float* dev, int* nit, int t, int nt, int bar_id) {
   const int tr = (R + 1) / 2, tcn = (R + 3) / 4;
   // C = I - A B (sub = true: returns the sum of squares of C) or C = Xc + A B
   auto prod = [&](const float* A, const float* B, const float* Xc, float* C, bool sub) -> float {
@@ -533,18 +536,24 @@ __device__ const float* ns_inverse(const float* T, float* X0, float* X1, float* 
   float* Xn = X1;
   float f = sqrtf(group_sum(prod(T, X, nullptr, E, true)));
   for (int it = 0;; ++it) {
-    if (f <= tol) {
-      *dev = f;
-      return X;
-    }
-    if (!(f < 1.f) || it == max_it) return nullptr;
+    *nit = it;
+    *dev = f;
+    if (f <= tol) return X;
+    if (!(f < gate) || it == max_it) return nullptr;
     prod(X, E, X, Xn, false);
     tc::named_bar(bar_id, nt);
     float* tmp = X;
     X = Xn;
     Xn = tmp;
     const float fn = sqrtf(group_sum(prod(T, X, nullptr, E, true)));
-    if (!(fn <= tol) && !(fn < 0.5f * f)) return nullptr;  // stalled at the FP32 floor above tol
+    // below 1 the residual at least squares: stop when it falls by less than
+    // half (the FP32 floor); above 1, while it falls at all (its spectral
+    // radius, which squares, may be below 1 with a larger Frobenius norm)
+    if (!(fn <= tol) && !(fn < (f < 1.f ? 0.5f * f : f))) {
+      *nit = it + 1;
+      *dev = fn;
+      return nullptr;
+    }
     f = fn;
   }
 }
@@ -552,8 +561,8 @@ __device__ const float* ns_inverse(const float* T, float* X0, float* X1, float* 
 template <class T>
 __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   unsigned long long prof_t = clock64();
-  __shared__ unsigned long long s_pf[16];  // cycles per phase (CTA 0, profiled runs)
-  if (threadIdx.x < 16) s_pf[threadIdx.x] = 0;
+  __shared__ unsigned long long s_pf[32];  // cycles per phase and counts (CTA 0, profiled runs)
+  if (threadIdx.x < 32) s_pf[threadIdx.x] = 0;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double s_irows[TDK_MAX_MODES];  // 1 / sqrt(rows of the updated factor of mode n)
   const int N = a.N, R = a.R;
@@ -721,8 +730,13 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           float* X0 = reinterpret_cast<float*>(Tid);
           for (int e = tid; e < R * R; e += NTP) X0[e] = xp[e];
           float dev = 1.f;
+          int nit = 0;
           Xi = ns_inverse(Lf, X0, nsX1, X0 + R * R, reinterpret_cast<float*>(gjs), R,
-                          sizeof(T) == 4 ? 0x1p-9f : 0x1p-17f, 6, &dev, tid, NTP, 1);
+                          sizeof(T) == 4 ? 0x1p-9f : 0x1p-17f, NS_MAX_IT, a.ns_gate, &dev, &nit, tid, NTP, 1);
+          if (a.prof && blockIdx.x == 0 && tid == 0) {
+            s_pf[18] += nit;
+            if (!Xi) s_pf[nit == 0 ? 16 : 17] += 1;  // rejected at the start / stalled
+          }
           if (Xi) {
             for (int e = tid; e < R * R; e += NTP) Lf[e] = Xi[e];
             if (sizeof(T) == 4 && dev <= 0x1p-13f) nref = 1;
@@ -1239,7 +1253,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   }
   if (a.prof && blockIdx.x == 0) {
     __syncthreads();
-    if (threadIdx.x < 16) a.prof[threadIdx.x] = s_pf[threadIdx.x];
+    if (threadIdx.x < 32) a.prof[threadIdx.x] = s_pf[threadIdx.x];
   }
   if (sweep > a.max_sweeps) sweep = a.max_sweeps;
   if (c == 0) {
@@ -1411,7 +1425,8 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
             float* X0 = reinterpret_cast<float*>(Ld);
             for (int e = tid; e < RR; e += 256) X0[e] = Xp[n * RR + e];
             float dev = 1.f;
-            Xi = ns_inverse(Lf, X0, Xns, X0 + RR, Lif, R, 0x1p-9f, 6, &dev, tid, 256, 2);
+            int nit = 0;
+            Xi = ns_inverse(Lf, X0, Xns, X0 + RR, Lif, R, 0x1p-9f, NS_MAX_IT, a.ns_gate, &dev, &nit, tid, 256, 2);
             if (Xi) {
               for (int e = tid; e < RR; e += 256) Lf[e] = Xi[e];
               mode = 1;
@@ -1764,6 +1779,10 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   PArgs<T> a{};
   a.N = N;
   a.R = R;
+  a.ns_gate = 1.f;
+#ifdef TDK_TESTING
+  if (const char* e = getenv("TDK_ALS_NS_GATE")) a.ns_gate = (float)atof(e);
+#endif
   // the l1 form updates the factors as A_n like the nonnegative forms
   a.nonneg = (o->nonneg || o->l1 > 0.0) ? 1 : 0;
   a.nn_rule = o->nonneg == TDK_NONNEG_HALS ? 1 : (o->nonneg == TDK_NONNEG_MU ? 2 : 0);
@@ -1903,8 +1922,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   const bool want_prof = false;
 #endif
   if (want_prof) {
-    TDK_CUDA_TRY(cudaMallocAsync((void**)&prof, 16 * sizeof(unsigned long long), ctx->stream));
-    TDK_CUDA_TRY(cudaMemsetAsync(prof, 0, 16 * sizeof(unsigned long long), ctx->stream));
+    TDK_CUDA_TRY(cudaMallocAsync((void**)&prof, 32 * sizeof(unsigned long long), ctx->stream));
+    TDK_CUDA_TRY(cudaMemsetAsync(prof, 0, 32 * sizeof(unsigned long long), ctx->stream));
   }
   a.prof = prof;
   a.status = ctx->d_status;
@@ -1948,7 +1967,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   TDK_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(PState), cudaMemcpyDeviceToHost, s));
   TDK_CUDA_TRY(cudaStreamSynchronize(s));
   if (want_prof) {
-    unsigned long long hp[16];
+    unsigned long long hp[32];
     TDK_CUDA_TRY(cudaMemcpyAsync(hp, prof, sizeof(hp), cudaMemcpyDeviceToHost, s));
     TDK_CUDA_TRY(cudaStreamSynchronize(s));
     cudaFree(prof);
@@ -1958,8 +1977,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
       fprintf(stderr, "tdk ALS profile (single CTA, Mcycles over %d sweeps):", hs.sweeps);
       for (int i = 0; i < 10; ++i) fprintf(stderr, " %s=%.3f", names[i], hp[i] / 1e6);
     } else {
-      fprintf(stderr, "tdk ALS profile: T_n build=%.3f Mcycles, FP64 inverses=%llu, Newton-Schulz inverses=%llu\n",
-              hp[7] / 1e6, hp[9], hp[10]);
+      fprintf(stderr, "tdk ALS profile: T_n build=%.3f Mcycles, FP64 inverses=%llu, Newton-Schulz inverses=%llu"
+              " (starts rejected %llu, stalled %llu, updates %llu)\n", hp[7] / 1e6, hp[9], hp[10], hp[16], hp[17],
+              hp[18]);
       const char* names[7] = {"inverse", "H_rows", "barrier1", "nonneg_rows+barrier2", "normalise+gram+resid",
                               "barrier3", "fit"};
       fprintf(stderr, "tdk ALS profile (CTA 0, Mcycles over %d sweeps, grid %d):", hs.sweeps, grid);

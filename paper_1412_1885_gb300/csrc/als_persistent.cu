@@ -1963,6 +1963,13 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
     TDK_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(NTP), args, smem, s));
     ctx->launches++;
   }
+  // the lift is queued before the one synchronisation: if the kernel asks for
+  // the pseudo-inverse (the kernel-per-step form then runs and rewrites the
+  // outputs) or ran out of time (the outputs hold the last iterate either
+  // way), lifting first does no harm
+  rc = als_finish(ctx, g, R, sizeof(T) == 8, reinterpret_cast<const void* const*>(a.Bout), U, a.lam_out,
+                  a.nonneg ? aw : nullptr, B_io, A_io, lambda_out);
+  if (rc) return rc;
   PState hs{};
   TDK_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(PState), cudaMemcpyDeviceToHost, s));
   TDK_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1992,10 +1999,6 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   }
   if (hs.status & ST_NEEDPINV) return TDK_ENOTSUP;  // the multi-kernel form has the pseudo-inverse
   if (hs.status & ST_TIMEOUT) return TDK_ETIMEOUT;
-  rc = als_finish(ctx, g, R, sizeof(T) == 8, reinterpret_cast<const void* const*>(a.Bout), U, a.lam_out,
-                  a.nonneg ? aw : nullptr, B_io, A_io, lambda_out);
-  if (rc) return rc;
-  TDK_CUDA_TRY(cudaStreamSynchronize(s));
   int status = TDK_OK;
   if (!hs.converged) status |= TDK_WNOCONV;
   if (rep) {

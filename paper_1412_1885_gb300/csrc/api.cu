@@ -28,6 +28,21 @@ int ws_reserve(tdk_ctx* ctx, size_t bytes) {
   return TDK_OK;
 }
 
+// A stream-ordered allocation from the context's own pool, whose release
+// threshold keeps freed memory for the next call: with the device's default
+// pool (threshold 0) every call paid about 100 us of host time to map its
+// buffers again after a synchronisation.
+int pool_alloc(tdk_ctx* ctx, void** p, size_t bytes) {
+  const cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream)
+                                  : cudaMallocAsync(p, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return TDK_ENOMEM;
+  }
+  return TDK_OK;
+}
+
 // geometry of a descriptor; the rule R_n + p <= I_n is checked against
 // i1_check for the first mode (a slab of a tensor whose first dimension is
 // i1_check may hold fewer rows than the sketch width)
@@ -74,10 +89,7 @@ static int seeded_w(tdk_ctx* ctx, const Geom& g, uint64_t seed, const int64_t* r
     for (int k = 0; k < g.N; ++k)
       if (k != n) total += (size_t)rows[k] * g.Rt[n];
   *buf = nullptr;
-  if (cudaMallocAsync((void**)buf, sizeof(double) * total, ctx->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return TDK_ENOMEM;
-  }
+  if (pool_alloc(ctx, (void**)buf, sizeof(double) * total)) return TDK_ENOMEM;
   double* mats[TDK_MAX_MODES * TDK_MAX_MODES] = {};
   size_t off = 0;
   for (int n = 0; n < g.N; ++n)
@@ -102,10 +114,7 @@ static int seeded_w(tdk_ctx* ctx, const Geom& g, uint64_t seed, const int64_t* r
 static int sketch_pass(tdk_ctx* ctx, const Geom& g, const tdk_tucker_desc* desc, const void* Y,
                        const double* const W[], double** Zout, double* normY2) {
   double* Z = nullptr;
-  if (cudaMallocAsync((void**)&Z, sizeof(double) * (size_t)g.zoff[g.N], ctx->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return TDK_ENOMEM;
-  }
+  if (pool_alloc(ctx, (void**)&Z, sizeof(double) * (size_t)g.zoff[g.N])) return TDK_ENOMEM;
   int rc = desc->prec == TDK_PREC_TC ? sketch_tc(ctx, g, desc->dtype, Y, W, Z, normY2)
                                      : sketch_simt(ctx, g, desc->dtype, Y, W, Z);
   if (rc == TDK_OK && normY2 && desc->prec != TDK_PREC_TC) rc = norm2_pass(ctx, g, desc->dtype, Y, normY2);
@@ -247,6 +256,19 @@ int tdk_ctx_create(tdk_ctx** out, int device, void* stream) {
     return TDK_ENOMEM;
   }
   cudaMemset(c->d_status, 0, sizeof(unsigned) * 4);
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      c->pool = nullptr;  // the device's default pool then
+    }
+  }
   if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -269,6 +291,7 @@ int tdk_ctx_destroy(tdk_ctx* c) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
   return TDK_OK;
 }
@@ -405,6 +428,7 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
       if (W && k != n && !W[n * g.N + k]) return TDK_EINVAL;
   }
   if (desc->prec == TDK_PREC_TC && desc->dtype == TDK_F64) return TDK_ENOTSUP;
+  TDK_HMARK("tucker_sketch: entry");
   cudaSetDevice(ctx->device);
   double* wbuf = nullptr;
   const double* wp[TDK_MAX_MODES * TDK_MAX_MODES];
@@ -416,7 +440,9 @@ int tucker_sketch(tdk_ctx* ctx, const tdk_tucker_desc* desc, const void* Y, cons
   }
   double* Z = nullptr;
   rc = sketch_pass(ctx, g, desc, Y, W, &Z, normY2);
+  TDK_HMARK("tucker_sketch: sketch pass queued");
   if (rc == TDK_OK) rc = cholqr2(ctx, g, Z, U_out);
+  TDK_HMARK("tucker_sketch: CholQR2 queued");
   if (rc == TDK_OK && Z_out) {
     for (int n = 0; n < g.N; ++n)
       if (Z_out[n]) {

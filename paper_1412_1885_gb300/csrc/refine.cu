@@ -48,12 +48,7 @@ struct DevBuf {
     if (p) cudaFreeAsync(p, ctx->stream);
   }
   int alloc(size_t bytes) {
-    if (cudaMallocAsync(&p, bytes < 256 ? 256 : bytes, ctx->stream) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      return TDK_ENOMEM;
-    }
-    return TDK_OK;
+    return pool_alloc(ctx, &p, bytes < 256 ? 256 : bytes);
   }
   template <class T>
   T* as() const {

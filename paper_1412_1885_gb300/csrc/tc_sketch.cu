@@ -1212,9 +1212,16 @@ __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double
   }
 }
 
-__global__ void w_to_f32(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    d[e] = (float)s[e];
+// FP32 copies of every W_k^(n) in one launch (blockIdx.y: the matrix)
+struct WCopies {
+  const double* s[TDK_MAX_MODES * TDK_MAX_MODES];
+  float* d[TDK_MAX_MODES * TDK_MAX_MODES];
+  int64_t n[TDK_MAX_MODES * TDK_MAX_MODES];
+};
+__global__ void w_to_f32(const __grid_constant__ WCopies c) {
+  const int m = blockIdx.y;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c.n[m]; e += (int64_t)gridDim.x * blockDim.x)
+    c.d[m][e] = (float)c.s[m][e];
 }
 
 // WN^T block: rows = channels of modes < N-1 (each padded to 16; one block for
@@ -1250,6 +1257,7 @@ static int launch_sketch(tdk_ctx* ctx, const CUtensorMap& tmY, const CUtensorMap
 int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const double* const W[], double* Zdst,
               double* normY2) {
   if (g.N < 3 || g.N > 4 || !tc_shape_ok(g, dtype) || dtype == TDK_F64) return TDK_ENOTSUP;
+  TDK_HMARK("sketch_tc: start");
   const bool f32 = dtype == TDK_F32;
   const int N = g.N, nj = N - 2, nl = N - 1;
   SkArgs a{};
@@ -1427,15 +1435,22 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
   int rc = ws_reserve(ctx, pl.off);
   if (rc) return rc;
   Carver cv(ctx->ws);
+  WCopies wc{};
+  int nw = 0;
   for (int n = 0; n < N; ++n)
     for (int k = 0; k < N; ++k) {
       a.Wf[n][k] = nullptr;
       if (k == n) continue;
       float* d = cv.take<float>((size_t)g.I[k] * g.Rt[n]);
-      w_to_f32<<<64, 256, 0, ctx->stream>>>(W[n * N + k], d, g.I[k] * g.Rt[n]);
-      TDK_LAUNCH_CHECK(ctx);
+      wc.s[nw] = W[n * N + k];
+      wc.d[nw] = d;
+      wc.n[nw] = g.I[k] * g.Rt[n];
+      ++nw;
       a.Wf[n][k] = d;
     }
+  w_to_f32<<<dim3(16, nw), 256, 0, ctx->stream>>>(wc);
+  TDK_LAUNCH_CHECK(ctx);
+  TDK_HMARK("sketch_tc: plan, workspace, W to FP32");
   __nv_bfloat16* wn = nullptr;
   if (!tw) {
     wn = cv.take<__nv_bfloat16>((size_t)N1 * ldw);
@@ -1446,6 +1461,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
     build_wn<<<128, 256, 0, ctx->stream>>>(wl, a, ldw, wn);
     TDK_LAUNCH_CHECK(ctx);
   }
+  TDK_HMARK("sketch_tc: W block");
   a.part = cv.take<float>((size_t)a.nunits * a.ustride);
   // ||Y||^2 on the side of the pass: the norm warps of the TMEM-W form, the
   // converter warps of FP32 data; per warp and CTA, summed in a fixed order
@@ -1470,6 +1486,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
       if (rc) return rc;
     }
   }
+  TDK_HMARK("sketch_tc: tensor maps");
   int grid = (int)std::min<int64_t>(a.nunits, ctx->num_sms);
   if (tw) {
     const size_t smem = 1024 + (size_t)tw_layout(a.S).total;
@@ -1493,6 +1510,7 @@ int sketch_tc(tdk_ctx* ctx, const Geom& g, int dtype, const void* Y, const doubl
                            : launch_sketch<false, 64>(ctx, tmY, tmW, a, grid, smem));
     if (rc) return rc;
   }
+  TDK_HMARK("sketch_tc: kernel launched");
   RedArgs ra{};
   ra.s = a;
   for (int n = 0; n <= N; ++n) ra.zoff[n] = g.zoff[n];

@@ -56,6 +56,27 @@ inline int take(cudaStream_t s, unsigned* w, unsigned* l) {
 #define TDK_CHECKED_UNIT(name)
 #endif
 
+// Host-side time marks of the test library: with TDK_HOST_MARKS set, each
+// TDK_HMARK("name") prints the microseconds since the previous mark of the
+// thread (where the host time of a call goes).  Nothing in other builds.
+#ifdef TDK_TESTING
+#include <chrono>
+#include <cstdlib>
+namespace tdk_chk {
+inline void hmark(const char* name) {
+  static const bool on = getenv("TDK_HOST_MARKS") != nullptr;
+  if (!on) return;
+  static thread_local std::chrono::steady_clock::time_point last = std::chrono::steady_clock::now();
+  const auto now = std::chrono::steady_clock::now();
+  fprintf(stderr, "tdk host: %s +%.1f us\n", name, std::chrono::duration<double, std::micro>(now - last).count());
+  last = now;
+}
+}  // namespace tdk_chk
+#define TDK_HMARK(name) tdk_chk::hmark(name)
+#else
+#define TDK_HMARK(name) ((void)0)
+#endif
+
 struct tdk_ctx {
   int device = 0;
   int num_sms = 0;
@@ -65,6 +86,7 @@ struct tdk_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   void* ws = nullptr;          // growable workspace
   size_t ws_size = 0;
+  cudaMemPool_t pool = nullptr;  // the context's stream-ordered pool (keeps its memory between calls)
   unsigned* d_status = nullptr;  // device status word (TDK_STATUS_* bits)
   int64_t launches = 0;
   int fail_alloc_after = -1;   // set only by the test library's hook: fail the n-th workspace growth
@@ -99,6 +121,8 @@ struct ProfScope {
 
 // ---- host helpers -------------------------------------------------------
 int ws_reserve(tdk_ctx* ctx, size_t bytes);
+// stream-ordered allocation from the context's pool (freed with cudaFreeAsync)
+int pool_alloc(tdk_ctx* ctx, void** p, size_t bytes);
 
 struct Carver {  // carves 256-byte-aligned slices out of the workspace
   char* base;

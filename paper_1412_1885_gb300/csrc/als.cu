@@ -535,7 +535,8 @@ __global__ void copy_f64_kernel(const double* __restrict__ s, double* __restrict
 // A_n = U_n B_n (FP64), lambda absorbed into the last factor
 template <class T>
 __global__ void lift_kernel(const double* __restrict__ U, const T* __restrict__ B, int64_t I, int64_t Rt, int R,
-                            const double* __restrict__ lam, double* __restrict__ A, double* __restrict__ Bout) {
+                            const double* __restrict__ lam, double* __restrict__ A, double* __restrict__ Bout,
+                            const float* __restrict__ Uf = nullptr) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * R; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / R;
     int r = (int)(e % R);
@@ -545,9 +546,14 @@ __global__ void lift_kernel(const double* __restrict__ U, const T* __restrict__ 
       for (int64_t q = 0; q < Rt; ++q) s = fma(U[i * Rt + q], (double)B[q * R + r], s);
     } else {
       // FP32 factors B: the product in FP32 (U rounded to FP32 adds one
-      // rounding of the same size as B's own), FP64 arithmetic being scarce
+      // rounding of the same size as B's own), FP64 arithmetic being scarce;
+      // from the FP32 copy of U when the caller has one (the conversions run
+      // at the FP64 rate)
       float sf = 0.f;
-      for (int64_t q = 0; q < Rt; ++q) sf = fmaf((float)U[i * Rt + q], (float)B[q * R + r], sf);
+      if (Uf)
+        for (int64_t q = 0; q < Rt; ++q) sf = fmaf(Uf[i * Rt + q], (float)B[q * R + r], sf);
+      else
+        for (int64_t q = 0; q < Rt; ++q) sf = fmaf((float)U[i * Rt + q], (float)B[q * R + r], sf);
       s = (double)sf;
     }
     A[e] = lam ? s * lam[r] : s;
@@ -831,7 +837,8 @@ int als_run_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* const U[], 
 }  // namespace
 
 int als_finish(tdk_ctx* ctx, const Geom& g, int R, bool dbl, const void* const* Bw, const double* const* U,
-               const double* lam, double* const* Aw, double* const* B_io, double* const* A_io, double* lambda_out) {
+               const double* lam, double* const* Aw, double* const* B_io, double* const* A_io, double* lambda_out,
+               const float* const* Uf) {
   cudaStream_t s = ctx->stream;
   for (int n = 0; n < g.N; ++n) {
     const double* lamp = (n == g.N - 1) ? lam : nullptr;
@@ -841,7 +848,7 @@ int als_finish(tdk_ctx* ctx, const Geom& g, int R, bool dbl, const void* const* 
                                                 A_io[n], B_io[n]);
       else
         lift_kernel<float><<<lift_grid(g.I[n], R), 256, 0, s>>>(U[n], reinterpret_cast<const float*>(Bw[n]), g.I[n], g.Rt[n], R, lamp,
-                                               A_io[n], B_io[n]);
+                                               A_io[n], B_io[n], Uf ? Uf[n] : nullptr);
       TDK_LAUNCH_CHECK(ctx);
     } else {
       scale_cols_kernel<<<128, 256, 0, s>>>(Aw[n], g.I[n], R, lamp, A_io[n]);

@@ -29,7 +29,8 @@ namespace tdk {
 // outputs of an ALS run: B_io <- B (normalised), A_io <- U_n B_n (or the
 // nonnegative A_n given in Aw), lambda absorbed into the last factor
 int als_finish(tdk_ctx* ctx, const Geom& g, int R, bool dbl, const void* const* Bw, const double* const* U,
-               const double* lam, double* const* Aw, double* const* B_io, double* const* A_io, double* lambda_out);
+               const double* lam, double* const* Aw, double* const* B_io, double* const* A_io, double* lambda_out,
+               const float* const* Uf);
 
 namespace {
 
@@ -37,6 +38,7 @@ constexpr int RMAXP = TDK_MAX_RANK;
 constexpr int NTP = 256;
 constexpr int ST_TIMEOUT = 0x100, ST_NEEDPINV = 0x200;
 constexpr int NS_MAX_IT = 8;  // Newton-Schulz updates before Gauss-Jordan takes over
+constexpr int NORM_BLOCKS = 64;  // blocks of the ||G||^2 pass
 
 struct PState {
   int sweeps;
@@ -1718,36 +1720,40 @@ __global__ void __launch_bounds__(NTS, 1) als_small_kernel(PArgs<T> a) {
   }
 }
 
+// ||G||^2 in two launches: each block sums a grid-stride share (FP64 cores in
+// FP64; FP32 cores in float-float, each square split exactly into hi + lo by
+// an FMA, FP64 arithmetic being scarce on this GPU) into parts[block], then
+// one block adds the parts in order.  (A Kahan sum that feeds its correction
+// back into the next addend loses up to half an FP32 unit of every square:
+// 7.8e-10 of ||G||^2 on a 20^3 core.)
 template <class T>
-__global__ void norm2_core(const T* __restrict__ G, int64_t n, double* __restrict__ out) {
+__global__ void norm2_core(const T* __restrict__ G, int64_t n, double* __restrict__ parts) {
   __shared__ double red[32];
-  double s = 0.0;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  double v;
   if (sizeof(T) == 8) {
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const double v = (double)G[e];
-      s = fma(v, v, s);
+    double s = 0.0;
+    for (int64_t e = t0; e < n; e += st) {
+      const double x = (double)G[e];
+      s = fma(x, x, s);
     }
+    v = block_sum_d(s, red);
   } else {
-    // FP32 core: each square is split exactly into hi + lo (an FMA gives the
-    // rounding error of the product) and summed in float-float, since FP64
-    // arithmetic is scarce on this GPU; FP64 only across threads.  (A Kahan
-    // sum that feeds its correction back into the next addend loses up to
-    // half an FP32 unit of every square: 7.8e-10 of ||G||^2 on a 20^3 core.)
     FFAcc acc;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const float v = (float)G[e];
-      const float sq = v * v;
-      acc.add(sq, fmaf(v, v, -sq));
+    for (int64_t e = t0; e < n; e += st) {
+      const float x = (float)G[e];
+      const float sq = x * x;
+      acc.add(sq, fmaf(x, x, -sq));
     }
-    s = acc.value();
+    v = block_sum_ff(acc, red);
   }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
+  if (threadIdx.x == 0) parts[blockIdx.x] = v;
+}
+__global__ void norm2_finish(const double* __restrict__ parts, int n, double* __restrict__ out) {
   if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-    *out = v;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += parts[i];
+    *out = s;
   }
 }
 
@@ -1890,6 +1896,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   pl.take<PState>(1);
   pl.take<unsigned>(2);
   pl.take<double>(1);
+  pl.take<double>(NORM_BLOCKS);
   pl.take<double>(grid);
   pl.take<float>((size_t)grid * N * R * R);
   int rc = ws_reserve(ctx, pl.off);
@@ -1913,6 +1920,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   a.st = cv.take<PState>(1);
   a.bar = cv.take<unsigned>(2);
   double* nG2 = cv.take<double>(1);
+  double* nparts = cv.take<double>(NORM_BLOCKS);
   a.rpart = cv.take<double>(grid);
   a.xprev = cv.take<float>((size_t)grid * N * R * R);
   unsigned long long* prof = nullptr;
@@ -1943,7 +1951,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
     a.init[n] = a.nonneg ? A_io[n] : B_io[n];
     a.Aout[n] = aw[n];  // running A_n; the caller's A_io stays the init until the end
   }
-  norm2_core<T><<<1, 1024, 0, s>>>(G, g.core_numel, nG2);
+  norm2_core<T><<<NORM_BLOCKS, 256, 0, s>>>(G, g.core_numel, nparts);
+  TDK_LAUNCH_CHECK(ctx);
+  norm2_finish<<<1, 32, 0, s>>>(nparts, NORM_BLOCKS, nG2);
   TDK_LAUNCH_CHECK(ctx);
   TDK_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s));
   // 3-way unconstrained cores that fit in one SM: the single-CTA kernel
@@ -1968,7 +1978,8 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   // outputs) or ran out of time (the outputs hold the last iterate either
   // way), lifting first does no harm
   rc = als_finish(ctx, g, R, sizeof(T) == 8, reinterpret_cast<const void* const*>(a.Bout), U, a.lam_out,
-                  a.nonneg ? aw : nullptr, B_io, A_io, lambda_out);
+                  a.nonneg ? aw : nullptr, B_io, A_io, lambda_out,
+                  sizeof(T) == 4 ? reinterpret_cast<const float* const*>(a.Uf) : nullptr);
   if (rc) return rc;
   PState hs{};
   TDK_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(PState), cudaMemcpyDeviceToHost, s));

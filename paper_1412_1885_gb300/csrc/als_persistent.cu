@@ -82,6 +82,7 @@ struct PArgs {
   unsigned long long* prof;     // optional: cycles per phase, CTA 0 (null = off)
   float* xprev;                 // grid kernel: [grid][N][R*R] each CTA's last FP32 inverse of T_n
   float ns_gate;                // Newton-Schulz start accepted while ||I - T X||_F < ns_gate
+  int64_t ulo_elems;            // FP32 nonneg: max I_n Rt_n (the staged low part of U_n)
   int64_t cache_elems;          // > 0: each CTA keeps its core slice of every mode in shared memory
   int64_t coff[TDK_MAX_MODES];  //   at these offsets of the cache (entries)
 };
@@ -309,8 +310,9 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 template <class T>
 struct PLayout {
   size_t o_bs, o_gram, o_bgram, o_tm, o_invd, o_part, o_lam, o_xrow, o_hrow, o_red, o_lf, o_tid, o_gjs, o_yf,
-      o_lamt, o_ilamt, o_slice, o_work, o_egram, o_ns, o_cache, total;
-  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram, int64_t cache) {
+      o_lamt, o_ilamt, o_slice, o_work, o_egram, o_ns, o_cache, o_ulo, total;
+  __host__ __device__ void plan(int N, int R, int btot, int64_t Qmax, int64_t Amax, bool egram, int64_t cache,
+                                int64_t ulo) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
       const size_t o = (off + 15) & ~size_t(15);
@@ -338,6 +340,7 @@ struct PLayout {
     o_egram = take(egram ? sizeof(T) * N * R * R : 0);  // Grams of A_p - U_p B_p
     o_ns = take(sizeof(float) * R * R);                 // Newton-Schulz iterate
     o_cache = take(sizeof(T) * (size_t)cache);          // core slices kept across sweeps
+    o_ulo = take(egram ? sizeof(T) * (size_t)ulo : 0);  // FP32 nonneg: U_n - Uf_n staged
     total = (off + 15) & ~size_t(15);
   }
 };
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   }
   PLayout<T> L;
   const bool leak32 = sizeof(T) == 4 && a.nonneg;  // FP32 nonneg: the out-of-subspace term from E_p
-  L.plan(N, R, btot, a.Qmax, a.Amax, leak32, a.cache_elems);
+  L.plan(N, R, btot, a.Qmax, a.Amax, leak32, a.cache_elems, a.ulo_elems);
   T* Bs = reinterpret_cast<T*>(sm + L.o_bs);         // factors, packed
   T* egram = reinterpret_cast<T*>(sm + L.o_egram);   // [N][R*R] Grams of D_p = A_p - U_p B_p
   T* gram = reinterpret_cast<T*>(sm + L.o_gram);     // [N][R*R]
@@ -598,6 +601,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
   T* slice = reinterpret_cast<T*>(sm + L.o_slice);   // [Qmax]
   T* work = reinterpret_cast<T*>(sm + L.o_work);     // [Amax * R]
   T* cache = reinterpret_cast<T*>(sm + L.o_cache);   // [cache_elems]
+  T* ulo_s = reinterpret_cast<T*>(sm + L.o_ulo);     // [ulo_elems]
 
   const int tid = threadIdx.x;
   const int G = gridDim.x, c = blockIdx.x;
@@ -1072,6 +1076,7 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       }
       if (a.nonneg)  // U_n staged in the work buffer for B_n = U_n^T A_n
         stage_cg(work, a.Uf[n], rows * Rn, tid, NTP);
+      if (leak32) stage_cg(ulo_s, a.Ulo[n], rows * Rn, tid, NTP);
       __syncthreads();
       PROF_MARK(14);
       gram_sym<T>(nb, rows, R, R, gram + n * R * R, tid, NTP);
@@ -1079,11 +1084,17 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       if (!a.nonneg) {
         for (int e = tid; e < Rn * R; e += NTP) Bs[boff[n] + e] = nb[e];
       } else {
+        // (four partial sums over the rows in flight, added in a fixed order)
         for (int e = tid; e < Rn * R; e += NTP) {
           const int q = e / R, r = e % R;
-          T s2 = T(0);
-          for (int64_t i = 0; i < rows; ++i) s2 = fma(work[i * Rn + q], nb[i * R + r], s2);
-          Bs[boff[n] + e] = s2;
+          T s4[4] = {T(0), T(0), T(0), T(0)};
+          int64_t i = 0;
+          for (; i + 3 < rows; i += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] = fma(work[(i + u) * Rn + q], nb[(i + u) * R + r], s4[u]);
+          }
+          for (; i < rows; ++i) s4[0] = fma(work[i * Rn + q], nb[i * R + r], s4[0]);
+          Bs[boff[n] + e] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
         if (c == 0)
           for (int64_t e = tid; e < rows * R; e += NTP) a.Aout[n][e] = (double)nb[e];
@@ -1095,17 +1106,25 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           // and its Gram E_n.  The out-of-subspace term of the fit is then a
           // sum of products that contain E (no difference of near-equal
           // norms), so its error stays far below the stopping tolerance
+          // (U_n's low part staged beside its high part; two entries per
+          // thread in flight, their compensated chains independent)
           __syncthreads();
-          for (int64_t e = tid; e < rows * R; e += NTP) {
-            const int64_t i = e / R;
-            const int r = (int)(e % R);
-            GramAcc<T> d;
-            d.s = nb[e];
+          const int nE = (int)(rows * R);
+          for (int e0 = tid; e0 < nE; e0 += 2 * NTP) {
+            const int e1 = e0 + NTP < nE ? e0 + NTP : e0;
+            const int i0 = e0 / R, r0 = e0 - i0 * R, i1 = e1 / R, r1 = e1 - i1 * R;
+            GramAcc<T> d0, d1;
+            d0.s = nb[e0];
+            d1.s = nb[e1];
             for (int q = 0; q < Rn; ++q) {
-              d.add(-work[i * Rn + q], Bs[boff[n] + q * R + r]);
-              d.add(-a.Ulo[n][i * Rn + q], Bs[boff[n] + q * R + r]);
+              const T b0 = Bs[boff[n] + q * R + r0], b1 = Bs[boff[n] + q * R + r1];
+              d0.add(-work[i0 * Rn + q], b0);
+              d1.add(-work[i1 * Rn + q], b1);
+              d0.add(-ulo_s[i0 * Rn + q], b0);
+              d1.add(-ulo_s[i1 * Rn + q], b1);
             }
-            nb[e] = d.value();
+            nb[e0] = d0.value();
+            if (e0 + NTP < nE) nb[e1] = d1.value();
           }
           __syncthreads();
           gram_sym<T>(nb, rows, R, R, egram + n * R * R, tid, NTP);
@@ -1244,10 +1263,12 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
       if (c == 0 && sweep - 1 < a.hist_cap) a.hist[sweep - 1] = f;
     }
     __syncthreads();
+    PROF_MARK(19);
     fit = red[0];
     fitY = red[1];
     const bool conv = red[2] != 0.0;
     __syncthreads();
+    PROF_MARK(20);
     if (conv) {
       converged = 1;
       break;
@@ -1822,21 +1843,61 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   a.Amax = std::max<int64_t>(a.Amax, Rtmax);
   if (a.nonneg)
     for (int n = 0; n < N; ++n) a.Amax = std::max<int64_t>(a.Amax, (g.I[n] * g.Rt[n] + R - 1) / R);
-  PLayout<T> lay;
-  lay.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg, 0);
-  size_t smem = lay.total + 64;
+  if (sizeof(T) == 4 && a.nonneg)
+    for (int n = 0; n < N; ++n) a.ulo_elems = std::max<int64_t>(a.ulo_elems, g.I[n] * g.Rt[n]);
+  // Buffer sizes for a grid: Qmax and Amax above hold whole rows of H_n;
+  // with the rows split over Pn CTAs a CTA stages and contracts only its
+  // part, so the slice and work buffers are sized for the largest part.
+  const int64_t Qwhole = a.Qmax, Awhole = a.Amax;
+  int64_t q_rows = 0;
+  auto size_for = [&](int grid_) {
+    q_rows = (a.nonneg ? Imax : Rtmax) * R;
+    int64_t q_slice = 0, a_rows = Rtmax;
+    if (a.nonneg)
+      for (int n = 0; n < N; ++n) a_rows = std::max<int64_t>(a_rows, (g.I[n] * g.Rt[n] + R - 1) / R);
+    for (int n = 0; n < N; ++n) {
+      int oth[TDK_MAX_MODES], no = 0;
+      for (int p = 0; p < N; ++p)
+        if (p != n) oth[no++] = p;
+      const int Rn = g.Rt[n], Rl = g.Rt[oth[no - 1]], R0o = g.Rt[oth[0]];
+      const int64_t per0 = g.core_numel / Rn / Rl / R0o;
+      const int Pn = std::max(1, std::min(grid_ / Rn, R0o));
+      const int64_t part = (R0o + Pn - 1) / Pn, rows0 = part * per0;
+      q_slice = std::max(q_slice, rows0 * Rl);
+      a_rows = std::max(a_rows, rows0);  // first product, in the work buffer
+      int64_t rows = rows0;
+      bool to_slice = true;  // the products alternate between the slice and work buffers
+      for (int k = no - 2; k >= 0; --k) {
+        rows /= (k == 0) ? part : g.Rt[oth[k]];
+        if (to_slice) q_rows = std::max(q_rows, rows * R);
+        else a_rows = std::max(a_rows, rows);
+        to_slice = !to_slice;
+      }
+    }
+    a.Amax = std::min(Awhole, a_rows);
+    a.Qmax = std::min(Qwhole, std::max(q_rows, q_slice));
+    PLayout<T> l;
+    l.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg, 0, a.ulo_elems);
+    return l.total + 64;
+  };
+  // rows of H_n are split over several CTAs (by ranges of the slowest other
+  // mode) when the whole GPU gives at least four per row; otherwise one CTA per
+  // row keeps the grid barriers cheap.  The sizes at one CTA per SM bound the
+  // shared memory; the occupancy they allow sets the grid, whose parts are no
+  // larger.
+  const int64_t rows_cap = a.nonneg ? std::max(Rtmax, Imax) : Rtmax;
+  auto grid_of = [&](int per_sm_) {
+    const int all = per_sm_ * ctx->num_sms;
+    return (all >= 4 * Rtmax) ? all : (int)std::min<int64_t>(all, rows_cap);
+  };
+  size_t smem = size_for(grid_of(1));
   if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;
   auto kern = als_persistent_kernel<T>;
   TDK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   TDK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTP, smem));
   if (per_sm < 1) return TDK_ENOTSUP;
-  // rows of H_n are split over several CTAs (by ranges of the slowest other
-  // mode) when the whole GPU gives at least four per row; otherwise one CTA per
-  // row keeps the grid barriers cheap
-  const int grid_all = per_sm * ctx->num_sms;
-  const int64_t rows_cap = a.nonneg ? std::max(Rtmax, Imax) : Rtmax;
-  int grid = (grid_all >= 4 * Rtmax) ? grid_all : (int)std::min<int64_t>(grid_all, rows_cap);
+  int grid = grid_of(per_sm);
 #ifdef TDK_TESTING
   // test hook: TDK_ALS_GRID=1 takes the grid kernel on a core the one-CTA
   // kernel would take; a larger value also caps the grid (another split of
@@ -1844,6 +1905,9 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
   const int grid_cap = getenv("TDK_ALS_GRID") ? atoi(getenv("TDK_ALS_GRID")) : 0;
   if (grid_cap > 1) grid = std::min(grid, grid_cap);
 #endif
+  smem = size_for(grid);
+  if (smem > (size_t)ctx->max_smem_optin) return TDK_ENOTSUP;  // (a capped test grid)
+  TDK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // Core slices kept in shared memory across sweeps, when every CTA has at
   // most one part of H_n per mode (the same part every sweep, as the kernel
   // splits the rows) and the slices fit beside the rest without lowering
@@ -1863,8 +1927,10 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
       cache += ((int64_t)(R0o + Pn - 1) / Pn * per0 * Rl + 3) / 4 * 4;
     }
     if (one_part && cache > 0) {
+      // the slice buffer then holds only the products and the update rows
+      const int64_t qc = std::min(a.Qmax, q_rows);
       PLayout<T> lc;
-      lc.plan(N, R, (int)btot, a.Qmax, a.Amax, sizeof(T) == 4 && a.nonneg, cache);
+      lc.plan(N, R, (int)btot, qc, a.Amax, sizeof(T) == 4 && a.nonneg, cache, a.ulo_elems);
       int per_sm_c = 0;
       if (lc.total + 64 <= (size_t)ctx->max_smem_optin &&
           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(lc.total + 64)) ==
@@ -1872,6 +1938,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kern, NTP, lc.total + 64) == cudaSuccess &&
           per_sm_c >= per_sm) {
         a.cache_elems = cache;
+        a.Qmax = qc;
         smem = lc.total + 64;
       } else {
         cudaGetLastError();
@@ -2005,6 +2072,7 @@ int als_persistent_t(tdk_ctx* ctx, const Geom& g, const T* G, const double* cons
       fprintf(stderr, "\n  inside H_rows: slice=%.3f first_product=%.3f other_products=%.3f (H_rows above: the"
               " solve and stores); inside normalise: norms+scale=%.3f gram=%.3f; sweep loop and fit tail=%.3f",
               hp[11] / 1e6, hp[12] / 1e6, hp[13] / 1e6, hp[14] / 1e6, hp[15] / 1e6, hp[8] / 1e6);
+      fprintf(stderr, " (scalar tail %.3f, its barrier %.3f)", hp[19] / 1e6, hp[20] / 1e6);
     }
     fprintf(stderr, "\n");
   }

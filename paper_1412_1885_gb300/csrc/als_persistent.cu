@@ -613,64 +613,67 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
     for (int n = 0; n < N; ++n)
       for (int64_t e = tid; e < a.I[n] * R; e += NTP) a.Aout[n][e] = a.init[n][e];
 
-  // ---- initial factors (raw) and their Grams
+  // ---- initial factors (raw) and their Grams.  Unconstrained: B_n as
+  //      given.  Nonnegative: A_n staged in FP32 in the update-rows buffer
+  //      and U_n (with its low part, FP32 nonneg) beside it, B_n = U_n^T A_n,
+  //      and for FP32 cores D_n = A_n - U_n B_n and its Gram E_n (see below),
+  //      all from shared memory
   for (int n = 0; n < N; ++n) {
+    const int Rn = a.Rt[n];
     if (!a.nonneg) {
-      for (int e = tid; e < a.Rt[n] * R; e += NTP) Bs[boff[n] + e] = (T)a.init[n][e];
+      for (int e = tid; e < Rn * R; e += NTP) Bs[boff[n] + e] = (T)a.init[n][e];
+      __syncthreads();
+      gram_sym<T>(Bs + boff[n], Rn, R, R, gram + n * R * R, tid, NTP);
+      gram_sym<T>(Bs + boff[n], Rn, R, R, bgram + n * R * R, tid, NTP);
     } else {
-      for (int e = tid; e < a.Rt[n] * R; e += NTP) {
+      const int64_t rows = a.I[n];
+      T* nb = slice;
+      stage_cg(nb, a.init[n], rows * R, tid, NTP);
+      stage_cg(work, a.Uf[n], rows * Rn, tid, NTP);
+      if (leak32) stage_cg(ulo_s, a.Ulo[n], rows * Rn, tid, NTP);
+      __syncthreads();
+      for (int e = tid; e < Rn * R; e += NTP) {
         const int q = e / R, r = e % R;
-        T s = T(0);
-        for (int64_t i = 0; i < a.I[n]; ++i) s = fma(a.Uf[n][i * a.Rt[n] + q], (T)a.init[n][i * R + r], s);
-        Bs[boff[n] + e] = s;
+        T s4[4] = {T(0), T(0), T(0), T(0)};
+        int64_t i = 0;
+        for (; i + 3 < rows; i += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s4[u] = fma(work[(i + u) * Rn + q], nb[(i + u) * R + r], s4[u]);
+        }
+        for (; i < rows; ++i) s4[0] = fma(work[i * Rn + q], nb[i * R + r], s4[0]);
+        Bs[boff[n] + e] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      }
+      gram_sym<T>(nb, rows, R, R, gram + n * R * R, tid, NTP);
+      __syncthreads();
+      gram_sym<T>(Bs + boff[n], Rn, R, R, bgram + n * R * R, tid, NTP);
+      if (leak32) {
+        const int nE = (int)(rows * R);
+        for (int e0 = tid; e0 < nE; e0 += 2 * NTP) {
+          const int e1 = e0 + NTP < nE ? e0 + NTP : e0;
+          const int i0 = e0 / R, r0 = e0 - i0 * R, i1 = e1 / R, r1 = e1 - i1 * R;
+          GramAcc<T> d0, d1;
+          d0.s = nb[e0];
+          d1.s = nb[e1];
+          for (int q = 0; q < Rn; ++q) {
+            const T b0 = Bs[boff[n] + q * R + r0], b1 = Bs[boff[n] + q * R + r1];
+            d0.add(-work[i0 * Rn + q], b0);
+            d1.add(-work[i1 * Rn + q], b1);
+            d0.add(-ulo_s[i0 * Rn + q], b0);
+            d1.add(-ulo_s[i1 * Rn + q], b1);
+          }
+          nb[e0] = d0.value();
+          if (e0 + NTP < nE) nb[e1] = d1.value();
+        }
+        __syncthreads();
+        gram_sym<T>(nb, rows, R, R, egram + n * R * R, tid, NTP);
       }
     }
-    for (int e = tid; e < R * R; e += NTP) {
-      const int r = e / R, s2 = e % R;
-      GramAcc<T> acc;
-      if (!a.nonneg) {
-        for (int q = 0; q < a.Rt[n]; ++q) acc.add((T)a.init[n][q * R + r], (T)a.init[n][q * R + s2]);
-      } else {
-        for (int64_t i = 0; i < a.I[n]; ++i) acc.add((T)a.init[n][i * R + r], (T)a.init[n][i * R + s2]);
-      }
-      gram[n * R * R + e] = acc.value();
-    }
+    __syncthreads();
   }
   for (int r = tid; r < R; r += NTP) {
     lam[r] = 1.0;
     lamT[r] = T(1);
   }
-  __syncthreads();
-  for (int n = 0; n < N; ++n)
-    for (int e = tid; e < R * R; e += NTP) {
-      const int r = e / R, s2 = e % R;
-      GramAcc<T> acc;
-      for (int q = 0; q < a.Rt[n]; ++q) acc.add(Bs[boff[n] + q * R + r], Bs[boff[n] + q * R + s2]);
-      bgram[n * R * R + e] = acc.value();
-    }
-  __syncthreads();
-  // FP32 nonneg: D_p = A_p - U_p B_p of the start, its Gram E_p (see below)
-  if (leak32)
-    for (int n = 0; n < N; ++n) {
-      for (int e = tid; e < R * R; e += NTP) {
-        const int r = e / R, s2 = e % R;
-        GramAcc<T> acc;
-        for (int64_t i = 0; i < a.I[n]; ++i) {
-          GramAcc<T> dr, ds;
-          dr.s = (T)a.init[n][i * R + r];
-          ds.s = (T)a.init[n][i * R + s2];
-          for (int q = 0; q < a.Rt[n]; ++q) {
-            const T uh = a.Uf[n][i * a.Rt[n] + q], ul = a.Ulo[n][i * a.Rt[n] + q];
-            dr.add(-uh, Bs[boff[n] + q * R + r]);
-            dr.add(-ul, Bs[boff[n] + q * R + r]);
-            ds.add(-uh, Bs[boff[n] + q * R + s2]);
-            ds.add(-ul, Bs[boff[n] + q * R + s2]);
-          }
-          acc.add(dr.value(), ds.value());
-        }
-        egram[n * R * R + e] = acc.value();
-      }
-    }
   __syncthreads();
   const double nG2 = *a.nG2;
   const double nY2 = a.nY2 ? *a.nY2 : 0.0;

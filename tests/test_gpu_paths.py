@@ -203,9 +203,9 @@ def test_nonneg_ffcp_on_the_4way_core_matches_oracle(tdk, ctx, dtype, form):
     """The 200^4 workload's data model (nonnegative CP rank 20, U[0, 1]
     factors, SNR 25 dB, clipped at 0) at 40 x 36 x 34 x 32, compressed to a
     30^4 core; projected LS FFCP with R = 20 for 10 sweeps from the same
-    start, in the form AUTO picks (the persistent grid kernel for an FP32
-    core; an FP64 core's working set exceeds its shared memory, so the
-    kernel-per-step form) and in the kernel-per-step form."""
+    start, in the form AUTO picks (the persistent grid kernel, whose buffers
+    hold one part of a split row of H_n, FP32 and FP64 cores alike) and in
+    the kernel-per-step form."""
     shape, ranks, p, R = (40, 36, 34, 32), (20, 20, 20, 20), 10, 20
     Y, W, _ = small_problem(shape, ranks, p, seed=3, dtype="f64", snr=25.0, R_cp=R, dist="uniform", clip0=True)
     ref = oracle.rand_tucker(Y, W)
@@ -214,7 +214,7 @@ def test_nonneg_ffcp_on_the_4way_core_matches_oracle(tdk, ctx, dtype, form):
     out = tdk.ffcp_als(ctx, dev_tensor(ref["G"], dtype), [dev_tensor(u, "f64") for u in ref["U"]], shape, ranks, p,
                        DT_CODE[dtype], R, max_sweeps=10, tol=0.0, nonneg=True, A0=[dev_tensor(a, "f64") for a in A0],
                        form=form)
-    assert out["form"] == ("grid" if form == "auto" and dtype == "f32" else "steps")
+    assert out["form"] == ("grid" if form == "auto" else "steps")
     assert out["sweeps"] == 10
     assert ctx.sync_status() == 0
     assert abs(out["fit_core"] - o["fit"]) < (1e-10 if dtype == "f64" else 1e-5), (out["fit_core"], o["fit"])

@@ -74,6 +74,41 @@ def test_als_grid_form_on_the_wide_core_matches_oracle(tdk, ctx, dtype):
         assert oracle.congruence(Ao, Ah) > 0.9999
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_newton_schulz_inverse_gives_the_gauss_jordan_solution(tdk, dtype, monkeypatch):
+    """From the second sweep on, the grid kernel inverts T_n by Newton-Schulz
+    steps from the previous sweep's inverse and refines the solves against
+    T_n in FP64; with the start gate at 0 every inverse is Gauss-Jordan.
+    Both must give the same iterates: on the 60^3 core with R = 40, 20
+    sweeps, B_n to 1e-9 (FP64 core: both solves are accurate far below that)
+    or fits to 1e-6 and congruence 0.9999 (FP32 core, whose rounding the two
+    paths meet in different places)."""
+    shape, ranks, p, R, ref = _wide_core(seed=6)
+    Rt = [r + p for r in ranks]
+    B0 = [dev_tensor(b, "f64") for b in synth.init_factors(Rt, R, 44)]
+    ctx_t = tdk.Context(0, testing=True)
+    try:
+        outs = []
+        for gate in ["1", "0"]:
+            monkeypatch.setenv("TDK_ALS_NS_GATE", gate)
+            outs.append(tdk.ffcp_als(ctx_t, dev_tensor(ref["G"], dtype), [dev_tensor(u, "f64") for u in ref["U"]],
+                                     shape, ranks, p, DT_CODE[dtype], R, max_sweeps=20, tol=0.0, B0=B0))
+            assert ctx_t.sync_status() == 0
+            assert outs[-1]["form"] == "grid"
+        monkeypatch.delenv("TDK_ALS_NS_GATE", raising=False)
+        if dtype == "f64":
+            for n in range(3):
+                assert np.allclose(host(outs[0]["B"][n]), host(outs[1]["B"][n]), atol=1e-9), n
+            assert abs(outs[0]["fit_core"] - outs[1]["fit_core"]) < 1e-12
+        else:
+            assert abs(outs[0]["fit_core"] - outs[1]["fit_core"]) < 1e-6
+            A = [[host(a) for a in o["A"]] for o in outs]
+            assert oracle.congruence(A[0], A[1]) > 0.9999
+    finally:
+        monkeypatch.delenv("TDK_ALS_NS_GATE", raising=False)
+        ctx_t.close()
+
+
 def test_als_grid_form_stopping_rule_matches_oracle_fp64(tdk, ctx):
     """The same 60^3 core to convergence (relative fit change below 1e-9):
     the grid kernel stops at the oracle's sweep."""

@@ -83,7 +83,7 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* _
   const int Rt = q.Rt[n];
   __shared__ double A[TDK_MAX_RANK * TDK_MAX_RANK];
   __shared__ double Ri[TDK_MAX_RANK * TDK_MAX_RANK];
-  __shared__ double inv_d[TDK_MAX_RANK], srow[TDK_MAX_RANK], dsq[TDK_MAX_RANK], idsq[TDK_MAX_RANK];
+  __shared__ double inv_d[TDK_MAX_RANK], srow[TDK_MAX_RANK], idsq[TDK_MAX_RANK];
   __shared__ double tiny_s;
   __shared__ int bad;
   if (fail[n]) return;
@@ -97,10 +97,15 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* _
     bad = !(A[0] > tiny_s);
     inv_d[0] = 1.0 / A[0];
   }
-  // right-looking Cholesky on the upper triangle, A = R^T R: step j scales the
-  // pivot row once (srow = A[j, :] / d_j) and updates the trailing triangle
-  // A[a, b] -= srow[a] A[j, b] (j < a <= b), one element per thread; rows are
-  // scaled by 1/sqrt(d) at the end (a row is not read again after its step)
+  // right-looking Cholesky on the upper triangle, A = L D L^T (L unit lower):
+  // step j scales the pivot row once (srow = A[j, :] / d_j, the multipliers
+  // L[:, j]) and updates the trailing triangle A[a, b] -= srow[a] A[j, b]
+  // (j < a <= b), one element per thread.  The same row operations, applied
+  // to M = I (M[a, c] -= srow[a] M[j, c] for a > j >= c, row j being final),
+  // leave M = L^{-1} when the loop ends, so R^{-1} = M^T D^{-1/2} needs no
+  // second pass of back substitution: one element per thread per step, no
+  // serial chains.
+  for (int e = tid; e < Rt * Rt; e += nth) Ri[e] = (e / Rt == e % Rt) ? 1.0 : 0.0;
   for (int j = 0; j < Rt; ++j) {
     __syncthreads();
     if (bad) break;
@@ -117,40 +122,24 @@ __global__ void chol_kernel(QRArgs q, const double* __restrict__ gram, double* _
         inv_d[a] = 1.0 / v;
       }
     }
+    const int w = j + 1;
+    for (int e = tid; e < m * w; e += nth) {
+      const int a = j + 1 + e / w, cidx = e % w;
+      Ri[a * Rt + cidx] = fma(-srow[a], Ri[j * Rt + cidx], Ri[a * Rt + cidx]);
+    }
   }
   __syncthreads();
   if (bad) {
     if (tid == 0) fail[n] = 1;
     return;
   }
-  for (int j = tid; j < Rt; j += nth) {
-    dsq[j] = sqrt(A[j * Rt + j]);
-    idsq[j] = 1.0 / dsq[j];
-  }
+  for (int j = tid; j < Rt; j += nth) idsq[j] = 1.0 / sqrt(A[j * Rt + j]);
   __syncthreads();
-  for (int e = tid; e < Rt * Rt; e += nth) {
-    const int j = e / Rt, b = e % Rt;
-    if (b > j) A[e] *= idsq[j];
-    else if (b == j) A[e] = dsq[j];
-  }
-  // Rinv = R^{-1} by Gauss-Jordan back substitution: X = I, then for k from
-  // the last row up: X[k, :] /= R_kk, X[i, :] -= R_ik X[k, :] (i < k), over the
-  // k x (Rt - k) block of columns >= k (X is upper triangular), one element per
-  // thread.  R is never updated (each step only clears column k of R).
-  for (int e = tid; e < Rt * Rt; e += nth) Ri[e] = (e / Rt == e % Rt) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int k = Rt - 1; k >= 0; --k) {
-    const int w = Rt - k;
-    for (int j = k + tid; j < Rt; j += nth) Ri[k * Rt + j] *= idsq[k];
-    __syncthreads();
-    for (int e = tid; e < k * w; e += nth) {
-      const int i = e / w, j = k + e % w;
-      Ri[i * Rt + j] = fma(-A[i * Rt + k], Ri[k * Rt + j], Ri[i * Rt + j]);
-    }
-    __syncthreads();
-  }
   double* out = rinv + (int64_t)n * TDK_MAX_RANK * TDK_MAX_RANK;
-  for (int e = tid; e < Rt * Rt; e += nth) out[e] = Ri[e];
+  for (int e = tid; e < Rt * Rt; e += nth) {
+    const int i = e / Rt, j = e % Rt;
+    out[e] = i <= j ? Ri[j * Rt + i] * idsq[j] : 0.0;  // R^{-1}[i, j] = M[j, i] / sqrt(d_j)
+  }
 }
 
 // Q = Z Rinv, row-wise; Qdst packed by zoff (dst_ptrs null) or per-mode pointers

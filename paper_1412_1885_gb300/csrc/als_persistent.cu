@@ -419,6 +419,115 @@ __device__ int gj_inverse_regs(F* A, F* buf, int R, F eps, int t, int nt, int ba
   return 1;
 }
 
+// The same elimination, two pivots per barrier: step k takes pivots k and
+// k+1 together, each entry composed from the two single-pivot updates (the
+// first pivot's update of the entry, of its row's entry in column k+1 and of
+// its column's entry in row k+1, then the second pivot's), so the result is
+// the one-pivot-per-step elimination's to the rounding of the same
+// operations, with half the barriers and dependency chains.  `buf` holds,
+// double-buffered, rows k and k+1 and columns k and k+1 (8 R entries); an
+// odd last pivot is a single step.  FP32 only (the FP64 fallback keeps the
+// one-pivot form and its 4 R buffer).
+template <int EPT>
+__device__ int gj_inverse_regs2(float* A, float* buf, int R, float eps, int t, int nt, int bar_id) {
+  tc::named_bar(bar_id, nt);  // `buf` may still be read by a previous call
+  float mx = 0.f;
+  for (int j = 0; j < R; ++j) mx = A[j * R + j] > mx ? A[j * R + j] : mx;
+  const float tiny = (float)R * eps * mx;
+  const int RR = R * R;
+  float a[EPT];
+  int ri[EPT], ci[EPT];  // row and column of each entry; -1: none
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = t + q * nt;
+    ri[q] = e < RR ? e / R : -1;
+    ci[q] = e < RR ? e - ri[q] * R : 0;
+    a[q] = e < RR ? A[e] : 0.f;
+  }
+  if (t < R) {
+    buf[t] = A[t];
+    buf[2 * R + t] = A[t * R];
+    if (R > 1) {
+      buf[R + t] = A[R + t];
+      buf[3 * R + t] = A[t * R + 1];
+    }
+  }
+  tc::named_bar(bar_id, nt);
+  int ok = 1;
+  for (int k = 0, h = 0; k < R; k += 2, h ^= 1) {
+    const float* rk = buf + h * 4 * R;  // row k
+    const float* rk1 = rk + R;          // row k+1
+    const float* ck = rk + 2 * R;       // column k
+    const float* ck1 = rk + 3 * R;      // column k+1
+    float* nx = buf + (h ^ 1) * 4 * R;  // rows and columns k+2, k+3
+    const float p00 = rk[k];
+    if (!(p00 > tiny)) {
+      ok = 0;
+      break;
+    }
+    const float ip0 = rcp_rn(p00);
+    if (k + 1 == R) {  // the odd last pivot alone
+      float rv[EPT], cv[EPT];
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        rv[q] = ri[q] >= 0 ? rk[ci[q]] : 0.f;
+        cv[q] = ri[q] >= 0 ? ck[ri[q]] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const bool r0 = ri[q] == k, c0 = ci[q] == k;
+        a[q] = r0 ? (c0 ? ip0 : rv[q] * ip0) : (c0 ? -cv[q] * ip0 : fmaf(-cv[q], rv[q] * ip0, a[q]));
+      }
+      tc::named_bar(bar_id, nt);
+      break;
+    }
+    const int k1 = k + 1;
+    const float u = rk[k1] * ip0;   // A[k][k1] / p00
+    const float w = rk1[k];         // A[k1][k]
+    const float s = fmaf(-w, u, rk1[k1]);
+    if (!(s > tiny)) {
+      ok = 0;
+      break;
+    }
+    const float is = rcp_rn(s);
+    float rv0[EPT], rv1[EPT], cv0[EPT], cv1[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const bool on = ri[q] >= 0;
+      rv0[q] = on ? rk[ci[q]] : 0.f;
+      rv1[q] = on ? rk1[ci[q]] : 0.f;
+      cv0[q] = on ? ck[ri[q]] : 0.f;
+      cv1[q] = on ? ck1[ri[q]] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int i = ri[q], j = ci[q];
+      // after the first pivot: the entry, its row's entry in column k1, its
+      // column's entry in row k1
+      const float aij = i == k ? (j == k ? ip0 : rv0[q] * ip0)
+                               : (j == k ? -cv0[q] * ip0 : fmaf(-cv0[q], rv0[q] * ip0, a[q]));
+      const float aik1 = i == k ? u : fmaf(-cv0[q], u, cv1[q]);
+      const float ak1j = j == k ? -w * ip0 : fmaf(-w, rv0[q] * ip0, rv1[q]);
+      a[q] = i == k1 ? (j == k1 ? is : ak1j * is) : (j == k1 ? -aik1 * is : fmaf(-aik1, ak1j * is, aij));
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (ri[q] < 0) continue;
+      if (ri[q] == k + 2) nx[ci[q]] = a[q];
+      if (ri[q] == k + 3) nx[R + ci[q]] = a[q];
+      if (ci[q] == k + 2) nx[2 * R + ri[q]] = a[q];
+      if (ci[q] == k + 3) nx[3 * R + ri[q]] = a[q];
+    }
+    tc::named_bar(bar_id, nt);
+  }
+  if (!ok) return 0;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (ri[q] >= 0) A[t + q * nt] = a[q];
+  tc::named_bar(bar_id, nt);
+  return 1;
+}
+
 template <class F>
 __device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, int bar_id);
 
@@ -428,6 +537,12 @@ __device__ int group_gj_inverse_smem(F* A, F* buf, int R, F eps, int t, int nt, 
 template <class F, int MAXEPT = 16>
 __device__ int group_gj_inverse(F* A, F* buf, int R, F eps, int t, int nt, int bar_id) {
   const int per = (R * R + nt - 1) / nt;
+  if constexpr (sizeof(F) == 4) {
+    float* Af = reinterpret_cast<float*>(A);
+    float* bf = reinterpret_cast<float*>(buf);
+    if (per <= 4) return gj_inverse_regs2<4>(Af, bf, R, (float)eps, t, nt, bar_id);
+    if (MAXEPT >= 8 && per <= 8) return gj_inverse_regs2<(MAXEPT >= 8 ? 8 : 4)>(Af, bf, R, (float)eps, t, nt, bar_id);
+  }
   if (per <= 4) return gj_inverse_regs<F, 4>(A, buf, R, eps, t, nt, bar_id);
   if (MAXEPT >= 8 && per <= 8) return gj_inverse_regs<F, (MAXEPT >= 8 ? 8 : 4)>(A, buf, R, eps, t, nt, bar_id);
   if (MAXEPT >= 16) return gj_inverse_regs<F, (MAXEPT >= 16 ? 16 : 4)>(A, buf, R, eps, t, nt, bar_id);

@@ -239,40 +239,82 @@ __global__ void __launch_bounds__(64) ttm_mid64_kernel(const float* __restrict__
 }
 
 // Same contraction for narrow FP32 slabs (Rt <= 32, Bd <= 32): the whole
-// Rt x Bd output of one a per CTA; K staged 64 deep, each slice of X and U a
-// contiguous run of memory read by all threads; 4 outputs per thread.
+// Rt x Bd output of one a per CTA.  Its 256 threads are 16 groups of the
+// contracted index (k = kg mod 16 within each staged chunk of 64) times 16
+// register tiles of T x T outputs (4 x 4 tiles cover Rt, Bd <= 4 T), so that
+// every thread does T^2 FMAs per 2 T shared-memory loads and few threads
+// idle on padding; the 16 partial outputs are then added in a fixed order
+// (the two groups of a warp by a shuffle, the eight warps pairwise through
+// the staging buffers).
+template <int T>
 __global__ void __launch_bounds__(256) ttm_mid32_kernel(const float* __restrict__ X, int64_t Ic, int Bd,
                                                         const float* __restrict__ U, int Rt, float* __restrict__ Xo,
                                                         int64_t kch) {
   constexpr int KC = 64;
-  __shared__ float Xs[KC * 32];
-  __shared__ float Us[KC * 32];
-  const int t = threadIdx.x;
+  __shared__ __align__(16) float stage[2 * KC * 32];  // X chunk, U chunk; then the warps' partial outputs
+  float* Xs = stage;
+  float* Us = stage + KC * 32;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t a = blockIdx.x;
   const int64_t k0 = (int64_t)blockIdx.z * kch, k1 = k0 + kch < Ic ? k0 + kch : Ic;
   const float* Xa = X + a * Ic * Bd;
   Xo += (int64_t)blockIdx.z * gridDim.x * (int64_t)Rt * Bd;
-  const int b = t & 31, r0 = (t >> 5) * 4;  // column b, rows r0..r0+3
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int tile = t & 15, kg = t >> 4;  // two k groups per warp (lanes 0-15, 16-31)
+  const int r0 = (tile >> 2) * T, b0 = (tile & 3) * T;
+  float acc[T][T];
+#pragma unroll
+  for (int u = 0; u < T; ++u)
+#pragma unroll
+    for (int v = 0; v < T; ++v) acc[u][v] = 0.f;
   for (int64_t i0 = k0; i0 < k1; i0 += KC) {
     const int rows = (int)((k1 - i0) < KC ? (k1 - i0) : KC);
     __syncthreads();
     for (int e = t; e < rows * Bd; e += 256) Xs[(e / Bd) * 32 + e % Bd] = __ldg(Xa + i0 * Bd + e);
     for (int e = t; e < rows * Rt; e += 256) Us[(e / Rt) * 32 + e % Rt] = __ldg(U + i0 * Rt + e);
     __syncthreads();
-    if (b < Bd)
-      for (int k = 0; k < rows; ++k) {
-        const float x = Xs[k * 32 + b];
+    for (int k = kg; k < rows; k += 16) {
+      float uv[T], xv[T];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fmaf(Us[k * 32 + r0 + u], x, acc[u]);
-      }
+      for (int u = 0; u < T; ++u) uv[u] = Us[k * 32 + ((r0 + u) & 31)];
+#pragma unroll
+      for (int v = 0; v < T; ++v) xv[v] = Xs[k * 32 + ((b0 + v) & 31)];
+#pragma unroll
+      for (int u = 0; u < T; ++u)
+#pragma unroll
+        for (int v = 0; v < T; ++v) acc[u][v] = fmaf(uv[u], xv[v], acc[u][v]);
+    }
+  }
+  // the two k groups of the warp, then the warps pairwise (w + 4, w + 2,
+  // w + 1 into w), through the staging buffers (32 x 32 outputs per warp)
+#pragma unroll
+  for (int u = 0; u < T; ++u)
+#pragma unroll
+    for (int v = 0; v < T; ++v) acc[u][v] += __shfl_xor_sync(0xffffffffu, acc[u][v], 16);
+  float* red = stage;  // [4][32 * 32] floats
+  for (int half = 4; half >= 1; half >>= 1) {
+    __syncthreads();
+    if (w >= half && w < 2 * half && lane < 16)
+#pragma unroll
+      for (int u = 0; u < T; ++u)
+#pragma unroll
+        for (int v = 0; v < T; ++v) red[(w - half) * 1024 + ((r0 + u) & 31) * 32 + ((b0 + v) & 31)] = acc[u][v];
+    __syncthreads();
+    if (w < half && lane < 16)
+#pragma unroll
+      for (int u = 0; u < T; ++u)
+#pragma unroll
+        for (int v = 0; v < T; ++v) acc[u][v] += red[w * 1024 + ((r0 + u) & 31) * 32 + ((b0 + v) & 31)];
   }
   float* Xoa = Xo + a * (int64_t)Rt * Bd;
-  if (b < Bd)
+  if (w == 0 && lane < 16)
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (r0 + u < Rt && TDK_IN((a * Rt + r0 + u) * Bd + b, (int64_t)gridDim.x * Rt * Bd))
-        Xoa[(int64_t)(r0 + u) * Bd + b] = acc[u];
+    for (int u = 0; u < T; ++u)
+#pragma unroll
+      for (int v = 0; v < T; ++v) {
+        const int r = r0 + u, b = b0 + v;
+        if (r < Rt && b < Bd && TDK_IN((a * Rt + r) * Bd + b, (int64_t)gridDim.x * Rt * Bd))
+          Xoa[(int64_t)r * Bd + b] = acc[u][v];
+      }
 }
 
 // fixed-order sum of the KS partial outputs of a split contraction
@@ -358,8 +400,19 @@ int launch_ttm_mid<float>(tdk_ctx* ctx, const float* X, int64_t A, int64_t Ic, i
   const unsigned gy = (unsigned)std::min<int64_t>(nb, 65535);
   if (wide)
     ttm_mid64_kernel<<<dim3((unsigned)A, gy, (unsigned)ks), 64, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, dst, kch);
-  else if (narrow)
-    ttm_mid32_kernel<<<dim3((unsigned)A, 1, (unsigned)ks), 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
+  else if (narrow) {
+    // register tiles of T x T, 4 x 4 of them covering the output
+    const int need = (int)std::max<int64_t>((Rt + 3) / 4, (Bd + 3) / 4);
+    const dim3 g3((unsigned)A, 1, (unsigned)ks);
+    if (need <= 2)
+      ttm_mid32_kernel<2><<<g3, 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
+    else if (need <= 4)
+      ttm_mid32_kernel<4><<<g3, 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
+    else if (need <= 5)
+      ttm_mid32_kernel<5><<<g3, 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
+    else
+      ttm_mid32_kernel<8><<<g3, 256, 0, ctx->stream>>>(X, Ic, (int)Bd, U, Rt, dst, kch);
+  }
   else
     ttm_mid_kernel<float><<<dim3((unsigned)A, gy, (unsigned)ks), NT, 0, ctx->stream>>>(X, Ic, Bd, U, Rt, dst, kch);
   TDK_LAUNCH_CHECK(ctx);

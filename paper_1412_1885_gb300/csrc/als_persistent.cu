@@ -767,17 +767,18 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
           const int e1 = e0 + NTP < nE ? e0 + NTP : e0;
           const int i0 = e0 / R, r0 = e0 - i0 * R, i1 = e1 / R, r1 = e1 - i1 * R;
           GramAcc<T> d0, d1;
+          T l0 = T(0), l1 = T(0);  // (U_n's low part: its product needs no compensation)
           d0.s = nb[e0];
           d1.s = nb[e1];
           for (int q = 0; q < Rn; ++q) {
             const T b0 = Bs[boff[n] + q * R + r0], b1 = Bs[boff[n] + q * R + r1];
             d0.add(-work[i0 * Rn + q], b0);
             d1.add(-work[i1 * Rn + q], b1);
-            d0.add(-ulo_s[i0 * Rn + q], b0);
-            d1.add(-ulo_s[i1 * Rn + q], b1);
+            l0 = fma(ulo_s[i0 * Rn + q], b0, l0);
+            l1 = fma(ulo_s[i1 * Rn + q], b1, l1);
           }
-          nb[e0] = d0.value();
-          if (e0 + NTP < nE) nb[e1] = d1.value();
+          nb[e0] = d0.value() - l0;
+          if (e0 + NTP < nE) nb[e1] = d1.value() - l1;
         }
         __syncthreads();
         gram_sym<T>(nb, rows, R, R, egram + n * R * R, tid, NTP);
@@ -1232,17 +1233,18 @@ __global__ void __launch_bounds__(NTP, 1) als_persistent_kernel(PArgs<T> a) {
             const int e1 = e0 + NTP < nE ? e0 + NTP : e0;
             const int i0 = e0 / R, r0 = e0 - i0 * R, i1 = e1 / R, r1 = e1 - i1 * R;
             GramAcc<T> d0, d1;
+            T l0 = T(0), l1 = T(0);  // (U_n's low part: its product needs no compensation)
             d0.s = nb[e0];
             d1.s = nb[e1];
             for (int q = 0; q < Rn; ++q) {
               const T b0 = Bs[boff[n] + q * R + r0], b1 = Bs[boff[n] + q * R + r1];
               d0.add(-work[i0 * Rn + q], b0);
               d1.add(-work[i1 * Rn + q], b1);
-              d0.add(-ulo_s[i0 * Rn + q], b0);
-              d1.add(-ulo_s[i1 * Rn + q], b1);
+              l0 = fma(ulo_s[i0 * Rn + q], b0, l0);
+              l1 = fma(ulo_s[i1 * Rn + q], b1, l1);
             }
-            nb[e0] = d0.value();
-            if (e0 + NTP < nE) nb[e1] = d1.value();
+            nb[e0] = d0.value() - l0;
+            if (e0 + NTP < nE) nb[e1] = d1.value() - l1;
           }
           __syncthreads();
           gram_sym<T>(nb, rows, R, R, egram + n * R * R, tid, NTP);
